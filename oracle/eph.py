@@ -1,0 +1,395 @@
+"""FP64 oracle: Wannier interpolation, e-ph matrix elements, RTA rates, collision integral, RK4.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Every function is the
+plain definition from the paper, in FP64, using NumPy's matmul/einsum and
+LAPACK's Hermitian eigensolver (``numpy.linalg.eigh``) as library steps.
+
+Notation (paper Sec. 2): k, q crystal coordinates; R integer lattice vectors
+in crystal coordinates, so k.R = 2 pi k.n; bands n (initial, at k) and m
+(final, at k+q); phonon modes nu; atom kappa with Cartesian direction alpha
+(index ka = 3 kappa + alpha).
+
+Units and readings (the paper does not fix them):
+  * energies, |g| and hbar*omega in eV; D(R) in eV/bohr^2; masses in amu;
+    g~(Re,Rp) numerically in eV/bohr, so that the zero-point length
+    sqrt(hbar / (2 M omega)) in bohr times g~ is in eV;
+  * Gamma and I[f] in 1/s, time step in fs;
+  * Gaussian delta: delta_s(x) = exp(-x^2/s^2) / (s sqrt(pi));
+  * modes with hbar*omega < OMEGA_MIN_EV contribute nothing (the acoustic modes at
+    q = Gamma), and negative eigenvalues of D(q) are clamped to 0;
+  * 1/N_q is the full q-grid count.
+
+Pins (tests/test_oracle_*.py):
+  * ``hamiltonian_k``/``bands``: closed form of the 1-band simple-cubic tight
+    binding; Hermiticity; H = U diag(eps) U^dagger.
+  * ``dynamical_matrix``/``phonons``: closed form of isotropic nearest-neighbour
+    springs; three zero modes at Gamma (acoustic sum rule); omega(-q) = omega(q).
+  * ``g_wannier``: the brute-force double sum ``g_wannier_brute`` on tiny
+    inputs (a different summation structure), and a hand-evaluated single
+    R-pair case.
+  * ``g_bloch``/``g_modes``: the Holstein-like closed form; gauge invariance of
+    degenerate-summed |g|^2 under random U(1)/U(d) eigenvector rotations; the
+    time-reversal partner identity |g_mn nu(k,q)|^2 = |g_nm nu(k+q,-q)|^2.
+  * ``scattering_rates``: brute-force pure-Python loops on a tiny grid; the
+    1-band Einstein closed form; Gamma >= 0; mode-resolved rates sum to total.
+  * ``collision``: sum over states vanishes for a symmetric list; it equals
+    -Gamma * delta f to first order around equilibrium (the RTA link of
+    Eq. scatter_rate); detailed balance on the ladder model.
+  * ``rk4_step``/``euler_step``: fourth / first order convergence on the
+    two-state closed form; carrier number conserved.
+Parity unpinned: absolute Gamma of real materials (no DFT data here).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# CODATA 2018
+HBAR_EVS = 6.582119569e-16        # eV s
+KB_EVK = 8.617333262e-5           # eV / K
+AMU_KG = 1.66053906660e-27        # kg
+BOHR_M = 0.529177210903e-10       # m
+EV_J = 1.602176634e-19            # J
+
+# (hbar omega)^2 [eV^2] = C_OMEGA * lambda, lambda an eigenvalue of the mass-scaled
+# dynamical matrix in eV/(bohr^2 amu).  The same number gives the squared
+# zero-point length: hbar/(2 M omega) [bohr^2] = C_OMEGA / (2 M[amu] hbar*omega[eV]).
+C_OMEGA = HBAR_EVS ** 2 * EV_J / (AMU_KG * BOHR_M ** 2)
+OMEGA_MIN_EV = 1e-4
+TWO_PI_OVER_HBAR = 2.0 * np.pi / HBAR_EVS   # 1/(eV s)
+
+
+# ----------------------------------------------------------------------------
+# Fourier phases
+# ----------------------------------------------------------------------------
+
+def phases(pts: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """e^{i k.R} for every point and lattice vector: shape (npts, nR)."""
+    return np.exp(2j * np.pi * (np.asarray(pts, np.float64) @ np.asarray(R, np.float64).T))
+
+
+# ----------------------------------------------------------------------------
+# electrons: Sec. 2.2.1, Eq. wannier_3
+# ----------------------------------------------------------------------------
+
+def hamiltonian_k(model, kpts: np.ndarray) -> np.ndarray:
+    """H^(W)(k) = sum_R e^{ik.R} H(R)  (Eq. wannier_3, first equality)."""
+    return np.einsum("kr,rij->kij", phases(kpts, model.R_H), model.H.astype(np.complex128))
+
+
+def bands(model, kpts: np.ndarray):
+    """eps_nk ascending and U(k) with H^(W)(k) = U diag(eps) U^dagger (Eq. wannier_3).
+
+    ``U[k, :, n]`` is the eigenvector of band n.
+    """
+    eps, U = np.linalg.eigh(hamiltonian_k(model, kpts))
+    return eps, U
+
+
+# ----------------------------------------------------------------------------
+# phonons: Sec. 2.2.2, Eq. IFC2
+# ----------------------------------------------------------------------------
+
+def dynamical_matrix(model, qpts: np.ndarray) -> np.ndarray:
+    """Mass-scaled D(q)_{ka,k'b} = sum_R e^{iq.R} D_{ka,k'b}(R) / sqrt(M_k M_k')  (Eq. IFC2).
+
+    D(R) is stored without the mass factor, as the paper states for Eq. IFC1.
+    """
+    Dq = np.einsum("qr,rab->qab", phases(qpts, model.R_D), model.D.astype(np.complex128))
+    m = np.repeat(np.asarray(model.mass, np.float64), 3)
+    return Dq / np.sqrt(m[:, None] * m[None, :])
+
+
+def phonons(model, qpts: np.ndarray):
+    """hbar*omega_nu q (eV, ascending) and eigenvectors e_nu q (columns) of D(q)."""
+    lam, e = np.linalg.eigh(dynamical_matrix(model, qpts))
+    hw = np.sqrt(C_OMEGA * np.clip(lam, 0.0, None))
+    return hw, e
+
+
+# ----------------------------------------------------------------------------
+# e-ph matrix elements: Sec. 2.2.3, Eqs. eph_mat_wann2, eph_mat, g_abs
+# ----------------------------------------------------------------------------
+
+def g_wannier_brute(model, kpts: np.ndarray, qpts: np.ndarray) -> np.ndarray:
+    """sum_{Re,Rp} e^{i(k.Re + q.Rp)} g~(Re,Rp) as a direct double sum (Eq. eph_mat_wann2).
+
+    One combined phase per (k, q, Re, Rp); pure loops over the point pairs.
+    Output [nk, nq, nmode, nw, nw].  Tiny inputs only.
+    """
+    g = model.g.astype(np.complex128)
+    Re = model.R_ge.astype(np.float64)
+    Rp = model.R_gp.astype(np.float64)
+    nk, nq = len(kpts), len(qpts)
+    out = np.zeros((nk, nq) + g.shape[2:], dtype=np.complex128)
+    for a in range(nk):
+        for b in range(nq):
+            arg = (Re @ kpts[a])[:, None] + (Rp @ qpts[b])[None, :]
+            ph = np.exp(2j * np.pi * arg)
+            out[a, b] = np.einsum("ep,epxij->xij", ph, g)
+    return out
+
+
+def g_wannier(model, kpts: np.ndarray, qpts: np.ndarray) -> np.ndarray:
+    """Same sum as ``g_wannier_brute`` with e^{i(k.Re+q.Rp)} = e^{ik.Re} e^{iq.Rp}:
+
+    first over Re for each k, then over Rp for each q.  Output
+    [nk, nq, nmode, nw, nw] (Wannier gauge, indices i j).
+    """
+    g = model.g
+    nge, ngp = g.shape[:2]
+    tail = g.shape[2:]
+    gk = phases(kpts, model.R_ge) @ g.reshape(nge, -1).astype(np.complex128)      # [nk, ngp*ncol]
+    gk = gk.reshape(len(kpts), ngp, -1)
+    pq = phases(qpts, model.R_gp)                                                   # [nq, ngp]
+    out = np.einsum("qp,kpc->kqc", pq, gk)
+    return out.reshape((len(kpts), len(qpts)) + tail)
+
+
+def g_bloch(gw: np.ndarray, Uk: np.ndarray, Ukq: np.ndarray) -> np.ndarray:
+    """g_mn = sum_ij U^dagger_mi(k+q) g_ij U_jn(k)  (Eq. eph_mat_wann2, outer sum).
+
+    gw [..., nmode, nw, nw], Uk [..., nw, nw] (broadcast over the mode axis),
+    Ukq [..., nw, nw].  Returns [..., nmode, nw(m), nw(n)].
+    """
+    return np.einsum("...im,...xij,...jn->...xmn", np.conj(Ukq), gw, Uk)
+
+
+def g_modes(gb: np.ndarray, hw: np.ndarray, e: np.ndarray, mass: np.ndarray) -> np.ndarray:
+    """g_mn nu = sqrt(hbar/(2 omega_nu)) sum_ka e^{ka}_nu / sqrt(M_k) g^{ka}_mn  (Eq. eph_mat).
+
+    gb [..., nmode(ka), nw, nw]; hw [..., nmode(nu)] in eV; e [..., nmode(ka), nmode(nu)].
+    Modes with hbar*omega below OMEGA_MIN_EV are set to zero.  Output [..., nu, m, n] in eV.
+    """
+    m = np.repeat(np.asarray(mass, np.float64), 3)                 # per ka
+    hw_safe = np.where(hw >= OMEGA_MIN_EV, hw, 1.0)
+    length = np.sqrt(C_OMEGA / (2.0 * m[..., :, None] * hw_safe[..., None, :]))   # [..., ka, nu] bohr
+    length = np.where(hw[..., None, :] >= OMEGA_MIN_EV, length, 0.0)
+    coef = e * length                                               # [..., ka, nu]
+    return np.einsum("...an,...amk->...nmk", coef, gb)
+
+
+def g_abs(gm: np.ndarray) -> np.ndarray:
+    """|g_nu(k,q)| = sqrt(sum_mn |g_mn nu|^2 / N_b)  (Eq. g_abs).  gm [..., nu, m, n]."""
+    nb = gm.shape[-1]
+    return np.sqrt(np.sum(np.abs(gm) ** 2, axis=(-1, -2)) / nb)
+
+
+# ----------------------------------------------------------------------------
+# occupations and the broadened delta
+# ----------------------------------------------------------------------------
+
+def fermi_dirac(eps, mu: float, T: float):
+    return 1.0 / (np.exp((np.asarray(eps) - mu) / (KB_EVK * T)) + 1.0)
+
+
+def bose_einstein(hw, T: float):
+    """N = 1/(e^{hw/kT} - 1); zero for modes below OMEGA_MIN_EV (they carry no weight)."""
+    hw = np.asarray(hw, np.float64)
+    safe = np.where(hw >= OMEGA_MIN_EV, hw, 1.0)
+    return np.where(hw >= OMEGA_MIN_EV, 1.0 / np.expm1(safe / (KB_EVK * T)), 0.0)
+
+
+def delta_gauss(x, sigma: float):
+    return np.exp(-(np.asarray(x) / sigma) ** 2) / (sigma * np.sqrt(np.pi))
+
+
+# ----------------------------------------------------------------------------
+# RTA scattering rates: Sec. 2.1.2, Eqs. scatter_rate and BTE_W
+# ----------------------------------------------------------------------------
+
+def scattering_rates(eps_k, eps_kq, hw, g2, T, mu, sigma, nq_total, mode_resolved=False):
+    """Gamma_nk = (1/N_q) sum_{m nu q} W (Eq. scatter_rate) with W of Eq. BTE_W.
+
+    eps_k [nk, nw(n)], eps_kq [nk, nq, nw(m)], hw [nq, nmode], g2 = |g_mn nu|^2
+    [nk, nq, nmode, nw(m), nw(n)].  Every term is kept (no delta truncation).
+    Returns Gamma [nk, nw] in 1/s, or [nk, nmode, nw] when ``mode_resolved``.
+    """
+    fm = fermi_dirac(eps_kq, mu, T)[:, :, None, :, None]           # final state occupation
+    N = bose_einstein(hw, T)[None, :, :, None, None]
+    en = eps_k[:, None, None, None, :]
+    em = eps_kq[:, :, None, :, None]
+    w = hw[None, :, :, None, None]
+    emit = delta_gauss(en - w - em, sigma) * (1.0 + N - fm)
+    absb = delta_gauss(en + w - em, sigma) * (N + fm)
+    live = (hw >= OMEGA_MIN_EV)[None, :, :, None, None]
+    W = TWO_PI_OVER_HBAR * g2 * np.where(live, emit + absb, 0.0)
+    if mode_resolved:
+        return W.sum(axis=(1, 3)) / nq_total                        # [nk, nmode, nw(n)]
+    return W.sum(axis=(1, 2, 3)) / nq_total
+
+
+def scattering_rates_grid(model, kgrid, qgrid, k_indices, T, mu, sigma, mode_resolved=False,
+                          q_chunk=None):
+    """Gamma_nk for the listed k-grid points with q summed over the full q grid.
+
+    k and k+q are both on the k grid (the q grid is commensurate), as the paper
+    requires for dynamics and the iterative BTE (Sec. 4.3).  Works one k (and
+    optionally one chunk of q) at a time to bound memory.
+    """
+    from synthetic import mp_grid  # point lists only
+    kg = np.asarray(kgrid)
+    qg = np.asarray(qgrid)
+    kpts_all = mp_grid(*kg)
+    qpts = mp_grid(*qg)
+    nq = len(qpts)
+    eps_all, U_all = bands(model, kpts_all)
+    hw, e = phonons(model, qpts)
+    kq_index = _kplusq_index(kg, qg)
+    nw, nm = model.nw, model.nmode
+    out = np.zeros((len(k_indices), nm, nw)) if mode_resolved else np.zeros((len(k_indices), nw))
+    q_chunk = q_chunk or nq
+    for a, ik in enumerate(k_indices):
+        k = kpts_all[ik:ik + 1]
+        for q0 in range(0, nq, q_chunk):
+            qs = slice(q0, min(nq, q0 + q_chunk))
+            ikq = kq_index[ik, qs]
+            gw = g_wannier(model, k, qpts[qs])[0]                  # [nq, nm, nw, nw]
+            gb = g_bloch(gw, U_all[ik][None], U_all[ikq])
+            gm = g_modes(gb, hw[qs], e[qs], model.mass)
+            g2 = np.abs(gm) ** 2
+            r = scattering_rates(eps_all[ik][None], eps_all[ikq][None], hw[qs], g2[None],
+                                 T, mu, sigma, nq, mode_resolved)
+            out[a] += r[0]
+    return out
+
+
+def _kplusq_index(kgrid, qgrid):
+    """Index of k+q on the k grid for every k-grid point k and q-grid point q."""
+    kg = np.asarray(kgrid)
+    qg = np.asarray(qgrid)
+    assert np.all(kg % qg == 0), "q grid must divide the k grid"
+    step = kg // qg
+    ki = np.stack(np.meshgrid(*[np.arange(n) for n in kg], indexing="ij"), -1).reshape(-1, 3)
+    qi = np.stack(np.meshgrid(*[np.arange(n) for n in qg], indexing="ij"), -1).reshape(-1, 3)
+    s = (ki[:, None, :] + qi[None, :, :] * step) % kg
+    return (s[..., 0] * kg[1] + s[..., 1]) * kg[2] + s[..., 2]
+
+
+# ----------------------------------------------------------------------------
+# collision integral: Sec. 2.1, Eq. e_ph_scattering with F_abs, F_em
+# ----------------------------------------------------------------------------
+
+def collision(f, eps, row, col, hw, g2, T, sigma, nq_total):
+    """I[f]_s for every state s (Eq. e_ph_scattering).
+
+    Each entry e is one (n k -> m k+q, nu) term: initial state row[e], final
+    state col[e], phonon energy hw[e] (eV), |g|^2 = g2[e] (eV^2).  Phonon
+    occupations are the equilibrium N(hw, T) (kept fixed, Sec. 2.1.1).
+    I_s = -(2 pi/hbar)(1/N_q) sum_{e: row=s} |g|^2 [delta(e_n - hw - e_m) F_em
+                                                  + delta(e_n + hw - e_m) F_abs].
+    """
+    f = np.asarray(f, np.float64)
+    fn, fm = f[row], f[col]
+    en, em = eps[row], eps[col]
+    N = bose_einstein(hw, T)
+    live = np.asarray(hw) >= OMEGA_MIN_EV
+    F_abs = fn * (1 - fm) * N - fm * (1 - fn) * (N + 1)
+    F_em = fn * (1 - fm) * (N + 1) - fm * (1 - fn) * N
+    term = np.asarray(g2, np.float64) * (delta_gauss(en - hw - em, sigma) * F_em
+                                         + delta_gauss(en + hw - em, sigma) * F_abs)
+    term = np.where(live, term, 0.0)
+    out = np.zeros_like(f)
+    np.add.at(out, row, term)
+    return -TWO_PI_OVER_HBAR / nq_total * out
+
+
+# ----------------------------------------------------------------------------
+# time stepping: Sec. 2.1.1 (explicit RK4, Euler)
+# ----------------------------------------------------------------------------
+
+def rk4_step(f, dt, rhs):
+    """Classic 4-stage Runge-Kutta step of df/dt = rhs(f)."""
+    k1 = rhs(f)
+    k2 = rhs(f + 0.5 * dt * k1)
+    k3 = rhs(f + 0.5 * dt * k2)
+    k4 = rhs(f + dt * k3)
+    return f + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+
+
+def euler_step(f, dt, rhs):
+    return f + dt * rhs(f)
+
+
+FS = 1e-15  # seconds per femtosecond
+
+
+def evolve(f0, dt_fs, nsteps, rhs, method="rk4"):
+    """Integrate df/dt = I[f] (1/s) for ``nsteps`` steps of ``dt_fs`` femtoseconds."""
+    step = rk4_step if method == "rk4" else euler_step
+    f = np.array(f0, np.float64)
+    for _ in range(nsteps):
+        f = step(f, dt_fs * FS, rhs)
+    return f
+
+
+# ----------------------------------------------------------------------------
+# (k, q)-pair scattering list on commensurate grids: Sec. 4.3
+# ----------------------------------------------------------------------------
+
+def collision_list_grid(model, grid, band_lo, band_hi, sigma=None, screen=0.0):
+    """All scattering terms between states (n, k) with k on ``grid`` and n in [band_lo, band_hi).
+
+    States are numbered s = ik * nb + (n - band_lo).  The q grid equals the k
+    grid, so k+q is always a state.  For each term (s -> s', nu, q) the list
+    holds |g_mn nu(k,q)|^2 and hbar*omega_nu q.  The unordered process
+    {s, s'} gets ONE |g|^2 value for both directions: the value computed in
+    the direction with s < s' (the reverse direction s' -> s at -q has the same
+    |g|^2 by the hermiticity of the perturbation), so that the sum of I[f]
+    over states vanishes to rounding.  With ``screen > 0`` a term is dropped
+    when both Gaussian factors exp(-x^2/sigma^2) are below ``screen``; the
+    rule is symmetric between the two directions.
+
+    Returns dict with row, col, mode (int arrays), g2, hw (float64), eps
+    (state energies) and nq.
+    """
+    from synthetic import mp_grid
+    g = np.asarray(grid)
+    pts = mp_grid(*g)
+    nk = len(pts)
+    nb = band_hi - band_lo
+    eps_all, U_all = bands(model, pts)
+    hw_all, e_all = phonons(model, pts)
+    kq = _kplusq_index(g, g)
+    neg_q = _kplusq_index(g, g)[0]            # index of -q: solve 0 + q' = -q on the grid
+    negidx = np.empty(nk, dtype=np.int64)
+    ki = np.stack(np.meshgrid(*[np.arange(n) for n in g], indexing="ij"), -1).reshape(-1, 3)
+    nki = (-ki) % g
+    negidx[:] = (nki[:, 0] * g[1] + nki[:, 1]) * g[2] + nki[:, 2]
+    del neg_q
+    nm = model.nmode
+    g2_all = np.empty((nk, nk, nm, nb, nb))       # [k, q, nu, m, n]
+    sel = slice(band_lo, band_hi)
+    for ik in range(nk):
+        gw = g_wannier(model, pts[ik:ik + 1], pts)[0]
+        gb = g_bloch(gw, U_all[ik][None], U_all[kq[ik]])
+        gm = g_modes(gb, hw_all, e_all, model.mass)[:, :, sel, sel]
+        g2_all[ik] = np.abs(gm) ** 2
+    rows, cols, modes, vals, hws = [], [], [], [], []
+    eps_state = eps_all[:, sel].reshape(-1)
+    for ik in range(nk):
+        for iq in range(nk):
+            ikq = kq[ik, iq]
+            for nu in range(nm):
+                for n in range(nb):
+                    s = ik * nb + n
+                    for m in range(nb):
+                        sp = ikq * nb + m
+                        if s <= sp:
+                            val = g2_all[ik, iq, nu, m, n]
+                        else:
+                            # reverse process: sp -> s at -q, initial band m, final band n
+                            val = g2_all[ikq, negidx[iq], nu, n, m]
+                        hw = hw_all[iq, nu]
+                        if screen > 0.0:
+                            x1 = eps_state[s] - hw - eps_state[sp]
+                            x2 = eps_state[s] + hw - eps_state[sp]
+                            if max(np.exp(-(x1 / sigma) ** 2), np.exp(-(x2 / sigma) ** 2)) < screen:
+                                continue
+                        rows.append(s)
+                        cols.append(sp)
+                        modes.append(nu)
+                        vals.append(val)
+                        hws.append(hw)
+    return {"row": np.array(rows, np.int64), "col": np.array(cols, np.int64),
+            "mode": np.array(modes, np.int64), "g2": np.array(vals), "hw": np.array(hws),
+            "eps": eps_state, "nq": nk, "nstates": nk * nb}
