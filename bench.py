@@ -1,0 +1,303 @@
+"""Throughput of the e-ph hot path on the silicon-like fcc workload.
+
+One step = one pass of the hot path over the whole workload: interpolate
+eps, U on the 40^3 k grid and omega, e on the 40^3 q grid is done once per
+model (set_grids); each timed step evaluates, for every k-point in the
+0.3 eV window above the band minimum and every q of the 40^3 grid, the
+Wannier interpolation of g (Re-sum with the U(k) fold, Rp-sum), the rotation
+by U(k+q), the mode projection, |g|^2, the Gaussian weights and Gamma_nk.
+The unit is the (k, q) pair.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--precision fp32|fp64|bf16x3|tf32x3]
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("(k,q) |g|² pairs/s and Γ_nk collision sums/s at stated err vs FP64; % of roofline")
+WORKLOAD = "fcc Si-like 8 bands, 2 atoms, 381 R_e x 381 R_p; 40^3 k (0.3 eV window) x 40^3 q; T=300 K, sigma=10 meV"
+KGRID = (40, 40, 40)
+T_K, SIGMA, WIN = 300.0, 0.010, 0.3
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def load_peaks():
+    try:
+        with open(PEAKS) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) == 8:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(model, n_k=2):
+    """The FP64 oracle as it stands on a bounded sample: n_k window k-points x all 40^3 q."""
+    from oracle import eph as O
+    import synthetic as S
+    t0 = time.perf_counter()
+    pts = S.mp_grid(*KGRID)
+    eps, _ = O.bands(model, pts)
+    emin = eps.min()
+    win = np.nonzero(((eps >= emin) & (eps <= emin + WIN)).any(1))[0]
+    sample = win[np.linspace(0, len(win) - 1, n_k).astype(int)]
+    O.scattering_rates_grid(model, KGRID, KGRID, sample, T_K, emin - WIN, SIGMA, q_chunk=16000)
+    dt = time.perf_counter() - t0
+    nq = int(np.prod(KGRID))
+    return {"value": n_k * nq / dt, "unit": "pairs/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": f"{n_k} window k-points x {nq} q (FP64 NumPy oracle, band interpolation of the 40^3 grid "
+                      f"included), {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import synthetic as S
+    model = S.model_c2()
+    for _ in range(args.warmup):
+        cpu_baseline(model, n_k=1)
+    t0 = time.perf_counter()
+    vals = [cpu_baseline(model, n_k=1) for _ in range(args.steps)]
+    dt = time.perf_counter() - t0
+    v = float(np.mean([x["value"] for x in vals]))
+    cb = dict(vals[-1])
+    cb["value"] = v
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_per_step": "1 window k-point x 64000 q"},
+        "cpu_baseline": cb, "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                                    "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import synthetic as S
+    from paper_2002_02045_gb300 import PRECISIONS, Context, build as _b
+    from paper_2002_02045_gb300.native import PROF_EPILOGUE, PROF_QSUM, PROF_RSUM
+
+    _b.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = PRECISIONS[args.precision]
+    model = S.model_c2()
+    ctx = Context(local)
+    ctx.pgb_set_model(model)
+    ctx.pgb_set_grids(KGRID, KGRID)
+    nk_grid = int(np.prod(KGRID))
+    eps = torch.empty((nk_grid, model.nw), dtype=torch.float64, device="cuda")
+    ctx.pgb_get_grid_energies(eps, None)
+    emin = float(eps.min())
+    mu = emin - WIN
+    kbuf = torch.empty((nk_grid,), dtype=torch.int32, device="cuda")
+    nwin = ctx.pgb_window(emin, emin + WIN, kbuf)
+    kidx = kbuf[:nwin].contiguous()
+    gam = torch.empty((nwin, model.nw), dtype=torch.float64, device="cuda")
+    nq = nk_grid
+    pairs = nwin * nq
+
+    def step():
+        ctx.pgb_scattering_rates(kidx, T_K, mu, SIGMA, prec, gam)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.pgb_profile(True)
+    for c in (PROF_QSUM, PROF_RSUM, PROF_EPILOGUE):
+        ctx.pgb_profile_read(c)
+    props = torch.cuda.get_device_properties(local)
+    clocks = ClockSampler(f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local))
+    n0 = ctx.pgb_launch_count()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    launches = ctx.pgb_launch_count() - n0
+    q_ms, q_n = ctx.pgb_profile_read(PROF_QSUM)
+    r_ms, _ = ctx.pgb_profile_read(PROF_RSUM)
+    p_ms, _ = ctx.pgb_profile_read(PROF_EPILOGUE)
+    ctx.pgb_profile(False)
+    value = world * pairs * args.steps / (ms * 1e-3)
+
+    # roofline of the dominant kernel: the Fourier sum over R_p (a complex contraction)
+    peaks, peak_src = load_peaks()
+    flop_per_pair = 8.0 * len(model.R_gp) * model.nmode * model.nw ** 2
+    achieved = flop_per_pair * pairs * args.steps / (q_ms * 1e-3) / 1e12
+    if args.precision in ("bf16x3", "tf32x3"):
+        peak = peaks["bf16_tflops"] * (1.0 if args.precision == "bf16x3" else 0.5)
+        roof = {"bound": "tensor", "peak_source": f"{peak_src} bf16" + (" x 1/2 (tf32 nominal ratio)"
+                                                                        if args.precision == "tf32x3" else "")}
+    else:
+        lanes = FP32_LANES if args.precision == "fp32" else 2   # FP64 units per SM on GB300 are few
+        peak = SM_COUNT * lanes * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        roof = {"bound": "alu", "peak_source": f"derived: {SM_COUNT} SMs x {lanes} lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz"}
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                 "traffic": None, "kernel": "q-sum (Fourier over R_p)",
+                 "algorithmic_flop_per_pair": flop_per_pair, "launches": q_n})
+    out = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3", "tf32x3": "tf32x3"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "kgrid": list(KGRID), "qgrid": list(KGRID), "nk_window": nwin,
+                   "pairs_per_step": pairs, "precision": args.precision,
+                   "l2": "inputs larger than L2 (g~ 446 MB, per-step intermediates > 1 GB)"},
+        "delta_terms_per_s": value * 2 * model.nw ** 2 * model.nmode,
+        "kernel_ms_per_step": {"q_sum": q_ms / args.steps, "r_sum": r_ms / args.steps,
+                               "epilogue": p_ms / args.steps},
+        "roofline": roof, "gpu_launches": launches, "clocks": clk,
+    }
+
+    if args.e2e and rank == 0:
+        out["e2e"] = e2e(ctx, model, prec, steps=1)
+    if args.cpu_baseline and rank == 0 and world == 1:
+        out["cpu_baseline"] = cpu_baseline(model)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e(ctx, model, prec, steps=1):
+    """Same metric through the public API with host buffers: model upload,
+    grids, window and rates, copies included."""
+    import torch
+    nk_grid = int(np.prod(KGRID))
+    g = np.ascontiguousarray(model.g)
+    h2d = sum(np.asarray(a).nbytes for a in (model.mass, model.R_H, model.H, model.R_D, model.D, model.R_ge,
+                                             model.R_gp, g))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.pgb_set_model(model)
+        ctx.pgb_set_grids(KGRID, KGRID)
+        eps = np.empty((nk_grid, model.nw))
+        ctx.pgb_get_grid_energies(eps, None)
+        emin = float(eps.min())
+        kl = np.empty(nk_grid, np.int32)
+        n = ctx.pgb_window(emin, emin + WIN, kl)
+        gam = np.empty((n, model.nw))
+        ctx.pgb_scattering_rates(np.ascontiguousarray(kl[:n]), T_K, emin - WIN, SIGMA, prec, gam)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": n * nk_grid / dt, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d + 4 * n),
+            "d2h_bytes_per_step": int(eps.nbytes + 4 * n + gam.nbytes),
+            "includes": "set_model (host validation + upload), set_grids, window, rates"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x3", "tf32x3"])
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    rank, world, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

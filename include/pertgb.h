@@ -1,0 +1,176 @@
+/*
+ * pertgb.h - C ABI of the GB300 e-ph hot path (Perturbo method, arXiv 2002.02045).
+ *
+ * The library evaluates, on one CUDA GPU:
+ *   - Wannier interpolation of bands and phonons       (Sec. 2.2.1 Eq. wannier_3; Sec. 2.2.2 Eq. IFC2)
+ *   - e-ph matrix elements g_mn nu(k,q)                 (Sec. 2.2.3 Eqs. eph_mat_wann2, eph_mat, g_abs)
+ *   - RTA scattering rates Gamma_nk                     (Sec. 2.1.2 Eqs. scatter_rate, BTE_W)
+ *   - the e-ph collision integral I[f]_nk               (Sec. 2.1 Eq. e_ph_scattering)
+ *   - explicit RK4 time stepping of df/dt = I[f]        (Sec. 2.1.1)
+ *
+ * Conventions (every entry point):
+ *   - k, q are crystal coordinates (units of the reciprocal vectors); R are
+ *     integer crystal coordinates; the Fourier phase is exp(2 pi i k.R).
+ *   - Complex arrays are interleaved (re, im) in the stated real type.
+ *   - Energies and hbar*omega in eV, D(R) in eV/bohr^2, masses in amu,
+ *     g~(Re,Rp) in eV/bohr, temperatures in K, rates and I[f] in 1/s, time
+ *     steps in fs.  Gaussian delta: exp(-x^2/s^2)/(s sqrt(pi)).  Modes with
+ *     hbar*omega < 1e-4 eV carry no weight.  1/N_q is the q-grid size.
+ *   - Grids are Gamma-centred Monkhorst-Pack: point p = (i1*n2 + i2)*n3 + i3
+ *     is (i1/n1, i2/n2, i3/n3).  The q grid must divide the k grid.
+ *   - Band index n is the initial state at k, m the final state at k+q.
+ *   - Buffers marked "host or device" may be either: device pointers are used
+ *     in place (stream-ordered, no synchronisation); host pointers are copied
+ *     through the context's stream and the call synchronises before returning.
+ *   - Caller owns every buffer it passes; the library owns the copies it makes
+ *     in set_model / set_grids / build_collision and frees them in destroy.
+ *   - Errors return a negative pgb_status and leave outputs unwritten for
+ *     argument errors; pgb_last_error() gives a message.  No call traps the
+ *     GPU, and there is no CPU fallback: without a usable CUDA device every
+ *     call returns PGB_ECUDA.
+ */
+#ifndef PERTGB_H
+#define PERTGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pgb_ctx pgb_ctx;
+
+typedef enum {
+    PGB_OK = 0,
+    PGB_EINVAL = -1,    /* bad argument, shape or unsupported mode            */
+    PGB_ESTATE = -2,    /* call order violated (e.g. rates before set_grids)   */
+    PGB_ENOMEM = -3,    /* device allocation failed                            */
+    PGB_ECUDA = -4,     /* CUDA runtime error                                  */
+    PGB_ETIMEOUT = -5,  /* a bounded device wait ran out                       */
+} pgb_status;
+
+typedef enum {
+    PGB_FP64 = 0,        /* every step in FP64                                       */
+    PGB_FP32 = 1,        /* Fourier sums and rotations in FP32 SIMT, energies FP64   */
+    PGB_TC_TF32X3 = 2,   /* q-sum on tcgen05 kind::tf32, 3-product hi/lo split        */
+    PGB_TC_BF16X3 = 3,   /* q-sum on tcgen05 kind::f16 (bf16), 3-product hi/lo split  */
+} pgb_precision;
+
+typedef enum {
+    PGB_G2_FULL = 0,     /* out[k][q][nu][m][n] = |g_mn nu(k,q)|^2, double, eV^2      */
+    PGB_G_ABS = 1,       /* out[k][q][nu] = |g_nu(k,q)| of Eq. g_abs, double, eV      */
+} pgb_g_output;
+
+/* Real-space model (all host pointers, copied by pgb_set_model).
+ * H(R): Eq. wannier_3 input, H[r][n][n'] = <n 0|H|n' R_r>, H(-R) = H(R)^dagger.
+ * D(R): Eq. IFC2 input without mass factor, D[r][ka][k'b] real, ka = 3 kappa + alpha.
+ * g~(Re,Rp): Eq. eph_mat_wann2 input on the dense product of two R lists,
+ *            g[re][rp][ka][i][j], complex64 (g_is_double = 0) or complex128.   */
+typedef struct {
+    int nw;                    /* Wannier functions (bands)          */
+    int nat;                   /* atoms; nmode = 3 nat               */
+    const double *mass;        /* [nat] amu                          */
+    int nR_H;
+    const int32_t *R_H;        /* [nR_H][3]                          */
+    const double *H;           /* [nR_H][nw][nw] complex128          */
+    int nR_D;
+    const int32_t *R_D;        /* [nR_D][3]                          */
+    const double *D;           /* [nR_D][3nat][3nat] real            */
+    int nR_ge;
+    const int32_t *R_ge;       /* [nR_ge][3]                         */
+    int nR_gp;
+    const int32_t *R_gp;       /* [nR_gp][3]                         */
+    const void *g;             /* [nR_ge][nR_gp][3nat][nw][nw]       */
+    int g_is_double;
+} pgb_model;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (NULL = the legacy default stream); every launch of the context goes there. */
+pgb_status pgb_create(pgb_ctx **out, int device, void *cuda_stream);
+void pgb_destroy(pgb_ctx *ctx);
+const char *pgb_last_error(const pgb_ctx *ctx);
+const char *pgb_status_string(int status);
+
+/* Copy the model to the device.  Checks: sizes > 0, nw <= 16, nat <= 5,
+ * finite values, H(-R) = H(R)^dagger and D(-R) = D(R)^T to 1e-10 (both R
+ * lists must be closed under inversion).  Returns PGB_EINVAL otherwise.      */
+pgb_status pgb_set_model(pgb_ctx *ctx, const pgb_model *model);
+
+/* Fix the k and q grids.  Computes eps_nk and U(k) on every k-grid point
+ * (Eq. wannier_3) and hbar*omega_nu q, e_nu q on every q-grid point (Eq. IFC2),
+ * in FP64 with a cyclic complex Jacobi eigensolver (ascending order).
+ * Each q-grid size must divide the k-grid size along the same axis.          */
+pgb_status pgb_set_grids(pgb_ctx *ctx, const int kgrid[3], const int qgrid[3]);
+
+/* Read the grid quantities computed by set_grids (host or device outputs).
+ * eps [Nk][nw] eV; hw [Nq][nmode] eV.  Either pointer may be NULL.           */
+pgb_status pgb_get_grid_energies(pgb_ctx *ctx, double *eps, double *hw);
+
+/* Energy window (Sec. 4.3): list the k-grid points that have at least one
+ * band in [e_lo, e_hi].  k_idx_out (host or device, capacity Nk) receives
+ * the ascending point indices, *n_out their count.                           */
+pgb_status pgb_window(pgb_ctx *ctx, double e_lo, double e_hi, int32_t *k_idx_out, int64_t *n_out);
+
+/* e-ph matrix elements at arbitrary points (Eqs. eph_mat_wann2, eph_mat).
+ * kpts [nk][3], qpts [nq][3] (host or device, crystal coordinates).  Bands at
+ * k, k+q and phonons at q are interpolated for the call.  precision: PGB_FP64
+ * or PGB_FP32.  out (host or device): see pgb_g_output, always double.        */
+pgb_status pgb_interpolate_g(pgb_ctx *ctx, const double *kpts, int64_t nk, const double *qpts,
+                             int64_t nq, int precision, int out_mode, double *out);
+
+/* RTA scattering rates (Eqs. scatter_rate, BTE_W) for the k-grid points
+ * k_idx[0..nk) (host or device) and every band, summing q over the whole q
+ * grid, m over every band and nu over every mode.  f0 is Fermi-Dirac at (T,
+ * mu), N0 Bose-Einstein at T.  Terms with |x|/sigma > 7 (x the energy
+ * mismatch) are skipped: each is below exp(-49) of a peak term.
+ * gamma_out [nk][nw] (host or device, 1/s); gamma_mode_out [nk][nmode][nw]
+ * or NULL.                                                                    */
+pgb_status pgb_scattering_rates(pgb_ctx *ctx, const int32_t *k_idx, int64_t nk, double T_K,
+                                double mu_eV, double sigma_eV, int precision, double *gamma_out,
+                                double *gamma_mode_out);
+
+/* Scattering list for the collision integral (Sec. 4.3 (k,q) pairs;
+ * Eq. e_ph_scattering).  States are s = ik*nb + (n - band_lo) for every
+ * k-grid point ik and n in [band_lo, band_hi); the q grid must equal the k
+ * grid.  Each entry e (host or device arrays, rows non-decreasing) is the
+ * term s = row[e] -> s' = col[e] by mode mode[e] with |g|^2 = g2[e] (eV^2);
+ * q is the k-grid difference k(s') - k(s).  For each entry the library
+ * computes, in FP64, a = (2pi/hbar)(1/Nq)|g|^2 [d_em (N+1) + d_abs N] and
+ * b = (2pi/hbar)(1/Nq)|g|^2 [d_em N + d_abs (N+1)] with d_em = delta(e_s - hw - e_s'),
+ * d_abs = delta(e_s + hw - e_s'), stores them as FP32 in a CSR list, and
+ * later evaluates I_s = sum_e [ -f_s (1 - f_s') a_e + f_s' (1 - f_s) b_e ].   */
+pgb_status pgb_build_collision(pgb_ctx *ctx, int band_lo, int band_hi, double T_K, double sigma_eV,
+                               int64_t nnz, const int32_t *row, const int32_t *col,
+                               const int32_t *mode, const float *g2);
+
+/* State energies of the collision list [nstates] (host or device).          */
+pgb_status pgb_collision_energies(pgb_ctx *ctx, double *eps_state, int64_t *nstates_out);
+
+/* I[f] (Eq. e_ph_scattering) for f [nstates] -> I_out [nstates], 1/s.       */
+pgb_status pgb_collision(pgb_ctx *ctx, const double *f, double *I_out);
+
+/* nsteps explicit RK4 steps (Sec. 2.1.1) of df/dt = I[f], step dt_fs, in place. */
+pgb_status pgb_step_rk4(pgb_ctx *ctx, double *f, double dt_fs, int64_t nsteps);
+
+/* Number of kernel launches this context has issued since creation.         */
+int64_t pgb_launch_count(const pgb_ctx *ctx);
+
+/* Kernel timing.  When enabled, the launches of the kernel classes below are
+ * bracketed with CUDA events on the context's stream (no synchronisation).
+ * pgb_profile_read synchronises the stream, returns the summed device time
+ * (ms) and launch count of one class since the last read, and resets them.  */
+enum {
+    PGB_PROF_QSUM = 0,      /* Fourier sum over R_p for every q (the dominant contraction) */
+    PGB_PROF_RSUM = 1,      /* Fourier sum over R_e for every k, with the U(k) fold        */
+    PGB_PROF_EPILOGUE = 2,  /* rotation, mode projection, |g|^2, delta weights, Gamma      */
+    PGB_PROF_COLLISION = 3, /* collision integral / RK4 stage                              */
+    PGB_PROF_BANDS = 4,     /* H(k), D(q) sums and eigensolves                             */
+    PGB_PROF_NKERNELS = 5
+};
+pgb_status pgb_profile(pgb_ctx *ctx, int enable);
+pgb_status pgb_profile_read(pgb_ctx *ctx, int kernel_class, double *total_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PERTGB_H */

@@ -1,0 +1,795 @@
+// C ABI entry points of libpertgb (declared in include/pertgb.h): argument
+// checks, host/device staging, memory ownership and the call sequences of the
+// interpolation, rates, collision and RK4 paths.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace pgb;
+
+namespace {
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Input buffer that is host or device: device pointers are used in place,
+// host pointers are copied to a stream-ordered temporary.
+template <typename T>
+struct In {
+    const T *dev = nullptr;
+    T *tmp = nullptr;
+    pgb_ctx *c = nullptr;
+    pgb_status init(pgb_ctx *ctx, const T *p, size_t n) {
+        c = ctx;
+        if (n == 0) return PGB_OK;
+        if (!p) {
+            c->err = "null input pointer";
+            return PGB_EINVAL;
+        }
+        if (is_device_ptr(p)) {
+            dev = p;
+            return PGB_OK;
+        }
+        PGB_CUDA_TRY(c, cudaMallocAsync((void **)&tmp, n * sizeof(T), c->stream));
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(tmp, p, n * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+        dev = tmp;
+        return PGB_OK;
+    }
+    ~In() {
+        if (tmp) cudaFreeAsync(tmp, c->stream);
+    }
+};
+
+// Output buffer that is host or device: host outputs are produced in a
+// temporary and copied back by finish(), which synchronises the stream.
+template <typename T>
+struct Out {
+    T *dev = nullptr;
+    T *host = nullptr;
+    T *tmp = nullptr;
+    size_t n = 0;
+    pgb_ctx *c = nullptr;
+    pgb_status init(pgb_ctx *ctx, T *p, size_t count) {
+        c = ctx;
+        n = count;
+        if (!p) return PGB_OK;
+        if (is_device_ptr(p)) {
+            dev = p;
+            return PGB_OK;
+        }
+        host = p;
+        if (n == 0) return PGB_OK;
+        PGB_CUDA_TRY(c, cudaMallocAsync((void **)&tmp, n * sizeof(T), c->stream));
+        dev = tmp;
+        return PGB_OK;
+    }
+    pgb_status finish() {
+        if (host && n) {
+            PGB_CUDA_TRY(c, cudaMemcpyAsync(host, tmp, n * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+            PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        }
+        return PGB_OK;
+    }
+    ~Out() {
+        if (tmp) cudaFreeAsync(tmp, c->stream);
+    }
+};
+
+// Stream-ordered temporary device array.
+template <typename T>
+struct Tmp {
+    T *p = nullptr;
+    pgb_ctx *c = nullptr;
+    pgb_status alloc(pgb_ctx *ctx, size_t n) {
+        c = ctx;
+        if (n == 0) return PGB_OK;
+        PGB_CUDA_TRY(c, cudaMallocAsync((void **)&p, n * sizeof(T), c->stream));
+        return PGB_OK;
+    }
+    ~Tmp() {
+        if (p) cudaFreeAsync(p, c->stream);
+    }
+};
+
+#define TRY(expr)                          \
+    do {                                   \
+        pgb_status _s = (expr);            \
+        if (_s != PGB_OK) return _s;       \
+    } while (0)
+
+pgb_status fail(pgb_ctx *c, pgb_status s, const std::string &msg) {
+    c->err = msg;
+    return s;
+}
+
+using RKey = std::tuple<int, int, int>;
+
+std::map<RKey, int> r_index(const int32_t *R, int n) {
+    std::map<RKey, int> m;
+    for (int i = 0; i < n; ++i) m[RKey(R[3 * i], R[3 * i + 1], R[3 * i + 2])] = i;
+    return m;
+}
+
+// Interpolate bands at arbitrary points: phases -> H(k) (complex GEMM) -> Jacobi.
+pgb_status bands_at(pgb_ctx *c, const double *d_pts, int64_t np, double *d_eps, double2 *d_U) {
+    const int nw2 = c->nw * c->nw;
+    Tmp<double2> ph, hk;
+    TRY(ph.alloc(c, (size_t)np * c->nRH));
+    TRY(hk.alloc(c, (size_t)np * nw2));
+    TRY(launch_phase_pts(c, d_pts, np, c->d_RH, c->nRH, ph.p, false));
+    TRY(launch_cgemm(c, false, 1, np, nw2, c->nRH, ph.p, c->nRH, 0, c->d_H, nw2, 0, hk.p, nw2, 0));
+    TRY(launch_heevj(c, np, c->nw, hk.p, nullptr, d_eps, d_U));
+    return PGB_OK;
+}
+
+// Interpolate phonons at arbitrary points: hbar*omega and mode coefficients.
+pgb_status phonons_at(pgb_ctx *c, const double *d_pts, int64_t np, double *d_hw, double2 *d_coef) {
+    const int nm2 = c->nm * c->nm;
+    Tmp<double2> ph, dq, ev;
+    Tmp<double> lam;
+    TRY(ph.alloc(c, (size_t)np * c->nRD));
+    TRY(dq.alloc(c, (size_t)np * nm2));
+    TRY(ev.alloc(c, (size_t)np * nm2));
+    TRY(lam.alloc(c, (size_t)np * c->nm));
+    TRY(launch_phase_pts(c, d_pts, np, c->d_RD, c->nRD, ph.p, false));
+    TRY(launch_cgemm(c, false, 1, np, nm2, c->nRD, ph.p, c->nRD, 0, c->d_D, nm2, 0, dq.p, nm2, 0));
+    TRY(launch_heevj(c, np, c->nm, dq.p, c->d_mode_scale, lam.p, ev.p));
+    TRY(launch_phonon_coef(c, np, c->nm, lam.p, ev.p, c->d_mode_scale, d_hw, d_coef));
+    return PGB_OK;
+}
+
+void free_grids(pgb_ctx *c) {
+    dfree(&c->d_eps);
+    dfree(&c->d_U);
+    dfree(&c->d_U32);
+    dfree(&c->d_hw);
+    dfree(&c->d_coef);
+    dfree(&c->d_coef32);
+    dfree(&c->d_phq64);
+    dfree(&c->d_phq32);
+    c->has_grids = false;
+}
+
+void free_coll(pgb_ctx *c) {
+    dfree(&c->d_eps_state);
+    dfree(&c->d_rowptr);
+    dfree(&c->d_col);
+    dfree(&c->d_a);
+    dfree(&c->d_b);
+    dfree(&c->d_rowsum_a);
+    for (int i = 0; i < 4; ++i) dfree(&c->d_f[i]);
+    c->has_coll = false;
+    c->nstates = c->nnz = 0;
+}
+
+void free_model(pgb_ctx *c) {
+    dfree(&c->d_RH);
+    dfree(&c->d_RD);
+    dfree(&c->d_Rge);
+    dfree(&c->d_Rgp);
+    dfree(&c->d_H);
+    dfree(&c->d_D);
+    dfree(&c->d_mode_scale);
+    dfree(&c->d_g64);
+    dfree(&c->d_g32);
+    c->has_model = false;
+}
+
+__global__ void k_f32_to_f64(const float2 *s, double2 *d, int64_t n) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) d[t] = make_double2(s[t].x, s[t].y);
+}
+
+}  // namespace
+
+namespace pgb {
+void prof_mark(pgb_ctx *c, int id) {
+    if (!c->prof) return;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaEventRecord(e, c->stream);
+    c->prof_ev[id].push_back(e);
+}
+
+pgb_status ensure_scratch(pgb_ctx *c, size_t bytes) {
+    if (bytes <= c->scratch_bytes) return PGB_OK;
+    if (c->scratch) {
+        PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        cudaFree(c->scratch);
+        c->scratch = nullptr;
+        c->scratch_bytes = 0;
+    }
+    PGB_CUDA_TRY(c, cudaMalloc(&c->scratch, bytes));
+    c->scratch_bytes = bytes;
+    return PGB_OK;
+}
+}  // namespace pgb
+
+// ===========================================================================
+// ABI
+// ===========================================================================
+extern "C" {
+
+const char *pgb_status_string(int s) {
+    switch (s) {
+        case PGB_OK: return "ok";
+        case PGB_EINVAL: return "invalid argument";
+        case PGB_ESTATE: return "call order violated";
+        case PGB_ENOMEM: return "device allocation failed";
+        case PGB_ECUDA: return "CUDA error";
+        case PGB_ETIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+pgb_status pgb_create(pgb_ctx **out, int device, void *cuda_stream) {
+    if (!out) return PGB_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return PGB_ECUDA;
+    }
+    if (device < 0 || device >= n) return PGB_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return PGB_ECUDA;
+    pgb_ctx *c = new (std::nothrow) pgb_ctx();
+    if (!c) return PGB_ENOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    *out = c;
+    return PGB_OK;
+}
+
+void pgb_destroy(pgb_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_coll(c);
+    free_grids(c);
+    free_model(c);
+    if (c->scratch) cudaFree(c->scratch);
+    for (auto &v : c->prof_ev)
+        for (auto e : v) cudaEventDestroy(e);
+    delete c;
+}
+
+const char *pgb_last_error(const pgb_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int64_t pgb_launch_count(const pgb_ctx *c) { return c ? c->launches : 0; }
+
+pgb_status pgb_profile(pgb_ctx *c, int enable) {
+    if (!c) return PGB_EINVAL;
+    c->prof = enable != 0;
+    return PGB_OK;
+}
+
+pgb_status pgb_profile_read(pgb_ctx *c, int id, double *total_ms, int64_t *launches) {
+    if (!c) return PGB_EINVAL;
+    if (id < 0 || id >= PGB_PROF_NKERNELS) return fail(c, PGB_EINVAL, "profile_read: unknown kernel class");
+    cudaSetDevice(c->device);
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    auto &ev = c->prof_ev[id];
+    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+        float ms = 0.f;
+        PGB_CUDA_TRY(c, cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+        c->prof_ms[id] += ms;
+        c->prof_n[id] += 1;
+    }
+    for (auto e : ev) cudaEventDestroy(e);
+    ev.clear();
+    if (total_ms) *total_ms = c->prof_ms[id];
+    if (launches) *launches = c->prof_n[id];
+    c->prof_ms[id] = 0.0;
+    c->prof_n[id] = 0;
+    return PGB_OK;
+}
+
+pgb_status pgb_set_model(pgb_ctx *c, const pgb_model *m) {
+    if (!c) return PGB_EINVAL;
+    if (!m) return fail(c, PGB_EINVAL, "set_model: null model");
+    cudaSetDevice(c->device);
+    if (m->nw < 1 || m->nw > kMaxNw) return fail(c, PGB_EINVAL, "set_model: nw must be 1..16");
+    if (m->nat < 1 || 3 * m->nat > kMaxNmode) return fail(c, PGB_EINVAL, "set_model: nat must be 1..5");
+    if (m->nR_H < 1 || m->nR_D < 1 || m->nR_ge < 1 || m->nR_gp < 1)
+        return fail(c, PGB_EINVAL, "set_model: every R list needs at least one vector");
+    if (!m->mass || !m->R_H || !m->H || !m->R_D || !m->D || !m->R_ge || !m->R_gp || !m->g)
+        return fail(c, PGB_EINVAL, "set_model: null array");
+    const int nw = m->nw, nm = 3 * m->nat, nw2 = nw * nw, nm2 = nm * nm;
+    for (int i = 0; i < m->nat; ++i)
+        if (!(m->mass[i] > 0.0) || !std::isfinite(m->mass[i]))
+            return fail(c, PGB_EINVAL, "set_model: masses must be positive");
+    // H(-R) = H(R)^dagger
+    {
+        auto idx = r_index(m->R_H, m->nR_H);
+        for (int r = 0; r < m->nR_H; ++r) {
+            auto it = idx.find(RKey(-m->R_H[3 * r], -m->R_H[3 * r + 1], -m->R_H[3 * r + 2]));
+            if (it == idx.end()) return fail(c, PGB_EINVAL, "set_model: R_H is not closed under inversion");
+            const double *a = m->H + 2 * (size_t)r * nw2;
+            const double *b = m->H + 2 * (size_t)it->second * nw2;
+            for (int i = 0; i < nw; ++i)
+                for (int j = 0; j < nw; ++j) {
+                    const double ar = a[2 * (i * nw + j)], ai = a[2 * (i * nw + j) + 1];
+                    const double br = b[2 * (j * nw + i)], bi = b[2 * (j * nw + i) + 1];
+                    if (!std::isfinite(ar) || !std::isfinite(ai))
+                        return fail(c, PGB_EINVAL, "set_model: non-finite H");
+                    if (std::fabs(ar - br) > 1e-10 * (1.0 + std::fabs(ar)) ||
+                        std::fabs(ai + bi) > 1e-10 * (1.0 + std::fabs(ai)))
+                        return fail(c, PGB_EINVAL, "set_model: H(-R) != H(R)^dagger");
+                }
+        }
+    }
+    // D(-R) = D(R)^T
+    {
+        auto idx = r_index(m->R_D, m->nR_D);
+        for (int r = 0; r < m->nR_D; ++r) {
+            auto it = idx.find(RKey(-m->R_D[3 * r], -m->R_D[3 * r + 1], -m->R_D[3 * r + 2]));
+            if (it == idx.end()) return fail(c, PGB_EINVAL, "set_model: R_D is not closed under inversion");
+            const double *a = m->D + (size_t)r * nm2;
+            const double *b = m->D + (size_t)it->second * nm2;
+            for (int i = 0; i < nm; ++i)
+                for (int j = 0; j < nm; ++j) {
+                    if (!std::isfinite(a[i * nm + j])) return fail(c, PGB_EINVAL, "set_model: non-finite D");
+                    if (std::fabs(a[i * nm + j] - b[j * nm + i]) > 1e-10 * (1.0 + std::fabs(a[i * nm + j])))
+                        return fail(c, PGB_EINVAL, "set_model: D(-R) != D(R)^T");
+                }
+        }
+    }
+    const size_t ng = (size_t)m->nR_ge * m->nR_gp * nm * nw2;
+    if (m->g_is_double) {
+        const double *g = (const double *)m->g;
+        for (size_t i = 0; i < 2 * ng; ++i)
+            if (!std::isfinite(g[i])) return fail(c, PGB_EINVAL, "set_model: non-finite g");
+    } else {
+        const float *g = (const float *)m->g;
+        for (size_t i = 0; i < 2 * ng; ++i)
+            if (!std::isfinite(g[i])) return fail(c, PGB_EINVAL, "set_model: non-finite g");
+    }
+
+    free_coll(c);
+    free_grids(c);
+    free_model(c);
+    c->nw = nw;
+    c->nat = m->nat;
+    c->nm = nm;
+    c->nRH = m->nR_H;
+    c->nRD = m->nR_D;
+    c->nRge = m->nR_ge;
+    c->nRgp = m->nR_gp;
+    c->mass.assign(m->mass, m->mass + m->nat);
+    TRY(dalloc(c, &c->d_RH, 3 * (size_t)c->nRH));
+    TRY(dalloc(c, &c->d_RD, 3 * (size_t)c->nRD));
+    TRY(dalloc(c, &c->d_Rge, 3 * (size_t)c->nRge));
+    TRY(dalloc(c, &c->d_Rgp, 3 * (size_t)c->nRgp));
+    TRY(dalloc(c, &c->d_H, (size_t)c->nRH * nw2));
+    TRY(dalloc(c, &c->d_D, (size_t)c->nRD * nm2));
+    TRY(dalloc(c, &c->d_mode_scale, (size_t)nm));
+    TRY(dalloc(c, &c->d_g64, ng));
+    TRY(dalloc(c, &c->d_g32, ng));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_RH, m->R_H, 12 * (size_t)c->nRH, cudaMemcpyHostToDevice, c->stream));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_RD, m->R_D, 12 * (size_t)c->nRD, cudaMemcpyHostToDevice, c->stream));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_Rge, m->R_ge, 12 * (size_t)c->nRge, cudaMemcpyHostToDevice, c->stream));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_Rgp, m->R_gp, 12 * (size_t)c->nRgp, cudaMemcpyHostToDevice, c->stream));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_H, m->H, 16 * (size_t)c->nRH * nw2, cudaMemcpyHostToDevice, c->stream));
+    std::vector<double> D2((size_t)2 * c->nRD * nm2, 0.0);
+    for (size_t i = 0; i < (size_t)c->nRD * nm2; ++i) D2[2 * i] = m->D[i];
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_D, D2.data(), 8 * D2.size(), cudaMemcpyHostToDevice, c->stream));
+    std::vector<double> sc(nm);
+    for (int ka = 0; ka < nm; ++ka) sc[ka] = 1.0 / std::sqrt(m->mass[ka / 3]);
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_mode_scale, sc.data(), 8 * (size_t)nm, cudaMemcpyHostToDevice, c->stream));
+    if (m->g_is_double) {
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_g64, m->g, 16 * ng, cudaMemcpyHostToDevice, c->stream));
+        TRY(launch_to_f32(c, c->d_g64, c->d_g32, (int64_t)ng));
+    } else {
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_g32, m->g, 8 * ng, cudaMemcpyHostToDevice, c->stream));
+        k_f32_to_f64<<<(unsigned int)((ng + 255) / 256), 256, 0, c->stream>>>(c->d_g32, c->d_g64, (int64_t)ng);
+        PGB_LAUNCH_CHECK(c);
+    }
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // host vectors above go out of scope
+    c->has_model = true;
+    return PGB_OK;
+}
+
+pgb_status pgb_set_grids(pgb_ctx *c, const int kgrid[3], const int qgrid[3]) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_model) return fail(c, PGB_ESTATE, "set_grids: call set_model first");
+    if (!kgrid || !qgrid) return fail(c, PGB_EINVAL, "set_grids: null grid");
+    for (int d = 0; d < 3; ++d) {
+        if (kgrid[d] < 1 || qgrid[d] < 1 || kgrid[d] > 1024 || qgrid[d] > 1024)
+            return fail(c, PGB_EINVAL, "set_grids: grid sizes must be 1..1024");
+        if (kgrid[d] % qgrid[d] != 0) return fail(c, PGB_EINVAL, "set_grids: q grid must divide the k grid");
+    }
+    free_coll(c);
+    free_grids(c);
+    for (int d = 0; d < 3; ++d) {
+        c->kg[d] = kgrid[d];
+        c->qg[d] = qgrid[d];
+    }
+    c->Nk = (int64_t)kgrid[0] * kgrid[1] * kgrid[2];
+    c->Nq = (int64_t)qgrid[0] * qgrid[1] * qgrid[2];
+    const int nw2 = c->nw * c->nw, nm2 = c->nm * c->nm;
+    TRY(dalloc(c, &c->d_eps, (size_t)c->Nk * c->nw));
+    TRY(dalloc(c, &c->d_U, (size_t)c->Nk * nw2));
+    TRY(dalloc(c, &c->d_U32, (size_t)c->Nk * nw2));
+    TRY(dalloc(c, &c->d_hw, (size_t)c->Nq * c->nm));
+    TRY(dalloc(c, &c->d_coef, (size_t)c->Nq * nm2));
+    TRY(dalloc(c, &c->d_coef32, (size_t)c->Nq * nm2));
+    {   // bands on the k grid (chunks bound the phase-table size)
+        const int64_t chunk = 1 << 16;
+        Tmp<double2> ph, hk;
+        TRY(ph.alloc(c, (size_t)std::min<int64_t>(chunk, c->Nk) * c->nRH));
+        TRY(hk.alloc(c, (size_t)std::min<int64_t>(chunk, c->Nk) * nw2));
+        std::vector<int32_t> idx;
+        Tmp<int32_t> didx;
+        TRY(didx.alloc(c, (size_t)std::min<int64_t>(chunk, c->Nk)));
+        for (int64_t k0 = 0; k0 < c->Nk; k0 += chunk) {
+            const int64_t nk = std::min<int64_t>(chunk, c->Nk - k0);
+            idx.resize(nk);
+            for (int64_t i = 0; i < nk; ++i) idx[i] = (int32_t)(k0 + i);
+            PGB_CUDA_TRY(c, cudaMemcpyAsync(didx.p, idx.data(), 4 * nk, cudaMemcpyHostToDevice, c->stream));
+            TRY(launch_phase_grid(c, c->kg, didx.p, nk, c->d_RH, c->nRH, ph.p, false));
+            TRY(launch_cgemm(c, false, 1, nk, nw2, c->nRH, ph.p, c->nRH, 0, c->d_H, nw2, 0, hk.p, nw2, 0));
+            TRY(launch_heevj(c, nk, c->nw, hk.p, nullptr, c->d_eps + k0 * c->nw, c->d_U + k0 * nw2));
+            PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        }
+    }
+    {   // phonons on the q grid
+        Tmp<double2> ph, dq, ev;
+        Tmp<double> lam;
+        TRY(ph.alloc(c, (size_t)c->Nq * c->nRD));
+        TRY(dq.alloc(c, (size_t)c->Nq * nm2));
+        TRY(ev.alloc(c, (size_t)c->Nq * nm2));
+        TRY(lam.alloc(c, (size_t)c->Nq * c->nm));
+        TRY(launch_phase_grid(c, c->qg, nullptr, c->Nq, c->d_RD, c->nRD, ph.p, false));
+        TRY(launch_cgemm(c, false, 1, c->Nq, nm2, c->nRD, ph.p, c->nRD, 0, c->d_D, nm2, 0, dq.p, nm2, 0));
+        TRY(launch_heevj(c, c->Nq, c->nm, dq.p, c->d_mode_scale, lam.p, ev.p));
+        TRY(launch_phonon_coef(c, c->Nq, c->nm, lam.p, ev.p, c->d_mode_scale, c->d_hw, c->d_coef));
+    }
+    TRY(launch_to_f32(c, c->d_U, c->d_U32, c->Nk * nw2));
+    TRY(launch_to_f32(c, c->d_coef, c->d_coef32, c->Nq * nm2));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->has_grids = true;
+    return PGB_OK;
+}
+
+pgb_status pgb_get_grid_energies(pgb_ctx *c, double *eps, double *hw) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_grids) return fail(c, PGB_ESTATE, "get_grid_energies: call set_grids first");
+    if (eps)
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(eps, c->d_eps, 8 * (size_t)c->Nk * c->nw, cudaMemcpyDefault, c->stream));
+    if (hw)
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(hw, c->d_hw, 8 * (size_t)c->Nq * c->nm, cudaMemcpyDefault, c->stream));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PGB_OK;
+}
+
+pgb_status pgb_window(pgb_ctx *c, double lo, double hi, int32_t *k_idx_out, int64_t *n_out) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_grids) return fail(c, PGB_ESTATE, "window: call set_grids first");
+    if (!k_idx_out || !n_out) return fail(c, PGB_EINVAL, "window: null output");
+    Tmp<int32_t> flag;
+    TRY(flag.alloc(c, (size_t)c->Nk));
+    TRY(launch_window(c, c->d_eps, c->Nk, c->nw, lo, hi, flag.p));
+    std::vector<int32_t> h(c->Nk);
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(h.data(), flag.p, 4 * (size_t)c->Nk, cudaMemcpyDeviceToHost, c->stream));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    std::vector<int32_t> list;
+    for (int64_t k = 0; k < c->Nk; ++k)
+        if (h[k]) list.push_back((int32_t)k);
+    *n_out = (int64_t)list.size();
+    if (!list.empty()) {
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(k_idx_out, list.data(), 4 * list.size(), cudaMemcpyDefault, c->stream));
+        PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    return PGB_OK;
+}
+
+pgb_status pgb_interpolate_g(pgb_ctx *c, const double *kpts, int64_t nk, const double *qpts, int64_t nq,
+                             int precision, int out_mode, double *out) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_model) return fail(c, PGB_ESTATE, "interpolate_g: call set_model first");
+    if (nk < 0 || nq < 0) return fail(c, PGB_EINVAL, "interpolate_g: negative size");
+    if (precision != PGB_FP64 && precision != PGB_FP32)
+        return fail(c, PGB_EINVAL, "interpolate_g: precision must be PGB_FP64 or PGB_FP32");
+    if (out_mode != PGB_G2_FULL && out_mode != PGB_G_ABS)
+        return fail(c, PGB_EINVAL, "interpolate_g: unknown out_mode");
+    if (!out && nk * nq > 0) return fail(c, PGB_EINVAL, "interpolate_g: null output");
+    if (nk == 0 || nq == 0) return PGB_OK;
+    const bool f32 = precision == PGB_FP32;
+    const int nw = c->nw, nm = c->nm, nw2 = nw * nw, nm2 = nm * nm;
+    const int64_t ncol = (int64_t)nm * nw2, npair = nk * nq;
+    const size_t es = f32 ? sizeof(float2) : sizeof(double2);
+    In<double> K, Q;
+    TRY(K.init(c, kpts, 3 * (size_t)nk));
+    TRY(Q.init(c, qpts, 3 * (size_t)nq));
+    const size_t full = (size_t)npair * nm * nw2;
+    Out<double> O;
+    TRY(O.init(c, out, out_mode == PGB_G2_FULL ? full : (size_t)npair * nm));
+    // bands at k and k+q, phonons at q (FP64)
+    Tmp<double> eps_k, eps_kq, hw_q;
+    Tmp<double2> U_k, U_kq, coef_q;
+    Tmp<double> kq;
+    TRY(eps_k.alloc(c, (size_t)nk * nw));
+    TRY(U_k.alloc(c, (size_t)nk * nw2));
+    TRY(kq.alloc(c, 3 * (size_t)npair));
+    TRY(eps_kq.alloc(c, (size_t)npair * nw));
+    TRY(U_kq.alloc(c, (size_t)npair * nw2));
+    TRY(hw_q.alloc(c, (size_t)nq * nm));
+    TRY(coef_q.alloc(c, (size_t)nq * nm2));
+    TRY(bands_at(c, K.dev, nk, eps_k.p, U_k.p));
+    TRY(launch_kplusq_pts(c, K.dev, nk, Q.dev, nq, kq.p));
+    TRY(bands_at(c, kq.p, npair, eps_kq.p, U_kq.p));
+    TRY(phonons_at(c, Q.dev, nq, hw_q.p, coef_q.p));
+    Tmp<float2> U_k32, U_kq32, coef_q32;
+    const void *Uk = U_k.p, *Ukq = U_kq.p, *cf = coef_q.p;
+    if (f32) {
+        TRY(U_k32.alloc(c, (size_t)nk * nw2));
+        TRY(U_kq32.alloc(c, (size_t)npair * nw2));
+        TRY(coef_q32.alloc(c, (size_t)nq * nm2));
+        TRY(launch_to_f32(c, U_k.p, U_k32.p, nk * nw2));
+        TRY(launch_to_f32(c, U_kq.p, U_kq32.p, npair * nw2));
+        TRY(launch_to_f32(c, coef_q.p, coef_q32.p, nq * nm2));
+        Uk = U_k32.p;
+        Ukq = U_kq32.p;
+        cf = coef_q32.p;
+    }
+    // g: Re-sum (GEMM), fold U(k), Rp-sum (batched GEMM), epilogue
+    Tmp<char> phk, S1, G, phq, C, fullbuf;
+    const int64_t nrow = (int64_t)c->nRgp * ncol;
+    TRY(phk.alloc(c, (size_t)nk * c->nRge * es));
+    TRY(S1.alloc(c, (size_t)nk * nrow * es));
+    TRY(G.alloc(c, (size_t)nk * nrow * es));
+    TRY(phq.alloc(c, (size_t)nq * c->nRgp * es));
+    TRY(C.alloc(c, (size_t)npair * ncol * es));
+    TRY(launch_phase_pts(c, K.dev, nk, c->d_Rge, c->nRge, phk.p, f32));
+    const void *g = f32 ? (const void *)c->d_g32 : (const void *)c->d_g64;
+    TRY(launch_cgemm(c, f32, 1, nk, nrow, c->nRge, phk.p, c->nRge, 0, g, nrow, 0, S1.p, nrow, 0));
+    TRY(launch_fold_u(c, f32, nk, nullptr, c->nRgp, nm, nw, S1.p, Uk, G.p));
+    TRY(launch_phase_pts(c, Q.dev, nq, c->d_Rgp, c->nRgp, phq.p, f32));
+    TRY(launch_cgemm(c, f32, nk, nq, ncol, c->nRgp, phq.p, c->nRgp, 0, G.p, ncol, nrow, C.p, ncol, nq * ncol));
+    double *fullp = O.dev;
+    if (out_mode == PGB_G_ABS) {
+        TRY(fullbuf.alloc(c, full * sizeof(double)));
+        fullp = (double *)fullbuf.p;
+    }
+    GArgs ga;
+    ga.nk = nk;
+    ga.nq = nq;
+    ga.nw = nw;
+    ga.nm = nm;
+    ga.C = C.p;
+    ga.Ukq = Ukq;
+    ga.coef = cf;
+    ga.out_mode = out_mode;
+    ga.out = fullp;
+    TRY(launch_g_epilogue(c, f32, ga));
+    if (out_mode == PGB_G_ABS) TRY(launch_g_abs(c, npair, nm, nw, fullp, O.dev));
+    TRY(O.finish());
+    return PGB_OK;
+}
+
+pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, double T, double mu, double sigma,
+                                int precision, double *gamma_out, double *gamma_mode_out) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_grids) return fail(c, PGB_ESTATE, "scattering_rates: call set_grids first");
+    if (nk < 0) return fail(c, PGB_EINVAL, "scattering_rates: negative nk");
+    if (!(T > 0.0) || !(sigma > 0.0) || !std::isfinite(mu))
+        return fail(c, PGB_EINVAL, "scattering_rates: need T > 0, sigma > 0, finite mu");
+    if (precision != PGB_FP64 && precision != PGB_FP32)
+        return fail(c, PGB_EINVAL, "scattering_rates: tensor-core precisions are not available in this build");
+    if (nk == 0) return PGB_OK;
+    if (!gamma_out) return fail(c, PGB_EINVAL, "scattering_rates: null gamma_out");
+    const bool f32 = precision == PGB_FP32;
+    const int nw = c->nw, nm = c->nm, nw2 = nw * nw;
+    const int64_t ncol = (int64_t)nm * nw2, nrow = (int64_t)c->nRgp * ncol;
+    const size_t es = f32 ? sizeof(float2) : sizeof(double2);
+
+    // k list: validate on the host
+    std::vector<int32_t> hk(nk);
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(hk.data(), k_idx, 4 * (size_t)nk, cudaMemcpyDefault, c->stream));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int64_t i = 0; i < nk; ++i)
+        if (hk[i] < 0 || hk[i] >= c->Nk) return fail(c, PGB_EINVAL, "scattering_rates: k index out of range");
+    Tmp<int32_t> dk;
+    TRY(dk.alloc(c, (size_t)nk));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(dk.p, hk.data(), 4 * (size_t)nk, cudaMemcpyHostToDevice, c->stream));
+
+    Out<double> Gm, Gmm;
+    TRY(Gm.init(c, gamma_out, (size_t)nk * nw));
+    TRY(Gmm.init(c, gamma_mode_out, (size_t)nk * nm * nw));
+
+    // q-grid phase table exp(i q.Rp), kept for later calls
+    void *phq = f32 ? (void *)c->d_phq32 : (void *)c->d_phq64;
+    if (!phq) {
+        if (f32) {
+            TRY(dalloc(c, &c->d_phq32, (size_t)c->Nq * c->nRgp));
+            phq = c->d_phq32;
+        } else {
+            TRY(dalloc(c, &c->d_phq64, (size_t)c->Nq * c->nRgp));
+            phq = c->d_phq64;
+        }
+        TRY(launch_phase_grid(c, c->qg, nullptr, c->Nq, c->d_Rgp, c->nRgp, phq, f32));
+    }
+
+    const int per = nm * nw;
+    const int qpb = std::max(1, 256 / per);
+    const int64_t nqblk = (c->Nq + qpb - 1) / qpb;
+    const size_t per_k = (size_t)(2 * nrow + c->Nq * ncol + c->nRge) * es + (size_t)nqblk * per * sizeof(double);
+    const size_t budget = (size_t)4 << 30;
+    int64_t nbmax = std::max<int64_t>(1, (int64_t)(budget / per_k));
+    nbmax = std::min<int64_t>(nbmax, std::min<int64_t>(nk, 65535));
+    TRY(ensure_scratch(c, nbmax * per_k));
+    char *base = (char *)c->scratch;
+    char *phk = base;
+    char *S1 = phk + (size_t)nbmax * c->nRge * es;
+    char *G = S1 + (size_t)nbmax * nrow * es;
+    char *Cb = G + (size_t)nbmax * nrow * es;
+    double *partial = (double *)(Cb + (size_t)nbmax * c->Nq * ncol * es);
+    const void *g = f32 ? (const void *)c->d_g32 : (const void *)c->d_g64;
+    const void *U = f32 ? (const void *)c->d_U32 : (const void *)c->d_U;
+    const void *cf = f32 ? (const void *)c->d_coef32 : (const void *)c->d_coef;
+    const double scale = kTwoPiOverHbar / ((double)c->Nq * sigma * kSqrtPi);
+    for (int64_t b0 = 0; b0 < nk; b0 += nbmax) {
+        const int64_t nb = std::min<int64_t>(nbmax, nk - b0);
+        const int32_t *kb = dk.p + b0;
+        prof_mark(c, PGB_PROF_RSUM);
+        TRY(launch_phase_grid(c, c->kg, kb, nb, c->d_Rge, c->nRge, phk, f32));
+        TRY(launch_cgemm(c, f32, 1, nb, nrow, c->nRge, phk, c->nRge, 0, g, nrow, 0, S1, nrow, 0));
+        TRY(launch_fold_u(c, f32, nb, kb, c->nRgp, nm, nw, S1, U, G));
+        prof_mark(c, PGB_PROF_RSUM);
+        prof_mark(c, PGB_PROF_QSUM);
+        TRY(launch_cgemm(c, f32, nb, c->Nq, ncol, c->nRgp, phq, c->nRgp, 0, G, ncol, nrow, Cb, ncol,
+                         c->Nq * ncol));
+        prof_mark(c, PGB_PROF_QSUM);
+        RatesArgs ra;
+        ra.nb = nb;
+        ra.kidx = kb;
+        ra.Nq = c->Nq;
+        for (int d = 0; d < 3; ++d) {
+            ra.kg[d] = c->kg[d];
+            ra.qg[d] = c->qg[d];
+        }
+        ra.nw = nw;
+        ra.nm = nm;
+        ra.C = Cb;
+        ra.U = U;
+        ra.coef = cf;
+        ra.eps = c->d_eps;
+        ra.hw = c->d_hw;
+        ra.T = T;
+        ra.mu = mu;
+        ra.sigma = sigma;
+        ra.partial = partial;
+        ra.nqblk = nqblk;
+        ra.qpb = qpb;
+        prof_mark(c, PGB_PROF_EPILOGUE);
+        TRY(launch_rates_epilogue(c, f32, ra));
+        prof_mark(c, PGB_PROF_EPILOGUE);
+        TRY(launch_rates_reduce(c, nb, nqblk, nm, nw, scale, partial, Gm.dev + b0 * nw,
+                                Gmm.dev ? Gmm.dev + b0 * nm * nw : nullptr));
+    }
+    TRY(Gm.finish());
+    TRY(Gmm.finish());
+    return PGB_OK;
+}
+
+pgb_status pgb_build_collision(pgb_ctx *c, int band_lo, int band_hi, double T, double sigma, int64_t nnz,
+                               const int32_t *row, const int32_t *col, const int32_t *mode, const float *g2) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_grids) return fail(c, PGB_ESTATE, "build_collision: call set_grids first");
+    for (int d = 0; d < 3; ++d)
+        if (c->kg[d] != c->qg[d]) return fail(c, PGB_EINVAL, "build_collision: the q grid must equal the k grid");
+    if (band_lo < 0 || band_hi > c->nw || band_lo >= band_hi)
+        return fail(c, PGB_EINVAL, "build_collision: need 0 <= band_lo < band_hi <= nw");
+    if (!(T > 0.0) || !(sigma > 0.0)) return fail(c, PGB_EINVAL, "build_collision: need T > 0, sigma > 0");
+    if (nnz < 0 || nnz > ((int64_t)1 << 40)) return fail(c, PGB_EINVAL, "build_collision: bad nnz");
+    const int nb = band_hi - band_lo;
+    const int64_t ns = c->Nk * nb;
+    if (ns > INT32_MAX) return fail(c, PGB_EINVAL, "build_collision: too many states");
+    free_coll(c);
+    In<int32_t> R, Cc, M;
+    In<float> G;
+    TRY(R.init(c, row, (size_t)nnz));
+    TRY(Cc.init(c, col, (size_t)nnz));
+    TRY(M.init(c, mode, (size_t)nnz));
+    TRY(G.init(c, g2, (size_t)nnz));
+    c->band_lo = band_lo;
+    c->band_hi = band_hi;
+    c->nstates = ns;
+    c->nnz = nnz;
+    pgb_status st = launch_coll_coeffs(c, T, sigma, R.dev, Cc.dev, M.dev, G.dev, nnz, nb);
+    if (st != PGB_OK) {
+        std::string e = c->err;
+        free_coll(c);
+        c->err = e;
+        return st;
+    }
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->has_coll = true;
+    return PGB_OK;
+}
+
+pgb_status pgb_collision_energies(pgb_ctx *c, double *eps_state, int64_t *nstates_out) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_coll) return fail(c, PGB_ESTATE, "collision_energies: call build_collision first");
+    if (nstates_out) *nstates_out = c->nstates;
+    if (eps_state) {
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(eps_state, c->d_eps_state, 8 * (size_t)c->nstates, cudaMemcpyDefault,
+                                        c->stream));
+        PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    return PGB_OK;
+}
+
+pgb_status pgb_collision(pgb_ctx *c, const double *f, double *I_out) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_coll) return fail(c, PGB_ESTATE, "collision: call build_collision first");
+    if (!f || !I_out) return fail(c, PGB_EINVAL, "collision: null pointer");
+    In<double> F;
+    TRY(F.init(c, f, (size_t)c->nstates));
+    Out<double> I;
+    TRY(I.init(c, I_out, (size_t)c->nstates));
+    TRY(launch_collision(c, F.dev, I.dev, -1, 0.0, nullptr, nullptr, nullptr));
+    TRY(I.finish());
+    return PGB_OK;
+}
+
+pgb_status pgb_step_rk4(pgb_ctx *c, double *f, double dt_fs, int64_t nsteps) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_coll) return fail(c, PGB_ESTATE, "step_rk4: call build_collision first");
+    if (!f) return fail(c, PGB_EINVAL, "step_rk4: null f");
+    if (nsteps < 0 || !std::isfinite(dt_fs)) return fail(c, PGB_EINVAL, "step_rk4: bad step");
+    const size_t ns = (size_t)c->nstates;
+    double *fd = f;
+    double *tmp = nullptr;
+    const bool host = !is_device_ptr(f);
+    if (host) {
+        PGB_CUDA_TRY(c, cudaMallocAsync((void **)&tmp, 8 * ns, c->stream));
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(tmp, f, 8 * ns, cudaMemcpyHostToDevice, c->stream));
+        fd = tmp;
+    }
+    const double dt = dt_fs * kFemto;
+    double *acc = c->d_f[0], *f1 = c->d_f[1], *f2 = c->d_f[2];
+    pgb_status st = PGB_OK;
+    for (int64_t s = 0; s < nsteps && st == PGB_OK; ++s) {
+        st = launch_collision(c, fd, nullptr, 0, dt, acc, f1, fd);
+        if (st == PGB_OK) st = launch_collision(c, f1, nullptr, 1, dt, acc, f2, fd);
+        if (st == PGB_OK) st = launch_collision(c, f2, nullptr, 2, dt, acc, f1, fd);
+        if (st == PGB_OK) st = launch_collision(c, f1, nullptr, 3, dt, acc, fd, fd);
+    }
+    if (host) {
+        if (st == PGB_OK) {
+            cudaMemcpyAsync(f, tmp, 8 * ns, cudaMemcpyDeviceToHost, c->stream);
+            if (cudaStreamSynchronize(c->stream) != cudaSuccess) st = fail(c, PGB_ECUDA, "step_rk4: copy back");
+        }
+        cudaFreeAsync(tmp, c->stream);
+    }
+    return st;
+}
+
+}  // extern "C"

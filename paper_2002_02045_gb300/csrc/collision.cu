@@ -1,0 +1,289 @@
+// Collision integral I[f] (Eq. e_ph_scattering) on a CSR scattering list and
+// the fused RK4 stages (Sec. 2.1.1).
+#include "internal.cuh"
+
+namespace pgb {
+
+static inline unsigned int div_up(int64_t a, int64_t b) { return (unsigned int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// list validation: bit 0 row out of range, 1 col out of range, 2 mode out of
+// range, 3 rows decreasing, 4 band of a state outside [band_lo, band_hi)
+// ---------------------------------------------------------------------------
+__global__ void k_coll_validate(int64_t nnz, int64_t nstates, int nm, const int32_t *__restrict__ row,
+                                const int32_t *__restrict__ col, const int32_t *__restrict__ mode,
+                                int *__restrict__ flag) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    int f = 0;
+    const int32_t r = row[e];
+    if (r < 0 || r >= nstates) f |= 1;
+    const int32_t cc = col[e];
+    if (cc < 0 || cc >= nstates) f |= 2;
+    const int32_t md = mode[e];
+    if (md < 0 || md >= nm) f |= 4;
+    if (e > 0 && row[e - 1] > r) f |= 8;
+    if (f) atomicOr(flag, f);
+}
+
+// ---------------------------------------------------------------------------
+// Per-entry coefficients, FP64 arithmetic, stored FP32:
+//   a = scale |g|^2 [d_em (N+1) + d_abs N],  b = scale |g|^2 [d_em N + d_abs (N+1)]
+// d_em = e^{-(x_em/s)^2}, x_em = (e_s - e_s') - hw, x_abs = (e_s - e_s') + hw,
+// scale = (2 pi/hbar) / (N_q s sqrt(pi)).  Because e_s' - e_s is the exact
+// negation of e_s - e_s', the reverse entry of a process gets a' = b and
+// b' = a bit for bit, so that sum_s I_s = 0 is not broken by the list.
+// ---------------------------------------------------------------------------
+struct CoeffArgs {
+    int64_t nnz;
+    const int32_t *row, *col, *mode;
+    const float *g2;
+    int nb, band_lo, nw, nm;
+    int kg[3];
+    const double *eps;   // [Nk][nw]
+    const double *hw;    // [Nq][nm] (q grid == k grid)
+    double T, sigma, scale;
+    int32_t *out_col;
+    float *a, *b;
+};
+
+__global__ void k_coll_coeffs(CoeffArgs p) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p.nnz) return;
+    const int32_t s = p.row[e], sp = p.col[e];
+    const int64_t k = s / p.nb, kp = sp / p.nb;
+    const int n = s % p.nb + p.band_lo, m = sp % p.nb + p.band_lo;
+    const int k3 = (int)(k % p.kg[2]), k2 = (int)((k / p.kg[2]) % p.kg[1]), k1 = (int)(k / ((int64_t)p.kg[1] * p.kg[2]));
+    const int l3 = (int)(kp % p.kg[2]), l2 = (int)((kp / p.kg[2]) % p.kg[1]), l1 = (int)(kp / ((int64_t)p.kg[1] * p.kg[2]));
+    const int q1 = (l1 - k1 + p.kg[0]) % p.kg[0], q2 = (l2 - k2 + p.kg[1]) % p.kg[1], q3 = (l3 - k3 + p.kg[2]) % p.kg[2];
+    const int64_t q = ((int64_t)q1 * p.kg[1] + q2) * p.kg[2] + q3;
+    const double w = p.hw[q * p.nm + p.mode[e]];
+    double a = 0.0, b = 0.0;
+    if (w >= kOmegaMinEv) {
+        const double N = 1.0 / expm1(w / (kBoltzEvK * p.T));
+        const double d = p.eps[k * p.nw + n] - p.eps[kp * p.nw + m];
+        const double is = 1.0 / p.sigma;
+        const double xe = (d - w) * is, xa = (d + w) * is;
+        const double de = exp(-xe * xe), da = exp(-xa * xa);
+        const double g = p.scale * (double)p.g2[e];
+        a = g * (de * (N + 1.0) + da * N);
+        b = g * (de * N + da * (N + 1.0));
+    }
+    p.out_col[e] = sp;
+    p.a[e] = (float)a;
+    p.b[e] = (float)b;
+}
+
+__global__ void k_rowptr(int64_t nstates, int64_t nnz, const int32_t *__restrict__ row, int64_t *__restrict__ rowptr) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s > nstates) return;
+    int64_t lo = 0, hi = nnz;   // first e with row[e] >= s
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (row[mid] < s)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    rowptr[s] = lo;
+}
+
+__global__ void k_eps_state(int64_t nstates, int nb, int band_lo, int nw, const double *__restrict__ eps,
+                            double *__restrict__ out) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nstates) return;
+    out[s] = eps[(s / nb) * nw + (s % nb) + band_lo];
+}
+
+// warp per row: sum of a (FP64) for the -f_s sum_e a_e term
+__global__ void k_rowsum(int64_t nstates, const int64_t *__restrict__ rowptr, const float *__restrict__ a,
+                         double *__restrict__ out) {
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= nstates) return;
+    double acc = 0.0;
+    for (int64_t e = rowptr[s] + lane; e < rowptr[s + 1]; e += 32) acc += (double)a[e];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[s] = acc;
+}
+
+pgb_status launch_coll_coeffs(pgb_ctx *c, double T, double sigma, const int32_t *row, const int32_t *col,
+                              const int32_t *mode, const float *g2, int64_t nnz, int nb) {
+    const int64_t ns = c->nstates;
+    if (nnz > 0) {
+        int *d_flag = nullptr;
+        PGB_CUDA_TRY(c, cudaMallocAsync((void **)&d_flag, sizeof(int), c->stream));
+        PGB_CUDA_TRY(c, cudaMemsetAsync(d_flag, 0, sizeof(int), c->stream));
+        k_coll_validate<<<div_up(nnz, 256), 256, 0, c->stream>>>(nnz, ns, c->nm, row, col, mode, d_flag);
+        PGB_LAUNCH_CHECK(c);
+        int flag = 0;
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        PGB_CUDA_TRY(c, cudaFreeAsync(d_flag, c->stream));
+        PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        if (flag) {
+            c->err = "build_collision: invalid list (flags " + std::to_string(flag) +
+                     ": 1 row range, 2 col range, 4 mode range, 8 rows not sorted)";
+            return PGB_EINVAL;
+        }
+    }
+    pgb_status st;
+    if ((st = dalloc(c, &c->d_eps_state, ns)) != PGB_OK) return st;
+    if ((st = dalloc(c, &c->d_rowptr, ns + 1)) != PGB_OK) return st;
+    if ((st = dalloc(c, &c->d_col, nnz)) != PGB_OK) return st;
+    if ((st = dalloc(c, &c->d_a, nnz)) != PGB_OK) return st;
+    if ((st = dalloc(c, &c->d_b, nnz)) != PGB_OK) return st;
+    if ((st = dalloc(c, &c->d_rowsum_a, ns)) != PGB_OK) return st;
+    for (int i = 0; i < 3; ++i)
+        if ((st = dalloc(c, &c->d_f[i], ns)) != PGB_OK) return st;
+
+    k_eps_state<<<div_up(ns, 256), 256, 0, c->stream>>>(ns, nb, c->band_lo, c->nw, c->d_eps, c->d_eps_state);
+    PGB_LAUNCH_CHECK(c);
+    if (nnz > 0) {
+        CoeffArgs p;
+        p.nnz = nnz;
+        p.row = row;
+        p.col = col;
+        p.mode = mode;
+        p.g2 = g2;
+        p.nb = nb;
+        p.band_lo = c->band_lo;
+        p.nw = c->nw;
+        p.nm = c->nm;
+        for (int d = 0; d < 3; ++d) p.kg[d] = c->kg[d];
+        p.eps = c->d_eps;
+        p.hw = c->d_hw;
+        p.T = T;
+        p.sigma = sigma;
+        p.scale = kTwoPiOverHbar / ((double)c->Nq * sigma * kSqrtPi);
+        p.out_col = c->d_col;
+        p.a = c->d_a;
+        p.b = c->d_b;
+        k_coll_coeffs<<<div_up(nnz, 256), 256, 0, c->stream>>>(p);
+        PGB_LAUNCH_CHECK(c);
+    }
+    k_rowptr<<<div_up(ns + 1, 256), 256, 0, c->stream>>>(ns, nnz, row, c->d_rowptr);
+    PGB_LAUNCH_CHECK(c);
+    k_rowsum<<<div_up(ns * 32, 256), 256, 0, c->stream>>>(ns, c->d_rowptr, c->d_a, c->d_rowsum_a);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// I_s = -f_s sum_e a_e + f_s sum_e f_c a_e + (1 - f_s) sum_e f_c b_e
+// (the bracket of Eq. e_ph_scattering expanded: -f_s(1-f_c) a + f_c(1-f_s) b).
+// One warp per row.  Entries stream as 16-byte vectors (4 entries per lane
+// per step) once the row is 16-byte aligned; products and 4-entry sums are
+// FP32, running sums and the row result FP64.  f_c is gathered from L2.
+// Stage -1 writes I; stages 0..3 fuse the RK4 combinations:
+//   0: acc = k1,  next = f + dt/2 k1      1: acc += 2 k2, next = f + dt/2 k2
+//   2: acc += 2 k3, next = f + dt k3      3: f = f + dt/6 (acc + k4)
+// ---------------------------------------------------------------------------
+struct CollArgs {
+    int64_t nstates;
+    const int64_t *rowptr;
+    const int32_t *col;
+    const float *a, *b;
+    const double *rowsum_a;
+    const double *fin;    // occupations the integral is evaluated at
+    const double *fbase;  // f at the start of the step
+    double *I;            // stage -1 output
+    double *acc;
+    double *fnext;
+    double dt;            // seconds
+    int stage;
+};
+
+__global__ void __launch_bounds__(256) k_collision(CollArgs p) {
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= p.nstates) return;
+    const int64_t beg = p.rowptr[s], end = p.rowptr[s + 1];
+    double sfa = 0.0, sfb = 0.0;
+    const double *__restrict__ fin = p.fin;
+    int64_t vbeg = (beg + 3) & ~(int64_t)3;
+    if (vbeg > end) vbeg = end;
+    const int64_t vend = vbeg + ((end - vbeg) & ~(int64_t)3);
+    // head (up to 3 entries) and tail (up to 3 entries)
+    {
+        int64_t e = -1;
+        if (lane < vbeg - beg)
+            e = beg + lane;
+        else if (lane >= 4 && lane - 4 < end - vend)
+            e = vend + (lane - 4);
+        if (e >= 0) {
+            const float fc = (float)fin[p.col[e]];
+            sfa += (double)(fc * p.a[e]);
+            sfb += (double)(fc * p.b[e]);
+        }
+    }
+    const int4 *col4 = reinterpret_cast<const int4 *>(p.col + vbeg);
+    const float4 *a4 = reinterpret_cast<const float4 *>(p.a + vbeg);
+    const float4 *b4 = reinterpret_cast<const float4 *>(p.b + vbeg);
+    const int64_t nv = (vend - vbeg) >> 2;
+    for (int64_t v = lane; v < nv; v += 32) {
+        const int4 cc = __ldcs(col4 + v);
+        const float4 aa = __ldcs(a4 + v);
+        const float4 bb = __ldcs(b4 + v);
+        const float f0 = (float)__ldg(fin + cc.x), f1 = (float)__ldg(fin + cc.y);
+        const float f2 = (float)__ldg(fin + cc.z), f3 = (float)__ldg(fin + cc.w);
+        const float pa = fmaf(f0, aa.x, fmaf(f1, aa.y, fmaf(f2, aa.z, f3 * aa.w)));
+        const float pb = fmaf(f0, bb.x, fmaf(f1, bb.y, fmaf(f2, bb.z, f3 * bb.w)));
+        sfa += (double)pa;
+        sfb += (double)pb;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sfa += __shfl_down_sync(0xffffffffu, sfa, o);
+        sfb += __shfl_down_sync(0xffffffffu, sfb, o);
+    }
+    if (lane == 0) {
+        const double fs = fin[s];
+        const double I = -fs * p.rowsum_a[s] + fs * sfa + (1.0 - fs) * sfb;
+        switch (p.stage) {
+            case -1:
+                p.I[s] = I;
+                break;
+            case 0:
+                p.acc[s] = I;
+                p.fnext[s] = p.fbase[s] + 0.5 * p.dt * I;
+                break;
+            case 1:
+                p.acc[s] += 2.0 * I;
+                p.fnext[s] = p.fbase[s] + 0.5 * p.dt * I;
+                break;
+            case 2:
+                p.acc[s] += 2.0 * I;
+                p.fnext[s] = p.fbase[s] + p.dt * I;
+                break;
+            default:
+                p.fnext[s] = p.fbase[s] + p.dt / 6.0 * (p.acc[s] + I);
+                break;
+        }
+    }
+}
+
+pgb_status launch_collision(pgb_ctx *c, const double *f, double *I, int stage, double dt, double *acc,
+                            double *fnext, const double *fbase) {
+    if (c->nstates == 0) return PGB_OK;
+    CollArgs p;
+    p.nstates = c->nstates;
+    p.rowptr = c->d_rowptr;
+    p.col = c->d_col;
+    p.a = c->d_a;
+    p.b = c->d_b;
+    p.rowsum_a = c->d_rowsum_a;
+    p.fin = f;
+    p.fbase = fbase;
+    p.I = I;
+    p.acc = acc;
+    p.fnext = fnext;
+    p.dt = dt;
+    p.stage = stage;
+    prof_mark(c, PGB_PROF_COLLISION);
+    k_collision<<<div_up(c->nstates * 32, 256), 256, 0, c->stream>>>(p);
+    prof_mark(c, PGB_PROF_COLLISION);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+}  // namespace pgb

@@ -1,0 +1,190 @@
+// Internal declarations shared by the translation units of libpertgb.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pertgb.h"
+
+// ---------------------------------------------------------------------------
+// physical constants (CODATA 2018)
+// ---------------------------------------------------------------------------
+namespace pgb {
+constexpr double kHbarEvS = 6.582119569e-16;     // eV s
+constexpr double kBoltzEvK = 8.617333262e-5;     // eV / K
+constexpr double kAmuKg = 1.66053906660e-27;     // kg
+constexpr double kBohrM = 0.529177210903e-10;    // m
+constexpr double kEvJ = 1.602176634e-19;         // J
+// (hbar w)^2 [eV^2] = kOmega2 * lambda for lambda in eV/(bohr^2 amu); the same
+// number divided by 2 M[amu] hbar w[eV] is the squared zero-point length in bohr^2.
+constexpr double kOmega2 = kHbarEvS * kHbarEvS * kEvJ / (kAmuKg * kBohrM * kBohrM);
+constexpr double kOmegaMinEv = 1e-4;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kSqrtPi = 1.77245385090551602730;
+constexpr double kTwoPiOverHbar = 2.0 * kPi / kHbarEvS;
+constexpr double kFemto = 1e-15;
+constexpr double kDeltaCut = 7.0;                // |x|/sigma beyond which a term is skipped
+constexpr int kMaxNw = 16;
+constexpr int kMaxNmode = 15;
+}  // namespace pgb
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct pgb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int64_t launches = 0;
+
+    // model
+    bool has_model = false;
+    int nw = 0, nat = 0, nm = 0;
+    int nRH = 0, nRD = 0, nRge = 0, nRgp = 0;
+    std::vector<double> mass;
+    int32_t *d_RH = nullptr, *d_RD = nullptr, *d_Rge = nullptr, *d_Rgp = nullptr;
+    double2 *d_H = nullptr;      // [nRH][nw*nw]
+    double2 *d_D = nullptr;      // [nRD][nm*nm] (imaginary part 0)
+    double *d_mode_scale = nullptr;  // [nm] 1/sqrt(M_kappa) per ka
+    double2 *d_g64 = nullptr;    // [nRge][nRgp*nm*nw*nw]
+    float2 *d_g32 = nullptr;
+
+    // grids
+    bool has_grids = false;
+    int kg[3] = {0, 0, 0}, qg[3] = {0, 0, 0};
+    int64_t Nk = 0, Nq = 0;
+    double *d_eps = nullptr;     // [Nk][nw]
+    double2 *d_U = nullptr;      // [Nk][nw][nw], U[i][n]
+    float2 *d_U32 = nullptr;
+    double *d_hw = nullptr;      // [Nq][nm]
+    double2 *d_coef = nullptr;   // [Nq][nm(nu)][nm(ka)] zero-point-scaled eigenvectors
+    float2 *d_coef32 = nullptr;
+    double2 *d_phq64 = nullptr;  // [Nq][nRgp] exp(i q.Rp), built on first use
+    float2 *d_phq32 = nullptr;
+
+    // collision list
+    bool has_coll = false;
+    int64_t nstates = 0, nnz = 0;
+    int band_lo = 0, band_hi = 0;
+    double *d_eps_state = nullptr;   // [nstates]
+    int64_t *d_rowptr = nullptr;     // [nstates+1]
+    int32_t *d_col = nullptr;        // [nnz]
+    float *d_a = nullptr, *d_b = nullptr;
+    double *d_rowsum_a = nullptr;    // [nstates]
+    double *d_f[4] = {nullptr, nullptr, nullptr, nullptr};  // RK4 stage buffers
+
+    // scratch (grown on demand, freed in destroy)
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+
+    // kernel timing with CUDA events on the context's stream (pgb_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_ev[PGB_PROF_NKERNELS];   // start, stop, start, stop, ...
+    double prof_ms[PGB_PROF_NKERNELS] = {0};
+    int64_t prof_n[PGB_PROF_NKERNELS] = {0};
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+#define PGB_CUDA_TRY(ctx, expr)                                                        \
+    do {                                                                               \
+        cudaError_t _e = (expr);                                                       \
+        if (_e != cudaSuccess) {                                                       \
+            (ctx)->err = std::string(#expr) + ": " + cudaGetErrorString(_e);           \
+            return _e == cudaErrorMemoryAllocation ? PGB_ENOMEM : PGB_ECUDA;           \
+        }                                                                              \
+    } while (0)
+
+#define PGB_LAUNCH_CHECK(ctx)                                                          \
+    do {                                                                               \
+        (ctx)->launches++;                                                             \
+        cudaError_t _e = cudaGetLastError();                                           \
+        if (_e != cudaSuccess) {                                                       \
+            (ctx)->err = std::string("kernel launch: ") + cudaGetErrorString(_e);      \
+            return PGB_ECUDA;                                                          \
+        }                                                                              \
+    } while (0)
+
+namespace pgb {
+
+pgb_status ensure_scratch(pgb_ctx *c, size_t bytes);
+// Bracket one launch of a timed kernel class with events (no-op unless enabled).
+void prof_mark(pgb_ctx *c, int id);
+template <typename T>
+pgb_status dalloc(pgb_ctx *c, T **p, size_t count) {
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    if (count == 0) return PGB_OK;
+    PGB_CUDA_TRY(c, cudaMalloc((void **)p, count * sizeof(T)));
+    return PGB_OK;
+}
+template <typename T>
+void dfree(T **p) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+}
+
+// interpolation kernels (interp.cu)
+pgb_status launch_phase_grid(pgb_ctx *c, const int grid[3], const int32_t *d_idx, int64_t npts,
+                             const int32_t *d_R, int nR, void *out, bool fp32);
+pgb_status launch_phase_pts(pgb_ctx *c, const double *d_pts, int64_t npts, const int32_t *d_R, int nR,
+                            void *out, bool fp32);
+pgb_status launch_cgemm(pgb_ctx *c, bool fp32, int64_t batch, int64_t M, int64_t N, int64_t K,
+                        const void *A, int64_t lda, int64_t strideA, const void *B, int64_t ldb,
+                        int64_t strideB, void *C, int64_t ldc, int64_t strideC);
+pgb_status launch_heevj(pgb_ctx *c, int64_t count, int n, double2 *d_mat, const double *d_scale,
+                        double *d_eval, double2 *d_evec);
+pgb_status launch_phonon_coef(pgb_ctx *c, int64_t nq, int nm, const double *d_eval,
+                              const double2 *d_evec, const double *d_mode_scale, double *d_hw,
+                              double2 *d_coef);
+pgb_status launch_to_f32(pgb_ctx *c, const double2 *src, float2 *dst, int64_t n);
+pgb_status launch_fold_u(pgb_ctx *c, bool fp32, int64_t nb, const int32_t *d_kidx, int nRgp, int nm,
+                         int nw, const void *S1, const void *U, void *G);
+struct RatesArgs {
+    int64_t nb;            // k points in this batch
+    const int32_t *kidx;   // [nb] k-grid indices (device)
+    int64_t Nq;
+    int kg[3], qg[3];
+    int nw, nm;
+    const void *C;         // [nb][Nq][nm*nw*nw] Wannier-gauge g with U(k) folded
+    const void *U;         // [Nk][nw][nw]
+    const void *coef;      // [Nq][nm][nm]
+    const double *eps;     // [Nk][nw]
+    const double *hw;      // [Nq][nm]
+    double T, mu, sigma;
+    double *partial;       // [nb][nqblk][nm][nw]
+    int64_t nqblk;
+    int qpb;               // q per block
+};
+pgb_status launch_rates_epilogue(pgb_ctx *c, bool fp32, const RatesArgs &a);
+pgb_status launch_rates_reduce(pgb_ctx *c, int64_t nb, int64_t nqblk, int nm, int nw, double scale,
+                               const double *partial, double *gamma, double *gamma_mode);
+struct GArgs {
+    int64_t nk, nq;
+    int nw, nm;
+    const void *C;         // [nk][nq][nm*nw*nw]
+    const void *Ukq;       // [nk*nq][nw][nw]
+    const void *coef;      // [nq][nm][nm]
+    int out_mode;
+    double *out;
+};
+pgb_status launch_g_epilogue(pgb_ctx *c, bool fp32, const GArgs &a);
+pgb_status launch_g_abs(pgb_ctx *c, int64_t npairs, int nm, int nw, const double *full, double *out);
+pgb_status launch_kplusq_pts(pgb_ctx *c, const double *d_k, int64_t nk, const double *d_q, int64_t nq,
+                             double *d_kq);
+pgb_status launch_window(pgb_ctx *c, const double *d_eps, int64_t Nk, int nw, double lo, double hi,
+                         int32_t *d_flag);
+
+// collision kernels (collision.cu)
+pgb_status launch_coll_coeffs(pgb_ctx *c, double T, double sigma, const int32_t *row, const int32_t *col,
+                              const int32_t *mode, const float *g2, int64_t nnz, int nb);
+pgb_status launch_collision(pgb_ctx *c, const double *f, double *I, int stage, double dt, double *acc,
+                            double *fnext, const double *fbase);
+
+}  // namespace pgb

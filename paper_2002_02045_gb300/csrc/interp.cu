@@ -1,0 +1,591 @@
+// Wannier interpolation kernels: Fourier phases, batched complex GEMM (SIMT),
+// Hermitian eigensolves, mode coefficients, U(k) fold, and the fused
+// rotation / mode projection / |g|^2 / scattering-rate epilogue.
+#include <cstdio>
+
+#include "cplx.cuh"
+#include "heevj.cuh"
+#include "internal.cuh"
+
+namespace pgb {
+
+static inline unsigned int div_up(int64_t a, int64_t b) { return (unsigned int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// Fourier phases exp(2 pi i k.R)
+// ---------------------------------------------------------------------------
+
+// Grid points (i1/n1, i2/n2, i3/n3): the argument is formed from the exact
+// integer residues (i_d R_d mod n_d), so it carries no accumulated rounding.
+template <typename T2>
+__global__ void k_phase_grid(int n1, int n2, int n3, const int32_t *__restrict__ idx, int64_t npts,
+                             const int32_t *__restrict__ R, int nR, T2 *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npts * nR) return;
+    const int64_t p = t / nR;
+    const int r = (int)(t % nR);
+    const int64_t pid = idx ? (int64_t)idx[p] : p;
+    const int i3 = (int)(pid % n3);
+    const int i2 = (int)((pid / n3) % n2);
+    const int i1 = (int)(pid / ((int64_t)n2 * n3));
+    int t1 = (int)(((int64_t)i1 * R[3 * r + 0]) % n1);
+    int t2 = (int)(((int64_t)i2 * R[3 * r + 1]) % n2);
+    int t3 = (int)(((int64_t)i3 * R[3 * r + 2]) % n3);
+    if (t1 < 0) t1 += n1;
+    if (t2 < 0) t2 += n2;
+    if (t3 < 0) t3 += n3;
+    double x = (double)t1 / n1 + (double)t2 / n2 + (double)t3 / n3;
+    x -= rint(x);
+    double s, c;
+    sincospi(2.0 * x, &s, &c);
+    T2 v;
+    v.x = c;
+    v.y = s;
+    out[t] = v;
+}
+
+template <typename T2>
+__global__ void k_phase_pts(const double *__restrict__ pts, int64_t npts, const int32_t *__restrict__ R,
+                            int nR, T2 *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npts * nR) return;
+    const int64_t p = t / nR;
+    const int r = (int)(t % nR);
+    double x = pts[3 * p + 0] * R[3 * r + 0] + pts[3 * p + 1] * R[3 * r + 1] + pts[3 * p + 2] * R[3 * r + 2];
+    x -= rint(x);
+    double s, c;
+    sincospi(2.0 * x, &s, &c);
+    T2 v;
+    v.x = c;
+    v.y = s;
+    out[t] = v;
+}
+
+pgb_status launch_phase_grid(pgb_ctx *c, const int grid[3], const int32_t *d_idx, int64_t npts,
+                             const int32_t *d_R, int nR, void *out, bool fp32) {
+    const int64_t n = npts * nR;
+    if (n == 0) return PGB_OK;
+    if (fp32)
+        k_phase_grid<float2><<<div_up(n, 256), 256, 0, c->stream>>>(grid[0], grid[1], grid[2], d_idx, npts, d_R,
+                                                                     nR, (float2 *)out);
+    else
+        k_phase_grid<double2><<<div_up(n, 256), 256, 0, c->stream>>>(grid[0], grid[1], grid[2], d_idx, npts,
+                                                                      d_R, nR, (double2 *)out);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+pgb_status launch_phase_pts(pgb_ctx *c, const double *d_pts, int64_t npts, const int32_t *d_R, int nR,
+                            void *out, bool fp32) {
+    const int64_t n = npts * nR;
+    if (n == 0) return PGB_OK;
+    if (fp32)
+        k_phase_pts<float2><<<div_up(n, 256), 256, 0, c->stream>>>(d_pts, npts, d_R, nR, (float2 *)out);
+    else
+        k_phase_pts<double2><<<div_up(n, 256), 256, 0, c->stream>>>(d_pts, npts, d_R, nR, (double2 *)out);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched complex GEMM (SIMT): C[b] = A[b] * B[b], row-major, interleaved.
+// 64x64 complex tile per 256-thread block, 4x4 complex outputs per thread,
+// k-slices of 8 staged in shared memory.  Used for the H(k), D(q) sums and
+// for both Fourier steps of g in the FP64 and plain FP32 forms.
+// ---------------------------------------------------------------------------
+constexpr int GBM = 64, GBN = 64, GBK = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgemm(int64_t M, int64_t N, int64_t K, const V2<T> *__restrict__ A,
+                                               int64_t lda, int64_t sA, const V2<T> *__restrict__ B, int64_t ldb,
+                                               int64_t sB, V2<T> *__restrict__ C, int64_t ldc, int64_t sC) {
+    using T2 = V2<T>;
+    __shared__ T2 As[GBK][GBM];
+    __shared__ T2 Bs[GBK][GBN];
+    const int64_t b = blockIdx.z;
+    A += b * sA;
+    B += b * sB;
+    C += b * sC;
+    const int64_t m0 = (int64_t)blockIdx.y * GBM;
+    const int64_t n0 = (int64_t)blockIdx.x * GBN;
+    const int t = threadIdx.x;
+    const int tx = t % 16, ty = t / 16;
+    T2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = cmake<T>(0, 0);
+    const T2 zero = cmake<T>(0, 0);
+    for (int64_t k0 = 0; k0 < K; k0 += GBK) {
+#pragma unroll
+        for (int e = t; e < GBM * GBK; e += 256) {
+            const int r = e / GBK, kk = e % GBK;
+            const int64_t gm = m0 + r, gk = k0 + kk;
+            As[kk][r] = (gm < M && gk < K) ? A[gm * lda + gk] : zero;
+        }
+#pragma unroll
+        for (int e = t; e < GBN * GBK; e += 256) {
+            const int kk = e / GBN, cc = e % GBN;
+            const int64_t gk = k0 + kk, gn = n0 + cc;
+            Bs[kk][cc] = (gk < K && gn < N) ? B[gk * ldb + gn] : zero;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; ++kk) {
+            T2 a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], bb[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t gm = m0 + ty + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t gn = n0 + tx + 16 * j;
+            if (gn < N) C[gm * ldc + gn] = acc[i][j];
+        }
+    }
+}
+
+pgb_status launch_cgemm(pgb_ctx *c, bool fp32, int64_t batch, int64_t M, int64_t N, int64_t K, const void *A,
+                        int64_t lda, int64_t strideA, const void *B, int64_t ldb, int64_t strideB, void *C,
+                        int64_t ldc, int64_t strideC) {
+    if (batch == 0 || M == 0 || N == 0) return PGB_OK;
+    if (div_up(M, GBM) > 65535u || batch > 65535) {
+        c->err = "cgemm: grid too large";
+        return PGB_EINVAL;
+    }
+    dim3 grid(div_up(N, GBN), div_up(M, GBM), (unsigned int)batch);
+    if (fp32)
+        k_cgemm<float><<<grid, 256, 0, c->stream>>>(M, N, K, (const float2 *)A, lda, strideA, (const float2 *)B,
+                                                     ldb, strideB, (float2 *)C, ldc, strideC);
+    else
+        k_cgemm<double><<<grid, 256, 0, c->stream>>>(M, N, K, (const double2 *)A, lda, strideA,
+                                                      (const double2 *)B, ldb, strideB, (double2 *)C, ldc,
+                                                      strideC);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Hermitian eigensolves, one matrix per thread (FP64).
+// scale (optional) multiplies entry (r, c) by scale[r] scale[c] first: with
+// scale = 1/sqrt(M_kappa) this forms the mass-scaled dynamical matrix.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void k_heevj(int64_t count, const double2 *__restrict__ mat, const double *__restrict__ scale,
+                        double *__restrict__ eval, double2 *__restrict__ evec) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    double2 A[N][N], V[N][N];
+    double w[N];
+    const double2 *m = mat + i * N * N;
+    for (int r = 0; r < N; ++r)
+        for (int cc = 0; cc < N; ++cc) {
+            double2 v = m[r * N + cc];
+            if (scale) {
+                const double s = scale[r] * scale[cc];
+                v.x *= s;
+                v.y *= s;
+            }
+            A[r][cc] = v;
+        }
+    // enforce exact Hermiticity of the input (average with the adjoint)
+    for (int r = 0; r < N; ++r) {
+        A[r][r].y = 0.0;
+        for (int cc = r + 1; cc < N; ++cc) {
+            const double2 u = A[r][cc], l = A[cc][r];
+            const double2 h = make_double2(0.5 * (u.x + l.x), 0.5 * (u.y - l.y));
+            A[r][cc] = h;
+            A[cc][r] = make_double2(h.x, -h.y);
+        }
+    }
+    heevj_one<N>(A, V, w);
+    for (int r = 0; r < N; ++r) eval[i * N + r] = w[r];
+    for (int r = 0; r < N; ++r)
+        for (int cc = 0; cc < N; ++cc) evec[i * N * N + r * N + cc] = V[r][cc];
+}
+
+pgb_status launch_heevj(pgb_ctx *c, int64_t count, int n, double2 *d_mat, const double *d_scale,
+                        double *d_eval, double2 *d_evec) {
+    if (count == 0) return PGB_OK;
+    const unsigned int g = div_up(count, 64);
+#define PGB_HEEVJ_CASE(NN)                                                                         \
+    case NN:                                                                                       \
+        k_heevj<NN><<<g, 64, 0, c->stream>>>(count, d_mat, d_scale, d_eval, d_evec);              \
+        break;
+    switch (n) {
+        PGB_HEEVJ_CASE(1)
+        PGB_HEEVJ_CASE(2)
+        PGB_HEEVJ_CASE(3)
+        PGB_HEEVJ_CASE(4)
+        PGB_HEEVJ_CASE(5)
+        PGB_HEEVJ_CASE(6)
+        PGB_HEEVJ_CASE(7)
+        PGB_HEEVJ_CASE(8)
+        PGB_HEEVJ_CASE(9)
+        PGB_HEEVJ_CASE(10)
+        PGB_HEEVJ_CASE(11)
+        PGB_HEEVJ_CASE(12)
+        PGB_HEEVJ_CASE(13)
+        PGB_HEEVJ_CASE(14)
+        PGB_HEEVJ_CASE(15)
+        PGB_HEEVJ_CASE(16)
+        default:
+            c->err = "eigensolver: matrix size must be 1..16";
+            return PGB_EINVAL;
+    }
+#undef PGB_HEEVJ_CASE
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Mode coefficients of Eq. eph_mat:
+//   coef[q][nu][ka] = e^{ka}_nu(q) / sqrt(M_kappa) * sqrt(hbar / (2 omega_nu q))   (bohr)
+// hbar*omega = sqrt(kOmega2 * max(lambda, 0)); modes below kOmegaMinEv get 0.
+// ---------------------------------------------------------------------------
+__global__ void k_phonon_coef(int64_t nq, int nm, const double *__restrict__ eval,
+                              const double2 *__restrict__ evec, const double *__restrict__ mode_scale,
+                              double *__restrict__ hw, double2 *__restrict__ coef) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nq * nm) return;
+    const int64_t q = t / nm;
+    const int nu = (int)(t % nm);
+    const double lam = eval[t];
+    const double w = sqrt(kOmega2 * fmax(lam, 0.0));
+    hw[t] = w;
+    const double len = (w >= kOmegaMinEv) ? sqrt(kOmega2 / (2.0 * w)) : 0.0;
+    for (int ka = 0; ka < nm; ++ka) {
+        const double2 e = evec[q * nm * nm + ka * nm + nu];
+        const double s = len * mode_scale[ka];
+        coef[(q * nm + nu) * nm + ka] = make_double2(e.x * s, e.y * s);
+    }
+}
+
+pgb_status launch_phonon_coef(pgb_ctx *c, int64_t nq, int nm, const double *d_eval, const double2 *d_evec,
+                              const double *d_mode_scale, double *d_hw, double2 *d_coef) {
+    if (nq == 0) return PGB_OK;
+    k_phonon_coef<<<div_up(nq * nm, 128), 128, 0, c->stream>>>(nq, nm, d_eval, d_evec, d_mode_scale, d_hw,
+                                                                d_coef);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+__global__ void k_to_f32(const double2 *__restrict__ s, float2 *__restrict__ d, int64_t n) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) d[t] = make_float2((float)s[t].x, (float)s[t].y);
+}
+
+pgb_status launch_to_f32(pgb_ctx *c, const double2 *src, float2 *dst, int64_t n) {
+    if (n == 0) return PGB_OK;
+    k_to_f32<<<div_up(n, 256), 256, 0, c->stream>>>(src, dst, n);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Fold U(k) into the Re-sum (right factor of the rotation in Eq. eph_mat_wann2):
+//   G[b][rp][ka][i][n] = sum_j S1[b][rp][ka][i][j] U_jn(k_b)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_fold_u(int64_t nb, const int32_t *__restrict__ kidx, int nRgp, int nm, int nw,
+                         const V2<T> *__restrict__ S1, const V2<T> *__restrict__ U, V2<T> *__restrict__ G) {
+    const int64_t per = (int64_t)nRgp * nm * nw * nw;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb * per) return;
+    const int64_t b = t / per;
+    const int64_t r = t % per;
+    const int n = (int)(r % nw);
+    const int64_t row = r / nw;           // (rp, ka, i)
+    const int64_t k = kidx ? (int64_t)kidx[b] : b;
+    const V2<T> *s = S1 + b * per + row * nw;
+    const V2<T> *u = U + k * nw * nw;
+    V2<T> acc = cmake<T>(0, 0);
+    for (int j = 0; j < nw; ++j) cfma(acc, s[j], u[j * nw + n]);
+    G[t] = acc;
+}
+
+pgb_status launch_fold_u(pgb_ctx *c, bool fp32, int64_t nb, const int32_t *d_kidx, int nRgp, int nm, int nw,
+                         const void *S1, const void *U, void *G) {
+    const int64_t n = nb * (int64_t)nRgp * nm * nw * nw;
+    if (n == 0) return PGB_OK;
+    if (fp32)
+        k_fold_u<float><<<div_up(n, 256), 256, 0, c->stream>>>(nb, d_kidx, nRgp, nm, nw, (const float2 *)S1,
+                                                               (const float2 *)U, (float2 *)G);
+    else
+        k_fold_u<double><<<div_up(n, 256), 256, 0, c->stream>>>(nb, d_kidx, nRgp, nm, nw, (const double2 *)S1,
+                                                                (const double2 *)U, (double2 *)G);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Rates epilogue (Eqs. eph_mat, scatter_rate, BTE_W), one thread per
+// (q, nu, n) of one k:
+//   G^nu_i  = sum_ka coef[q][nu][ka] C[b][q][ka][i][n]          (mode projection)
+//   g_mn nu = sum_i conj(U_im(k+q)) G^nu_i                        (left rotation)
+//   acc    += |g|^2 [ e^{-(x_em/s)^2} (1 + N - f_m) + e^{-(x_abs/s)^2} (N + f_m) ]
+// with x_em = e_n(k) - hw - e_m(k+q), x_abs = e_n(k) + hw - e_m(k+q).  Terms
+// with |x|/s > kDeltaCut are skipped before the rotation is formed.  The
+// energies, occupations and Gaussian factors are FP64; the block sums over
+// its q in a fixed order and writes one partial per (nu, n).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t kplusq_index(int64_t k, int64_t q, const int kg[3], const int qg[3]) {
+    const int k3 = (int)(k % kg[2]), k2 = (int)((k / kg[2]) % kg[1]), k1 = (int)(k / ((int64_t)kg[1] * kg[2]));
+    const int q3 = (int)(q % qg[2]), q2 = (int)((q / qg[2]) % qg[1]), q1 = (int)(q / ((int64_t)qg[1] * qg[2]));
+    const int s1 = (k1 + q1 * (kg[0] / qg[0])) % kg[0];
+    const int s2 = (k2 + q2 * (kg[1] / qg[1])) % kg[1];
+    const int s3 = (k3 + q3 * (kg[2] / qg[2])) % kg[2];
+    return ((int64_t)s1 * kg[1] + s2) * kg[2] + s3;
+}
+
+template <typename T>
+__global__ void k_rates_epilogue(RatesArgs a) {
+    using T2 = V2<T>;
+    extern __shared__ double red[];
+    const int per = a.nm * a.nw;
+    const int t = threadIdx.x;
+    const int ql = t / per;
+    const int r = t % per;
+    const int nu = r / a.nw;
+    const int n = r % a.nw;
+    const int64_t b = blockIdx.y;
+    const int64_t q = (int64_t)blockIdx.x * a.qpb + ql;
+    double acc = 0.0;
+    if (ql < a.qpb && q < a.Nq) {
+        const int64_t k = a.kidx[b];
+        const int64_t kq = kplusq_index(k, q, a.kg, a.qg);
+        const int ncol = per * a.nw;
+        const double w = a.hw[q * a.nm + nu];
+        if (w >= kOmegaMinEv) {
+            const T2 *Cq = (const T2 *)a.C + ((int64_t)b * a.Nq + q) * ncol;
+            const T2 *cf = (const T2 *)a.coef + (q * a.nm + nu) * a.nm;
+            T2 gv[kMaxNw];
+#pragma unroll
+            for (int i = 0; i < kMaxNw; ++i) gv[i] = cmake<T>(0, 0);
+            for (int ka = 0; ka < a.nm; ++ka) {
+                const T2 cc = cf[ka];
+#pragma unroll
+                for (int i = 0; i < kMaxNw; ++i)
+                    if (i < a.nw) cfma(gv[i], cc, Cq[(ka * a.nw + i) * a.nw + n]);
+            }
+            const double kT = kBoltzEvK * a.T;
+            const double N = 1.0 / expm1(w / kT);
+            const double en = a.eps[k * a.nw + n];
+            const double cut = kDeltaCut * a.sigma;
+            const double is = 1.0 / a.sigma;
+            const T2 *Ukq = (const T2 *)a.U + kq * a.nw * a.nw;
+            for (int m = 0; m < a.nw; ++m) {
+                const double em = a.eps[kq * a.nw + m];
+                const double xe = en - w - em, xa = en + w - em;
+                const bool le = fabs(xe) <= cut, la = fabs(xa) <= cut;
+                if (!(le || la)) continue;
+                T2 g = cmake<T>(0, 0);
+#pragma unroll
+                for (int i = 0; i < kMaxNw; ++i)
+                    if (i < a.nw) cfma_conj(g, Ukq[i * a.nw + m], gv[i]);
+                const double g2 = (double)cabs2(g);
+                const double fm = 1.0 / (exp((em - a.mu) / kT) + 1.0);
+                double W = 0.0;
+                if (le) W += exp(-(xe * is) * (xe * is)) * (1.0 + N - fm);
+                if (la) W += exp(-(xa * is) * (xa * is)) * (N + fm);
+                acc += g2 * W;
+            }
+        }
+    }
+    red[t] = acc;
+    __syncthreads();
+    if (ql == 0 && t < per) {
+        double s = 0.0;
+        for (int l = 0; l < a.qpb; ++l) s += red[l * per + r];
+        a.partial[((int64_t)b * a.nqblk + blockIdx.x) * per + r] = s;
+    }
+}
+
+pgb_status launch_rates_epilogue(pgb_ctx *c, bool fp32, const RatesArgs &a) {
+    const int per = a.nm * a.nw;
+    const int threads = a.qpb * per;
+    dim3 grid((unsigned int)a.nqblk, (unsigned int)a.nb);
+    const size_t sh = (size_t)threads * sizeof(double);
+    if (fp32)
+        k_rates_epilogue<float><<<grid, threads, sh, c->stream>>>(a);
+    else
+        k_rates_epilogue<double><<<grid, threads, sh, c->stream>>>(a);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+// gamma_mode[b][nu][n] = scale * sum_blk partial[b][blk][nu][n]; gamma[b][n] = sum_nu
+__global__ void k_rates_reduce(int64_t nb, int64_t nqblk, int nm, int nw, double scale,
+                               const double *__restrict__ partial, double *__restrict__ gamma,
+                               double *__restrict__ gamma_mode) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb * nw) return;
+    const int64_t b = t / nw;
+    const int n = (int)(t % nw);
+    const int per = nm * nw;
+    double tot = 0.0;
+    for (int nu = 0; nu < nm; ++nu) {
+        double s = 0.0;
+        for (int64_t blk = 0; blk < nqblk; ++blk) s += partial[(b * nqblk + blk) * per + nu * nw + n];
+        s *= scale;
+        if (gamma_mode) gamma_mode[(b * nm + nu) * nw + n] = s;
+        tot += s;
+    }
+    gamma[b * nw + n] = tot;
+}
+
+pgb_status launch_rates_reduce(pgb_ctx *c, int64_t nb, int64_t nqblk, int nm, int nw, double scale,
+                               const double *partial, double *gamma, double *gamma_mode) {
+    if (nb == 0) return PGB_OK;
+    k_rates_reduce<<<div_up(nb * nw, 128), 128, 0, c->stream>>>(nb, nqblk, nm, nw, scale, partial, gamma,
+                                                                  gamma_mode);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// |g|^2 output for arbitrary (k, q) lists (Eqs. eph_mat_wann2, eph_mat, g_abs).
+// One thread per (k, q, nu, n); writes |g_mn nu|^2 for every m.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_g_epilogue(GArgs a) {
+    using T2 = V2<T>;
+    const int per = a.nm * a.nw;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.nk * a.nq * per) return;
+    const int64_t pair = t / per;     // k * nq + q
+    const int r = (int)(t % per);
+    const int nu = r / a.nw, n = r % a.nw;
+    const int64_t q = pair % a.nq;
+    const int ncol = per * a.nw;
+    const T2 *Cq = (const T2 *)a.C + pair * ncol;
+    const T2 *cf = (const T2 *)a.coef + (q * a.nm + nu) * a.nm;
+    T2 gv[kMaxNw];
+#pragma unroll
+    for (int i = 0; i < kMaxNw; ++i) gv[i] = cmake<T>(0, 0);
+    for (int ka = 0; ka < a.nm; ++ka) {
+        const T2 cc = cf[ka];
+#pragma unroll
+        for (int i = 0; i < kMaxNw; ++i)
+            if (i < a.nw) cfma(gv[i], cc, Cq[(ka * a.nw + i) * a.nw + n]);
+    }
+    const T2 *U = (const T2 *)a.Ukq + pair * a.nw * a.nw;
+    for (int m = 0; m < a.nw; ++m) {
+        T2 g = cmake<T>(0, 0);
+#pragma unroll
+        for (int i = 0; i < kMaxNw; ++i)
+            if (i < a.nw) cfma_conj(g, U[i * a.nw + m], gv[i]);
+        a.out[((pair * a.nm + nu) * a.nw + m) * a.nw + n] = (double)cabs2(g);
+    }
+}
+
+__global__ void k_g_abs(int64_t npairs, int nm, int nw, const double *__restrict__ full, double *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npairs * nm) return;
+    double s = 0.0;
+    const double *f = full + t * nw * nw;
+    for (int e = 0; e < nw * nw; ++e) s += f[e];
+    out[t] = sqrt(s / nw);
+}
+
+pgb_status launch_g_epilogue(pgb_ctx *c, bool fp32, const GArgs &a) {
+    const int64_t n = a.nk * a.nq * a.nm * a.nw;
+    if (n == 0) return PGB_OK;
+    if (fp32)
+        k_g_epilogue<float><<<div_up(n, 128), 128, 0, c->stream>>>(a);
+    else
+        k_g_epilogue<double><<<div_up(n, 128), 128, 0, c->stream>>>(a);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+pgb_status launch_g_abs(pgb_ctx *c, int64_t npairs, int nm, int nw, const double *full, double *out) {
+    if (npairs == 0) return PGB_OK;
+    k_g_abs<<<div_up(npairs * nm, 128), 128, 0, c->stream>>>(npairs, nm, nw, full, out);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+__global__ void k_kplusq_pts(const double *__restrict__ k, int64_t nk, const double *__restrict__ q, int64_t nq,
+                             double *__restrict__ kq) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nk * nq) return;
+    const int64_t a = t / nq, b = t % nq;
+    for (int d = 0; d < 3; ++d) kq[3 * t + d] = k[3 * a + d] + q[3 * b + d];
+}
+
+pgb_status launch_kplusq_pts(pgb_ctx *c, const double *d_k, int64_t nk, const double *d_q, int64_t nq,
+                             double *d_kq) {
+    if (nk * nq == 0) return PGB_OK;
+    k_kplusq_pts<<<div_up(nk * nq, 256), 256, 0, c->stream>>>(d_k, nk, d_q, nq, d_kq);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+__global__ void k_window(const double *__restrict__ eps, int64_t Nk, int nw, double lo, double hi,
+                         int32_t *__restrict__ flag) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nk) return;
+    int f = 0;
+    for (int n = 0; n < nw; ++n) {
+        const double e = eps[k * nw + n];
+        f |= (e >= lo && e <= hi);
+    }
+    flag[k] = f;
+}
+
+pgb_status launch_window(pgb_ctx *c, const double *d_eps, int64_t Nk, int nw, double lo, double hi,
+                         int32_t *d_flag) {
+    if (Nk == 0) return PGB_OK;
+    k_window<<<div_up(Nk, 256), 256, 0, c->stream>>>(d_eps, Nk, nw, lo, hi, d_flag);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+}  // namespace pgb
+
+// Host-side self test of the eigensolver (the same template the kernels run),
+// so that its arithmetic can be checked without a GPU.
+extern "C" int pgb_selftest_heevj(int n, int count, const double *mat, double *eval, double *evec) {
+    using namespace pgb;
+#define PGB_HOST_CASE(NN)                                                        \
+    case NN:                                                                     \
+        for (int i = 0; i < count; ++i) {                                        \
+            double2 A[NN][NN], V[NN][NN];                                        \
+            double w[NN];                                                        \
+            for (int r = 0; r < NN; ++r)                                         \
+                for (int cc = 0; cc < NN; ++cc)                                  \
+                    A[r][cc] = make_double2(mat[2 * ((i * NN + r) * NN + cc)],   \
+                                            mat[2 * ((i * NN + r) * NN + cc) + 1]); \
+            heevj_one<NN>(A, V, w);                                              \
+            for (int r = 0; r < NN; ++r) eval[i * NN + r] = w[r];                \
+            for (int r = 0; r < NN; ++r)                                         \
+                for (int cc = 0; cc < NN; ++cc) {                                \
+                    evec[2 * ((i * NN + r) * NN + cc)] = V[r][cc].x;             \
+                    evec[2 * ((i * NN + r) * NN + cc) + 1] = V[r][cc].y;         \
+                }                                                                \
+        }                                                                        \
+        return 0;
+    switch (n) {
+        PGB_HOST_CASE(1)
+        PGB_HOST_CASE(2)
+        PGB_HOST_CASE(3)
+        PGB_HOST_CASE(6)
+        PGB_HOST_CASE(8)
+        PGB_HOST_CASE(16)
+        default:
+            return -1;
+    }
+#undef PGB_HOST_CASE
+}

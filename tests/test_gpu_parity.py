@@ -1,0 +1,312 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (design notes): FP64 path 1e-10 relative; FP32 path 1e-5 on |g|^2
+(per element with a 1e-3 block floor, plus normwise) and on Gamma (per state
+with a 1e-6 max floor).  Per-element |g|^2 is compared only where it is
+gauge invariant: degenerate phonon modes (all three modes of the
+simple-cubic model) are summed first.
+"""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import eph as O
+
+from helpers import assert_close_blocks, assert_rates_close, degenerate_sum
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_02045_gb300 import build
+    build.build()
+    from paper_2002_02045_gb300 import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def c2():
+    return S.model_c2()
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x)).cuda()
+
+
+def empty(shape, dtype=torch.float64):
+    return torch.empty(shape, dtype=dtype, device="cuda")
+
+
+# ----------------------------------------------------------------------------
+# bands and phonons (Eqs. wannier_3, IFC2)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which,grid", [("c1", (6, 6, 6)), ("c2", (12, 12, 12)), ("c2", (5, 7, 3))])
+def test_grid_bands_phonons(ctx, c1, c2, which, grid):
+    m = c1 if which == "c1" else c2
+    ctx.pgb_set_model(m)
+    ctx.pgb_set_grids(grid, grid)
+    n = int(np.prod(grid))
+    eps = empty((n, m.nw))
+    hw = empty((n, m.nmode))
+    ctx.pgb_get_grid_energies(eps, hw)
+    pts = S.mp_grid(*grid)
+    e_ref, _ = O.bands(m, pts)
+    w_ref, _ = O.phonons(m, pts)
+    assert np.abs(eps.cpu().numpy() - e_ref).max() < 1e-11
+    assert np.abs(hw.cpu().numpy() - w_ref).max() < 1e-9
+
+
+# ----------------------------------------------------------------------------
+# |g|^2 at arbitrary points (Eqs. eph_mat_wann2, eph_mat, g_abs)
+# ----------------------------------------------------------------------------
+
+def oracle_g2(m, k, q):
+    ek, Uk = O.bands(m, k)
+    hw, e = O.phonons(m, q)
+    out = np.zeros((len(k), len(q), m.nmode, m.nw, m.nw))
+    for a in range(len(k)):
+        ekq, Ukq = O.bands(m, k[a:a + 1] + q)
+        gw = O.g_wannier(m, k[a:a + 1], q)[0]
+        gb = O.g_bloch(gw, Uk[a][None], Ukq)
+        out[a] = np.abs(O.g_modes(gb, hw, e, m.mass)) ** 2
+    return out, hw
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_interpolate_g_c1(ctx, c1, prec):
+    from paper_2002_02045_gb300 import PGB_G2_FULL, PGB_G_ABS, PRECISIONS
+    rng = np.random.default_rng(1)
+    k = rng.uniform(-1, 1, (3, 3))
+    q = rng.uniform(-1, 1, (5, 3))
+    ctx.pgb_set_model(c1)
+    out = empty((3, 5, 3, 2, 2))
+    ctx.pgb_interpolate_g(dev(k), dev(q), PRECISIONS[prec], PGB_G2_FULL, out)
+    ref, hw = oracle_g2(c1, k, q)
+    got = out.cpu().numpy()
+    # the three modes are degenerate everywhere: compare mode sums per (m, n)
+    assert_close_blocks(got.sum(2), ref.sum(2), TOL[prec], block_axes=(2, 3), label="c1 g2")
+    # Eq. g_abs output, host buffers in and out
+    ga = np.zeros((3, 5, 3))
+    ctx.pgb_interpolate_g(k, q, PRECISIONS[prec], PGB_G_ABS, ga)
+    assert_close_blocks((ga ** 2).sum(2) * 2, ref.sum((2, 3, 4)), TOL[prec], block_axes=(1,), label="g_abs")
+
+
+def test_interpolate_g_c2_fp32(ctx, c2):
+    from paper_2002_02045_gb300 import PGB_G2_FULL, PGB_FP32
+    rng = np.random.default_rng(2)
+    k = rng.uniform(-0.5, 0.5, (2, 3))
+    q = rng.uniform(-0.5, 0.5, (7, 3))
+    ctx.pgb_set_model(c2)
+    out = empty((2, 7, 6, 8, 8))
+    ctx.pgb_interpolate_g(dev(k), dev(q), PGB_FP32, PGB_G2_FULL, out)
+    ref, hw = oracle_g2(c2, k, q)
+    got = out.cpu().numpy()
+    # generic points: modes and bands non-degenerate, every element is gauge invariant
+    hwb = np.broadcast_to(hw[None], (2, 7, 6))
+    assert_close_blocks(degenerate_sum(got, hwb, 2), degenerate_sum(ref, hwb, 2), 1e-5,
+                        block_axes=(2, 3, 4), label="c2 g2")
+
+
+# ----------------------------------------------------------------------------
+# scattering rates (Eqs. scatter_rate, BTE_W)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_rates_c1_full(ctx, c1, prec):
+    from paper_2002_02045_gb300 import PRECISIONS
+    T, mu, sig = 300.0, 0.5, 0.005
+    ctx.pgb_set_model(c1)
+    ctx.pgb_set_grids((6, 6, 6), (6, 6, 6))
+    kidx = np.arange(216, dtype=np.int32)
+    gam = empty((216, 2))
+    gmode = empty((216, 3, 2))
+    ctx.pgb_scattering_rates(dev(kidx), T, mu, sig, PRECISIONS[prec], gam, gmode)
+    ref = O.scattering_rates_grid(c1, (6, 6, 6), (6, 6, 6), kidx, T, mu, sig)
+    g = gam.cpu().numpy()
+    assert_rates_close(g, ref, TOL[prec], label=f"c1 gamma {prec}")
+    assert np.allclose(gmode.cpu().numpy().sum(1), g, rtol=1e-13)
+    assert np.all(g >= 0)
+
+
+def test_rates_c1_ragged_and_host_buffers(ctx, c1):
+    # a k list that is not a multiple of anything, with repeats, on host memory
+    from paper_2002_02045_gb300 import PGB_FP64
+    T, mu, sig = 250.0, 0.3, 0.01
+    ctx.pgb_set_model(c1)
+    ctx.pgb_set_grids((6, 6, 6), (3, 3, 3))
+    kidx = np.array([215, 0, 17, 17, 100], dtype=np.int32)
+    gam = np.zeros((5, 2))
+    ctx.pgb_scattering_rates(kidx, T, mu, sig, PGB_FP64, gam)
+    ref = O.scattering_rates_grid(c1, (6, 6, 6), (3, 3, 3), kidx, T, mu, sig)
+    assert_rates_close(gam, ref, 1e-10, label="c1 coarse q")
+
+
+def test_rates_c2_reduced_fp32(ctx, c2):
+    from paper_2002_02045_gb300 import PGB_FP32
+    T, sig = 300.0, 0.010
+    kg, qg = (20, 20, 20), (10, 10, 10)
+    ctx.pgb_set_model(c2)
+    ctx.pgb_set_grids(kg, qg)
+    eps = empty((8000, 8))
+    ctx.pgb_get_grid_energies(eps, None)
+    e_ref, _ = O.bands(c2, S.mp_grid(*kg))
+    emin = e_ref.min()
+    mu = emin - 0.3
+    win = np.nonzero(((e_ref >= emin) & (e_ref <= emin + 0.3)).any(1))[0].astype(np.int32)
+    kbuf = empty((8000,), torch.int32)
+    n = ctx.pgb_window(emin, emin + 0.3, kbuf)
+    assert n == len(win) and np.array_equal(kbuf[:n].cpu().numpy(), win)
+    sample = win[:: max(1, len(win) // 7)][:7]
+    gam = empty((len(sample), 8))
+    ctx.pgb_scattering_rates(dev(sample), T, mu, sig, PGB_FP32, gam)
+    ref = O.scattering_rates_grid(c2, kg, qg, sample, T, mu, sig)
+    assert_rates_close(gam.cpu().numpy(), ref, 1e-5, label="c2 reduced")
+
+
+@pytest.mark.slow
+def test_rates_c2_full_size_sampled(ctx, c2):
+    """Full 40^3 x 40^3 workload over the whole 0.3 eV window, as the bench runs
+    it; three window k-points are recomputed by the oracle and compared."""
+    from paper_2002_02045_gb300 import PGB_FP32
+    T, sig = 300.0, 0.010
+    g = (40, 40, 40)
+    ctx.pgb_set_model(c2)
+    ctx.pgb_set_grids(g, g)
+    eps = empty((64000, 8))
+    ctx.pgb_get_grid_energies(eps, None)
+    emin = float(eps.min())
+    kbuf = empty((64000,), torch.int32)
+    n = ctx.pgb_window(emin, emin + 0.3, kbuf)
+    assert 0.03 < n / 64000 < 0.07
+    kidx = kbuf[:n].contiguous()
+    gam = empty((n, 8))
+    ctx.pgb_scattering_rates(kidx, T, emin - 0.3, sig, PGB_FP32, gam)
+    got = gam.cpu().numpy()
+    assert np.all(np.isfinite(got)) and np.all(got >= 0)
+    pick = [0, n // 2, n - 1]
+    kl = kidx.cpu().numpy()[pick]
+    e_ref, _ = O.bands(c2, S.mp_grid(*g)[kl])
+    assert np.abs(e_ref - eps.cpu().numpy()[kl]).max() < 1e-11
+    ref = O.scattering_rates_grid(c2, g, g, kl, T, emin - 0.3, sig, q_chunk=16000)
+    assert_rates_close(got[pick], ref, 1e-5, label="c2 full size")
+
+
+# ----------------------------------------------------------------------------
+# collision integral and RK4 (Eq. e_ph_scattering, Sec. 2.1.1)
+# ----------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def c1_list(c1):
+    return O.collision_list_grid(c1, (3, 3, 3), 0, 2)
+
+
+def build_list(ctx, m, L, grid, band_lo, band_hi, T, sig):
+    ctx.pgb_set_model(m)
+    ctx.pgb_set_grids(grid, grid)
+    ctx.pgb_build_collision(band_lo, band_hi, T, sig, dev(L["row"].astype(np.int32)),
+                            dev(L["col"].astype(np.int32)), dev(L["mode"].astype(np.int32)),
+                            dev(L["g2"].astype(np.float32)))
+
+
+def oracle_rhs(L, T, sig):
+    g2 = L["g2"].astype(np.float32).astype(np.float64)   # the list is handed over in FP32
+
+    def rhs(f):
+        return O.collision(f, L["eps"], L["row"], L["col"], L["hw"], g2, T, sig, L["nq"])
+    return rhs
+
+
+def test_collision_c1(ctx, c1, c1_list):
+    T, sig = 300.0, 0.02
+    L = c1_list
+    build_list(ctx, c1, L, (3, 3, 3), 0, 2, T, sig)
+    es = empty((L["nstates"],))
+    assert ctx.pgb_collision_energies(es) == L["nstates"]
+    assert np.abs(es.cpu().numpy() - L["eps"]).max() < 1e-11
+    rng = np.random.default_rng(4)
+    f = rng.uniform(0, 1, L["nstates"])
+    I = empty((L["nstates"],))
+    ctx.pgb_collision(dev(f), I)
+    ref = oracle_rhs(L, T, sig)(f)
+    got = I.cpu().numpy()
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-5 * scale
+    assert abs(got.sum()) <= 1e-6 * scale
+    # host buffers give the same numbers
+    Ih = np.zeros(L["nstates"])
+    ctx.pgb_collision(f, Ih)
+    assert np.array_equal(Ih, got)
+
+
+def test_rk4_c1_1000_steps(ctx, c1, c1_list):
+    T, sig = 300.0, 0.02
+    L = c1_list
+    build_list(ctx, c1, L, (3, 3, 3), 0, 2, T, sig)
+    f0 = S.pulse_occupations(L["eps"], L["eps"].min(), centre=3.0, width=1.0, amplitude=0.2)
+    f = dev(f0)
+    ctx.pgb_step_rk4(f, 1.0, 1000)
+    ref = O.evolve(f0, 1.0, 1000, oracle_rhs(L, T, sig))
+    got = f.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-6
+    assert abs(got.sum() - f0.sum()) <= 1e-9 * f0.sum()
+    assert np.abs(got - f0).max() > 1e-3      # it did evolve
+
+
+def test_collision_edge_cases(ctx, c1):
+    from paper_2002_02045_gb300 import PgbError
+    ctx.pgb_set_model(c1)
+    ctx.pgb_set_grids((2, 2, 2), (2, 2, 2))
+    e = np.zeros(0, np.int32)
+    ctx.pgb_build_collision(0, 2, 300.0, 0.01, e, e, e, np.zeros(0, np.float32))
+    I = np.ones(16)
+    ctx.pgb_collision(np.full(16, 0.3), I)
+    assert np.all(I == 0.0)
+    # a single entry: only its row is non-zero, empty rows stay zero
+    row = np.array([3], np.int32)
+    col = np.array([9], np.int32)
+    mode = np.array([4 % 3], np.int32)
+    ctx.pgb_build_collision(0, 2, 300.0, 0.5, row, col, mode, np.array([1e-4], np.float32))
+    ctx.pgb_collision(np.full(16, 0.3), I)
+    assert np.count_nonzero(I) <= 1
+    # rows out of order and out of range are rejected
+    with pytest.raises(PgbError):
+        ctx.pgb_build_collision(0, 2, 300.0, 0.01, np.array([5, 2], np.int32), np.array([1, 1], np.int32),
+                                np.array([0, 0], np.int32), np.array([1.0, 1.0], np.float32))
+    with pytest.raises(PgbError):
+        ctx.pgb_build_collision(0, 2, 300.0, 0.01, np.array([16], np.int32), np.array([1], np.int32),
+                                np.array([0], np.int32), np.array([1.0], np.float32))
+    with pytest.raises(PgbError):
+        ctx.pgb_build_collision(1, 1, 300.0, 0.01, row, col, mode, np.array([1.0], np.float32))
+
+
+def test_argument_errors(ctx, c1):
+    from paper_2002_02045_gb300 import PGB_FP64, PGB_TC_BF16X3, PgbError
+    ctx.pgb_set_model(c1)
+    with pytest.raises(PgbError):
+        ctx.pgb_scattering_rates(np.zeros(1, np.int32), 300, 0, 0.01, PGB_FP64, np.zeros((1, 2)))
+    with pytest.raises(PgbError):
+        ctx.pgb_set_grids((6, 6, 6), (4, 4, 4))
+    ctx.pgb_set_grids((4, 4, 4), (2, 2, 2))
+    with pytest.raises(PgbError):
+        ctx.pgb_scattering_rates(np.array([64], np.int32), 300, 0, 0.01, PGB_FP64, np.zeros((1, 2)))
+    with pytest.raises(PgbError):
+        ctx.pgb_scattering_rates(np.array([1], np.int32), 300, 0, -0.01, PGB_FP64, np.zeros((1, 2)))
+    bad = S.model_c1()
+    bad.H = bad.H.copy()
+    bad.H[3, 0, 1] += 0.1
+    with pytest.raises(PgbError):
+        ctx.pgb_set_model(bad)
+    # empty k list is a no-op
+    ctx.pgb_set_model(c1)
+    ctx.pgb_set_grids((4, 4, 4), (2, 2, 2))
+    ctx.pgb_scattering_rates(np.zeros(0, np.int32), 300, 0, 0.01, PGB_FP64, np.zeros((0, 2)))
