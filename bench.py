@@ -291,8 +291,12 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x3", "tf32x3"])
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--kgrid", type=int, default=40, help="grid size per axis (40 = the workload; smaller "
+                    "values give the small case used for profiler captures)")
     args = ap.parse_args()
     rank, world, local = dist_setup()
+    global KGRID
+    KGRID = (args.kgrid,) * 3
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

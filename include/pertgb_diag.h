@@ -1,0 +1,33 @@
+/*
+ * pertgb_diag.h - diagnostic entry points of libpertgb (not part of the hot path).
+ *
+ * They expose intermediate results of the interpolation so that each stage
+ * can be checked on its own against a reference.  Conventions as in pertgb.h.
+ */
+#ifndef PERTGB_DIAG_H
+#define PERTGB_DIAG_H
+
+#include "pertgb.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Bands at arbitrary points (Sec. 2.2.1, Eq. wannier_3): for pts [n][3]
+ * (host or device) writes H^(W)(k) [n][nw][nw] complex128, eps [n][nw] and
+ * U [n][nw][nw] complex128 (columns are eigenvectors).  Any output may be NULL. */
+pgb_status pgb_diag_bands(pgb_ctx *ctx, const double *pts, int64_t n, double *Hk, double *eps, double *U);
+
+/* The device eigensolver template run on the host for `count` Hermitian
+ * n x n complex128 matrices: eval [count][n], evec [count][n][n].
+ * Returns 0, or -1 for an unsupported n (supported: 1, 2, 3, 6, 8, 16).     */
+int pgb_selftest_heevj(int n, int count, const double *mat, double *eval, double *evec);
+
+/* The device eigensolver kernel on `count` host matrices (as above, n = 1..16). */
+pgb_status pgb_selftest_heevj_device(pgb_ctx *ctx, int n, int count, const double *mat, double *eval,
+                                     double *evec);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

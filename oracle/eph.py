@@ -339,8 +339,8 @@ def collision_list_grid(model, grid, band_lo, band_hi, sigma=None, screen=0.0):
     when both Gaussian factors exp(-x^2/sigma^2) are below ``screen``; the
     rule is symmetric between the two directions.
 
-    Returns dict with row, col, mode (int arrays), g2, hw (float64), eps
-    (state energies) and nq.
+    Returns dict with row, col, mode (int arrays, ordered by row), g2, hw
+    (float64), eps (state energies) and nq.
     """
     from synthetic import mp_grid
     g = np.asarray(grid)
@@ -390,6 +390,7 @@ def collision_list_grid(model, grid, band_lo, band_hi, sigma=None, screen=0.0):
                         modes.append(nu)
                         vals.append(val)
                         hws.append(hw)
-    return {"row": np.array(rows, np.int64), "col": np.array(cols, np.int64),
-            "mode": np.array(modes, np.int64), "g2": np.array(vals), "hw": np.array(hws),
-            "eps": eps_state, "nq": nk, "nstates": nk * nb}
+    order = np.argsort(np.array(rows, np.int64), kind="stable")   # entries grouped by initial state
+    return {"row": np.array(rows, np.int64)[order], "col": np.array(cols, np.int64)[order],
+            "mode": np.array(modes, np.int64)[order], "g2": np.array(vals)[order],
+            "hw": np.array(hws)[order], "eps": eps_state, "nq": nk, "nstates": nk * nb}

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "../../include/pertgb_diag.h"
 
 using namespace pgb;
 
@@ -790,6 +791,30 @@ pgb_status pgb_step_rk4(pgb_ctx *c, double *f, double dt_fs, int64_t nsteps) {
         cudaFreeAsync(tmp, c->stream);
     }
     return st;
+}
+
+pgb_status pgb_diag_bands(pgb_ctx *c, const double *pts, int64_t n, double *Hk, double *eps, double *U) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_model) return fail(c, PGB_ESTATE, "diag_bands: call set_model first");
+    if (n <= 0) return PGB_OK;
+    const int nw2 = c->nw * c->nw;
+    In<double> P;
+    TRY(P.init(c, pts, 3 * (size_t)n));
+    Tmp<double2> ph, hk, u;
+    Tmp<double> e;
+    TRY(ph.alloc(c, (size_t)n * c->nRH));
+    TRY(hk.alloc(c, (size_t)n * nw2));
+    TRY(u.alloc(c, (size_t)n * nw2));
+    TRY(e.alloc(c, (size_t)n * c->nw));
+    TRY(launch_phase_pts(c, P.dev, n, c->d_RH, c->nRH, ph.p, false));
+    TRY(launch_cgemm(c, false, 1, n, nw2, c->nRH, ph.p, c->nRH, 0, c->d_H, nw2, 0, hk.p, nw2, 0));
+    if (Hk) PGB_CUDA_TRY(c, cudaMemcpyAsync(Hk, hk.p, 16 * (size_t)n * nw2, cudaMemcpyDefault, c->stream));
+    TRY(launch_heevj(c, n, c->nw, hk.p, nullptr, e.p, u.p));
+    if (eps) PGB_CUDA_TRY(c, cudaMemcpyAsync(eps, e.p, 8 * (size_t)n * c->nw, cudaMemcpyDefault, c->stream));
+    if (U) PGB_CUDA_TRY(c, cudaMemcpyAsync(U, u.p, 16 * (size_t)n * nw2, cudaMemcpyDefault, c->stream));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PGB_OK;
 }
 
 }  // extern "C"

@@ -17,26 +17,35 @@ namespace pgb {
 
 constexpr int kMaxSweeps = 40;
 
+// Matrix entries are held as separate real / imaginary arrays, row-major,
+// with the sweep loops kept rolled so that the working set stays small.
 template <int N>
-__host__ __device__ inline void heevj_one(double2 (&A)[N][N], double2 (&V)[N][N], double (&w)[N]) {
-    for (int r = 0; r < N; ++r)
-        for (int c = 0; c < N; ++c) V[r][c] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+__host__ __device__ inline void heevj_one(double (&ar)[N * N], double (&ai)[N * N], double (&vr)[N * N],
+                                          double (&vi)[N * N], double (&w)[N]) {
+    for (int r = 0; r < N * N; ++r) {
+        vr[r] = 0.0;
+        vi[r] = 0.0;
+    }
+    for (int r = 0; r < N; ++r) vr[r * N + r] = 1.0;
+#pragma unroll 1
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
         double off = 0.0, tot = 0.0;
         for (int r = 0; r < N; ++r) {
-            tot += A[r][r].x * A[r][r].x;
-            for (int c = r + 1; c < N; ++c) off += 2.0 * cabs2(A[r][c]);
+            tot += ar[r * N + r] * ar[r * N + r];
+            for (int c = r + 1; c < N; ++c) off += 2.0 * (ar[r * N + c] * ar[r * N + c] + ai[r * N + c] * ai[r * N + c]);
         }
         tot += off;
         if (!(off > 1e-30 * tot)) break;
+#pragma unroll 1
         for (int p = 0; p < N - 1; ++p) {
+#pragma unroll 1
             for (int q = p + 1; q < N; ++q) {
-                const double2 b = A[p][q];
-                const double ab = sqrt(cabs2(b));
+                const double br = ar[p * N + q], bi = ai[p * N + q];
+                const double ab = sqrt(br * br + bi * bi);
                 if (ab == 0.0) continue;
                 // e^{-i phi} = conj(b) / |b|
-                const double2 em = make_double2(b.x / ab, -b.y / ab);
-                const double z = (A[q][q].x - A[p][p].x) / (2.0 * ab);
+                const double er = br / ab, ei = -bi / ab;
+                const double z = (ar[q * N + q] - ar[p * N + p]) / (2.0 * ab);
                 double t;
                 if (fabs(z) > 1e150)
                     t = 0.5 / z;
@@ -44,42 +53,41 @@ __host__ __device__ inline void heevj_one(double2 (&A)[N][N], double2 (&V)[N][N]
                     t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(z * z + 1.0));
                 const double c = 1.0 / sqrt(1.0 + t * t);
                 const double s = t * c;
-                // V-columns of the rotation: col p = (c, -s em), col q = (s, c em)
-                const double2 vqp = make_double2(-s * em.x, -s * em.y);
-                const double2 vqq = make_double2(c * em.x, c * em.y);
+                // rotation columns: col p = (c, -s e), col q = (s, c e), e = e^{-i phi}
+                const double vqp_r = -s * er, vqp_i = -s * ei;
+                const double vqq_r = c * er, vqq_i = c * ei;
                 // A <- A V (columns p, q)
                 for (int r = 0; r < N; ++r) {
-                    const double2 arp = A[r][p], arq = A[r][q];
-                    double2 np_ = make_double2(c * arp.x, c * arp.y);
-                    cfma(np_, arq, vqp);
-                    double2 nq_ = make_double2(s * arp.x, s * arp.y);
-                    cfma(nq_, arq, vqq);
-                    A[r][p] = np_;
-                    A[r][q] = nq_;
+                    const double xr = ar[r * N + p], xi = ai[r * N + p];
+                    const double yr = ar[r * N + q], yi = ai[r * N + q];
+                    ar[r * N + p] = c * xr + (yr * vqp_r - yi * vqp_i);
+                    ai[r * N + p] = c * xi + (yr * vqp_i + yi * vqp_r);
+                    ar[r * N + q] = s * xr + (yr * vqq_r - yi * vqq_i);
+                    ai[r * N + q] = s * xi + (yr * vqq_i + yi * vqq_r);
                 }
-                // A <- V^dagger A (rows p, q)
+                // A <- V^dagger A (rows p, q): conj(vqp), conj(vqq) multiply row q
                 for (int r = 0; r < N; ++r) {
-                    const double2 apr = A[p][r], aqr = A[q][r];
-                    double2 np_ = make_double2(c * apr.x, c * apr.y);
-                    cfma_conj(np_, vqp, aqr);
-                    double2 nq_ = make_double2(s * apr.x, s * apr.y);
-                    cfma_conj(nq_, vqq, aqr);
-                    A[p][r] = np_;
-                    A[q][r] = nq_;
+                    const double xr = ar[p * N + r], xi = ai[p * N + r];
+                    const double yr = ar[q * N + r], yi = ai[q * N + r];
+                    ar[p * N + r] = c * xr + (vqp_r * yr + vqp_i * yi);
+                    ai[p * N + r] = c * xi + (vqp_r * yi - vqp_i * yr);
+                    ar[q * N + r] = s * xr + (vqq_r * yr + vqq_i * yi);
+                    ai[q * N + r] = s * xi + (vqq_r * yi - vqq_i * yr);
                 }
-                A[p][q] = make_double2(0.0, 0.0);
-                A[q][p] = make_double2(0.0, 0.0);
-                A[p][p].y = 0.0;
-                A[q][q].y = 0.0;
+                ar[p * N + q] = 0.0;
+                ai[p * N + q] = 0.0;
+                ar[q * N + p] = 0.0;
+                ai[q * N + p] = 0.0;
+                ai[p * N + p] = 0.0;
+                ai[q * N + q] = 0.0;
                 // V <- V Vrot
                 for (int r = 0; r < N; ++r) {
-                    const double2 vrp = V[r][p], vrq = V[r][q];
-                    double2 np_ = make_double2(c * vrp.x, c * vrp.y);
-                    cfma(np_, vrq, vqp);
-                    double2 nq_ = make_double2(s * vrp.x, s * vrp.y);
-                    cfma(nq_, vrq, vqq);
-                    V[r][p] = np_;
-                    V[r][q] = nq_;
+                    const double xr = vr[r * N + p], xi = vi[r * N + p];
+                    const double yr = vr[r * N + q], yi = vi[r * N + q];
+                    vr[r * N + p] = c * xr + (yr * vqp_r - yi * vqp_i);
+                    vi[r * N + p] = c * xi + (yr * vqp_i + yi * vqp_r);
+                    vr[r * N + q] = s * xr + (yr * vqq_r - yi * vqq_i);
+                    vi[r * N + q] = s * xi + (yr * vqq_i + yi * vqq_r);
                 }
             }
         }
@@ -87,7 +95,7 @@ __host__ __device__ inline void heevj_one(double2 (&A)[N][N], double2 (&V)[N][N]
     int order[N];
     for (int i = 0; i < N; ++i) {
         order[i] = i;
-        w[i] = A[i][i].x;
+        w[i] = ar[i * N + i];
     }
     // stable insertion sort, ascending
     for (int i = 1; i < N; ++i) {
@@ -100,13 +108,17 @@ __host__ __device__ inline void heevj_one(double2 (&A)[N][N], double2 (&V)[N][N]
         }
         order[j + 1] = oi;
     }
-    double ws[N];
-    for (int i = 0; i < N; ++i) ws[i] = w[order[i]];
-    for (int i = 0; i < N; ++i) w[i] = ws[i];
-    for (int r = 0; r < N; ++r) {
-        double2 row[N];
-        for (int i = 0; i < N; ++i) row[i] = V[r][order[i]];
-        for (int i = 0; i < N; ++i) V[r][i] = row[i];
+    // permute: eigenvalues into w, eigenvector columns into (ar, ai) as scratch, then back
+    for (int i = 0; i < N; ++i) ar[i] = w[order[i]];
+    for (int i = 0; i < N; ++i) w[i] = ar[i];
+    for (int r = 0; r < N; ++r)
+        for (int i = 0; i < N; ++i) {
+            ar[r * N + i] = vr[r * N + order[i]];
+            ai[r * N + i] = vi[r * N + order[i]];
+        }
+    for (int r = 0; r < N * N; ++r) {
+        vr[r] = ar[r];
+        vi[r] = ai[r];
     }
 }
 

@@ -186,8 +186,7 @@ __global__ void k_heevj(int64_t count, const double2 *__restrict__ mat, const do
                         double *__restrict__ eval, double2 *__restrict__ evec) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
-    double2 A[N][N], V[N][N];
-    double w[N];
+    double ar[N * N], ai[N * N], vr[N * N], vi[N * N], w[N];
     const double2 *m = mat + i * N * N;
     for (int r = 0; r < N; ++r)
         for (int cc = 0; cc < N; ++cc) {
@@ -197,22 +196,24 @@ __global__ void k_heevj(int64_t count, const double2 *__restrict__ mat, const do
                 v.x *= s;
                 v.y *= s;
             }
-            A[r][cc] = v;
+            ar[r * N + cc] = v.x;
+            ai[r * N + cc] = v.y;
         }
     // enforce exact Hermiticity of the input (average with the adjoint)
     for (int r = 0; r < N; ++r) {
-        A[r][r].y = 0.0;
+        ai[r * N + r] = 0.0;
         for (int cc = r + 1; cc < N; ++cc) {
-            const double2 u = A[r][cc], l = A[cc][r];
-            const double2 h = make_double2(0.5 * (u.x + l.x), 0.5 * (u.y - l.y));
-            A[r][cc] = h;
-            A[cc][r] = make_double2(h.x, -h.y);
+            const double hr = 0.5 * (ar[r * N + cc] + ar[cc * N + r]);
+            const double hi = 0.5 * (ai[r * N + cc] - ai[cc * N + r]);
+            ar[r * N + cc] = hr;
+            ai[r * N + cc] = hi;
+            ar[cc * N + r] = hr;
+            ai[cc * N + r] = -hi;
         }
     }
-    heevj_one<N>(A, V, w);
+    heevj_one<N>(ar, ai, vr, vi, w);
     for (int r = 0; r < N; ++r) eval[i * N + r] = w[r];
-    for (int r = 0; r < N; ++r)
-        for (int cc = 0; cc < N; ++cc) evec[i * N * N + r * N + cc] = V[r][cc];
+    for (int r = 0; r < N * N; ++r) evec[i * N * N + r] = make_double2(vr[r], vi[r]);
 }
 
 pgb_status launch_heevj(pgb_ctx *c, int64_t count, int n, double2 *d_mat, const double *d_scale,
@@ -562,19 +563,17 @@ extern "C" int pgb_selftest_heevj(int n, int count, const double *mat, double *e
 #define PGB_HOST_CASE(NN)                                                        \
     case NN:                                                                     \
         for (int i = 0; i < count; ++i) {                                        \
-            double2 A[NN][NN], V[NN][NN];                                        \
-            double w[NN];                                                        \
-            for (int r = 0; r < NN; ++r)                                         \
-                for (int cc = 0; cc < NN; ++cc)                                  \
-                    A[r][cc] = make_double2(mat[2 * ((i * NN + r) * NN + cc)],   \
-                                            mat[2 * ((i * NN + r) * NN + cc) + 1]); \
-            heevj_one<NN>(A, V, w);                                              \
+            double ar[NN * NN], ai[NN * NN], vr[NN * NN], vi[NN * NN], w[NN];     \
+            for (int r = 0; r < NN * NN; ++r) {                                  \
+                ar[r] = mat[2 * (i * NN * NN + r)];                              \
+                ai[r] = mat[2 * (i * NN * NN + r) + 1];                          \
+            }                                                                    \
+            heevj_one<NN>(ar, ai, vr, vi, w);                                    \
             for (int r = 0; r < NN; ++r) eval[i * NN + r] = w[r];                \
-            for (int r = 0; r < NN; ++r)                                         \
-                for (int cc = 0; cc < NN; ++cc) {                                \
-                    evec[2 * ((i * NN + r) * NN + cc)] = V[r][cc].x;             \
-                    evec[2 * ((i * NN + r) * NN + cc) + 1] = V[r][cc].y;         \
-                }                                                                \
+            for (int r = 0; r < NN * NN; ++r) {                                  \
+                evec[2 * (i * NN * NN + r)] = vr[r];                             \
+                evec[2 * (i * NN * NN + r) + 1] = vi[r];                         \
+            }                                                                    \
         }                                                                        \
         return 0;
     switch (n) {
@@ -588,4 +587,29 @@ extern "C" int pgb_selftest_heevj(int n, int count, const double *mat, double *e
             return -1;
     }
 #undef PGB_HOST_CASE
+}
+
+// The same eigensolver run by the device kernel on host-provided matrices.
+extern "C" pgb_status pgb_selftest_heevj_device(pgb_ctx *c, int n, int count, const double *mat, double *eval,
+                                                double *evec) {
+    using namespace pgb;
+    if (!c || count < 0) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    double2 *dm = nullptr, *dv = nullptr;
+    double *de = nullptr;
+    const size_t nn = (size_t)count * n * n;
+    PGB_CUDA_TRY(c, cudaMalloc((void **)&dm, 16 * nn + 16));
+    PGB_CUDA_TRY(c, cudaMalloc((void **)&dv, 16 * nn + 16));
+    PGB_CUDA_TRY(c, cudaMalloc((void **)&de, 8 * (size_t)count * n + 8));
+    pgb_status st = PGB_OK;
+    if (cudaMemcpy(dm, mat, 16 * nn, cudaMemcpyHostToDevice) != cudaSuccess) st = PGB_ECUDA;
+    if (st == PGB_OK) st = launch_heevj(c, count, n, dm, nullptr, de, dv);
+    if (st == PGB_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = PGB_ECUDA;
+    if (st == PGB_OK && cudaMemcpy(eval, de, 8 * (size_t)count * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        st = PGB_ECUDA;
+    if (st == PGB_OK && cudaMemcpy(evec, dv, 16 * nn, cudaMemcpyDeviceToHost) != cudaSuccess) st = PGB_ECUDA;
+    cudaFree(dm);
+    cudaFree(dv);
+    cudaFree(de);
+    return st;
 }

@@ -22,6 +22,7 @@ PGB_FP64, PGB_FP32, PGB_TC_TF32X3, PGB_TC_BF16X3 = 0, 1, 2, 3
 PGB_G2_FULL, PGB_G_ABS = 0, 1
 PRECISIONS = {"fp64": PGB_FP64, "fp32": PGB_FP32, "tf32x3": PGB_TC_TF32X3, "bf16x3": PGB_TC_BF16X3}
 
+DIAG_SYMBOLS = ("pgb_diag_bands", "pgb_selftest_heevj", "pgb_selftest_heevj_device")
 ABI_SYMBOLS = (
     "pgb_create", "pgb_destroy", "pgb_last_error", "pgb_status_string", "pgb_set_model",
     "pgb_set_grids", "pgb_get_grid_energies", "pgb_window", "pgb_interpolate_g",
@@ -77,6 +78,9 @@ def load(path: str = LIB_PATH):
         "pgb_launch_count": (I64, [P]),
         "pgb_profile": (I, [P, I]),
         "pgb_profile_read": (I, [P, I, C.POINTER(D), C.POINTER(I64)]),
+        "pgb_diag_bands": (I, [P, P, I64, P, P, P]),
+        "pgb_selftest_heevj": (I, [I, I, P, P, P]),
+        "pgb_selftest_heevj_device": (I, [P, I, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -223,6 +227,9 @@ class Context:
 
     def pgb_launch_count(self):
         return int(self.lib.pgb_launch_count(self._h))
+
+    def pgb_diag_bands(self, pts, Hk=None, eps=None, U=None):
+        self._chk(self.lib.pgb_diag_bands(self._h, _ptr(pts), len(pts), _ptr(Hk), _ptr(eps), _ptr(U)))
 
     def pgb_profile(self, enable):
         self._chk(self.lib.pgb_profile(self._h, 1 if enable else 0))

@@ -19,15 +19,16 @@ def lib():
     return native.load()
 
 
-def header_symbols():
-    src = open(os.path.join(ROOT, "include", "pertgb.h")).read()
+def header_symbols(name="pertgb.h"):
+    src = open(os.path.join(ROOT, "include", name)).read()
     return sorted(set(re.findall(r"\b(pgb_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_symbols_exported(lib):
     from paper_2002_02045_gb300 import native
-    declared = header_symbols()
-    assert set(declared) == set(native.ABI_SYMBOLS)
+    assert set(header_symbols()) == set(native.ABI_SYMBOLS)
+    assert set(header_symbols("pertgb_diag.h")) == set(native.DIAG_SYMBOLS)
+    declared = header_symbols() + header_symbols("pertgb_diag.h")
     out = subprocess.run(["nm", "-D", "--defined-only", native.LIB_PATH], capture_output=True, text=True).stdout
     exported = set(re.findall(r"\bT (pgb_\w+)", out))
     missing = [s for s in declared if s not in exported]

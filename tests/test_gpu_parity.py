@@ -50,6 +50,46 @@ def empty(shape, dtype=torch.float64):
 # bands and phonons (Eqs. wannier_3, IFC2)
 # ----------------------------------------------------------------------------
 
+@pytest.mark.parametrize("n", [1, 2, 3, 6, 8, 12, 16])
+def test_device_jacobi_matches_lapack(ctx, n):
+    import ctypes as C
+    rng = np.random.default_rng(100 + n)
+    cnt = 200
+    A = rng.normal(size=(cnt, n, n)) + 1j * rng.normal(size=(cnt, n, n))
+    A = np.ascontiguousarray(A + np.conj(np.swapaxes(A, -1, -2)))
+    if n >= 3:
+        Q = np.linalg.qr(rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)))[0]
+        w = np.arange(n, dtype=float)
+        w[1] = w[0]
+        A[0] = Q @ np.diag(w) @ np.conj(Q.T)
+    ev = np.zeros((cnt, n))
+    V = np.zeros((cnt, n, n), complex)
+    st = ctx.lib.pgb_selftest_heevj_device(ctx._h, n, cnt, A.ctypes.data, ev.ctypes.data, V.ctypes.data)
+    assert st == 0
+    ref = np.linalg.eigh(A)[0]
+    assert np.abs(ev - ref).max() < 1e-12 * np.abs(ref).max()
+    rec = np.einsum("kin,kn,kjn->kij", V, ev, np.conj(V))
+    assert np.abs(rec - A).max() < 1e-12 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("which", ["c1", "c2"])
+def test_diag_hamiltonian_and_eigen(ctx, c1, c2, which):
+    m = c1 if which == "c1" else c2
+    ctx.pgb_set_model(m)
+    rng = np.random.default_rng(9)
+    k = rng.uniform(-1, 1, (37, 3))
+    nw = m.nw
+    Hk = np.zeros((37, nw, nw), complex)
+    eps = np.zeros((37, nw))
+    U = np.zeros((37, nw, nw), complex)
+    ctx.pgb_diag_bands(k, Hk, eps, U)
+    ref = O.hamiltonian_k(m, k)
+    assert np.abs(Hk - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+    e_ref, _ = O.bands(m, k)
+    assert np.abs(eps - e_ref).max() < 1e-11
+    rec = np.einsum("kin,kn,kjn->kij", U, eps, np.conj(U))
+    assert np.abs(rec - ref).max() < 1e-11
+
 @pytest.mark.parametrize("which,grid", [("c1", (6, 6, 6)), ("c2", (12, 12, 12)), ("c2", (5, 7, 3))])
 def test_grid_bands_phonons(ctx, c1, c2, which, grid):
     m = c1 if which == "c1" else c2
@@ -111,10 +151,12 @@ def test_interpolate_g_c2_fp32(ctx, c2):
     ctx.pgb_interpolate_g(dev(k), dev(q), PGB_FP32, PGB_G2_FULL, out)
     ref, hw = oracle_g2(c2, k, q)
     got = out.cpu().numpy()
-    # generic points: modes and bands non-degenerate, every element is gauge invariant
+    # generic points: modes and bands non-degenerate, every element is gauge invariant.
+    # FP32 amplitudes carry an absolute error ~1e-7 |g|_max, so |g|^2 elements get a
+    # floor of 1e-2 of the block maximum; the normwise bound stays 1e-5.
     hwb = np.broadcast_to(hw[None], (2, 7, 6))
     assert_close_blocks(degenerate_sum(got, hwb, 2), degenerate_sum(ref, hwb, 2), 1e-5,
-                        block_axes=(2, 3, 4), label="c2 g2")
+                        block_axes=(2, 3, 4), floor=1e-2, label="c2 g2")
 
 
 # ----------------------------------------------------------------------------
@@ -162,11 +204,17 @@ def test_rates_c2_reduced_fp32(ctx, c2):
     e_ref, _ = O.bands(c2, S.mp_grid(*kg))
     emin = e_ref.min()
     mu = emin - 0.3
-    win = np.nonzero(((e_ref >= emin) & (e_ref <= emin + 0.3)).any(1))[0].astype(np.int32)
+    win = set(np.nonzero(((e_ref >= emin) & (e_ref <= emin + 0.3)).any(1))[0].tolist())
     kbuf = empty((8000,), torch.int32)
     n = ctx.pgb_window(emin, emin + 0.3, kbuf)
-    assert n == len(win) and np.array_equal(kbuf[:n].cpu().numpy(), win)
-    sample = win[:: max(1, len(win) // 7)][:7]
+    got_win = kbuf[:n].cpu().numpy()
+    assert np.all(np.diff(got_win) > 0)
+    # membership may differ only where a band sits on a window edge to rounding
+    for k in win.symmetric_difference(got_win.tolist()):
+        edge = np.minimum(np.abs(e_ref[k] - emin), np.abs(e_ref[k] - emin - 0.3)).min()
+        assert edge < 1e-10, (k, edge)
+    both = np.array(sorted(win.intersection(got_win.tolist())), np.int32)
+    sample = both[:: max(1, len(both) // 7)][:7]
     gam = empty((len(sample), 8))
     ctx.pgb_scattering_rates(dev(sample), T, mu, sig, PGB_FP32, gam)
     ref = O.scattering_rates_grid(c2, kg, qg, sample, T, mu, sig)
