@@ -634,9 +634,11 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
     }
 
     const int per = nm * nw;
-    const int qpb = std::max(1, 256 / per);
-    const int64_t nqblk = (c->Nq + qpb - 1) / qpb;
-    const size_t per_k = (size_t)(2 * nrow + c->Nq * ncol + c->nRge) * es + (size_t)nqblk * per * sizeof(double);
+    const int qpb = std::max(1, 256 / nw);
+    const int qiters = 8;
+    const int64_t nqblk = (c->Nq + (int64_t)qpb * qiters - 1) / ((int64_t)qpb * qiters);
+    const size_t per_k = (size_t)(2 * nrow + c->Nq * ncol + c->nRge) * es + (size_t)nqblk * per * sizeof(double) +
+                         (size_t)per * sizeof(double);
     const size_t budget = (size_t)4 << 30;
     int64_t nbmax = std::max<int64_t>(1, (int64_t)(budget / per_k));
     nbmax = std::min<int64_t>(nbmax, std::min<int64_t>(nk, 65535));
@@ -647,6 +649,14 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
     char *G = S1 + (size_t)nbmax * nrow * es;
     char *Cb = G + (size_t)nbmax * nrow * es;
     double *partial = (double *)(Cb + (size_t)nbmax * c->Nq * ncol * es);
+    double *gmode_tmp = partial + (size_t)nbmax * nqblk * per;
+    Tmp<double> focc, nbe;
+    Tmp<float> eps32, hw32;
+    TRY(focc.alloc(c, (size_t)c->Nk * nw));
+    TRY(eps32.alloc(c, (size_t)c->Nk * nw));
+    TRY(nbe.alloc(c, (size_t)c->Nq * nm));
+    TRY(hw32.alloc(c, (size_t)c->Nq * nm));
+    TRY(launch_occ_tables(c, T, mu, focc.p, eps32.p, nbe.p, hw32.p));
     const void *g = f32 ? (const void *)c->d_g32 : (const void *)c->d_g64;
     const void *U = f32 ? (const void *)c->d_U32 : (const void *)c->d_U;
     const void *cf = f32 ? (const void *)c->d_coef32 : (const void *)c->d_coef;
@@ -681,14 +691,19 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
         ra.T = T;
         ra.mu = mu;
         ra.sigma = sigma;
+        ra.eps32 = eps32.p;
+        ra.focc = focc.p;
+        ra.nbe = nbe.p;
+        ra.hw32 = hw32.p;
         ra.partial = partial;
         ra.nqblk = nqblk;
         ra.qpb = qpb;
+        ra.qiters = qiters;
         prof_mark(c, PGB_PROF_EPILOGUE);
         TRY(launch_rates_epilogue(c, f32, ra));
         prof_mark(c, PGB_PROF_EPILOGUE);
         TRY(launch_rates_reduce(c, nb, nqblk, nm, nw, scale, partial, Gm.dev + b0 * nw,
-                                Gmm.dev ? Gmm.dev + b0 * nm * nw : nullptr));
+                                Gmm.dev ? Gmm.dev + b0 * nm * nw : gmode_tmp));
     }
     TRY(Gm.finish());
     TRY(Gmm.finish());

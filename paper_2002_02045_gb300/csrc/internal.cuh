@@ -158,10 +158,17 @@ struct RatesArgs {
     const double *eps;     // [Nk][nw]
     const double *hw;      // [Nq][nm]
     double T, mu, sigma;
+    const float *eps32;    // [Nk][nw] screening copy
+    const double *focc;    // [Nk][nw] Fermi-Dirac occupations
+    const double *nbe;     // [Nq][nm] Bose-Einstein occupations
+    const float *hw32;     // [Nq][nm]
     double *partial;       // [nb][nqblk][nm][nw]
     int64_t nqblk;
-    int qpb;               // q per block
+    int qpb;               // q per block and iteration
+    int qiters;            // iterations per block
 };
+pgb_status launch_occ_tables(pgb_ctx *c, double T, double mu, double *focc, float *eps32, double *nbe,
+                             float *hw32);
 pgb_status launch_rates_epilogue(pgb_ctx *c, bool fp32, const RatesArgs &a);
 pgb_status launch_rates_reduce(pgb_ctx *c, int64_t nb, int64_t nqblk, int nm, int nw, double scale,
                                const double *partial, double *gamma, double *gamma_mode);

@@ -1,6 +1,7 @@
 // Wannier interpolation kernels: Fourier phases, batched complex GEMM (SIMT),
 // Hermitian eigensolves, mode coefficients, U(k) fold, and the fused
 // rotation / mode projection / |g|^2 / scattering-rate epilogue.
+#include <algorithm>
 #include <cstdio>
 
 #include "cplx.cuh"
@@ -296,7 +297,9 @@ pgb_status launch_to_f32(pgb_ctx *c, const double2 *src, float2 *dst, int64_t n)
 
 // ---------------------------------------------------------------------------
 // Fold U(k) into the Re-sum (right factor of the rotation in Eq. eph_mat_wann2):
-//   G[b][rp][ka][i][n] = sum_j S1[b][rp][ka][i][j] U_jn(k_b)
+//   G[b][rp][n][ka][i] = sum_j S1[b][rp][ka][i][j] U_jn(k_b)
+// The output columns are ordered (n, ka, i) so that everything one initial
+// band n needs is contiguous.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_fold_u(int64_t nb, const int32_t *__restrict__ kidx, int nRgp, int nm, int nw,
@@ -306,10 +309,12 @@ __global__ void k_fold_u(int64_t nb, const int32_t *__restrict__ kidx, int nRgp,
     if (t >= nb * per) return;
     const int64_t b = t / per;
     const int64_t r = t % per;
-    const int n = (int)(r % nw);
-    const int64_t row = r / nw;           // (rp, ka, i)
+    const int i = (int)(r % nw);
+    const int ka = (int)((r / nw) % nm);
+    const int n = (int)((r / ((int64_t)nw * nm)) % nw);
+    const int64_t rp = r / ((int64_t)nw * nm * nw);
     const int64_t k = kidx ? (int64_t)kidx[b] : b;
-    const V2<T> *s = S1 + b * per + row * nw;
+    const V2<T> *s = S1 + b * per + ((rp * nm + ka) * nw + i) * nw;
     const V2<T> *u = U + k * nw * nw;
     V2<T> acc = cmake<T>(0, 0);
     for (int j = 0; j < nw; ++j) cfma(acc, s[j], u[j * nw + n]);
@@ -331,15 +336,18 @@ pgb_status launch_fold_u(pgb_ctx *c, bool fp32, int64_t nb, const int32_t *d_kid
 }
 
 // ---------------------------------------------------------------------------
-// Rates epilogue (Eqs. eph_mat, scatter_rate, BTE_W), one thread per
-// (q, nu, n) of one k:
-//   G^nu_i  = sum_ka coef[q][nu][ka] C[b][q][ka][i][n]          (mode projection)
-//   g_mn nu = sum_i conj(U_im(k+q)) G^nu_i                        (left rotation)
-//   acc    += |g|^2 [ e^{-(x_em/s)^2} (1 + N - f_m) + e^{-(x_abs/s)^2} (N + f_m) ]
-// with x_em = e_n(k) - hw - e_m(k+q), x_abs = e_n(k) + hw - e_m(k+q).  Terms
-// with |x|/s > kDeltaCut are skipped before the rotation is formed.  The
-// energies, occupations and Gaussian factors are FP64; the block sums over
-// its q in a fixed order and writes one partial per (nu, n).
+// Rates epilogue (Eqs. eph_mat, scatter_rate, BTE_W).  One thread per (q, n)
+// of one k; C holds the Wannier-gauge g with U(k) folded, columns (n, ka, i).
+//   1. screen: the (m, nu) with |e_n(k) - e_m(k+q) -+ hw_nu(q)| <= 7 sigma
+//      (FP32 energies with a 1e-4 eV margin) - usually few;
+//   2. for each nu that has a survivor, project on the mode:
+//        G^nu_i = sum_ka coef[q][nu][ka] C[b][q][n][ka][i];
+//   3. for each surviving m rotate, g = sum_i conj(U_im(k+q)) G^nu_i, and add
+//        |g|^2 [ e^{-(x_em/s)^2} (1 + N - f_m) + e^{-(x_abs/s)^2} (N + f_m) ]
+//      with x formed in FP64 (FP32 path: the Gaussian of the FP64 argument is
+//      taken in FP32, relative error < 3e-6).
+// Per-thread sums over its q are FP64; the block reduces its q in a fixed
+// order and writes one partial per (nu, n).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int64_t kplusq_index(int64_t k, int64_t q, const int kg[3], const int qg[3]) {
     const int k3 = (int)(k % kg[2]), k2 = (int)((k / kg[2]) % kg[1]), k1 = (int)(k / ((int64_t)kg[1] * kg[2]));
@@ -350,74 +358,109 @@ __device__ __forceinline__ int64_t kplusq_index(int64_t k, int64_t q, const int 
     return ((int64_t)s1 * kg[1] + s2) * kg[2] + s3;
 }
 
+template <typename T> __device__ __forceinline__ T gauss(double y2);
+template <> __device__ __forceinline__ float gauss<float>(double y2) { return expf(-(float)y2); }
+template <> __device__ __forceinline__ double gauss<double>(double y2) { return exp(-y2); }
+
 template <typename T>
-__global__ void k_rates_epilogue(RatesArgs a) {
+__global__ void __launch_bounds__(256) k_rates_epilogue(RatesArgs a) {
     using T2 = V2<T>;
-    extern __shared__ double red[];
-    const int per = a.nm * a.nw;
-    const int t = threadIdx.x;
-    const int ql = t / per;
-    const int r = t % per;
-    const int nu = r / a.nw;
-    const int n = r % a.nw;
+    extern __shared__ double red[];                 // [qpb][nm][nw]
+    const int nw = a.nw, nm = a.nm;
+    const int ql = threadIdx.x / nw;
+    const int n = threadIdx.x % nw;
     const int64_t b = blockIdx.y;
-    const int64_t q = (int64_t)blockIdx.x * a.qpb + ql;
-    double acc = 0.0;
-    if (ql < a.qpb && q < a.Nq) {
-        const int64_t k = a.kidx[b];
-        const int64_t kq = kplusq_index(k, q, a.kg, a.qg);
-        const int ncol = per * a.nw;
-        const double w = a.hw[q * a.nm + nu];
-        if (w >= kOmegaMinEv) {
-            const T2 *Cq = (const T2 *)a.C + ((int64_t)b * a.Nq + q) * ncol;
-            const T2 *cf = (const T2 *)a.coef + (q * a.nm + nu) * a.nm;
-            T2 gv[kMaxNw];
+    const int64_t k = a.kidx[b];
+    const int ncol = nm * nw * nw;
+    double acc[kMaxNmode];
 #pragma unroll
-            for (int i = 0; i < kMaxNw; ++i) gv[i] = cmake<T>(0, 0);
-            for (int ka = 0; ka < a.nm; ++ka) {
-                const T2 cc = cf[ka];
+    for (int v = 0; v < kMaxNmode; ++v) acc[v] = 0.0;
+    if (ql < a.qpb) {
+        const double en = a.eps[k * nw + n];
+        const float en32 = (float)en;
+        const float cut32 = (float)(kDeltaCut * a.sigma) + 1e-4f;
+        const double ycut2 = kDeltaCut * kDeltaCut;
+        const double is = 1.0 / a.sigma;
+        const int64_t q0 = (int64_t)blockIdx.x * a.qpb * a.qiters;
+        for (int it = 0; it < a.qiters; ++it) {
+            const int64_t q = q0 + (int64_t)it * a.qpb + ql;
+            if (q >= a.Nq) break;
+            const int64_t kq = kplusq_index(k, q, a.kg, a.qg);
+            // 1. screening mask over (nu, m), nu-major
+            float em32[kMaxNw];
 #pragma unroll
-                for (int i = 0; i < kMaxNw; ++i)
-                    if (i < a.nw) cfma(gv[i], cc, Cq[(ka * a.nw + i) * a.nw + n]);
+            for (int m = 0; m < kMaxNw; ++m) em32[m] = (m < nw) ? a.eps32[kq * nw + m] : 0.f;
+            uint32_t live[kMaxNmode];
+            bool any = false;
+            for (int v = 0; v < nm; ++v) {
+                const float w = a.hw32[q * nm + v];
+                uint32_t bits = 0;
+                if (w >= (float)kOmegaMinEv) {
+#pragma unroll
+                    for (int m = 0; m < kMaxNw; ++m) {
+                        if (m < nw) {
+                            const float d = en32 - em32[m];
+                            if (fabsf(d - w) <= cut32 || fabsf(d + w) <= cut32) bits |= 1u << m;
+                        }
+                    }
+                }
+                live[v] = bits;
+                any |= bits != 0;
             }
-            const double kT = kBoltzEvK * a.T;
-            const double N = 1.0 / expm1(w / kT);
-            const double en = a.eps[k * a.nw + n];
-            const double cut = kDeltaCut * a.sigma;
-            const double is = 1.0 / a.sigma;
-            const T2 *Ukq = (const T2 *)a.U + kq * a.nw * a.nw;
-            for (int m = 0; m < a.nw; ++m) {
-                const double em = a.eps[kq * a.nw + m];
-                const double xe = en - w - em, xa = en + w - em;
-                const bool le = fabs(xe) <= cut, la = fabs(xa) <= cut;
-                if (!(le || la)) continue;
-                T2 g = cmake<T>(0, 0);
+            if (!any) continue;
+            const T2 *Cn = (const T2 *)a.C + ((int64_t)b * a.Nq + q) * ncol + (int64_t)n * nm * nw;
+            const T2 *Ukq = (const T2 *)a.U + kq * nw * nw;
+            for (int v = 0; v < nm; ++v) {
+                if (!live[v]) continue;
+                // 2. mode projection for this nu
+                const T2 *cf = (const T2 *)a.coef + (q * nm + v) * nm;
+                T2 gv[kMaxNw];
 #pragma unroll
-                for (int i = 0; i < kMaxNw; ++i)
-                    if (i < a.nw) cfma_conj(g, Ukq[i * a.nw + m], gv[i]);
-                const double g2 = (double)cabs2(g);
-                const double fm = 1.0 / (exp((em - a.mu) / kT) + 1.0);
-                double W = 0.0;
-                if (le) W += exp(-(xe * is) * (xe * is)) * (1.0 + N - fm);
-                if (la) W += exp(-(xa * is) * (xa * is)) * (N + fm);
-                acc += g2 * W;
+                for (int i = 0; i < kMaxNw; ++i) gv[i] = cmake<T>(0, 0);
+                for (int ka = 0; ka < nm; ++ka) {
+                    const T2 cc = cf[ka];
+#pragma unroll
+                    for (int i = 0; i < kMaxNw; ++i)
+                        if (i < nw) cfma(gv[i], cc, Cn[ka * nw + i]);
+                }
+                const double w = a.hw[q * nm + v];
+                const T N = (T)a.nbe[q * nm + v];
+                // 3. rotation and weights for the surviving m
+                uint32_t bits = live[v];
+                while (bits) {
+                    const int m = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    T2 g = cmake<T>(0, 0);
+#pragma unroll
+                    for (int i = 0; i < kMaxNw; ++i)
+                        if (i < nw) cfma_conj(g, Ukq[i * nw + m], gv[i]);
+                    const T g2 = cabs2(g);
+                    const double d = en - a.eps[kq * nw + m];
+                    const double ye = (d - w) * is, ya = (d + w) * is;
+                    const T fm = (T)a.focc[kq * nw + m];
+                    T W = 0;
+                    if (ye * ye <= ycut2) W += gauss<T>(ye * ye) * ((T)1 + N - fm);
+                    if (ya * ya <= ycut2) W += gauss<T>(ya * ya) * (N + fm);
+                    acc[v] += (double)(g2 * W);
+                }
             }
         }
     }
-    red[t] = acc;
+    // block reduction over q (fixed order)
+    const int per = nm * nw;
+    for (int v = 0; v < nm; ++v) red[(ql * nm + v) * nw + n] = (ql < a.qpb) ? acc[v] : 0.0;
     __syncthreads();
-    if (ql == 0 && t < per) {
-        double s = 0.0;
-        for (int l = 0; l < a.qpb; ++l) s += red[l * per + r];
-        a.partial[((int64_t)b * a.nqblk + blockIdx.x) * per + r] = s;
+    for (int r = threadIdx.x; r < per; r += blockDim.x) {
+        double sum = 0.0;
+        for (int l = 0; l < a.qpb; ++l) sum += red[l * per + r];
+        a.partial[((int64_t)b * a.nqblk + blockIdx.x) * per + r] = sum;
     }
 }
 
 pgb_status launch_rates_epilogue(pgb_ctx *c, bool fp32, const RatesArgs &a) {
-    const int per = a.nm * a.nw;
-    const int threads = a.qpb * per;
+    const int threads = a.qpb * a.nw;
     dim3 grid((unsigned int)a.nqblk, (unsigned int)a.nb);
-    const size_t sh = (size_t)threads * sizeof(double);
+    const size_t sh = (size_t)a.qpb * a.nm * a.nw * sizeof(double);
     if (fp32)
         k_rates_epilogue<float><<<grid, threads, sh, c->stream>>>(a);
     else
@@ -426,31 +469,70 @@ pgb_status launch_rates_epilogue(pgb_ctx *c, bool fp32, const RatesArgs &a) {
     return PGB_OK;
 }
 
-// gamma_mode[b][nu][n] = scale * sum_blk partial[b][blk][nu][n]; gamma[b][n] = sum_nu
-__global__ void k_rates_reduce(int64_t nb, int64_t nqblk, int nm, int nw, double scale,
-                               const double *__restrict__ partial, double *__restrict__ gamma,
+// Occupation and screening tables for one rates call:
+//   focc[k][n] = 1/(e^{(e-mu)/kT} + 1), eps32 = (float)eps;  nbe[q][nu] = 1/(e^{hw/kT} - 1), hw32.
+__global__ void k_occ_tables(int64_t Nk, int nw, int64_t Nq, int nm, const double *__restrict__ eps,
+                             const double *__restrict__ hw, double T, double mu, double *__restrict__ focc,
+                             float *__restrict__ eps32, double *__restrict__ nbe, float *__restrict__ hw32) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double kT = kBoltzEvK * T;
+    if (t < Nk * nw) {
+        const double e = eps[t];
+        focc[t] = 1.0 / (exp((e - mu) / kT) + 1.0);
+        eps32[t] = (float)e;
+    }
+    if (t < Nq * nm) {
+        const double w = hw[t];
+        nbe[t] = (w >= kOmegaMinEv) ? 1.0 / expm1(w / kT) : 0.0;
+        hw32[t] = (float)w;
+    }
+}
+
+pgb_status launch_occ_tables(pgb_ctx *c, double T, double mu, double *focc, float *eps32, double *nbe,
+                             float *hw32) {
+    const int64_t n = std::max<int64_t>(c->Nk * c->nw, c->Nq * c->nm);
+    k_occ_tables<<<div_up(n, 256), 256, 0, c->stream>>>(c->Nk, c->nw, c->Nq, c->nm, c->d_eps, c->d_hw, T, mu,
+                                                         focc, eps32, nbe, hw32);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+// gamma_mode[b][nu][n] = scale * sum_blk partial[b][blk][nu][n]: one block per
+// (b, nu, n), strided partial sums then a shared-memory tree (fixed order).
+__global__ void k_rates_reduce(int64_t nqblk, int per, double scale, const double *__restrict__ partial,
                                double *__restrict__ gamma_mode) {
+    __shared__ double sh[256];
+    const int64_t b = blockIdx.y;
+    const int r = blockIdx.x;
+    double s = 0.0;
+    for (int64_t blk = threadIdx.x; blk < nqblk; blk += blockDim.x) s += partial[(b * nqblk + blk) * per + r];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gamma_mode[b * per + r] = scale * sh[0];
+}
+
+__global__ void k_rates_modesum(int64_t nb, int nm, int nw, const double *__restrict__ gamma_mode,
+                                double *__restrict__ gamma) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nb * nw) return;
     const int64_t b = t / nw;
     const int n = (int)(t % nw);
-    const int per = nm * nw;
-    double tot = 0.0;
-    for (int nu = 0; nu < nm; ++nu) {
-        double s = 0.0;
-        for (int64_t blk = 0; blk < nqblk; ++blk) s += partial[(b * nqblk + blk) * per + nu * nw + n];
-        s *= scale;
-        if (gamma_mode) gamma_mode[(b * nm + nu) * nw + n] = s;
-        tot += s;
-    }
-    gamma[b * nw + n] = tot;
+    double s = 0.0;
+    for (int v = 0; v < nm; ++v) s += gamma_mode[(b * nm + v) * nw + n];
+    gamma[t] = s;
 }
 
 pgb_status launch_rates_reduce(pgb_ctx *c, int64_t nb, int64_t nqblk, int nm, int nw, double scale,
                                const double *partial, double *gamma, double *gamma_mode) {
     if (nb == 0) return PGB_OK;
-    k_rates_reduce<<<div_up(nb * nw, 128), 128, 0, c->stream>>>(nb, nqblk, nm, nw, scale, partial, gamma,
-                                                                  gamma_mode);
+    dim3 grid((unsigned int)(nm * nw), (unsigned int)nb);
+    k_rates_reduce<<<grid, 256, 0, c->stream>>>(nqblk, nm * nw, scale, partial, gamma_mode);
+    PGB_LAUNCH_CHECK(c);
+    k_rates_modesum<<<div_up(nb * nw, 128), 128, 0, c->stream>>>(nb, nm, nw, gamma_mode, gamma);
     PGB_LAUNCH_CHECK(c);
     return PGB_OK;
 }
@@ -479,7 +561,7 @@ __global__ void k_g_epilogue(GArgs a) {
         const T2 cc = cf[ka];
 #pragma unroll
         for (int i = 0; i < kMaxNw; ++i)
-            if (i < a.nw) cfma(gv[i], cc, Cq[(ka * a.nw + i) * a.nw + n]);
+            if (i < a.nw) cfma(gv[i], cc, Cq[(n * a.nm + ka) * a.nw + i]);
     }
     const T2 *U = (const T2 *)a.Ukq + pair * a.nw * a.nw;
     for (int m = 0; m < a.nw; ++m) {
