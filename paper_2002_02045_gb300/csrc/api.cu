@@ -162,6 +162,9 @@ void free_grids(pgb_ctx *c) {
     dfree(&c->d_coef32);
     dfree(&c->d_phq64);
     dfree(&c->d_phq32);
+    if (c->d_asplit) cudaFree(c->d_asplit);
+    c->d_asplit = nullptr;
+    c->asplit_prec = -1;
     c->has_grids = false;
 }
 
@@ -266,6 +269,7 @@ void pgb_destroy(pgb_ctx *c) {
     free_grids(c);
     free_model(c);
     if (c->scratch) cudaFree(c->scratch);
+    if (c->d_err) cudaFree(c->d_err);
     for (auto &v : c->prof_ev)
         for (auto e : v) cudaEventDestroy(e);
     delete c;
@@ -597,14 +601,20 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
     if (nk < 0) return fail(c, PGB_EINVAL, "scattering_rates: negative nk");
     if (!(T > 0.0) || !(sigma > 0.0) || !std::isfinite(mu))
         return fail(c, PGB_EINVAL, "scattering_rates: need T > 0, sigma > 0, finite mu");
-    if (precision != PGB_FP64 && precision != PGB_FP32)
-        return fail(c, PGB_EINVAL, "scattering_rates: tensor-core precisions are not available in this build");
+    if (precision < PGB_FP64 || precision > PGB_TC_BF16X3)
+        return fail(c, PGB_EINVAL, "scattering_rates: unknown precision");
+    const bool tcp = precision == PGB_TC_TF32X3 || precision == PGB_TC_BF16X3;
+    const bool tf32 = precision == PGB_TC_TF32X3;
+    if (tcp && !tc_supported(c->nm * c->nw * c->nw))
+        return fail(c, PGB_EINVAL, "scattering_rates: tensor-core path needs nmode*nw*nw to be a multiple of 96");
     if (nk == 0) return PGB_OK;
     if (!gamma_out) return fail(c, PGB_EINVAL, "scattering_rates: null gamma_out");
-    const bool f32 = precision == PGB_FP32;
+    const bool f32 = precision != PGB_FP64;
     const int nw = c->nw, nm = c->nm, nw2 = nw * nw;
     const int64_t ncol = (int64_t)nm * nw2, nrow = (int64_t)c->nRgp * ncol;
     const size_t es = f32 ? sizeof(float2) : sizeof(double2);
+    const int Kp = tc_kpad(c->nRgp);
+    const size_t tes = tf32 ? 4 : 2;
 
     // k list: validate on the host
     std::vector<int32_t> hk(nk);
@@ -637,19 +647,33 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
     const int qpb = std::max(1, 256 / nw);
     const int qiters = 8;
     const int64_t nqblk = (c->Nq + (int64_t)qpb * qiters - 1) / ((int64_t)qpb * qiters);
-    const size_t per_k = (size_t)(2 * nrow + c->Nq * ncol + c->nRge) * es + (size_t)nqblk * per * sizeof(double) +
-                         (size_t)per * sizeof(double);
+    // scratch carve-up, every piece 256-byte aligned (TMA and vector loads)
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    int64_t nbmax = 0;
+    size_t o_S1 = 0, o_G = 0, o_C = 0, o_part = 0, o_gm = 0, o_B = 0, total = 0;
+    auto layout = [&](int64_t nbm) {
+        o_S1 = al((size_t)nbm * c->nRge * es);
+        o_G = o_S1 + al((size_t)nbm * nrow * es);
+        o_C = o_G + al((size_t)nbm * nrow * es);
+        o_part = o_C + al((size_t)nbm * c->Nq * ncol * es);
+        o_gm = o_part + al((size_t)nbm * nqblk * per * sizeof(double));
+        o_B = o_gm + al((size_t)nbm * per * sizeof(double));
+        total = o_B + (tcp ? al((size_t)nbm * 4 * ncol * Kp * tes) : 0);
+    };
+    layout(1);
     const size_t budget = (size_t)4 << 30;
-    int64_t nbmax = std::max<int64_t>(1, (int64_t)(budget / per_k));
+    nbmax = std::max<int64_t>(1, (int64_t)(budget / total));
     nbmax = std::min<int64_t>(nbmax, std::min<int64_t>(nk, 65535));
-    TRY(ensure_scratch(c, nbmax * per_k));
+    layout(nbmax);
+    TRY(ensure_scratch(c, total));
     char *base = (char *)c->scratch;
     char *phk = base;
-    char *S1 = phk + (size_t)nbmax * c->nRge * es;
-    char *G = S1 + (size_t)nbmax * nrow * es;
-    char *Cb = G + (size_t)nbmax * nrow * es;
-    double *partial = (double *)(Cb + (size_t)nbmax * c->Nq * ncol * es);
-    double *gmode_tmp = partial + (size_t)nbmax * nqblk * per;
+    char *S1 = base + o_S1;
+    char *G = base + o_G;
+    char *Cb = base + o_C;
+    double *partial = (double *)(base + o_part);
+    double *gmode_tmp = (double *)(base + o_gm);
+    void *Bsplit = base + o_B;
     Tmp<double> focc, nbe;
     Tmp<float> eps32, hw32;
     TRY(focc.alloc(c, (size_t)c->Nk * nw));
@@ -657,6 +681,22 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
     TRY(nbe.alloc(c, (size_t)c->Nq * nm));
     TRY(hw32.alloc(c, (size_t)c->Nq * nm));
     TRY(launch_occ_tables(c, T, mu, focc.p, eps32.p, nbe.p, hw32.p));
+    if (tcp) {
+        if (!c->d_err) {
+            PGB_CUDA_TRY(c, cudaMalloc((void **)&c->d_err, sizeof(int)));
+        }
+        PGB_CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+        if (c->asplit_prec != precision) {
+            if (c->d_asplit) {
+                PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+                cudaFree(c->d_asplit);
+                c->d_asplit = nullptr;
+            }
+            PGB_CUDA_TRY(c, cudaMalloc(&c->d_asplit, (size_t)4 * c->Nq * Kp * tes));
+            TRY(launch_split_phases(c, tf32, c->qg, c->Nq, c->d_Rgp, c->nRgp, Kp, c->d_asplit));
+            c->asplit_prec = precision;
+        }
+    }
     const void *g = f32 ? (const void *)c->d_g32 : (const void *)c->d_g64;
     const void *U = f32 ? (const void *)c->d_U32 : (const void *)c->d_U;
     const void *cf = f32 ? (const void *)c->d_coef32 : (const void *)c->d_coef;
@@ -669,10 +709,17 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
         TRY(launch_cgemm(c, f32, 1, nb, nrow, c->nRge, phk, c->nRge, 0, g, nrow, 0, S1, nrow, 0));
         TRY(launch_fold_u(c, f32, nb, kb, c->nRgp, nm, nw, S1, U, G));
         prof_mark(c, PGB_PROF_RSUM);
-        prof_mark(c, PGB_PROF_QSUM);
-        TRY(launch_cgemm(c, f32, nb, c->Nq, ncol, c->nRgp, phq, c->nRgp, 0, G, ncol, nrow, Cb, ncol,
-                         c->Nq * ncol));
-        prof_mark(c, PGB_PROF_QSUM);
+        if (tcp) {
+            TRY(launch_split_g(c, tf32, nb, c->nRgp, (int)ncol, Kp, G, Bsplit));
+            prof_mark(c, PGB_PROF_QSUM);
+            TRY(launch_tc_qsum(c, tf32, nb, c->Nq, (int)ncol, Kp, c->d_asplit, Bsplit, (float2 *)Cb, c->d_err));
+            prof_mark(c, PGB_PROF_QSUM);
+        } else {
+            prof_mark(c, PGB_PROF_QSUM);
+            TRY(launch_cgemm(c, f32, nb, c->Nq, ncol, c->nRgp, phq, c->nRgp, 0, G, ncol, nrow, Cb, ncol,
+                             c->Nq * ncol));
+            prof_mark(c, PGB_PROF_QSUM);
+        }
         RatesArgs ra;
         ra.nb = nb;
         ra.kidx = kb;
@@ -704,6 +751,13 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
         prof_mark(c, PGB_PROF_EPILOGUE);
         TRY(launch_rates_reduce(c, nb, nqblk, nm, nw, scale, partial, Gm.dev + b0 * nw,
                                 Gmm.dev ? Gmm.dev + b0 * nm * nw : gmode_tmp));
+    }
+    if (tcp) {
+        int herr = 0;
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        if (herr) return fail(c, PGB_ETIMEOUT, "scattering_rates: a tensor-core pipeline wait ran out (bits " +
+                                                   std::to_string(herr) + ")");
     }
     TRY(Gm.finish());
     TRY(Gmm.finish());

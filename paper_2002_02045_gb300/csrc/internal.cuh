@@ -64,6 +64,9 @@ struct pgb_ctx {
     float2 *d_coef32 = nullptr;
     double2 *d_phq64 = nullptr;  // [Nq][nRgp] exp(i q.Rp), built on first use
     float2 *d_phq32 = nullptr;
+    void *d_asplit = nullptr;    // [4][Nq][Kp] hi/lo split phases for the tensor-core q-sum
+    int asplit_prec = -1;        // precision the split was built for
+    int *d_err = nullptr;        // device error word of the tensor-core kernels
 
     // collision list
     bool has_coll = false;
@@ -187,6 +190,15 @@ pgb_status launch_kplusq_pts(pgb_ctx *c, const double *d_k, int64_t nk, const do
                              double *d_kq);
 pgb_status launch_window(pgb_ctx *c, const double *d_eps, int64_t Nk, int nw, double lo, double hi,
                          int32_t *d_flag);
+
+// tensor-core q-sum (tc_qsum.cu)
+int tc_kpad(int nR);
+bool tc_supported(int ncol);
+pgb_status launch_split_phases(pgb_ctx *c, bool tf32, const int grid[3], int64_t Nq, const int32_t *d_R, int nR,
+                               int Kp, void *out);
+pgb_status launch_split_g(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out);
+pgb_status launch_tc_qsum(pgb_ctx *c, bool tf32, int64_t nb, int64_t Nq, int ncol, int Kp, void *Asplit,
+                          void *Bsplit, float2 *C, int *d_err);
 
 // collision kernels (collision.cu)
 pgb_status launch_coll_coeffs(pgb_ctx *c, double T, double sigma, const int32_t *row, const int32_t *col,

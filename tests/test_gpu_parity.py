@@ -221,6 +221,28 @@ def test_rates_c2_reduced_fp32(ctx, c2):
     assert_rates_close(gam.cpu().numpy(), ref, 1e-5, label="c2 reduced")
 
 
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-3), ("tf32x3", 1e-5)])
+def test_rates_c2_reduced_tensor_core(ctx, c2, prec, tol):
+    """Tensor-core q-sum (tcgen05, split precision) against the oracle; the
+    10^3 q grid leaves a ragged last tile of 104 q."""
+    from paper_2002_02045_gb300 import PRECISIONS
+    T, sig = 300.0, 0.010
+    kg, qg = (20, 20, 20), (10, 10, 10)
+    ctx.pgb_set_model(c2)
+    ctx.pgb_set_grids(kg, qg)
+    e_ref, _ = O.bands(c2, S.mp_grid(*kg))
+    emin = e_ref.min()
+    mu = emin - 0.3
+    win = np.nonzero(((e_ref >= emin + 1e-9) & (e_ref <= emin + 0.3 - 1e-9)).any(1))[0].astype(np.int32)
+    sample = win[:: max(1, len(win) // 9)][:9]
+    gam = empty((len(sample), 8))
+    gmode = empty((len(sample), 6, 8))
+    ctx.pgb_scattering_rates(dev(sample), T, mu, sig, PRECISIONS[prec], gam, gmode)
+    ref = O.scattering_rates_grid(c2, kg, qg, sample, T, mu, sig)
+    assert_rates_close(gam.cpu().numpy(), ref, tol, label=f"c2 reduced {prec}")
+    assert np.allclose(gmode.cpu().numpy().sum(1), gam.cpu().numpy(), rtol=1e-13)
+
+
 @pytest.mark.slow
 def test_rates_c2_full_size_sampled(ctx, c2):
     """Full 40^3 x 40^3 workload over the whole 0.3 eV window, as the bench runs
