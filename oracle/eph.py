@@ -234,15 +234,15 @@ def scattering_rates_grid(model, kgrid, qgrid, k_indices, T, mu, sigma, mode_res
     nq = len(qpts)
     eps_all, U_all = bands(model, kpts_all)
     hw, e = phonons(model, qpts)
-    kq_index = _kplusq_index(kg, qg)
     nw, nm = model.nw, model.nmode
     out = np.zeros((len(k_indices), nm, nw)) if mode_resolved else np.zeros((len(k_indices), nw))
     q_chunk = q_chunk or nq
     for a, ik in enumerate(k_indices):
         k = kpts_all[ik:ik + 1]
+        kq_row = _kplusq_row(kg, qg, ik)
         for q0 in range(0, nq, q_chunk):
             qs = slice(q0, min(nq, q0 + q_chunk))
-            ikq = kq_index[ik, qs]
+            ikq = kq_row[qs]
             gw = g_wannier(model, k, qpts[qs])[0]                  # [nq, nm, nw, nw]
             gb = g_bloch(gw, U_all[ik][None], U_all[ikq])
             gm = g_modes(gb, hw[qs], e[qs], model.mass)
@@ -251,6 +251,17 @@ def scattering_rates_grid(model, kgrid, qgrid, k_indices, T, mu, sigma, mode_res
                                  T, mu, sigma, nq, mode_resolved)
             out[a] += r[0]
     return out
+
+
+def _kplusq_row(kgrid, qgrid, ik):
+    """Index of k+q on the k grid for one k-grid point and every q-grid point."""
+    kg = np.asarray(kgrid)
+    qg = np.asarray(qgrid)
+    assert np.all(kg % qg == 0), "q grid must divide the k grid"
+    k = np.array([ik // (kg[1] * kg[2]), (ik // kg[2]) % kg[1], ik % kg[2]])
+    qi = np.stack(np.meshgrid(*[np.arange(n) for n in qg], indexing="ij"), -1).reshape(-1, 3)
+    s = (k[None, :] + qi * (kg // qg)) % kg
+    return (s[:, 0] * kg[1] + s[:, 1]) * kg[2] + s[:, 2]
 
 
 def _kplusq_index(kgrid, qgrid):

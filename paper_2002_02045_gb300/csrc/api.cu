@@ -157,6 +157,7 @@ void free_grids(pgb_ctx *c) {
     dfree(&c->d_eps);
     dfree(&c->d_U);
     dfree(&c->d_U32);
+    dfree(&c->d_U32T);
     dfree(&c->d_hw);
     dfree(&c->d_coef);
     dfree(&c->d_coef32);
@@ -433,6 +434,7 @@ pgb_status pgb_set_grids(pgb_ctx *c, const int kgrid[3], const int qgrid[3]) {
     TRY(dalloc(c, &c->d_eps, (size_t)c->Nk * c->nw));
     TRY(dalloc(c, &c->d_U, (size_t)c->Nk * nw2));
     TRY(dalloc(c, &c->d_U32, (size_t)c->Nk * nw2));
+    TRY(dalloc(c, &c->d_U32T, (size_t)c->Nk * nw2));
     TRY(dalloc(c, &c->d_hw, (size_t)c->Nq * c->nm));
     TRY(dalloc(c, &c->d_coef, (size_t)c->Nq * nm2));
     TRY(dalloc(c, &c->d_coef32, (size_t)c->Nq * nm2));
@@ -468,6 +470,15 @@ pgb_status pgb_set_grids(pgb_ctx *c, const int kgrid[3], const int qgrid[3]) {
         TRY(launch_phonon_coef(c, c->Nq, c->nm, lam.p, ev.p, c->d_mode_scale, c->d_hw, c->d_coef));
     }
     TRY(launch_to_f32(c, c->d_U, c->d_U32, c->Nk * nw2));
+    TRY(launch_transpose_u(c));
+    {   // energy shift of the FP32 tables: every shifted band energy >= 1 eV
+        std::vector<double> e((size_t)c->Nk * c->nw);
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(e.data(), c->d_eps, 8 * e.size(), cudaMemcpyDeviceToHost, c->stream));
+        PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        double lo = e.empty() ? 0.0 : e[0];
+        for (double x : e) lo = std::min(lo, x);
+        c->eps_ref = std::floor(lo) - 1.0;
+    }
     TRY(launch_to_f32(c, c->d_coef, c->d_coef32, c->Nq * nm2));
     PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     c->has_grids = true;
@@ -644,9 +655,10 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
     }
 
     const int per = nm * nw;
+    const bool fused = tcp && tc_fused_supported(nw, nm);
     const int qpb = std::max(1, 256 / nw);
     const int qiters = 8;
-    const int64_t nqblk = (c->Nq + (int64_t)qpb * qiters - 1) / ((int64_t)qpb * qiters);
+    const int64_t nqblk = fused ? (c->Nq + 127) / 128 : (c->Nq + (int64_t)qpb * qiters - 1) / ((int64_t)qpb * qiters);
     // scratch carve-up, every piece 256-byte aligned (TMA and vector loads)
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     int64_t nbmax = 0;
@@ -655,7 +667,7 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
         o_S1 = al((size_t)nbm * c->nRge * es);
         o_G = o_S1 + al((size_t)nbm * nrow * es);
         o_C = o_G + al((size_t)nbm * nrow * es);
-        o_part = o_C + al((size_t)nbm * c->Nq * ncol * es);
+        o_part = o_C + (fused ? 0 : al((size_t)nbm * c->Nq * ncol * es));
         o_gm = o_part + al((size_t)nbm * nqblk * per * sizeof(double));
         o_B = o_gm + al((size_t)nbm * per * sizeof(double));
         total = o_B + (tcp ? al((size_t)nbm * 4 * ncol * Kp * tes) : 0);
@@ -681,6 +693,15 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
     TRY(nbe.alloc(c, (size_t)c->Nq * nm));
     TRY(hw32.alloc(c, (size_t)c->Nq * nm));
     TRY(launch_occ_tables(c, T, mu, focc.p, eps32.p, nbe.p, hw32.p));
+    Tmp<float2> ehl, whl;
+    Tmp<float> focc32, nbe32;
+    if (fused) {
+        TRY(ehl.alloc(c, (size_t)c->Nk * nw));
+        TRY(focc32.alloc(c, (size_t)c->Nk * nw));
+        TRY(whl.alloc(c, (size_t)c->Nq * nm));
+        TRY(nbe32.alloc(c, (size_t)c->Nq * nm));
+        TRY(launch_fp32_tables(c, focc.p, nbe.p, ehl.p, focc32.p, whl.p, nbe32.p));
+    }
     if (tcp) {
         if (!c->d_err) {
             PGB_CUDA_TRY(c, cudaMalloc((void **)&c->d_err, sizeof(int)));
@@ -709,6 +730,26 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
         TRY(launch_cgemm(c, f32, 1, nb, nrow, c->nRge, phk, c->nRge, 0, g, nrow, 0, S1, nrow, 0));
         TRY(launch_fold_u(c, f32, nb, kb, c->nRgp, nm, nw, S1, U, G));
         prof_mark(c, PGB_PROF_RSUM);
+        if (fused) {
+            TRY(launch_split_g(c, tf32, nb, c->nRgp, (int)ncol, Kp, G, Bsplit));
+            FusedLaunch L;
+            L.nb = nb;
+            L.kidx = kb;
+            L.Kp = Kp;
+            L.Bsplit = Bsplit;
+            L.ehl = ehl.p;
+            L.focc32 = focc32.p;
+            L.whl = whl.p;
+            L.nbe32 = nbe32.p;
+            L.sigma = sigma;
+            L.partial = partial;
+            prof_mark(c, PGB_PROF_QSUM);
+            TRY(launch_tc_rates(c, tf32, L));
+            prof_mark(c, PGB_PROF_QSUM);
+            TRY(launch_rates_reduce(c, nb, nqblk, nm, nw, scale, partial, Gm.dev + b0 * nw,
+                                    Gmm.dev ? Gmm.dev + b0 * nm * nw : gmode_tmp));
+            continue;
+        }
         if (tcp) {
             TRY(launch_split_g(c, tf32, nb, c->nRgp, (int)ncol, Kp, G, Bsplit));
             prof_mark(c, PGB_PROF_QSUM);

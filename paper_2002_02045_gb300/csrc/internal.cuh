@@ -56,9 +56,11 @@ struct pgb_ctx {
     bool has_grids = false;
     int kg[3] = {0, 0, 0}, qg[3] = {0, 0, 0};
     int64_t Nk = 0, Nq = 0;
+    double eps_ref = 0.0;        // band-energy shift of the FP32 (hi, lo) energy tables
     double *d_eps = nullptr;     // [Nk][nw]
     double2 *d_U = nullptr;      // [Nk][nw][nw], U[i][n]
     float2 *d_U32 = nullptr;
+    float2 *d_U32T = nullptr;    // [Nk][n][i] (transpose, FP32) for the fused tensor-core epilogue
     double *d_hw = nullptr;      // [Nq][nm]
     double2 *d_coef = nullptr;   // [Nq][nm(nu)][nm(ka)] zero-point-scaled eigenvectors
     float2 *d_coef32 = nullptr;
@@ -199,6 +201,25 @@ pgb_status launch_split_phases(pgb_ctx *c, bool tf32, const int grid[3], int64_t
 pgb_status launch_split_g(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out);
 pgb_status launch_tc_qsum(pgb_ctx *c, bool tf32, int64_t nb, int64_t Nq, int ncol, int Kp, void *Asplit,
                           void *Bsplit, float2 *C, int *d_err);
+
+// fused tensor-core rates (tc_rates.cu)
+struct FusedLaunch {
+    int64_t nb;
+    const int32_t *kidx;
+    int Kp;
+    void *Bsplit;
+    const float2 *ehl;     // [Nk][nw] (e - e_ref) as hi + lo floats
+    const float *focc32;   // [Nk][nw]
+    const float2 *whl;     // [Nq][nm] hbar*omega as hi + lo floats
+    const float *nbe32;    // [Nq][nm]
+    double sigma;
+    double *partial;   // [nb][ceil(Nq/128)][nm][nw]
+};
+pgb_status launch_fp32_tables(pgb_ctx *c, const double *focc, const double *nbe, float2 *ehl, float *focc32,
+                              float2 *whl, float *nbe32);
+bool tc_fused_supported(int nw, int nm);
+pgb_status launch_tc_rates(pgb_ctx *c, bool tf32, const FusedLaunch &L);
+pgb_status launch_transpose_u(pgb_ctx *c);
 
 // collision kernels (collision.cu)
 pgb_status launch_coll_coeffs(pgb_ctx *c, double T, double sigma, const int32_t *row, const int32_t *col,

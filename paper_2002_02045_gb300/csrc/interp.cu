@@ -283,6 +283,24 @@ pgb_status launch_phonon_coef(pgb_ctx *c, int64_t nq, int nm, const double *d_ev
     return PGB_OK;
 }
 
+__global__ void k_transpose_u(int64_t Nk, int nw, const double2 *__restrict__ U, float2 *__restrict__ UT) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= Nk * nw * nw) return;
+    const int64_t k = t / (nw * nw);
+    const int r = (int)(t % (nw * nw));
+    const int n = r / nw, i = r % nw;
+    const double2 u = U[k * nw * nw + i * nw + n];
+    UT[t] = make_float2((float)u.x, (float)u.y);
+}
+
+pgb_status launch_transpose_u(pgb_ctx *c) {
+    const int64_t n = c->Nk * c->nw * c->nw;
+    if (n == 0) return PGB_OK;
+    k_transpose_u<<<div_up(n, 256), 256, 0, c->stream>>>(c->Nk, c->nw, c->d_U, c->d_U32T);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
 __global__ void k_to_f32(const double2 *__restrict__ s, float2 *__restrict__ d, int64_t n) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) d[t] = make_float2((float)s[t].x, (float)s[t].y);
@@ -493,6 +511,37 @@ pgb_status launch_occ_tables(pgb_ctx *c, double T, double mu, double *focc, floa
     const int64_t n = std::max<int64_t>(c->Nk * c->nw, c->Nq * c->nm);
     k_occ_tables<<<div_up(n, 256), 256, 0, c->stream>>>(c->Nk, c->nw, c->Nq, c->nm, c->d_eps, c->d_hw, T, mu,
                                                          focc, eps32, nbe, hw32);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+// FP32 tables of the fused tensor-core epilogue: energies shifted by eps_ref
+// (so that every shifted energy is at least 1 eV) split into hi + lo floats,
+// occupations rounded to FP32.
+__global__ void k_fp32_tables(int64_t Nk, int nw, int64_t Nq, int nm, const double *__restrict__ eps,
+                              const double *__restrict__ hw, double eps_ref, const double *__restrict__ focc,
+                              const double *__restrict__ nbe, float2 *__restrict__ ehl, float *__restrict__ focc32,
+                              float2 *__restrict__ whl, float *__restrict__ nbe32) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < Nk * nw) {
+        const double e = eps[t] - eps_ref;
+        const float hi = (float)e;
+        ehl[t] = make_float2(hi, (float)(e - (double)hi));
+        focc32[t] = (float)focc[t];
+    }
+    if (t < Nq * nm) {
+        const double w = hw[t];
+        const float hi = (float)w;
+        whl[t] = make_float2(hi, (float)(w - (double)hi));
+        nbe32[t] = (float)nbe[t];
+    }
+}
+
+pgb_status launch_fp32_tables(pgb_ctx *c, const double *focc, const double *nbe, float2 *ehl, float *focc32,
+                              float2 *whl, float *nbe32) {
+    const int64_t n = std::max<int64_t>(c->Nk * c->nw, c->Nq * c->nm);
+    k_fp32_tables<<<div_up(n, 256), 256, 0, c->stream>>>(c->Nk, c->nw, c->Nq, c->nm, c->d_eps, c->d_hw, c->eps_ref,
+                                                          focc, nbe, ehl, focc32, whl, nbe32);
     PGB_LAUNCH_CHECK(c);
     return PGB_OK;
 }

@@ -243,6 +243,27 @@ def test_rates_c2_reduced_tensor_core(ctx, c2, prec, tol):
     assert np.allclose(gmode.cpu().numpy().sum(1), gam.cpu().numpy(), rtol=1e-13)
 
 
+def test_rates_unfused_tensor_core_4band(ctx, c2):
+    """A 4-band cut of the fcc model (nmode*nw*nw = 96) runs the tensor-core
+    q-sum as its own kernel followed by the SIMT epilogue."""
+    from paper_2002_02045_gb300 import PRECISIONS
+    m = S.model_c2()
+    m.H = np.ascontiguousarray(m.H[:, :4, :4])
+    m.g = np.ascontiguousarray(m.g[..., :4, :4])
+    T, sig = 300.0, 0.010
+    kg, qg = (12, 12, 12), (6, 6, 6)
+    ctx.pgb_set_model(m)
+    ctx.pgb_set_grids(kg, qg)
+    e_ref, _ = O.bands(m, S.mp_grid(*kg))
+    mu = e_ref.min() - 0.3
+    sample = np.array([3, 200, 1000, 1727], np.int32)
+    ref = O.scattering_rates_grid(m, kg, qg, sample, T, mu, sig)
+    for prec, tol in (("bf16x3", 1e-3), ("tf32x3", 1e-5)):
+        gam = empty((4, 4))
+        ctx.pgb_scattering_rates(dev(sample), T, mu, sig, PRECISIONS[prec], gam)
+        assert_rates_close(gam.cpu().numpy(), ref, tol, label=f"4-band {prec}")
+
+
 @pytest.mark.slow
 def test_rates_c2_full_size_sampled(ctx, c2):
     """Full 40^3 x 40^3 workload over the whole 0.3 eV window, as the bench runs
@@ -259,16 +280,23 @@ def test_rates_c2_full_size_sampled(ctx, c2):
     n = ctx.pgb_window(emin, emin + 0.3, kbuf)
     assert 0.03 < n / 64000 < 0.07
     kidx = kbuf[:n].contiguous()
-    gam = empty((n, 8))
-    ctx.pgb_scattering_rates(kidx, T, emin - 0.3, sig, PGB_FP32, gam)
-    got = gam.cpu().numpy()
-    assert np.all(np.isfinite(got)) and np.all(got >= 0)
+    from paper_2002_02045_gb300 import PGB_TC_BF16X3
+    results = {}
+    for name, prec in (("fp32", PGB_FP32), ("bf16x3", PGB_TC_BF16X3)):
+        gam = empty((n, 8))
+        ctx.pgb_scattering_rates(kidx, T, emin - 0.3, sig, prec, gam)
+        got = gam.cpu().numpy()
+        assert np.all(np.isfinite(got)) and np.all(got >= 0)
+        results[name] = got
     pick = [0, n // 2, n - 1]
     kl = kidx.cpu().numpy()[pick]
     e_ref, _ = O.bands(c2, S.mp_grid(*g)[kl])
     assert np.abs(e_ref - eps.cpu().numpy()[kl]).max() < 1e-11
     ref = O.scattering_rates_grid(c2, g, g, kl, T, emin - 0.3, sig, q_chunk=16000)
-    assert_rates_close(got[pick], ref, 1e-5, label="c2 full size")
+    assert_rates_close(results["fp32"][pick], ref, 1e-5, label="c2 full size fp32")
+    assert_rates_close(results["bf16x3"][pick], ref, 1e-3, label="c2 full size bf16x3")
+    # every window k: the two GPU forms agree within the looser bound
+    assert_rates_close(results["bf16x3"], results["fp32"], 1e-3, label="bf16x3 vs fp32, all k")
 
 
 # ----------------------------------------------------------------------------
