@@ -152,6 +152,29 @@ pgb_status pgb_collision(pgb_ctx *ctx, const double *f, double *I_out);
 /* nsteps explicit RK4 steps (Sec. 2.1.1) of df/dt = I[f], step dt_fs, in place. */
 pgb_status pgb_step_rk4(pgb_ctx *ctx, double *f, double dt_fs, int64_t nsteps);
 
+/* Allocation-free scattering rates (no counterpart in the paper).
+ *
+ * For callers that cannot allocate device memory during the call - a host
+ * framework that has already handed the GPU's memory to its own pool, or a
+ * service whose request path forbids cudaMalloc because an allocation can
+ * synchronise the device.  Computes the same Gamma_nk as
+ * pgb_scattering_rates with precision PGB_FP32 (no mode-resolved output), but
+ * every temporary lives in one fixed device array of
+ * PGB_NOALLOC_SCRATCH_BYTES that the library holds on each GPU until the
+ * process exits; the call makes no allocation of any kind.
+ *   - k_idx [nk] and gamma_out [nk][nw] must be device pointers (no host
+ *     staging, since that would need a buffer); otherwise PGB_EINVAL.
+ *   - A grid whose scratch for a single k-point exceeds the array returns
+ *     PGB_EINVAL with the required size in pgb_last_error(); larger k lists
+ *     are processed in batches that fit.
+ *   - The first call on each device looks up the array's device address;
+ *     make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents: calls
+ *     that overlap on the GPU race and must be serialised by the caller.    */
+#define PGB_NOALLOC_SCRATCH_BYTES (64u << 20)
+pgb_status pgb_scattering_rates_noalloc(pgb_ctx *ctx, const int32_t *k_idx, int64_t nk, double T_K,
+                                        double mu_eV, double sigma_eV, double *gamma_out);
+
 /* Number of kernel launches this context has issued since creation.         */
 int64_t pgb_launch_count(const pgb_ctx *ctx);
 

@@ -28,7 +28,9 @@ ABI_SYMBOLS = (
     "pgb_set_grids", "pgb_get_grid_energies", "pgb_window", "pgb_interpolate_g",
     "pgb_scattering_rates", "pgb_build_collision", "pgb_collision_energies", "pgb_collision",
     "pgb_step_rk4", "pgb_launch_count", "pgb_profile", "pgb_profile_read",
+    "pgb_scattering_rates_noalloc",
 )
+PGB_NOALLOC_SCRATCH_BYTES = 64 << 20
 PROF_QSUM, PROF_RSUM, PROF_EPILOGUE, PROF_COLLISION, PROF_BANDS = 0, 1, 2, 3, 4
 
 
@@ -77,6 +79,7 @@ def load(path: str = LIB_PATH):
         "pgb_step_rk4": (I, [P, P, D, I64]),
         "pgb_launch_count": (I64, [P]),
         "pgb_profile": (I, [P, I]),
+        "pgb_scattering_rates_noalloc": (I, [P, P, I64, D, D, D, P]),
         "pgb_profile_read": (I, [P, I, C.POINTER(D), C.POINTER(I64)]),
         "pgb_diag_bands": (I, [P, P, I64, P, P, P]),
         "pgb_selftest_heevj": (I, [I, I, P, P, P]),
@@ -200,6 +203,12 @@ class Context:
         self._chk(self.lib.pgb_scattering_rates(self._h, _ptr(k_idx), len(k_idx), float(T), float(mu),
                                                 float(sigma), int(precision), _ptr(gamma_out),
                                                 _ptr(gamma_mode_out)))
+
+    def pgb_scattering_rates_noalloc(self, k_idx, T, mu, sigma, gamma_out):
+        _check_dtype(k_idx, "int32")
+        _check_dtype(gamma_out, "float64")
+        self._chk(self.lib.pgb_scattering_rates_noalloc(self._h, _ptr(k_idx), len(k_idx), float(T), float(mu),
+                                                        float(sigma), _ptr(gamma_out)))
 
     def pgb_build_collision(self, band_lo, band_hi, T, sigma, row, col, mode, g2):
         for a, k in ((row, "int32"), (col, "int32"), (mode, "int32"), (g2, "float32")):
