@@ -337,7 +337,7 @@ def evolve(f0, dt_fs, nsteps, rhs, method="rk4"):
 # (k, q)-pair scattering list on commensurate grids: Sec. 4.3
 # ----------------------------------------------------------------------------
 
-def collision_list_grid(model, grid, band_lo, band_hi, sigma=None, screen=0.0):
+def collision_list_grid(model, grid, band_lo, band_hi, sigma=None, screen=0.0, window=None):
     """All scattering terms between states (n, k) with k on ``grid`` and n in [band_lo, band_hi).
 
     States are numbered s = ik * nb + (n - band_lo).  The q grid equals the k
@@ -348,7 +348,8 @@ def collision_list_grid(model, grid, band_lo, band_hi, sigma=None, screen=0.0):
     |g|^2 by the hermiticity of the perturbation), so that the sum of I[f]
     over states vanishes to rounding.  With ``screen > 0`` a term is dropped
     when both Gaussian factors exp(-x^2/sigma^2) are below ``screen``; the
-    rule is symmetric between the two directions.
+    rule is symmetric between the two directions.  With ``window = (lo, hi)``
+    only states with lo <= eps <= hi take part (Sec. 4.3 energy window).
 
     Returns dict with row, col, mode (int arrays, ordered by row), g2, hw
     (float64), eps (state energies) and nq.
@@ -377,20 +378,29 @@ def collision_list_grid(model, grid, band_lo, band_hi, sigma=None, screen=0.0):
         g2_all[ik] = np.abs(gm) ** 2
     rows, cols, modes, vals, hws = [], [], [], [], []
     eps_state = eps_all[:, sel].reshape(-1)
+    inwin = np.ones(len(eps_state), bool)
+    if window is not None:
+        inwin = (eps_state >= window[0]) & (eps_state <= window[1])
     for ik in range(nk):
         for iq in range(nk):
             ikq = kq[ik, iq]
             for nu in range(nm):
                 for n in range(nb):
                     s = ik * nb + n
+                    if not inwin[s]:
+                        continue
                     for m in range(nb):
                         sp = ikq * nb + m
+                        if not inwin[sp]:
+                            continue
                         if s <= sp:
                             val = g2_all[ik, iq, nu, m, n]
                         else:
                             # reverse process: sp -> s at -q, initial band m, final band n
                             val = g2_all[ikq, negidx[iq], nu, n, m]
                         hw = hw_all[iq, nu]
+                        if hw < OMEGA_MIN_EV:
+                            continue      # carries no weight (acoustic modes at q = Gamma)
                         if screen > 0.0:
                             x1 = eps_state[s] - hw - eps_state[sp]
                             x2 = eps_state[s] + hw - eps_state[sp]
@@ -405,3 +415,47 @@ def collision_list_grid(model, grid, band_lo, band_hi, sigma=None, screen=0.0):
     return {"row": np.array(rows, np.int64)[order], "col": np.array(cols, np.int64)[order],
             "mode": np.array(modes, np.int64)[order], "g2": np.array(vals)[order],
             "hw": np.array(hws)[order], "eps": eps_state, "nq": nk, "nstates": nk * nb}
+
+
+def collision_rows(model, grid, band_lo, band_hi, states, f, T, sigma, window=None):
+    """I[f]_s (Eq. e_ph_scattering) for selected states s = ik*nb + (n - band_lo).
+
+    Sums over every q of the grid (= k grid), every final band m in
+    [band_lo, band_hi) whose state lies in the window, and every mode, with
+    |g_mn nu(k,q)|^2 interpolated at the initial k (no screening).  Needs only
+    the interpolation at the listed k-points, so it serves as a per-row check of
+    lists too large for ``collision_list_grid``.
+    """
+    from synthetic import mp_grid
+    g = np.asarray(grid)
+    pts = mp_grid(*g)
+    nk = len(pts)
+    nb = band_hi - band_lo
+    sel = slice(band_lo, band_hi)
+    eps_all, U_all = bands(model, pts)
+    hw_all, e_all = phonons(model, pts)
+    eps_state = eps_all[:, sel].reshape(-1)
+    inwin = np.ones(len(eps_state), bool)
+    if window is not None:
+        inwin = (eps_state >= window[0]) & (eps_state <= window[1])
+    f = np.asarray(f, np.float64)
+    N = bose_einstein(hw_all, T)                                   # [q, nu]
+    live = hw_all >= OMEGA_MIN_EV
+    out = []
+    for s in states:
+        ik, n = divmod(int(s), nb)
+        kq = _kplusq_row(g, g, ik)
+        gw = g_wannier(model, pts[ik:ik + 1], pts)[0]
+        gb = g_bloch(gw, U_all[ik][None], U_all[kq])
+        g2 = np.abs(g_modes(gb, hw_all, e_all, model.mass)[:, :, sel, sel][:, :, :, n]) ** 2       # [q, nu, m]
+        sp = kq[:, None] * nb + np.arange(nb)[None, :]              # [q, m]
+        fn, fm = f[s], f[sp][:, None, :]
+        en, em = eps_state[s], eps_state[sp][:, None, :]
+        w = hw_all[:, :, None]
+        Nq = N[:, :, None]
+        F_abs = fn * (1 - fm) * Nq - fm * (1 - fn) * (Nq + 1)
+        F_em = fn * (1 - fm) * (Nq + 1) - fm * (1 - fn) * Nq
+        term = g2 * (delta_gauss(en - w - em, sigma) * F_em + delta_gauss(en + w - em, sigma) * F_abs)
+        mask = live[:, :, None] & inwin[sp][:, None, :]
+        out.append(-TWO_PI_OVER_HBAR / nk * np.sum(np.where(mask, term, 0.0)))
+    return np.array(out)

@@ -117,3 +117,26 @@ def test_detailed_balance_ladder():
     # a non-equilibrium occupation does scatter
     I2 = O.collision(f0 * 1.1, L["eps"], L["row"], L["col"], L["hw"], L["g2"], T, sig, L["nq"])
     assert np.abs(I2).max() > 1e-3 * np.max(g * f0)
+
+
+def test_collision_rows_match_list_and_window():
+    # The per-row evaluation (interpolation at the initial k only) and the
+    # symmetric list give the same I_s; a window removes out-of-window states
+    # from both.
+    m = S.model_c1()
+    rng = np.random.default_rng(5)
+    L = O.collision_list_grid(m, (3, 3, 3), 0, 2)
+    f = rng.uniform(0, 1, L["nstates"])
+    I = O.collision(f, L["eps"], L["row"], L["col"], L["hw"], L["g2"], 300.0, 0.02, L["nq"])
+    rows = [1, 9, 30, 53]
+    r = O.collision_rows(m, (3, 3, 3), 0, 2, rows, f, 300.0, 0.02)
+    assert np.allclose(r, I[rows], rtol=1e-11, atol=1e-12 * np.abs(I).max())
+    win = (np.median(L["eps"]) - 0.5, np.median(L["eps"]) + 1.0)
+    Lw = O.collision_list_grid(m, (3, 3, 3), 0, 2, window=win)
+    inw = (L["eps"] >= win[0]) & (L["eps"] <= win[1])
+    assert inw.sum() < len(inw) and np.all(inw[Lw["row"]]) and np.all(inw[Lw["col"]])
+    Iw = O.collision(f, Lw["eps"], Lw["row"], Lw["col"], Lw["hw"], Lw["g2"], 300.0, 0.02, Lw["nq"])
+    sel = [s for s in range(54) if inw[s]][:4]
+    rw = O.collision_rows(m, (3, 3, 3), 0, 2, sel, f, 300.0, 0.02, window=win)
+    assert np.allclose(rw, Iw[sel], rtol=1e-11, atol=1e-12 * np.abs(Iw).max())
+    assert abs(Iw.sum()) < 1e-12 * np.abs(Iw).max() * len(Iw)
