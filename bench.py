@@ -177,6 +177,8 @@ def run_ours(args, rank, world, local):
     mu = emin - WIN
     kbuf = torch.empty((nk_grid,), dtype=torch.int32, device="cuda")
     nwin = ctx.pgb_window(emin, emin + WIN, kbuf)
+    if args.max_k:
+        nwin = min(nwin, args.max_k)
     kidx = kbuf[:nwin].contiguous()
     gam = torch.empty((nwin, model.nw), dtype=torch.float64, device="cuda")
     nq = nk_grid
@@ -226,14 +228,20 @@ def run_ours(args, rank, world, local):
         lanes = FP32_LANES if args.precision == "fp32" else 2   # FP64 units per SM on GB300 are few
         peak = SM_COUNT * lanes * 2 * SM_MAX_MHZ * 1e6 / 1e12
         roof = {"bound": "alu", "peak_source": f"derived: {SM_COUNT} SMs x {lanes} lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz"}
+    issue = 3.0 if args.precision in ("bf16x3", "tf32x3") else 1.0
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                 "traffic": None, "kernel": "q-sum (Fourier over R_p)",
-                 "algorithmic_flop_per_pair": flop_per_pair, "launches": q_n})
+                 "traffic": None,
+                 "kernel": ("fused q-sum + rotation/projection/Gamma epilogue (k_tc_rates)"
+                            if issue > 1 else "q-sum complex GEMM (k_cgemm)"),
+                 "algorithmic_flop_per_pair": flop_per_pair, "launches": q_n,
+                 "pairs_per_launch": pairs * args.steps / max(1, q_n),
+                 "issued_mma_achieved": achieved * issue, "issued_mma_frac": achieved * issue / peak})
     out = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3", "tf32x3": "tf32x3"}[args.precision],
         "data": "synthetic",
+        "tolerance_vs_fp64": {"bf16x3": 1e-3, "tf32x3": 1e-5, "fp32": 1e-5, "fp64": 1e-10}[args.precision],
         "config": {"workload": WORKLOAD, "kgrid": list(KGRID), "qgrid": list(KGRID), "nk_window": nwin,
                    "pairs_per_step": pairs, "precision": args.precision,
                    "l2": "inputs larger than L2 (g~ 446 MB, per-step intermediates > 1 GB)"},
@@ -243,6 +251,24 @@ def run_ours(args, rank, world, local):
         "roofline": roof, "gpu_launches": launches, "clocks": clk,
     }
 
+    if args.variants and rank == 0:
+        out["variants"] = {}
+        for name in ("tf32x3", "fp32"):
+            if name == args.precision:
+                continue
+            p2 = PRECISIONS[name]
+            ctx.pgb_scattering_rates(kidx, T_K, mu, SIGMA, p2, gam)
+            torch.cuda.synchronize()
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            ctx.pgb_scattering_rates(kidx, T_K, mu, SIGMA, p2, gam)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            out["variants"][name] = {"value": pairs / (v0.elapsed_time(v1) * 1e-3), "unit": "pairs/s",
+                                     "ms_per_step": v0.elapsed_time(v1),
+                                     "tolerance_vs_fp64": {"tf32x3": 1e-5, "fp32": 1e-5}[name]}
+    if args.dynamics:
+        out["dynamics"] = dynamics(ctx, model, args, world, peaks, peak_src)
     if args.e2e and rank == 0:
         out["e2e"] = e2e(ctx, model, prec, steps=1)
     if args.cpu_baseline and rank == 0 and world == 1:
@@ -253,6 +279,65 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+DYN_GRID = (30, 30, 30)
+DYN_WINDOW = 0.6
+
+
+def dynamics(ctx, model, args, world, peaks, peak_src):
+    """Real-time BTE on the 30^3 grid: two lowest bands, states within 0.6 eV of
+    the band minimum, list built on the device (untimed setup), then RK4 steps
+    of dt = 1 fs from the hot-carrier pulse (timed)."""
+    import torch
+    import synthetic as S
+    from paper_2002_02045_gb300.native import PROF_COLLISION
+    ctx.pgb_set_grids(DYN_GRID, DYN_GRID)
+    nk = int(np.prod(DYN_GRID))
+    eps = torch.empty((nk, model.nw), dtype=torch.float64, device="cuda")
+    ctx.pgb_get_grid_energies(eps, None)
+    emin = float(eps[:, :2].min())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nnz = ctx.pgb_build_collision_grid(0, 2, emin, emin + DYN_WINDOW, T_K, SIGMA)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    es = torch.empty((2 * nk,), dtype=torch.float64, device="cuda")
+    ctx.pgb_collision_energies(es)
+    f = torch.as_tensor(S.pulse_occupations(es.cpu().numpy(), emin)).cuda()
+    n0 = float(f.sum())
+    ctx.pgb_step_rk4(f, 1.0, 5)                       # warm-up
+    torch.cuda.synchronize()
+    ctx.pgb_profile(True)
+    ctx.pgb_profile_read(PROF_COLLISION)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.pgb_step_rk4(f, 1.0, args.dyn_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    k_ms, k_n = ctx.pgb_profile_read(PROF_COLLISION)
+    ctx.pgb_profile(False)
+    evals = 4 * args.dyn_steps
+    byte_per_entry = 12.0
+    achieved = byte_per_entry * nnz * evals / (k_ms * 1e-3) / 1e9
+    return {
+        "metric": "collision-entry evaluations/s (RK4, 4 evaluations per step)",
+        "value": world * nnz * evals / (ms * 1e-3), "unit": "entries/s",
+        "rk4_steps_per_s": world * args.dyn_steps / (ms * 1e-3), "steps": args.dyn_steps,
+        "ms_per_rk4_step": ms / args.dyn_steps, "nnz": nnz, "states": 2 * nk,
+        "config": {"workload": f"same model, {DYN_GRID[0]}^3 k = q grid, 2 lowest bands, states within "
+                               f"{DYN_WINDOW} eV of the band minimum, 7 sigma screen, dt = 1 fs, hot-carrier pulse",
+                   "list_build_s": build_s},
+        "carrier_number_drift": abs(float(f.sum()) - n0) / n0,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_collision",
+                     "peak_source": peak_src, "algorithmic_bytes_per_entry": byte_per_entry,
+                     "entries_per_launch": nnz, "launches": k_n},
+    }
 
 
 def e2e(ctx, model, prec, steps=1):
@@ -288,7 +373,14 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x3", "tf32x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "fp64", "bf16x3", "tf32x3"])
+    ap.add_argument("--no-dynamics", dest="dynamics", action="store_false",
+                    help="skip the real-time BTE (collision + RK4) measurement")
+    ap.add_argument("--dyn-steps", type=int, default=200)
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="skip the one-step TF32x3 and FP32 SIMT measurements")
+    ap.add_argument("--max-k", type=int, default=0,
+                    help="use only the first N window k-points (small case for profiler captures)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--kgrid", type=int, default=40, help="grid size per axis (40 = the workload; smaller "

@@ -143,6 +143,23 @@ pgb_status pgb_build_collision(pgb_ctx *ctx, int band_lo, int band_hi, double T_
                                int64_t nnz, const int32_t *row, const int32_t *col,
                                const int32_t *mode, const float *g2);
 
+/* Scattering list built on the device from the model (Sec. 4.3): states
+ * s = ik*nb + (n - band_lo) for every k-grid point and n in [band_lo,
+ * band_hi) (q grid = k grid); only states with e_lo <= eps <= e_hi take part
+ * (the others keep empty rows).  For every (k, q) with both states in the
+ * window and every mode, the term is kept when |x_em| or |x_abs| is at most
+ * 7 sigma; |g_mn nu(k,q)|^2 comes from the FP32 interpolation (Eqs.
+ * eph_mat_wann2, eph_mat).  Each unordered process is evaluated once (s <=
+ * s') and written to both rows with the same |g|^2, so sum_s I_s = 0 to
+ * rounding.  Entries are ordered by (row, col, mode).  Then proceeds as
+ * pgb_build_collision.  *nnz_out (may be NULL) receives the entry count.     */
+pgb_status pgb_build_collision_grid(pgb_ctx *ctx, int band_lo, int band_hi, double e_lo, double e_hi, double T_K,
+                                    double sigma_eV, int64_t *nnz_out);
+
+/* Copy out the list built by pgb_build_collision_grid: row, col, mode int32
+ * and |g|^2 float32, [nnz] each (host or device; any may be NULL).           */
+pgb_status pgb_collision_list(pgb_ctx *ctx, int32_t *row, int32_t *col, int32_t *mode, float *g2);
+
 /* State energies of the collision list [nstates] (host or device).          */
 pgb_status pgb_collision_energies(pgb_ctx *ctx, double *eps_state, int64_t *nstates_out);
 

@@ -27,6 +27,12 @@ int pgb_selftest_heevj(int n, int count, const double *mat, double *eval, double
 pgb_status pgb_selftest_heevj_device(pgb_ctx *ctx, int n, int count, const double *mat, double *eval,
                                      double *evec);
 
+/* Bounded-wait self-test: one GPU thread waits on an mbarrier that nothing
+ * arrives on, using the same clock-bounded wait as the tensor-core pipelines
+ * (budget in SM clock cycles, 1..2^32).  Returns PGB_ETIMEOUT when the wait
+ * ran out and the kernel returned normally, which is the expected result.   */
+pgb_status pgb_selftest_wait_timeout(pgb_ctx *ctx, long long budget_cycles);
+
 #ifdef __cplusplus
 }
 #endif

@@ -161,6 +161,7 @@ void free_grids(pgb_ctx *c) {
     dfree(&c->d_hw);
     dfree(&c->d_coef);
     dfree(&c->d_coef32);
+    dfree(&c->d_coefT);
     dfree(&c->d_phq64);
     dfree(&c->d_phq32);
     if (c->d_asplit) cudaFree(c->d_asplit);
@@ -177,6 +178,10 @@ void free_coll(pgb_ctx *c) {
     dfree(&c->d_b);
     dfree(&c->d_rowsum_a);
     for (int i = 0; i < 4; ++i) dfree(&c->d_f[i]);
+    dfree(&c->d_coo_row);
+    dfree(&c->d_coo_col);
+    dfree(&c->d_coo_mode);
+    dfree(&c->d_coo_g2);
     c->has_coll = false;
     c->nstates = c->nnz = 0;
 }
@@ -438,6 +443,7 @@ pgb_status pgb_set_grids(pgb_ctx *c, const int kgrid[3], const int qgrid[3]) {
     TRY(dalloc(c, &c->d_hw, (size_t)c->Nq * c->nm));
     TRY(dalloc(c, &c->d_coef, (size_t)c->Nq * nm2));
     TRY(dalloc(c, &c->d_coef32, (size_t)c->Nq * nm2));
+    TRY(dalloc(c, &c->d_coefT, (size_t)c->Nq * nm2));
     {   // bands on the k grid (chunks bound the phase-table size)
         const int64_t chunk = 1 << 16;
         Tmp<double2> ph, hk;
@@ -480,6 +486,7 @@ pgb_status pgb_set_grids(pgb_ctx *c, const int kgrid[3], const int qgrid[3]) {
         c->eps_ref = std::floor(lo) - 1.0;
     }
     TRY(launch_to_f32(c, c->d_coef, c->d_coef32, c->Nq * nm2));
+    TRY(launch_transpose_coef(c));
     PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     c->has_grids = true;
     return PGB_OK;
@@ -923,6 +930,137 @@ pgb_status pgb_diag_bands(pgb_ctx *c, const double *pts, int64_t n, double *Hk, 
     TRY(launch_heevj(c, n, c->nw, hk.p, nullptr, e.p, u.p));
     if (eps) PGB_CUDA_TRY(c, cudaMemcpyAsync(eps, e.p, 8 * (size_t)n * c->nw, cudaMemcpyDefault, c->stream));
     if (U) PGB_CUDA_TRY(c, cudaMemcpyAsync(U, u.p, 16 * (size_t)n * nw2, cudaMemcpyDefault, c->stream));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PGB_OK;
+}
+
+pgb_status pgb_build_collision_grid(pgb_ctx *c, int band_lo, int band_hi, double e_lo, double e_hi, double T,
+                                    double sigma, int64_t *nnz_out) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_grids) return fail(c, PGB_ESTATE, "build_collision_grid: call set_grids first");
+    for (int d = 0; d < 3; ++d)
+        if (c->kg[d] != c->qg[d]) return fail(c, PGB_EINVAL, "build_collision_grid: the q grid must equal the k grid");
+    if (band_lo < 0 || band_hi > c->nw || band_lo >= band_hi)
+        return fail(c, PGB_EINVAL, "build_collision_grid: need 0 <= band_lo < band_hi <= nw");
+    if (!(T > 0.0) || !(sigma > 0.0) || !(e_lo <= e_hi))
+        return fail(c, PGB_EINVAL, "build_collision_grid: need T > 0, sigma > 0, e_lo <= e_hi");
+    const int nbnd = band_hi - band_lo;
+    const int64_t ns = c->Nk * nbnd;
+    if (ns > (1 << 24)) return fail(c, PGB_EINVAL, "build_collision_grid: too many states");
+    free_coll(c);
+    const int nw = c->nw, nm = c->nm;
+    const int64_t ncol = (int64_t)nm * nw * nw, nrow = (int64_t)c->nRgp * ncol, nsub = (int64_t)nbnd * nm * nw;
+    // window flags and the k-points that hold at least one window state
+    std::vector<double> eps((size_t)c->Nk * nw);
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(eps.data(), c->d_eps, 8 * eps.size(), cudaMemcpyDeviceToHost, c->stream));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    std::vector<uint8_t> inwin((size_t)ns, 0);
+    std::vector<int32_t> active;
+    for (int64_t k = 0; k < c->Nk; ++k) {
+        bool any = false;
+        for (int nl = 0; nl < nbnd; ++nl) {
+            const double e = eps[(size_t)k * nw + band_lo + nl];
+            const bool in = e >= e_lo && e <= e_hi;
+            inwin[(size_t)k * nbnd + nl] = in ? 1 : 0;
+            any |= in;
+        }
+        if (any) active.push_back((int32_t)k);
+    }
+    const int64_t na = (int64_t)active.size();
+    Tmp<uint8_t> d_inwin;
+    Tmp<int32_t> d_active;
+    TRY(d_inwin.alloc(c, (size_t)ns));
+    TRY(d_active.alloc(c, (size_t)std::max<int64_t>(na, 1)));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(d_inwin.p, inwin.data(), ns, cudaMemcpyHostToDevice, c->stream));
+    if (na) PGB_CUDA_TRY(c, cudaMemcpyAsync(d_active.p, active.data(), 4 * na, cudaMemcpyHostToDevice, c->stream));
+    Tmp<unsigned long long> counter;
+    TRY(counter.alloc(c, 1));
+    PGB_CUDA_TRY(c, cudaMemsetAsync(counter.p, 0, 8, c->stream));
+    ListLaunch L;
+    L.nb = na;
+    L.kidx = d_active.p;
+    L.band_lo = band_lo;
+    L.nbnd = nbnd;
+    L.inwin = d_inwin.p;
+    L.cut = kDeltaCut * sigma;
+    TRY(list_count(c, L, counter.p));
+    unsigned long long total = 0;
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(&total, counter.p, 8, cudaMemcpyDeviceToHost, c->stream));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (total > (unsigned long long)INT32_MAX * 8)
+        return fail(c, PGB_EINVAL, "build_collision_grid: list too large");
+    // keys and values, with the radix sort's alternate buffers
+    Tmp<uint64_t> keys, keys2;
+    Tmp<float> vals, vals2;
+    TRY(keys.alloc(c, (size_t)std::max<unsigned long long>(total, 1)));
+    TRY(keys2.alloc(c, (size_t)std::max<unsigned long long>(total, 1)));
+    TRY(vals.alloc(c, (size_t)std::max<unsigned long long>(total, 1)));
+    TRY(vals2.alloc(c, (size_t)std::max<unsigned long long>(total, 1)));
+    PGB_CUDA_TRY(c, cudaMemsetAsync(counter.p, 0, 8, c->stream));
+    // q-grid phases (FP32, kept for later calls)
+    if (!c->d_phq32) {
+        TRY(dalloc(c, &c->d_phq32, (size_t)c->Nq * c->nRgp));
+        TRY(launch_phase_grid(c, c->qg, nullptr, c->Nq, c->d_Rgp, c->nRgp, c->d_phq32, true));
+    }
+    const size_t es = sizeof(float2);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t per_k = al(c->nRge * es) + 2 * al(nrow * es) + al((size_t)c->Nq * nsub * es);
+    int64_t nbmax = std::max<int64_t>(1, (int64_t)(((size_t)4 << 30) / per_k));
+    nbmax = std::min<int64_t>(nbmax, std::max<int64_t>(na, 1));
+    nbmax = std::min<int64_t>(nbmax, 65535);
+    TRY(ensure_scratch(c, nbmax * per_k + 4096));
+    char *base = (char *)c->scratch;
+    char *phk = base;
+    char *S1 = phk + al(nbmax * c->nRge * es);
+    char *G = S1 + al(nbmax * nrow * es);
+    char *Cb = G + al(nbmax * nrow * es);
+    for (int64_t b0 = 0; b0 < na; b0 += nbmax) {
+        const int64_t nb = std::min<int64_t>(nbmax, na - b0);
+        const int32_t *kb = d_active.p + b0;
+        TRY(launch_phase_grid(c, c->kg, kb, nb, c->d_Rge, c->nRge, phk, true));
+        TRY(launch_cgemm(c, true, 1, nb, nrow, c->nRge, phk, c->nRge, 0, c->d_g32, nrow, 0, S1, nrow, 0));
+        TRY(launch_fold_u(c, true, nb, kb, c->nRgp, nm, nw, S1, c->d_U32, G));
+        // q-sum over the columns of the listed bands only
+        TRY(launch_cgemm(c, true, nb, c->Nq, nsub, c->nRgp, c->d_phq32, c->nRgp, 0,
+                         (const float2 *)G + (int64_t)band_lo * nm * nw, ncol, nrow, Cb, nsub, c->Nq * nsub));
+        ListLaunch Lb = L;
+        Lb.nb = nb;
+        Lb.kidx = kb;
+        TRY(list_fill(c, Lb, Cb, counter.p, keys.p, vals.p, total));
+    }
+    unsigned long long filled = 0;
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(&filled, counter.p, 8, cudaMemcpyDeviceToHost, c->stream));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (filled != total) return fail(c, PGB_ECUDA, "build_collision_grid: count and fill passes disagree");
+    TRY(dalloc(c, &c->d_coo_row, (size_t)total));
+    TRY(dalloc(c, &c->d_coo_col, (size_t)total));
+    TRY(dalloc(c, &c->d_coo_mode, (size_t)total));
+    TRY(dalloc(c, &c->d_coo_g2, (size_t)total));
+    TRY(list_sort_decode(c, (int64_t)total, (int)ns, keys.p, vals.p, keys2.p, vals2.p, c->d_coo_row, c->d_coo_col,
+                         c->d_coo_mode, c->d_coo_g2));
+    c->band_lo = band_lo;
+    c->band_hi = band_hi;
+    c->nstates = ns;
+    c->nnz = (int64_t)total;
+    pgb_status st = launch_coll_coeffs(c, T, sigma, c->d_coo_row, c->d_coo_col, c->d_coo_mode, c->d_coo_g2,
+                                       (int64_t)total, nbnd);
+    if (st != PGB_OK) return st;
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->has_coll = true;
+    if (nnz_out) *nnz_out = (int64_t)total;
+    return PGB_OK;
+}
+
+pgb_status pgb_collision_list(pgb_ctx *c, int32_t *row, int32_t *col, int32_t *mode, float *g2) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_coll || !c->d_coo_row) return fail(c, PGB_ESTATE, "collision_list: no list built from the grid");
+    const size_t n = (size_t)c->nnz;
+    if (row) PGB_CUDA_TRY(c, cudaMemcpyAsync(row, c->d_coo_row, 4 * n, cudaMemcpyDefault, c->stream));
+    if (col) PGB_CUDA_TRY(c, cudaMemcpyAsync(col, c->d_coo_col, 4 * n, cudaMemcpyDefault, c->stream));
+    if (mode) PGB_CUDA_TRY(c, cudaMemcpyAsync(mode, c->d_coo_mode, 4 * n, cudaMemcpyDefault, c->stream));
+    if (g2) PGB_CUDA_TRY(c, cudaMemcpyAsync(g2, c->d_coo_g2, 4 * n, cudaMemcpyDefault, c->stream));
     PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return PGB_OK;
 }

@@ -56,8 +56,12 @@ __global__ void k_coll_coeffs(CoeffArgs p) {
     const int k3 = (int)(k % p.kg[2]), k2 = (int)((k / p.kg[2]) % p.kg[1]), k1 = (int)(k / ((int64_t)p.kg[1] * p.kg[2]));
     const int l3 = (int)(kp % p.kg[2]), l2 = (int)((kp / p.kg[2]) % p.kg[1]), l1 = (int)(kp / ((int64_t)p.kg[1] * p.kg[2]));
     const int q1 = (l1 - k1 + p.kg[0]) % p.kg[0], q2 = (l2 - k2 + p.kg[1]) % p.kg[1], q3 = (l3 - k3 + p.kg[2]) % p.kg[2];
+    // q and -q have the same frequencies; the smaller of the two indices is
+    // used so that both directions of a process see bit-identical hw
     const int64_t q = ((int64_t)q1 * p.kg[1] + q2) * p.kg[2] + q3;
-    const double w = p.hw[q * p.nm + p.mode[e]];
+    const int r1 = (p.kg[0] - q1) % p.kg[0], r2 = (p.kg[1] - q2) % p.kg[1], r3 = (p.kg[2] - q3) % p.kg[2];
+    const int64_t qm = ((int64_t)r1 * p.kg[1] + r2) * p.kg[2] + r3;
+    const double w = p.hw[(q < qm ? q : qm) * p.nm + p.mode[e]];
     double a = 0.0, b = 0.0;
     if (w >= kOmegaMinEv) {
         const double N = 1.0 / expm1(w / (kBoltzEvK * p.T));

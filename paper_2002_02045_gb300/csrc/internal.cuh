@@ -60,10 +60,11 @@ struct pgb_ctx {
     double *d_eps = nullptr;     // [Nk][nw]
     double2 *d_U = nullptr;      // [Nk][nw][nw], U[i][n]
     float2 *d_U32 = nullptr;
-    float2 *d_U32T = nullptr;    // [Nk][n][i] (transpose, FP32) for the fused tensor-core epilogue
+    float2 *d_U32T = nullptr;    // [n][i][Nk] FP32, grid index fastest (fused tensor-core epilogue)
     double *d_hw = nullptr;      // [Nq][nm]
     double2 *d_coef = nullptr;   // [Nq][nm(nu)][nm(ka)] zero-point-scaled eigenvectors
     float2 *d_coef32 = nullptr;
+    float2 *d_coefT = nullptr;   // [nu][ka][Nq] FP32, grid index fastest (fused tensor-core epilogue)
     double2 *d_phq64 = nullptr;  // [Nq][nRgp] exp(i q.Rp), built on first use
     float2 *d_phq32 = nullptr;
     void *d_asplit = nullptr;    // [4][Nq][Kp] hi/lo split phases for the tensor-core q-sum
@@ -80,6 +81,8 @@ struct pgb_ctx {
     float *d_a = nullptr, *d_b = nullptr;
     double *d_rowsum_a = nullptr;    // [nstates]
     double *d_f[4] = {nullptr, nullptr, nullptr, nullptr};  // RK4 stage buffers
+    int32_t *d_coo_row = nullptr, *d_coo_col = nullptr, *d_coo_mode = nullptr;  // list built from the grid
+    float *d_coo_g2 = nullptr;
 
     // scratch (grown on demand, freed in destroy)
     void *scratch = nullptr;
@@ -208,10 +211,10 @@ struct FusedLaunch {
     const int32_t *kidx;
     int Kp;
     void *Bsplit;
-    const float2 *ehl;     // [Nk][nw] (e - e_ref) as hi + lo floats
-    const float *focc32;   // [Nk][nw]
-    const float2 *whl;     // [Nq][nm] hbar*omega as hi + lo floats
-    const float *nbe32;    // [Nq][nm]
+    const float2 *ehl;     // [nw][Nk] (e - e_ref) as hi + lo floats
+    const float *focc32;   // [nw][Nk]
+    const float2 *whl;     // [nm][Nq] hbar*omega as hi + lo floats
+    const float *nbe32;    // [nm][Nq]
     double sigma;
     double *partial;   // [nb][ceil(Nq/128)][nm][nw]
 };
@@ -220,6 +223,21 @@ pgb_status launch_fp32_tables(pgb_ctx *c, const double *focc, const double *nbe,
 bool tc_fused_supported(int nw, int nm);
 pgb_status launch_tc_rates(pgb_ctx *c, bool tf32, const FusedLaunch &L);
 pgb_status launch_transpose_u(pgb_ctx *c);
+pgb_status launch_transpose_coef(pgb_ctx *c);
+
+// scattering list from the grid (list.cu)
+struct ListLaunch {
+    int64_t nb;
+    const int32_t *kidx;
+    int band_lo, nbnd;
+    const uint8_t *inwin;
+    double cut;
+};
+pgb_status list_count(pgb_ctx *c, const ListLaunch &L, unsigned long long *d_counter);
+pgb_status list_fill(pgb_ctx *c, const ListLaunch &L, const void *C, unsigned long long *d_counter, uint64_t *keys,
+                     float *vals, unsigned long long cap);
+pgb_status list_sort_decode(pgb_ctx *c, int64_t n, int ns, uint64_t *keys, float *vals, uint64_t *keys_alt,
+                            float *vals_alt, int32_t *row, int32_t *col, int32_t *mode, float *g2);
 
 // collision kernels (collision.cu)
 pgb_status launch_coll_coeffs(pgb_ctx *c, double T, double sigma, const int32_t *row, const int32_t *col,

@@ -283,11 +283,12 @@ pgb_status launch_phonon_coef(pgb_ctx *c, int64_t nq, int nm, const double *d_ev
     return PGB_OK;
 }
 
+// U(k) in FP32 with the grid index fastest: UT[(n * nw + i) * Nk + k] = U_in(k).
 __global__ void k_transpose_u(int64_t Nk, int nw, const double2 *__restrict__ U, float2 *__restrict__ UT) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= Nk * nw * nw) return;
-    const int64_t k = t / (nw * nw);
-    const int r = (int)(t % (nw * nw));
+    const int64_t k = t % Nk;
+    const int r = (int)(t / Nk);
     const int n = r / nw, i = r % nw;
     const double2 u = U[k * nw * nw + i * nw + n];
     UT[t] = make_float2((float)u.x, (float)u.y);
@@ -297,6 +298,24 @@ pgb_status launch_transpose_u(pgb_ctx *c) {
     const int64_t n = c->Nk * c->nw * c->nw;
     if (n == 0) return PGB_OK;
     k_transpose_u<<<div_up(n, 256), 256, 0, c->stream>>>(c->Nk, c->nw, c->d_U, c->d_U32T);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+// Mode coefficients in FP32 with the grid index fastest: coefT[(nu * nm + ka) * Nq + q].
+__global__ void k_transpose_coef(int64_t Nq, int nm, const double2 *__restrict__ coef, float2 *__restrict__ cT) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= Nq * nm * nm) return;
+    const int64_t q = t % Nq;
+    const int r = (int)(t / Nq);
+    const double2 v = coef[q * nm * nm + r];
+    cT[t] = make_float2((float)v.x, (float)v.y);
+}
+
+pgb_status launch_transpose_coef(pgb_ctx *c) {
+    const int64_t n = c->Nq * c->nm * c->nm;
+    if (n == 0) return PGB_OK;
+    k_transpose_coef<<<div_up(n, 256), 256, 0, c->stream>>>(c->Nq, c->nm, c->d_coef, c->d_coefT);
     PGB_LAUNCH_CHECK(c);
     return PGB_OK;
 }
@@ -515,25 +534,29 @@ pgb_status launch_occ_tables(pgb_ctx *c, double T, double mu, double *focc, floa
     return PGB_OK;
 }
 
-// FP32 tables of the fused tensor-core epilogue: energies shifted by eps_ref
-// (so that every shifted energy is at least 1 eV) split into hi + lo floats,
-// occupations rounded to FP32.
+// FP32 tables of the fused tensor-core epilogue, grid index fastest: energies
+// shifted by eps_ref (so that every shifted energy is at least 1 eV) split
+// into hi + lo floats, occupations rounded to FP32.
 __global__ void k_fp32_tables(int64_t Nk, int nw, int64_t Nq, int nm, const double *__restrict__ eps,
                               const double *__restrict__ hw, double eps_ref, const double *__restrict__ focc,
                               const double *__restrict__ nbe, float2 *__restrict__ ehl, float *__restrict__ focc32,
                               float2 *__restrict__ whl, float *__restrict__ nbe32) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < Nk * nw) {
-        const double e = eps[t] - eps_ref;
+    if (t < Nk * nw) {   // t = n * Nk + k
+        const int64_t k = t % Nk;
+        const int n = (int)(t / Nk);
+        const double e = eps[k * nw + n] - eps_ref;
         const float hi = (float)e;
         ehl[t] = make_float2(hi, (float)(e - (double)hi));
-        focc32[t] = (float)focc[t];
+        focc32[t] = (float)focc[k * nw + n];
     }
-    if (t < Nq * nm) {
-        const double w = hw[t];
+    if (t < Nq * nm) {   // t = nu * Nq + q
+        const int64_t q = t % Nq;
+        const int v = (int)(t / Nq);
+        const double w = hw[q * nm + v];
         const float hi = (float)w;
         whl[t] = make_float2(hi, (float)(w - (double)hi));
-        nbe32[t] = (float)nbe[t];
+        nbe32[t] = (float)nbe[q * nm + v];
     }
 }
 

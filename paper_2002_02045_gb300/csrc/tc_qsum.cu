@@ -308,6 +308,18 @@ int make_map(CUtensorMap *m, void *base, bool tf32, int Kp, int64_t d1, int64_t 
     return (int)r;
 }
 
+// One thread waits on an mbarrier that nothing arrives on, with the same
+// bounded wait the pipelines use; the run-out is reported through *err.
+__global__ void k_wait_timeout(long long budget, int *err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(tc::smem_addr(&bar), 1);
+        tc::fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !tc::mbar_wait(tc::smem_addr(&bar), 0, budget)) atomicOr(err, 8);
+}
+
 }  // namespace
 
 int tc_kpad(int nR) { return ((nR + 31) / 32) * 32; }
@@ -376,3 +388,31 @@ pgb_status launch_tc_qsum(pgb_ctx *c, bool tf32, int64_t nb, int64_t Nq, int nco
 }
 
 }  // namespace pgb
+
+// Diagnostic: exercise the bounded-wait path (see include/pertgb_diag.h).
+extern "C" pgb_status pgb_selftest_wait_timeout(pgb_ctx *c, long long budget_cycles) {
+    using namespace pgb;
+    if (!c || budget_cycles <= 0 || budget_cycles > (1ll << 32)) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    int *d = nullptr;
+    PGB_CUDA_TRY(c, cudaMalloc((void **)&d, sizeof(int)));
+    int h = 0;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) {
+        k_wait_timeout<<<1, 32, 0, c->stream>>>(budget_cycles, d);
+        c->launches++;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        c->err = std::string("selftest_wait_timeout: ") + cudaGetErrorString(e);
+        return PGB_ECUDA;
+    }
+    if (h) {
+        c->err = "selftest_wait_timeout: the wait ran out as intended (bits " + std::to_string(h) + ")";
+        return PGB_ETIMEOUT;
+    }
+    return PGB_OK;
+}

@@ -55,15 +55,17 @@ constexpr int NBARS = 2 * STAGES + 2 * 2 + 1;   // full, empty, acc_full[2], acc
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512;
 
 struct FusedArgs {
-    int nb, Nq, Kp, nqt, gk;
+    int nb, Nq, Nk, Kp, nqt, gk;
     const int32_t *kidx;
     int kg[3], qg[3];
-    const float2 *ehl;     // [Nk][NW] shifted band energy as (hi, lo) floats
-    const float *focc;     // [Nk][NW]
-    const float2 *UT;      // [Nk][m][i]
-    const float2 *coef;    // [Nq][nu][ka]
-    const float2 *whl;     // [Nq][NM] hbar*omega as (hi, lo) floats
-    const float *nbe;      // [Nq][NM]
+    // per-grid-point tables, grid index fastest so that a warp's 32
+    // consecutive q (and nearly consecutive k+q) read whole sectors
+    const float2 *ehl;     // [NW][Nk] shifted band energy as (hi, lo) floats
+    const float *focc;     // [NW][Nk]
+    const float2 *UT;      // [m][i][Nk]
+    const float2 *coef;    // [nu][ka][Nq]
+    const float2 *whl;     // [NM][Nq] hbar*omega as (hi, lo) floats
+    const float *nbe;      // [NM][Nq]
     float inv_sigma;
     float cut;             // screening bound on |x|, eV
     double *partial;       // [nb][nqt][NM][NW]
@@ -267,11 +269,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     t3 -= (t3 >= kg2) ? kg2 : 0;
                     kq = (t1 * kg1 + t2) * kg2 + t3;
 #pragma unroll
-                    for (int m = 0; m < NWF; ++m) em[m] = a.ehl[kq * NWF + m];
+                    for (int m = 0; m < NWF; ++m) em[m] = a.ehl[(size_t)m * a.Nk + kq];
 #pragma unroll
                     for (int v = 0; v < NMF; ++v) {
-                        wv[v] = a.whl[q * NMF + v];
-                        nb_[v] = a.nbe[q * NMF + v];
+                        wv[v] = a.whl[(size_t)v * a.Nq + q];
+                        nb_[v] = a.nbe[(size_t)v * a.Nq + q];
                     }
                 }
             }
@@ -313,9 +315,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
             for (int v = 0; v < NMF; ++v) acc[v] = 0.f;
             if (valid) {
-                const float2 en = a.ehl[k * NWF + n];
-                const float2 *cf = a.coef + (size_t)q * NMF * NMF;
-                const float2 *Ut = a.UT + (size_t)kq * NWF * NWF;
+                const float2 en = a.ehl[(size_t)n * a.Nk + k];
 #pragma unroll
                 for (int v = 0; v < NMF; ++v) {
                     if (!(wv[v].x + wv[v].y >= (float)kOmegaMinEv)) continue;
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
 #pragma unroll
                     for (int ka = 0; ka < NMF; ++ka) {
-                        const float2 c = cf[v * NMF + ka];
+                        const float2 c = a.coef[(size_t)(v * NMF + ka) * a.Nq + q];
 #pragma unroll
                         for (int i = 0; i < NWF; ++i) {
                             const float xr = gr[ka * NWF + i], xi = gi[ka * NWF + i];
@@ -352,16 +352,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         float grr = 0.f, gii = 0.f;
 #pragma unroll
                         for (int i = 0; i < NWF; ++i) {
-                            const float2 u = Ut[m * NWF + i];     // U_im(k+q), conjugated below
+                            const float2 u = a.UT[(size_t)(m * NWF + i) * a.Nk + kq];   // U_im(k+q), conjugated below
                             grr = fmaf(u.x, pr[i], fmaf(u.y, pi[i], grr));
                             gii = fmaf(u.x, pi[i], fmaf(-u.y, pr[i], gii));
                         }
                         const float g2 = grr * grr + gii * gii;
-                        const float2 e_m = a.ehl[kq * NWF + m];
+                        const float2 e_m = a.ehl[(size_t)m * a.Nk + kq];
                         const float dh = en.x - e_m.x, dl = en.y - e_m.y;
                         const float xe = (dh - wv[v].x) + (dl - wv[v].y);
                         const float xa = (dh + wv[v].x) + (dl + wv[v].y);
-                        const float f = a.focc[kq * NWF + m];
+                        const float f = a.focc[(size_t)m * a.Nk + kq];
                         const float ye = xe * a.inv_sigma, ya = xa * a.inv_sigma;
                         float W = 0.f;
                         if (fabsf(xe) <= a.cut) W += expf(-ye * ye) * (1.f + N - f);
@@ -437,9 +437,10 @@ pgb_status launch_tc_rates(pgb_ctx *c, bool tf32, const FusedLaunch &L) {
     FusedArgs a;
     a.nb = (int)L.nb;
     a.Nq = (int)c->Nq;
+    a.Nk = (int)c->Nk;
     a.Kp = L.Kp;
     a.nqt = nqt;
-    a.gk = std::max(1, std::min<int>(8, (int)L.nb));
+    a.gk = std::max(1, std::min<int>(16, (int)L.nb));
     a.kidx = L.kidx;
     for (int d = 0; d < 3; ++d) {
         a.kg[d] = c->kg[d];
@@ -448,7 +449,7 @@ pgb_status launch_tc_rates(pgb_ctx *c, bool tf32, const FusedLaunch &L) {
     a.ehl = L.ehl;
     a.focc = L.focc32;
     a.UT = c->d_U32T;
-    a.coef = c->d_coef32;
+    a.coef = c->d_coefT;
     a.whl = L.whl;
     a.nbe = L.nbe32;
     a.inv_sigma = (float)(1.0 / L.sigma);

@@ -22,13 +22,13 @@ PGB_FP64, PGB_FP32, PGB_TC_TF32X3, PGB_TC_BF16X3 = 0, 1, 2, 3
 PGB_G2_FULL, PGB_G_ABS = 0, 1
 PRECISIONS = {"fp64": PGB_FP64, "fp32": PGB_FP32, "tf32x3": PGB_TC_TF32X3, "bf16x3": PGB_TC_BF16X3}
 
-DIAG_SYMBOLS = ("pgb_diag_bands", "pgb_selftest_heevj", "pgb_selftest_heevj_device")
+DIAG_SYMBOLS = ("pgb_diag_bands", "pgb_selftest_heevj", "pgb_selftest_heevj_device", "pgb_selftest_wait_timeout")
 ABI_SYMBOLS = (
     "pgb_create", "pgb_destroy", "pgb_last_error", "pgb_status_string", "pgb_set_model",
     "pgb_set_grids", "pgb_get_grid_energies", "pgb_window", "pgb_interpolate_g",
     "pgb_scattering_rates", "pgb_build_collision", "pgb_collision_energies", "pgb_collision",
     "pgb_step_rk4", "pgb_launch_count", "pgb_profile", "pgb_profile_read",
-    "pgb_scattering_rates_noalloc",
+    "pgb_scattering_rates_noalloc", "pgb_build_collision_grid", "pgb_collision_list",
 )
 PGB_NOALLOC_SCRATCH_BYTES = 64 << 20
 PROF_QSUM, PROF_RSUM, PROF_EPILOGUE, PROF_COLLISION, PROF_BANDS = 0, 1, 2, 3, 4
@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
         "pgb_scattering_rates": (I, [P, P, I64, D, D, D, I, P, P]),
         "pgb_build_collision": (I, [P, I, I, D, D, I64, P, P, P, P]),
         "pgb_collision_energies": (I, [P, P, C.POINTER(I64)]),
+        "pgb_build_collision_grid": (I, [P, I, I, D, D, D, D, C.POINTER(I64)]),
+        "pgb_collision_list": (I, [P, P, P, P, P]),
         "pgb_collision": (I, [P, P, P]),
         "pgb_step_rk4": (I, [P, P, D, I64]),
         "pgb_launch_count": (I64, [P]),
@@ -84,6 +86,7 @@ def load(path: str = LIB_PATH):
         "pgb_diag_bands": (I, [P, P, I64, P, P, P]),
         "pgb_selftest_heevj": (I, [I, I, P, P, P]),
         "pgb_selftest_heevj_device": (I, [P, I, I, P, P, P]),
+        "pgb_selftest_wait_timeout": (I, [P, C.c_longlong]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -218,6 +221,17 @@ class Context:
             raise ValueError("row, col, mode, g2 must have equal length")
         self._chk(self.lib.pgb_build_collision(self._h, int(band_lo), int(band_hi), float(T), float(sigma),
                                                n, _ptr(row), _ptr(col), _ptr(mode), _ptr(g2)))
+
+    def pgb_build_collision_grid(self, band_lo, band_hi, e_lo, e_hi, T, sigma):
+        n = C.c_int64(0)
+        self._chk(self.lib.pgb_build_collision_grid(self._h, int(band_lo), int(band_hi), float(e_lo), float(e_hi),
+                                                    float(T), float(sigma), C.byref(n)))
+        return int(n.value)
+
+    def pgb_collision_list(self, row=None, col=None, mode=None, g2=None):
+        for a, k in ((row, "int32"), (col, "int32"), (mode, "int32"), (g2, "float32")):
+            _check_dtype(a, k)
+        self._chk(self.lib.pgb_collision_list(self._h, _ptr(row), _ptr(col), _ptr(mode), _ptr(g2)))
 
     def pgb_collision_energies(self, eps_state=None):
         n = C.c_int64(0)

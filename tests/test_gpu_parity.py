@@ -72,6 +72,19 @@ def test_device_jacobi_matches_lapack(ctx, n):
     assert np.abs(rec - A).max() < 1e-12 * np.abs(A).max()
 
 
+def test_bounded_wait_reports_timeout_and_context_survives(ctx, c1):
+    # a wait that nothing satisfies ends after its budget with PGB_ETIMEOUT;
+    # the context stays usable afterwards
+    st = ctx.lib.pgb_selftest_wait_timeout(ctx._h, 2_000_000)
+    assert st == -5
+    assert b"ran out" in ctx.lib.pgb_last_error(ctx._h)
+    ctx.pgb_set_model(c1)
+    ctx.pgb_set_grids((2, 2, 2), (2, 2, 2))
+    eps = np.zeros((8, 2))
+    ctx.pgb_get_grid_energies(eps, None)
+    assert np.all(np.isfinite(eps))
+
+
 @pytest.mark.parametrize("which", ["c1", "c2"])
 def test_diag_hamiltonian_and_eigen(ctx, c1, c2, which):
     m = c1 if which == "c1" else c2
@@ -408,3 +421,85 @@ def test_argument_errors(ctx, c1):
     ctx.pgb_set_model(c1)
     ctx.pgb_set_grids((4, 4, 4), (2, 2, 2))
     ctx.pgb_scattering_rates(np.zeros(0, np.int32), 300, 0, 0.01, PGB_FP64, np.zeros((0, 2)))
+
+
+# ----------------------------------------------------------------------------
+# scattering list built on the device (Sec. 4.3)
+# ----------------------------------------------------------------------------
+
+def test_grid_list_matches_oracle_list(ctx, c2):
+    """The device-built list has exactly the oracle's (row, col, mode) entries
+    (7 sigma screen, energy window) and the same mode-summed |g|^2; its
+    collision integral matches the oracle's on the oracle's own list."""
+    T, sig = 300.0, 0.02
+    grid = (5, 5, 5)
+    e_ref, _ = O.bands(c2, S.mp_grid(*grid))
+    emin = e_ref[:, :2].min()
+    win = (emin, emin + 1.2)
+    L = O.collision_list_grid(c2, grid, 0, 2, sigma=sig, screen=np.exp(-49.0), window=win)
+    ctx.pgb_set_model(c2)
+    ctx.pgb_set_grids(grid, grid)
+    nnz = ctx.pgb_build_collision_grid(0, 2, win[0], win[1], T, sig)
+    row = np.zeros(nnz, np.int32)
+    col = np.zeros(nnz, np.int32)
+    mode = np.zeros(nnz, np.int32)
+    g2 = np.zeros(nnz, np.float32)
+    ctx.pgb_collision_list(row, col, mode, g2)
+    key_gpu = (row.astype(np.int64) * 1000 + col) * 8 + mode
+    key_ref = (L["row"] * 1000 + L["col"]) * 8 + L["mode"]
+    assert nnz == len(key_ref) and np.array_equal(key_gpu, np.sort(key_ref))
+    assert np.all(np.diff(key_gpu) > 0)
+    # mode-summed |g|^2 per (row, col): gauge invariant at degenerate q
+    pair_g = row.astype(np.int64) * 1000 + col
+    pair_r = L["row"] * 1000 + L["col"]
+    up, inv = np.unique(pair_g, return_inverse=True)
+    sg = np.bincount(inv, weights=g2.astype(np.float64))
+    ur, invr = np.unique(pair_r, return_inverse=True)
+    sr = np.bincount(invr, weights=L["g2"])
+    assert np.array_equal(up, ur)
+    assert np.all(np.abs(sg - sr) <= 1e-5 * (sr + 1e-2 * sr.max()))
+    rng = np.random.default_rng(8)
+    f = rng.uniform(0, 0.5, L["nstates"])
+    I = np.zeros(L["nstates"])
+    ctx.pgb_collision(f, I)
+    ref = O.collision(f, L["eps"], L["row"], L["col"], L["hw"], L["g2"], T, sig, L["nq"])
+    assert np.abs(I - ref).max() <= 1e-5 * np.abs(ref).max()
+    assert abs(I.sum()) <= 1e-6 * np.abs(ref).max()
+
+
+@pytest.mark.slow
+def test_grid_list_full_size_sampled_rows(ctx, c2):
+    """The dynamics workload: 30^3 grid, two lowest bands, states in a 0.6 eV
+    window above the band minimum (~1.2e8 entries).  Sampled rows of I[f] at the
+    hot-carrier pulse are recomputed by the oracle row by row; sum_s I_s
+    vanishes and 20 RK4 steps conserve the carrier number."""
+    T, sig = 300.0, 0.010
+    grid = (30, 30, 30)
+    ctx.pgb_set_model(c2)
+    ctx.pgb_set_grids(grid, grid)
+    eps = empty((27000, 8))
+    ctx.pgb_get_grid_energies(eps, None)
+    e2 = eps.cpu().numpy()[:, :2]
+    emin = float(e2.min())
+    win = (emin, emin + 0.6)
+    nnz = ctx.pgb_build_collision_grid(0, 2, win[0], win[1], T, sig)
+    assert 5e7 < nnz < 3e8
+    es = empty((54000,))
+    ctx.pgb_collision_energies(es)
+    f0 = S.pulse_occupations(es.cpu().numpy(), emin)
+    f = dev(f0)
+    I = empty((54000,))
+    ctx.pgb_collision(f, I)
+    got = I.cpu().numpy()
+    inw = (e2.reshape(-1) >= win[0]) & (e2.reshape(-1) <= win[1])
+    active = np.nonzero(inw)[0]
+    pick = active[[0, len(active) // 3, (2 * len(active)) // 3]]
+    ref = O.collision_rows(c2, grid, 0, 2, pick, f0, T, sig, window=win)
+    scale = np.abs(got).max()
+    assert np.all(np.abs(got[pick] - ref) <= 1e-5 * (np.abs(ref) + 1e-3 * scale)), (got[pick], ref)
+    assert abs(got.sum()) <= 1e-6 * np.abs(got).sum()
+    assert np.all(got[~inw] == 0.0)
+    ctx.pgb_step_rk4(f, 1.0, 20)
+    ff = f.cpu().numpy()
+    assert abs(ff.sum() - f0.sum()) <= 1e-9 * f0.sum()
+    assert np.abs(ff - f0).max() > 1e-4
