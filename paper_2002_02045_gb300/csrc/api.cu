@@ -177,7 +177,10 @@ void free_coll(pgb_ctx *c) {
     dfree(&c->d_a);
     dfree(&c->d_b);
     dfree(&c->d_rowsum_a);
+    dfree(&c->d_active_rows);
+    c->nrows_active = 0;
     for (int i = 0; i < 4; ++i) dfree(&c->d_f[i]);
+    for (int i = 0; i < 3; ++i) dfree(&c->d_f32[i]);
     dfree(&c->d_coo_row);
     dfree(&c->d_coo_col);
     dfree(&c->d_coo_mode);
@@ -871,7 +874,8 @@ pgb_status pgb_collision(pgb_ctx *c, const double *f, double *I_out) {
     TRY(F.init(c, f, (size_t)c->nstates));
     Out<double> I;
     TRY(I.init(c, I_out, (size_t)c->nstates));
-    TRY(launch_collision(c, F.dev, I.dev, -1, 0.0, nullptr, nullptr, nullptr));
+    TRY(launch_f64_to_f32(c, F.dev, c->d_f32[0], c->nstates));
+    TRY(launch_collision(c, F.dev, c->d_f32[0], I.dev, -1, 0.0, nullptr, nullptr, nullptr, nullptr));
     TRY(I.finish());
     return PGB_OK;
 }
@@ -894,11 +898,19 @@ pgb_status pgb_step_rk4(pgb_ctx *c, double *f, double dt_fs, int64_t nsteps) {
     const double dt = dt_fs * kFemto;
     double *acc = c->d_f[0], *f1 = c->d_f[1], *f2 = c->d_f[2];
     pgb_status st = PGB_OK;
+    // states without entries are not visited by the kernel: their stage values are f
+    float *g0 = c->d_f32[0], *g1 = c->d_f32[1], *g2 = c->d_f32[2];
+    if (launch_f64_to_f32(c, fd, g0, (int64_t)ns) != PGB_OK ||
+        cudaMemcpyAsync(f1, fd, 8 * ns, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(f2, fd, 8 * ns, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(g1, g0, 4 * ns, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(g2, g0, 4 * ns, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        st = fail(c, PGB_ECUDA, "step_rk4: stage buffer set-up");
     for (int64_t s = 0; s < nsteps && st == PGB_OK; ++s) {
-        st = launch_collision(c, fd, nullptr, 0, dt, acc, f1, fd);
-        if (st == PGB_OK) st = launch_collision(c, f1, nullptr, 1, dt, acc, f2, fd);
-        if (st == PGB_OK) st = launch_collision(c, f2, nullptr, 2, dt, acc, f1, fd);
-        if (st == PGB_OK) st = launch_collision(c, f1, nullptr, 3, dt, acc, fd, fd);
+        st = launch_collision(c, fd, g0, nullptr, 0, dt, acc, f1, g1, fd);
+        if (st == PGB_OK) st = launch_collision(c, f1, g1, nullptr, 1, dt, acc, f2, g2, fd);
+        if (st == PGB_OK) st = launch_collision(c, f2, g2, nullptr, 2, dt, acc, f1, g1, fd);
+        if (st == PGB_OK) st = launch_collision(c, f1, g1, nullptr, 3, dt, acc, fd, g0, fd);
     }
     if (host) {
         if (st == PGB_OK) {

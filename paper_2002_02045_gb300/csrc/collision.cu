@@ -1,5 +1,7 @@
 // Collision integral I[f] (Eq. e_ph_scattering) on a CSR scattering list and
 // the fused RK4 stages (Sec. 2.1.1).
+#include <vector>
+
 #include "internal.cuh"
 
 namespace pgb {
@@ -139,6 +141,8 @@ pgb_status launch_coll_coeffs(pgb_ctx *c, double T, double sigma, const int32_t 
     if ((st = dalloc(c, &c->d_rowsum_a, ns)) != PGB_OK) return st;
     for (int i = 0; i < 3; ++i)
         if ((st = dalloc(c, &c->d_f[i], ns)) != PGB_OK) return st;
+    for (int i = 0; i < 3; ++i)
+        if ((st = dalloc(c, &c->d_f32[i], ns)) != PGB_OK) return st;
 
     k_eps_state<<<div_up(ns, 256), 256, 0, c->stream>>>(ns, nb, c->band_lo, c->nw, c->d_eps, c->d_eps_state);
     PGB_LAUNCH_CHECK(c);
@@ -169,122 +173,186 @@ pgb_status launch_coll_coeffs(pgb_ctx *c, double T, double sigma, const int32_t 
     PGB_LAUNCH_CHECK(c);
     k_rowsum<<<div_up(ns * 32, 256), 256, 0, c->stream>>>(ns, c->d_rowptr, c->d_a, c->d_rowsum_a);
     PGB_LAUNCH_CHECK(c);
+    // non-empty rows, the only ones the collision kernel visits
+    std::vector<int64_t> rp((size_t)ns + 1);
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(rp.data(), c->d_rowptr, 8 * rp.size(), cudaMemcpyDeviceToHost, c->stream));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    std::vector<int32_t> act;
+    for (int64_t r = 0; r < ns; ++r)
+        if (rp[r + 1] > rp[r]) act.push_back((int32_t)r);
+    c->nrows_active = (int64_t)act.size();
+    if ((st = dalloc(c, &c->d_active_rows, std::max<size_t>(act.size(), 1))) != PGB_OK) return st;
+    if (!act.empty())
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_active_rows, act.data(), 4 * act.size(), cudaMemcpyHostToDevice,
+                                        c->stream));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return PGB_OK;
 }
 
 // ---------------------------------------------------------------------------
 // I_s = -f_s sum_e a_e + f_s sum_e f_c a_e + (1 - f_s) sum_e f_c b_e
 // (the bracket of Eq. e_ph_scattering expanded: -f_s(1-f_c) a + f_c(1-f_s) b).
-// One warp per row.  Entries stream as 16-byte vectors (4 entries per lane
-// per step) once the row is 16-byte aligned; products and 4-entry sums are
-// FP32, running sums and the row result FP64.  f_c is gathered from L2.
-// Stage -1 writes I; stages 0..3 fuse the RK4 combinations:
+// One 256-thread block per non-empty row (rows of the dynamics workload hold
+// ~2e4 entries, so a row needs many loads in flight).  Entries stream as
+// 16-byte vectors (4 entries per thread per step, two steps in flight) once the
+// row is 16-byte aligned.  The FP64 rate is a small fraction of the FP32 rate,
+// so no per-entry work touches FP64: f_c is gathered from an FP32 copy written
+// by the previous stage, products and running sums are FP32 with Kahan
+// compensation, and only the per-row combination is FP64.  Stage -1 writes I; stages 0..3 fuse the RK4
+// combinations:
 //   0: acc = k1,  next = f + dt/2 k1      1: acc += 2 k2, next = f + dt/2 k2
 //   2: acc += 2 k3, next = f + dt k3      3: f = f + dt/6 (acc + k4)
+// Empty rows have I = 0 and are not launched; their stage values stay f.
 // ---------------------------------------------------------------------------
 struct CollArgs {
-    int64_t nstates;
+    int64_t nrows;           // non-empty rows
+    const int32_t *rows;     // [nrows] state index of each non-empty row
     const int64_t *rowptr;
     const int32_t *col;
     const float *a, *b;
     const double *rowsum_a;
     const double *fin;    // occupations the integral is evaluated at
+    const float *fin32;   // FP32 copy of fin (gathered per entry)
     const double *fbase;  // f at the start of the step
     double *I;            // stage -1 output
     double *acc;
     double *fnext;
+    float *fnext32;       // FP32 copy of fnext (stages 0..3)
     double dt;            // seconds
     int stage;
 };
 
-__global__ void __launch_bounds__(256) k_collision(CollArgs p) {
-    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (s >= p.nstates) return;
+constexpr int kCollThreads = 256;
+
+__global__ void __launch_bounds__(kCollThreads) k_collision(CollArgs p) {
+    __shared__ double red[2][kCollThreads / 32];
+    const int64_t r = blockIdx.x;
+    if (r >= p.nrows) return;
+    const int s = p.rows[r];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t beg = p.rowptr[s], end = p.rowptr[s + 1];
-    double sfa = 0.0, sfb = 0.0;
-    const double *__restrict__ fin = p.fin;
+    const float *__restrict__ f32 = p.fin32;
+    // Kahan-compensated FP32 sums
+    float sa = 0.f, ca = 0.f, sb = 0.f, cb = 0.f;
+    auto kadd = [](float &sum, float &comp, float x) {
+        const float y = x - comp;
+        const float t2 = sum + y;
+        comp = (t2 - sum) - y;
+        sum = t2;
+    };
     int64_t vbeg = (beg + 3) & ~(int64_t)3;
     if (vbeg > end) vbeg = end;
     const int64_t vend = vbeg + ((end - vbeg) & ~(int64_t)3);
-    // head (up to 3 entries) and tail (up to 3 entries)
-    {
+    {   // head (up to 3 entries) and tail (up to 3 entries)
         int64_t e = -1;
-        if (lane < vbeg - beg)
-            e = beg + lane;
-        else if (lane >= 4 && lane - 4 < end - vend)
-            e = vend + (lane - 4);
+        if (t < vbeg - beg)
+            e = beg + t;
+        else if (t >= 4 && t - 4 < end - vend)
+            e = vend + (t - 4);
         if (e >= 0) {
-            const float fc = (float)fin[p.col[e]];
-            sfa += (double)(fc * p.a[e]);
-            sfb += (double)(fc * p.b[e]);
+            const float fc = f32[p.col[e]];
+            kadd(sa, ca, fc * p.a[e]);
+            kadd(sb, cb, fc * p.b[e]);
         }
     }
     const int4 *col4 = reinterpret_cast<const int4 *>(p.col + vbeg);
     const float4 *a4 = reinterpret_cast<const float4 *>(p.a + vbeg);
     const float4 *b4 = reinterpret_cast<const float4 *>(p.b + vbeg);
     const int64_t nv = (vend - vbeg) >> 2;
-    for (int64_t v = lane; v < nv; v += 32) {
+#pragma unroll 2
+    for (int64_t v = t; v < nv; v += kCollThreads) {
         const int4 cc = __ldcs(col4 + v);
         const float4 aa = __ldcs(a4 + v);
         const float4 bb = __ldcs(b4 + v);
-        const float f0 = (float)__ldg(fin + cc.x), f1 = (float)__ldg(fin + cc.y);
-        const float f2 = (float)__ldg(fin + cc.z), f3 = (float)__ldg(fin + cc.w);
-        const float pa = fmaf(f0, aa.x, fmaf(f1, aa.y, fmaf(f2, aa.z, f3 * aa.w)));
-        const float pb = fmaf(f0, bb.x, fmaf(f1, bb.y, fmaf(f2, bb.z, f3 * bb.w)));
-        sfa += (double)pa;
-        sfb += (double)pb;
+        const float f0 = __ldg(f32 + cc.x), f1 = __ldg(f32 + cc.y);
+        const float f2 = __ldg(f32 + cc.z), f3 = __ldg(f32 + cc.w);
+        kadd(sa, ca, fmaf(f0, aa.x, fmaf(f1, aa.y, fmaf(f2, aa.z, f3 * aa.w))));
+        kadd(sb, cb, fmaf(f0, bb.x, fmaf(f1, bb.y, fmaf(f2, bb.z, f3 * bb.w))));
     }
+    double sfa = (double)sa - (double)ca, sfb = (double)sb - (double)cb;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sfa += __shfl_down_sync(0xffffffffu, sfa, o);
         sfb += __shfl_down_sync(0xffffffffu, sfb, o);
     }
     if (lane == 0) {
-        const double fs = fin[s];
+        red[0][warp] = sfa;
+        red[1][warp] = sfb;
+    }
+    __syncthreads();
+    if (t == 0) {
+        sfa = 0.0;
+        sfb = 0.0;
+        for (int w = 0; w < kCollThreads / 32; ++w) {
+            sfa += red[0][w];
+            sfb += red[1][w];
+        }
+        const double fs = p.fin[s];
         const double I = -fs * p.rowsum_a[s] + fs * sfa + (1.0 - fs) * sfb;
+        double fn = 0.0;
         switch (p.stage) {
             case -1:
                 p.I[s] = I;
                 break;
             case 0:
                 p.acc[s] = I;
-                p.fnext[s] = p.fbase[s] + 0.5 * p.dt * I;
+                fn = p.fbase[s] + 0.5 * p.dt * I;
                 break;
             case 1:
                 p.acc[s] += 2.0 * I;
-                p.fnext[s] = p.fbase[s] + 0.5 * p.dt * I;
+                fn = p.fbase[s] + 0.5 * p.dt * I;
                 break;
             case 2:
                 p.acc[s] += 2.0 * I;
-                p.fnext[s] = p.fbase[s] + p.dt * I;
+                fn = p.fbase[s] + p.dt * I;
                 break;
             default:
-                p.fnext[s] = p.fbase[s] + p.dt / 6.0 * (p.acc[s] + I);
+                fn = p.fbase[s] + p.dt / 6.0 * (p.acc[s] + I);
                 break;
+        }
+        if (p.stage >= 0) {
+            p.fnext[s] = fn;
+            p.fnext32[s] = (float)fn;
         }
     }
 }
 
-pgb_status launch_collision(pgb_ctx *c, const double *f, double *I, int stage, double dt, double *acc,
-                            double *fnext, const double *fbase) {
+__global__ void k_to_f32_real(const double *__restrict__ x, float *__restrict__ y, int64_t n) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) y[t] = (float)x[t];
+}
+
+pgb_status launch_f64_to_f32(pgb_ctx *c, const double *x, float *y, int64_t n) {
+    if (n == 0) return PGB_OK;
+    k_to_f32_real<<<div_up(n, 256), 256, 0, c->stream>>>(x, y, n);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+pgb_status launch_collision(pgb_ctx *c, const double *f, const float *f32, double *I, int stage, double dt,
+                            double *acc, double *fnext, float *fnext32, const double *fbase) {
     if (c->nstates == 0) return PGB_OK;
+    if (stage == -1) PGB_CUDA_TRY(c, cudaMemsetAsync(I, 0, 8 * (size_t)c->nstates, c->stream));
+    if (c->nrows_active == 0) return PGB_OK;
     CollArgs p;
-    p.nstates = c->nstates;
+    p.nrows = c->nrows_active;
+    p.rows = c->d_active_rows;
     p.rowptr = c->d_rowptr;
     p.col = c->d_col;
     p.a = c->d_a;
     p.b = c->d_b;
     p.rowsum_a = c->d_rowsum_a;
     p.fin = f;
+    p.fin32 = f32;
     p.fbase = fbase;
     p.I = I;
     p.acc = acc;
     p.fnext = fnext;
+    p.fnext32 = fnext32;
     p.dt = dt;
     p.stage = stage;
     prof_mark(c, PGB_PROF_COLLISION);
-    k_collision<<<div_up(c->nstates * 32, 256), 256, 0, c->stream>>>(p);
+    k_collision<<<(unsigned)c->nrows_active, kCollThreads, 0, c->stream>>>(p);
     prof_mark(c, PGB_PROF_COLLISION);
     PGB_LAUNCH_CHECK(c);
     return PGB_OK;

@@ -80,7 +80,10 @@ struct pgb_ctx {
     int32_t *d_col = nullptr;        // [nnz]
     float *d_a = nullptr, *d_b = nullptr;
     double *d_rowsum_a = nullptr;    // [nstates]
+    int32_t *d_active_rows = nullptr;   // non-empty rows
+    int64_t nrows_active = 0;
     double *d_f[4] = {nullptr, nullptr, nullptr, nullptr};  // RK4 stage buffers
+    float *d_f32[3] = {nullptr, nullptr, nullptr};          // FP32 copies gathered by the collision kernel
     int32_t *d_coo_row = nullptr, *d_coo_col = nullptr, *d_coo_mode = nullptr;  // list built from the grid
     float *d_coo_g2 = nullptr;
 
@@ -242,7 +245,8 @@ pgb_status list_sort_decode(pgb_ctx *c, int64_t n, int ns, uint64_t *keys, float
 // collision kernels (collision.cu)
 pgb_status launch_coll_coeffs(pgb_ctx *c, double T, double sigma, const int32_t *row, const int32_t *col,
                               const int32_t *mode, const float *g2, int64_t nnz, int nb);
-pgb_status launch_collision(pgb_ctx *c, const double *f, double *I, int stage, double dt, double *acc,
-                            double *fnext, const double *fbase);
+pgb_status launch_collision(pgb_ctx *c, const double *f, const float *f32, double *I, int stage, double dt,
+                            double *acc, double *fnext, float *fnext32, const double *fbase);
+pgb_status launch_f64_to_f32(pgb_ctx *c, const double *x, float *y, int64_t n);
 
 }  // namespace pgb
