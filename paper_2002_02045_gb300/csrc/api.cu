@@ -680,7 +680,7 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
         o_part = o_C + (fused ? 0 : al((size_t)nbm * c->Nq * ncol * es));
         o_gm = o_part + al((size_t)nbm * nqblk * per * sizeof(double));
         o_B = o_gm + al((size_t)nbm * per * sizeof(double));
-        total = o_B + (tcp ? al((size_t)nbm * 4 * ncol * Kp * tes) : 0);
+        total = o_B + (tcp ? al((size_t)nbm * (fused ? 6 : 4) * ncol * Kp * tes) : 0);
     };
     layout(1);
     const size_t budget = (size_t)4 << 30;
@@ -741,7 +741,7 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
         TRY(launch_fold_u(c, f32, nb, kb, c->nRgp, nm, nw, S1, U, G));
         prof_mark(c, PGB_PROF_RSUM);
         if (fused) {
-            TRY(launch_split_g(c, tf32, nb, c->nRgp, (int)ncol, Kp, G, Bsplit));
+            TRY(launch_split_g6(c, tf32, nb, c->nRgp, (int)ncol, Kp, G, Bsplit));
             FusedLaunch L;
             L.nb = nb;
             L.kidx = kb;

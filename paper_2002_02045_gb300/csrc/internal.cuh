@@ -205,6 +205,7 @@ bool tc_supported(int ncol);
 pgb_status launch_split_phases(pgb_ctx *c, bool tf32, const int grid[3], int64_t Nq, const int32_t *d_R, int nR,
                                int Kp, void *out);
 pgb_status launch_split_g(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out);
+pgb_status launch_split_g6(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out);
 pgb_status launch_tc_qsum(pgb_ctx *c, bool tf32, int64_t nb, int64_t Nq, int ncol, int Kp, void *Asplit,
                           void *Bsplit, float2 *C, int *d_err);
 

@@ -276,6 +276,32 @@ __global__ void k_split_g(int64_t nb, int nR, int ncol, int Kp, const float2 *__
     o[3 * per] = l;
 }
 
+// B parts for the fused kernel: [b][6][ncol][Kp] = Br_hi, Br_lo, Bi_hi, Bi_lo,
+// -Bi_hi, -Bi_lo (the negated copy lets one MMA form [C_re | C_im]).
+template <bool TF32>
+__global__ void k_split_g6(int64_t nb, int nR, int ncol, int Kp, const float2 *__restrict__ G,
+                           typename Split<TF32>::E *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)ncol * Kp;
+    if (t >= nb * per) return;
+    const int64_t b = t / per;
+    const int64_t r = t % per;
+    const int c = (int)(r / Kp);
+    const int p = (int)(r % Kp);
+    float2 v = make_float2(0.f, 0.f);
+    if (p < nR) v = G[(b * nR + p) * ncol + c];
+    typename Split<TF32>::E h, l;
+    typename Split<TF32>::E *o = out + b * 6 * per + r;
+    Split<TF32>::run((double)v.x, h, l);
+    o[0 * per] = h;
+    o[1 * per] = l;
+    Split<TF32>::run((double)v.y, h, l);
+    o[2 * per] = h;
+    o[3 * per] = l;
+    o[4 * per] = -h;
+    o[5 * per] = -l;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -347,6 +373,18 @@ pgb_status launch_split_g(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, i
         k_split_g<true><<<g, 256, 0, c->stream>>>(nb, nR, ncol, Kp, (const float2 *)G, (float *)out);
     else
         k_split_g<false><<<g, 256, 0, c->stream>>>(nb, nR, ncol, Kp, (const float2 *)G, (__nv_bfloat16 *)out);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+pgb_status launch_split_g6(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out) {
+    const int64_t n = nb * (int64_t)ncol * Kp;
+    if (n == 0) return PGB_OK;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    if (tf32)
+        k_split_g6<true><<<g, 256, 0, c->stream>>>(nb, nR, ncol, Kp, (const float2 *)G, (float *)out);
+    else
+        k_split_g6<false><<<g, 256, 0, c->stream>>>(nb, nR, ncol, Kp, (const float2 *)G, (__nv_bfloat16 *)out);
     PGB_LAUNCH_CHECK(c);
     return PGB_OK;
 }

@@ -33,12 +33,16 @@ namespace pgb {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 96;
+constexpr int BN = 96;                    // complex columns per tile
 constexpr int STAGES = 3;
 constexpr int ROWB = 64;
 constexpr int A_PART = BM * ROWB;
 constexpr int B_PART = BN * ROWB;
-constexpr int STAGE_BYTES = 4 * A_PART + 4 * B_PART;
+// B stage regions (hi, lo): rows [-Bi | Br | Bi], so [Br; Bi] (rows 96..287) and
+// [-Bi; Br] (rows 0..191) are both contiguous 192-row MMA operands
+constexpr int B_REGION = 3 * B_PART;
+constexpr int STAGE_BYTES = 4 * A_PART + 2 * B_REGION;
+constexpr int MN = 2 * BN;                // MMA N: re and im columns together
 constexpr long long WAIT_BUDGET = 1ll << 31;
 constexpr int NWF = 8, NMF = 6;           // band and mode counts of this kernel
 constexpr int PER_N = NWF * NMF;          // 48 columns per initial band
@@ -159,9 +163,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 uint8_t *st = smem + s * STAGE_BYTES;
                 for (int p = 0; p < 4; ++p)
                     tc::tma_load_3d(tc::smem_addr(st + p * A_PART), &tA, fb, kc * EK, qt * BM, p);
-                for (int p = 0; p < 4; ++p)
-                    tc::tma_load_3d(tc::smem_addr(st + 4 * A_PART + p * B_PART), &tB, fb, kc * EK, np * BN,
-                                    b * 4 + p);
+                // B parts in global memory: 0 Br_hi, 1 Br_lo, 2 Bi_hi, 3 Bi_lo, 4 -Bi_hi, 5 -Bi_lo
+                uint8_t *bh = st + 4 * A_PART, *bl = bh + B_REGION;
+                uint8_t *dstp[6] = {bh + B_PART, bl + B_PART, bh + 2 * B_PART, bl + 2 * B_PART, bh, bl};
+                for (int p = 0; p < 6; ++p)
+                    tc::tma_load_3d(tc::smem_addr(dstp[p]), &tB, fb, kc * EK, np * BN, b * 6 + p);
             }
         }
         for (int j = (it > STAGES ? it - STAGES : 0); j < it; ++j)
@@ -169,8 +175,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else if (warp == 1 && lane == 0) {
         // ------------------------------ MMA issuer ------------------------------
         constexpr uint32_t fmt = TF32 ? 2u : 1u;
-        constexpr uint32_t idp = tc::make_idesc(fmt, BM, BN, false);
-        constexpr uint32_t idn = tc::make_idesc(fmt, BM, BN, true);
+        constexpr uint32_t idp = tc::make_idesc(fmt, BM, MN, false);
         int it = 0, tl = 0;
         for (int tile = blockIdx.x * NPAIR; tile < nunits * NPAIR && !*abort_flag;
              tile += (tile % NPAIR == NPAIR - 1) ? (gridDim.x - 1) * NPAIR + 1 : 1, ++tl) {
@@ -182,9 +187,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             tc::fence_after_sync();
             const uint32_t d0 = tbase + buf * NACC * BN;
-            const uint32_t d_re = d0, d_im = d0 + BN;
-            const uint32_t d_rec = (NACC == 4) ? d0 + 2 * BN : d_re;
-            const uint32_t d_imc = (NACC == 4) ? d0 + 3 * BN : d_im;
+            // [re | im] main accumulator; TF32 keeps the corrections in a second one
+            const uint32_t d_main = d0, d_corr = (NACC == 4) ? d0 + MN : d0;
             bool ok = true;
             for (int kc = 0; kc < nk; ++kc, ++it) {
                 const int s = it % STAGES;
@@ -203,23 +207,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const uint64_t arl = tc::desc_sw64(st + 1 * A_PART + off);
                     const uint64_t aih = tc::desc_sw64(st + 2 * A_PART + off);
                     const uint64_t ail = tc::desc_sw64(st + 3 * A_PART + off);
-                    const uint32_t bb = st + 4 * A_PART + off;
-                    const uint64_t brh = tc::desc_sw64(bb + 0 * B_PART), brl = tc::desc_sw64(bb + 1 * B_PART);
-                    const uint64_t bih = tc::desc_sw64(bb + 2 * B_PART), bil = tc::desc_sw64(bb + 3 * B_PART);
+                    const uint32_t bh = st + 4 * A_PART + off, bl = bh + B_REGION;
+                    const uint64_t b1h = tc::desc_sw64(bh + B_PART), b1l = tc::desc_sw64(bl + B_PART);   // [Br; Bi]
+                    const uint64_t b2h = tc::desc_sw64(bh), b2l = tc::desc_sw64(bl);                     // [-Bi; Br]
                     const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
                     const uint32_t acc_c = (NACC == 4) ? acc : 1u;
-                    tc::mma<TF32>(d_re, arh, brh, idp, acc);
-                    tc::mma<TF32>(d_re, aih, bih, idn, 1);
-                    tc::mma<TF32>(d_rec, arh, brl, idp, acc_c);
-                    tc::mma<TF32>(d_rec, arl, brh, idp, 1);
-                    tc::mma<TF32>(d_rec, aih, bil, idn, 1);
-                    tc::mma<TF32>(d_rec, ail, bih, idn, 1);
-                    tc::mma<TF32>(d_im, arh, bih, idp, acc);
-                    tc::mma<TF32>(d_im, aih, brh, idp, 1);
-                    tc::mma<TF32>(d_imc, arh, bil, idp, acc_c);
-                    tc::mma<TF32>(d_imc, arl, bih, idp, 1);
-                    tc::mma<TF32>(d_imc, aih, brl, idp, 1);
-                    tc::mma<TF32>(d_imc, ail, brh, idp, 1);
+                    // [C_re | C_im] += Ar [Br | Bi] + Ai [-Bi | Br]
+                    tc::mma<TF32>(d_main, arh, b1h, idp, acc);
+                    tc::mma<TF32>(d_main, aih, b2h, idp, 1);
+                    tc::mma<TF32>(d_corr, arh, b1l, idp, acc_c);
+                    tc::mma<TF32>(d_corr, arl, b1h, idp, 1);
+                    tc::mma<TF32>(d_corr, aih, b2l, idp, 1);
+                    tc::mma<TF32>(d_corr, ail, b2h, idp, 1);
                 }
                 tc::mma_commit(tc::smem_addr(empty + s));
             }
@@ -428,7 +427,7 @@ pgb_status launch_tc_rates(pgb_ctx *c, bool tf32, const FusedLaunch &L) {
     const int nqt = (int)((c->Nq + BM - 1) / BM);
     CUtensorMap tA, tB;
     const int ra = make_map3(&tA, c->d_asplit, tf32, L.Kp, c->Nq, 4, BM);
-    const int rb = ra == 0 ? make_map3(&tB, L.Bsplit, tf32, L.Kp, NWF * NMF * NWF, L.nb * 4, BN) : 0;
+    const int rb = ra == 0 ? make_map3(&tB, L.Bsplit, tf32, L.Kp, NWF * NMF * NWF, L.nb * 6, BN) : 0;
     if (ra != 0 || rb != 0) {
         c->err = "fused tensor-core rates: cuTensorMapEncodeTiled failed (A " + std::to_string(ra) + ", B " +
                  std::to_string(rb) + ")";
