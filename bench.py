@@ -34,6 +34,11 @@ KGRID = (40, 40, 40)
 T_K, SIGMA, WIN = 300.0, 0.010, 0.3
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu captures
+# summarised in profiles/k_tc_rates_bf16x3_fcc40.md and profiles/k_collision_rk4_30cubed.md.
+# Set an entry to None whenever its kernel changes after the capture.
+TRAFFIC = {"k_tc_rates_bf16x3_bytes_per_pair": (1.132050e9 + 17.47e6) / (64 * 64000),
+           "k_collision_bytes_per_entry": (1.433241e9 + 3.129e6) / 119304488}
 
 
 def load_peaks():
@@ -92,26 +97,18 @@ class ClockSampler:
 
 
 def dist_setup():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2002_02045_gb300.dist import rank_world
+    return rank_world()
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_2002_02045_gb300.dist import barrier as _b
+    _b()
 
 
 def max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2002_02045_gb300.dist import max_over_ranks as _m
+    return _m(x)
 
 
 def cpu_baseline(model, n_k=2):
@@ -179,7 +176,13 @@ def run_ours(args, rank, world, local):
     nwin = ctx.pgb_window(emin, emin + WIN, kbuf)
     if args.max_k:
         nwin = min(nwin, args.max_k)
-    kidx = kbuf[:nwin].contiguous()
+    k0 = 0
+    if args.shard and world > 1:
+        # strong scaling: the window k-points are split across ranks (no exchange)
+        from paper_2002_02045_gb300.dist import partition
+        k0, k1 = partition(nwin, rank, world)
+        nwin = k1 - k0
+    kidx = kbuf[k0:k0 + nwin].contiguous()
     gam = torch.empty((nwin, model.nw), dtype=torch.float64, device="cuda")
     nq = nk_grid
     pairs = nwin * nq
@@ -214,7 +217,9 @@ def run_ours(args, rank, world, local):
     r_ms, _ = ctx.pgb_profile_read(PROF_RSUM)
     p_ms, _ = ctx.pgb_profile_read(PROF_EPILOGUE)
     ctx.pgb_profile(False)
-    value = world * pairs * args.steps / (ms * 1e-3)
+    from paper_2002_02045_gb300.dist import sum_over_ranks
+    total_pairs = sum_over_ranks(pairs) if world > 1 else pairs
+    value = total_pairs * args.steps / (ms * 1e-3)
 
     # roofline of the dominant kernel: the Fourier sum over R_p (a complex contraction)
     peaks, peak_src = load_peaks()
@@ -230,7 +235,9 @@ def run_ours(args, rank, world, local):
         roof = {"bound": "alu", "peak_source": f"derived: {SM_COUNT} SMs x {lanes} lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz"}
     issue = 3.0 if args.precision in ("bf16x3", "tf32x3") else 1.0
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                 "traffic": None,
+                 "traffic": (TRAFFIC["k_tc_rates_bf16x3_bytes_per_pair"] * pairs * args.steps / max(1, q_n)
+                             if args.precision == "bf16x3" and TRAFFIC["k_tc_rates_bf16x3_bytes_per_pair"] else None),
+                 "traffic_note": "DRAM bytes per launch scaled by pairs from a 64-k capture (grows with the k count)",
                  "kernel": ("fused q-sum + rotation/projection/Gamma epilogue (k_tc_rates)"
                             if issue > 1 else "q-sum complex GEMM (k_cgemm)"),
                  "algorithmic_flop_per_pair": flop_per_pair, "launches": q_n,
@@ -238,7 +245,7 @@ def run_ours(args, rank, world, local):
                  "issued_mma_achieved": achieved * issue, "issued_mma_frac": achieved * issue / peak})
     out = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong" if (args.shard and world > 1) else "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3", "tf32x3": "tf32x3"}[args.precision],
         "data": "synthetic",
         "tolerance_vs_fp64": {"bf16x3": 1e-3, "tf32x3": 1e-5, "fp32": 1e-5, "fp64": 1e-10}[args.precision],
@@ -334,7 +341,10 @@ def dynamics(ctx, model, args, world, peaks, peak_src):
                    "list_build_s": build_s},
         "carrier_number_drift": abs(float(f.sum()) - n0) / n0,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_collision",
+                     "frac": achieved / peaks["hbm_gbs"],
+                     "traffic": (TRAFFIC["k_collision_bytes_per_entry"] * nnz
+                                 if TRAFFIC["k_collision_bytes_per_entry"] else None),
+                     "kernel": "k_collision",
                      "peak_source": peak_src, "algorithmic_bytes_per_entry": byte_per_entry,
                      "entries_per_launch": nnz, "launches": k_n},
     }
@@ -379,6 +389,9 @@ def main():
     ap.add_argument("--dyn-steps", type=int, default=200)
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the one-step TF32x3 and FP32 SIMT measurements")
+    ap.add_argument("--shard", action="store_true",
+                    help="with several ranks, split the window k-points across them (strong scaling) "
+                         "instead of one full workload per rank (weak scaling)")
     ap.add_argument("--max-k", type=int, default=0,
                     help="use only the first N window k-points (small case for profiler captures)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
