@@ -37,6 +37,13 @@ Pins (tests/test_oracle_*.py):
     Eq. scatter_rate); detailed balance on the ladder model.
   * ``rk4_step``/``euler_step``: fourth / first order convergence on the
     two-state closed form; carrier number conserved.
+  * ``collision_vjp``: central finite differences on an unsymmetric random
+    list with self-terms (I is quadratic in f and linear in |g|^2, so the
+    differences are exact up to rounding); J^T 1 = 0 and opposite |g|^2
+    derivatives of partner entries on a symmetric list.
+  * ``rk4_adjoint``: (P(dt A)^T)^n lam on linear systems, P the degree-4
+    Taylor polynomial; finite differences of ``evolve`` on a grid list; the
+    carrier-number covector 1 is carried back unchanged.
 Parity unpinned: absolute Gamma of real materials (no DFT data here).
 """
 from __future__ import annotations
@@ -331,6 +338,73 @@ def evolve(f0, dt_fs, nsteps, rhs, method="rk4"):
     for _ in range(nsteps):
         f = step(f, dt_fs * FS, rhs)
     return f
+
+
+# ----------------------------------------------------------------------------
+# reverse-mode derivatives of I[f] (Eq. e_ph_scattering) and of RK4 (Sec. 2.1.1)
+# ----------------------------------------------------------------------------
+
+def collision_vjp(f, lam, eps, row, col, hw, g2, T, sigma, nq_total):
+    """Products with the transposed derivatives of I[f] (Eq. e_ph_scattering).
+
+    Returns (J^T lam, d) with J_sc = dI_s/df_c and d[e] = sum_s lam_s dI_s/d|g|^2_e,
+    by the chain rule applied to each term of ``collision``: term e depends on
+    f_n = f[row[e]] and f_m = f[col[e]] through F_em and F_abs, is linear in
+    |g|^2_e, and enters I_row[e] with the factor -(2 pi/hbar)/N_q.
+    """
+    f = np.asarray(f, np.float64)
+    lam = np.asarray(lam, np.float64)
+    fn, fm = f[row], f[col]
+    en, em = eps[row], eps[col]
+    N = bose_einstein(hw, T)
+    live = np.asarray(hw) >= OMEGA_MIN_EV
+    d_em = delta_gauss(en - hw - em, sigma)
+    d_abs = delta_gauss(en + hw - em, sigma)
+    F_abs = fn * (1 - fm) * N - fm * (1 - fn) * (N + 1)
+    F_em = fn * (1 - fm) * (N + 1) - fm * (1 - fn) * N
+    dFabs_dfn = (1 - fm) * N + fm * (N + 1)
+    dFabs_dfm = -fn * N - (1 - fn) * (N + 1)
+    dFem_dfn = (1 - fm) * (N + 1) + fm * N
+    dFem_dfm = -fn * (N + 1) - (1 - fn) * N
+    w = np.where(live, -TWO_PI_OVER_HBAR / nq_total * lam[row], 0.0)
+    g2 = np.asarray(g2, np.float64)
+    out = np.zeros_like(f)
+    np.add.at(out, row, w * g2 * (d_em * dFem_dfn + d_abs * dFabs_dfn))
+    np.add.at(out, col, w * g2 * (d_em * dFem_dfm + d_abs * dFabs_dfm))
+    return out, w * (d_em * F_em + d_abs * F_abs)
+
+
+def rk4_adjoint(f0, dt_fs, nsteps, rhs, vjp, lam_end):
+    """Derivatives of a loss L(f(t_end)) through ``evolve(f0, dt_fs, nsteps, rhs)``.
+
+    ``vjp(x, kappa)`` returns (J(x)^T kappa, dtheta) for J = d rhs/dx at x and
+    dtheta = kappa . d rhs/dtheta of the rhs parameters theta.  Given
+    lam_end = dL/df(t_end), returns (dL/df0, dL/dtheta): reverse-mode
+    differentiation of each step f' = f + dt/6 (k1 + 2 k2 + 2 k3 + k4),
+    k1 = rhs(f), k2 = rhs(f + dt/2 k1), k3 = rhs(f + dt/2 k2), k4 = rhs(f + dt k3),
+    taken from the last step back to the first.  All forward states are kept.
+    """
+    dt = dt_fs * FS
+    states = [np.array(f0, np.float64)]
+    for _ in range(nsteps):
+        states.append(rk4_step(states[-1], dt, rhs))
+    lam = np.array(lam_end, np.float64)
+    dtheta = 0.0
+    for x1 in reversed(states[:-1]):
+        k1 = rhs(x1)
+        x2 = x1 + 0.5 * dt * k1
+        k2 = rhs(x2)
+        x3 = x1 + 0.5 * dt * k2
+        k3 = rhs(x3)
+        x4 = x1 + dt * k3
+        # adjoints of k4, k3, k2, k1 in turn; v_i is the adjoint reaching x_i
+        v4, t4 = vjp(x4, dt / 6.0 * lam)
+        v3, t3 = vjp(x3, dt / 3.0 * lam + dt * v4)
+        v2, t2 = vjp(x2, dt / 3.0 * lam + 0.5 * dt * v3)
+        v1, t1 = vjp(x1, dt / 6.0 * lam + 0.5 * dt * v2)
+        lam = lam + v1 + v2 + v3 + v4
+        dtheta = dtheta + t1 + t2 + t3 + t4
+    return lam, dtheta
 
 
 # ----------------------------------------------------------------------------
