@@ -156,7 +156,8 @@ pgb_status pgb_build_collision(pgb_ctx *ctx, int band_lo, int band_hi, double T_
 pgb_status pgb_build_collision_grid(pgb_ctx *ctx, int band_lo, int band_hi, double e_lo, double e_hi, double T_K,
                                     double sigma_eV, int64_t *nnz_out);
 
-/* Copy out the list built by pgb_build_collision_grid: row, col, mode int32
+/* Copy out the current list (as given to pgb_build_collision, or as built by
+ * pgb_build_collision_grid, with |g|^2 as last set): row, col, mode int32
  * and |g|^2 float32, [nnz] each (host or device; any may be NULL).           */
 pgb_status pgb_collision_list(pgb_ctx *ctx, int32_t *row, int32_t *col, int32_t *mode, float *g2);
 
@@ -168,6 +169,38 @@ pgb_status pgb_collision(pgb_ctx *ctx, const double *f, double *I_out);
 
 /* nsteps explicit RK4 steps (Sec. 2.1.1) of df/dt = I[f], step dt_fs, in place. */
 pgb_status pgb_step_rk4(pgb_ctx *ctx, double *f, double dt_fs, int64_t nsteps);
+
+/* Replace |g|^2 of every entry of the current list, keeping its rows,
+ * columns and modes: g2 [nnz] float32 (host or device), eV^2.  a and b are
+ * recomputed as in pgb_build_collision.  For fitting |g|^2 with the
+ * derivatives below.                                                         */
+pgb_status pgb_collision_set_g2(pgb_ctx *ctx, const float *g2);
+
+/* Reverse-mode derivatives of I[f] (Eq. e_ph_scattering) at f [nstates]:
+ * for a covector lam [nstates],
+ *   vjp_f[c]  = sum_s lam_s dI_s/df_c            [nstates], 1/s
+ *   vjp_g2[e] = sum_s lam_s dI_s/d|g|^2_e        [nnz] in list order, 1/(s eV^2)
+ * (vjp_g2 may be NULL).  Any list is accepted: the column sums run over a
+ * transposed copy of the list, built on first use and kept with the list.
+ * Arithmetic as pgb_collision (FP32 entry products, compensated sums, FP64
+ * per state).  All arrays host or device.                                    */
+pgb_status pgb_collision_vjp(pgb_ctx *ctx, const double *f, const double *lam, double *vjp_f, double *vjp_g2);
+
+/* Discrete adjoint of pgb_step_rk4 (Sec. 2.1.1 stepping of Eq. e_ph_scattering).
+ * Runs nsteps RK4 steps of dt_fs from f0 [nstates] (not modified) exactly as
+ * pgb_step_rk4 does, then for a loss L(f(t_end)) with lam_end = dL/df(t_end)
+ * [nstates] returns
+ *   lam_0  [nstates]  dL/df0 (the reverse-mode derivative of the RK4 steps
+ *                     as computed, stage by stage),
+ *   dL_dg2 [nnz]      dL/d|g|^2_e in list order, or NULL to skip it,
+ *   f_end  [nstates]  f(t_end), bit-identical to pgb_step_rk4, or NULL.
+ * f is kept every `checkpoint` steps (values < 1 mean 1) and each segment is
+ * recomputed once during the reverse sweep, storing its stage states: device
+ * memory is about (nsteps/checkpoint + 8 checkpoint + 12) nstates doubles,
+ * plus 8 nnz bytes with dL_dg2, plus 24 nnz bytes for the transposed list.
+ * All arrays host or device.                                                 */
+pgb_status pgb_rk4_adjoint(pgb_ctx *ctx, const double *f0, double dt_fs, int64_t nsteps, int64_t checkpoint,
+                           const double *lam_end, double *lam_0, double *dL_dg2, double *f_end);
 
 /* Allocation-free scattering rates (no counterpart in the paper).
  *
@@ -205,7 +238,8 @@ enum {
     PGB_PROF_EPILOGUE = 2,  /* rotation, mode projection, |g|^2, delta weights, Gamma      */
     PGB_PROF_COLLISION = 3, /* collision integral / RK4 stage                              */
     PGB_PROF_BANDS = 4,     /* H(k), D(q) sums and eigensolves                             */
-    PGB_PROF_NKERNELS = 5
+    PGB_PROF_ADJOINT = 5,   /* transposed-list column pass of the reverse-mode derivatives */
+    PGB_PROF_NKERNELS = 6
 };
 pgb_status pgb_profile(pgb_ctx *ctx, int enable);
 pgb_status pgb_profile_read(pgb_ctx *ctx, int kernel_class, double *total_ms, int64_t *launches);

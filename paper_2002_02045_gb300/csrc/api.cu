@@ -185,6 +185,7 @@ void free_coll(pgb_ctx *c) {
     dfree(&c->d_coo_col);
     dfree(&c->d_coo_mode);
     dfree(&c->d_coo_g2);
+    free_adjoint(c);
     c->has_coll = false;
     c->nstates = c->nnz = 0;
 }
@@ -840,7 +841,18 @@ pgb_status pgb_build_collision(pgb_ctx *c, int band_lo, int band_hi, double T, d
     c->band_hi = band_hi;
     c->nstates = ns;
     c->nnz = nnz;
-    pgb_status st = launch_coll_coeffs(c, T, sigma, R.dev, Cc.dev, M.dev, G.dev, nnz, nb);
+    // the list is kept on the device (pgb_collision_list, pgb_collision_set_g2, derivatives)
+    TRY(dalloc(c, &c->d_coo_row, (size_t)nnz));
+    TRY(dalloc(c, &c->d_coo_col, (size_t)nnz));
+    TRY(dalloc(c, &c->d_coo_mode, (size_t)nnz));
+    TRY(dalloc(c, &c->d_coo_g2, (size_t)nnz));
+    if (nnz > 0) {
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_coo_row, R.dev, 4 * (size_t)nnz, cudaMemcpyDeviceToDevice, c->stream));
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_coo_col, Cc.dev, 4 * (size_t)nnz, cudaMemcpyDeviceToDevice, c->stream));
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_coo_mode, M.dev, 4 * (size_t)nnz, cudaMemcpyDeviceToDevice, c->stream));
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_coo_g2, G.dev, 4 * (size_t)nnz, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    pgb_status st = launch_coll_coeffs(c, T, sigma, c->d_coo_row, c->d_coo_col, c->d_coo_mode, c->d_coo_g2, nnz, nb);
     if (st != PGB_OK) {
         std::string e = c->err;
         free_coll(c);
@@ -920,6 +932,62 @@ pgb_status pgb_step_rk4(pgb_ctx *c, double *f, double dt_fs, int64_t nsteps) {
         cudaFreeAsync(tmp, c->stream);
     }
     return st;
+}
+
+pgb_status pgb_collision_set_g2(pgb_ctx *c, const float *g2) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_coll) return fail(c, PGB_ESTATE, "collision_set_g2: call build_collision first");
+    const size_t n = (size_t)c->nnz;
+    if (n == 0) return PGB_OK;
+    In<float> G;
+    TRY(G.init(c, g2, n));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_coo_g2, G.dev, 4 * n, cudaMemcpyDeviceToDevice, c->stream));
+    TRY(launch_coll_values(c, c->d_coo_row, c->d_coo_col, c->d_coo_mode, c->d_coo_g2, c->nnz));
+    TRY(launch_coll_rowsum(c));
+    TRY(adjoint_values_changed(c));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PGB_OK;
+}
+
+pgb_status pgb_collision_vjp(pgb_ctx *c, const double *f, const double *lam, double *vjp_f, double *vjp_g2) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_coll) return fail(c, PGB_ESTATE, "collision_vjp: call build_collision first");
+    if (!f || !lam || !vjp_f) return fail(c, PGB_EINVAL, "collision_vjp: null pointer");
+    const size_t ns = (size_t)c->nstates;
+    In<double> F, L;
+    TRY(F.init(c, f, ns));
+    TRY(L.init(c, lam, ns));
+    Out<double> V, G;
+    TRY(V.init(c, vjp_f, ns));
+    TRY(G.init(c, vjp_g2, (size_t)c->nnz));
+    TRY(collision_vjp(c, F.dev, L.dev, V.dev, G.dev));
+    TRY(V.finish());
+    TRY(G.finish());
+    return PGB_OK;
+}
+
+pgb_status pgb_rk4_adjoint(pgb_ctx *c, const double *f0, double dt_fs, int64_t nsteps, int64_t checkpoint,
+                           const double *lam_end, double *lam_0, double *dL_dg2, double *f_end) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_coll) return fail(c, PGB_ESTATE, "rk4_adjoint: call build_collision first");
+    if (!f0 || !lam_end || !lam_0) return fail(c, PGB_EINVAL, "rk4_adjoint: null pointer");
+    if (nsteps < 0 || !std::isfinite(dt_fs)) return fail(c, PGB_EINVAL, "rk4_adjoint: bad step");
+    const size_t ns = (size_t)c->nstates;
+    In<double> F, L;
+    TRY(F.init(c, f0, ns));
+    TRY(L.init(c, lam_end, ns));
+    Out<double> L0, G, FE;
+    TRY(L0.init(c, lam_0, ns));
+    TRY(G.init(c, dL_dg2, (size_t)c->nnz));
+    TRY(FE.init(c, f_end, ns));
+    TRY(rk4_adjoint(c, F.dev, dt_fs, nsteps, checkpoint, L.dev, L0.dev, G.dev, FE.dev));
+    TRY(L0.finish());
+    TRY(G.finish());
+    TRY(FE.finish());
+    return PGB_OK;
 }
 
 pgb_status pgb_diag_bands(pgb_ctx *c, const double *pts, int64_t n, double *Hk, double *eps, double *U) {
@@ -1067,7 +1135,7 @@ pgb_status pgb_build_collision_grid(pgb_ctx *c, int band_lo, int band_hi, double
 pgb_status pgb_collision_list(pgb_ctx *c, int32_t *row, int32_t *col, int32_t *mode, float *g2) {
     if (!c) return PGB_EINVAL;
     cudaSetDevice(c->device);
-    if (!c->has_coll || !c->d_coo_row) return fail(c, PGB_ESTATE, "collision_list: no list built from the grid");
+    if (!c->has_coll) return fail(c, PGB_ESTATE, "collision_list: call build_collision first");
     const size_t n = (size_t)c->nnz;
     if (row) PGB_CUDA_TRY(c, cudaMemcpyAsync(row, c->d_coo_row, 4 * n, cudaMemcpyDefault, c->stream));
     if (col) PGB_CUDA_TRY(c, cudaMemcpyAsync(col, c->d_coo_col, 4 * n, cudaMemcpyDefault, c->stream));

@@ -2,6 +2,7 @@
 // the fused RK4 stages (Sec. 2.1.1).
 #include <vector>
 
+#include "coeffs.cuh"
 #include "internal.cuh"
 
 namespace pgb {
@@ -31,20 +32,15 @@ __global__ void k_coll_validate(int64_t nnz, int64_t nstates, int nm, const int3
 // ---------------------------------------------------------------------------
 // Per-entry coefficients, FP64 arithmetic, stored FP32:
 //   a = scale |g|^2 [d_em (N+1) + d_abs N],  b = scale |g|^2 [d_em N + d_abs (N+1)]
-// d_em = e^{-(x_em/s)^2}, x_em = (e_s - e_s') - hw, x_abs = (e_s - e_s') + hw,
-// scale = (2 pi/hbar) / (N_q s sqrt(pi)).  Because e_s' - e_s is the exact
-// negation of e_s - e_s', the reverse entry of a process gets a' = b and
-// b' = a bit for bit, so that sum_s I_s = 0 is not broken by the list.
+// scale = (2 pi/hbar) / (N_q s sqrt(pi)).  The reverse entry of a process gets
+// a' = b and b' = a bit for bit (coll_brackets), so that sum_s I_s = 0 is not
+// broken by the list.
 // ---------------------------------------------------------------------------
 struct CoeffArgs {
     int64_t nnz;
     const int32_t *row, *col, *mode;
     const float *g2;
-    int nb, band_lo, nw, nm;
-    int kg[3];
-    const double *eps;   // [Nk][nw]
-    const double *hw;    // [Nq][nm] (q grid == k grid)
-    double T, sigma, scale;
+    CoeffGeom g;
     int32_t *out_col;
     float *a, *b;
 };
@@ -52,32 +48,12 @@ struct CoeffArgs {
 __global__ void k_coll_coeffs(CoeffArgs p) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= p.nnz) return;
-    const int32_t s = p.row[e], sp = p.col[e];
-    const int64_t k = s / p.nb, kp = sp / p.nb;
-    const int n = s % p.nb + p.band_lo, m = sp % p.nb + p.band_lo;
-    const int k3 = (int)(k % p.kg[2]), k2 = (int)((k / p.kg[2]) % p.kg[1]), k1 = (int)(k / ((int64_t)p.kg[1] * p.kg[2]));
-    const int l3 = (int)(kp % p.kg[2]), l2 = (int)((kp / p.kg[2]) % p.kg[1]), l1 = (int)(kp / ((int64_t)p.kg[1] * p.kg[2]));
-    const int q1 = (l1 - k1 + p.kg[0]) % p.kg[0], q2 = (l2 - k2 + p.kg[1]) % p.kg[1], q3 = (l3 - k3 + p.kg[2]) % p.kg[2];
-    // q and -q have the same frequencies; the smaller of the two indices is
-    // used so that both directions of a process see bit-identical hw
-    const int64_t q = ((int64_t)q1 * p.kg[1] + q2) * p.kg[2] + q3;
-    const int r1 = (p.kg[0] - q1) % p.kg[0], r2 = (p.kg[1] - q2) % p.kg[1], r3 = (p.kg[2] - q3) % p.kg[2];
-    const int64_t qm = ((int64_t)r1 * p.kg[1] + r2) * p.kg[2] + r3;
-    const double w = p.hw[(q < qm ? q : qm) * p.nm + p.mode[e]];
-    double a = 0.0, b = 0.0;
-    if (w >= kOmegaMinEv) {
-        const double N = 1.0 / expm1(w / (kBoltzEvK * p.T));
-        const double d = p.eps[k * p.nw + n] - p.eps[kp * p.nw + m];
-        const double is = 1.0 / p.sigma;
-        const double xe = (d - w) * is, xa = (d + w) * is;
-        const double de = exp(-xe * xe), da = exp(-xa * xa);
-        const double g = p.scale * (double)p.g2[e];
-        a = g * (de * (N + 1.0) + da * N);
-        b = g * (de * N + da * (N + 1.0));
-    }
-    p.out_col[e] = sp;
-    p.a[e] = (float)a;
-    p.b[e] = (float)b;
+    double ca, cb;
+    coll_brackets(p.g, p.row[e], p.col[e], p.mode[e], ca, cb);
+    const double gs = p.g.scale * (double)p.g2[e];
+    p.out_col[e] = p.col[e];
+    p.a[e] = (float)(gs * ca);
+    p.b[e] = (float)(gs * cb);
 }
 
 __global__ void k_rowptr(int64_t nstates, int64_t nnz, const int32_t *__restrict__ row, int64_t *__restrict__ rowptr) {
@@ -113,6 +89,48 @@ __global__ void k_rowsum(int64_t nstates, const int64_t *__restrict__ rowptr, co
     if (lane == 0) out[s] = acc;
 }
 
+CoeffGeom coeff_geom(const pgb_ctx *c) {
+    CoeffGeom g;
+    g.nb = c->coll_nb;
+    g.band_lo = c->band_lo;
+    g.nw = c->nw;
+    g.nm = c->nm;
+    for (int d = 0; d < 3; ++d) g.kg[d] = c->kg[d];
+    g.eps = c->d_eps;
+    g.hw = c->d_hw;
+    g.T = c->coll_T;
+    g.sigma = c->coll_sigma;
+    g.scale = kTwoPiOverHbar / ((double)c->Nq * c->coll_sigma * kSqrtPi);
+    return g;
+}
+
+// a, b (and the column copy) of every entry from |g|^2; the row sums of a follow
+// once the row pointers exist.
+pgb_status launch_coll_values(pgb_ctx *c, const int32_t *row, const int32_t *col, const int32_t *mode,
+                              const float *g2, int64_t nnz) {
+    if (nnz == 0) return PGB_OK;
+    CoeffArgs p;
+    p.nnz = nnz;
+    p.row = row;
+    p.col = col;
+    p.mode = mode;
+    p.g2 = g2;
+    p.g = coeff_geom(c);
+    p.out_col = c->d_col;
+    p.a = c->d_a;
+    p.b = c->d_b;
+    k_coll_coeffs<<<div_up(nnz, 256), 256, 0, c->stream>>>(p);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+pgb_status launch_coll_rowsum(pgb_ctx *c) {
+    if (c->nstates == 0) return PGB_OK;
+    k_rowsum<<<div_up(c->nstates * 32, 256), 256, 0, c->stream>>>(c->nstates, c->d_rowptr, c->d_a, c->d_rowsum_a);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
 pgb_status launch_coll_coeffs(pgb_ctx *c, double T, double sigma, const int32_t *row, const int32_t *col,
                               const int32_t *mode, const float *g2, int64_t nnz, int nb) {
     const int64_t ns = c->nstates;
@@ -146,29 +164,10 @@ pgb_status launch_coll_coeffs(pgb_ctx *c, double T, double sigma, const int32_t 
 
     k_eps_state<<<div_up(ns, 256), 256, 0, c->stream>>>(ns, nb, c->band_lo, c->nw, c->d_eps, c->d_eps_state);
     PGB_LAUNCH_CHECK(c);
-    if (nnz > 0) {
-        CoeffArgs p;
-        p.nnz = nnz;
-        p.row = row;
-        p.col = col;
-        p.mode = mode;
-        p.g2 = g2;
-        p.nb = nb;
-        p.band_lo = c->band_lo;
-        p.nw = c->nw;
-        p.nm = c->nm;
-        for (int d = 0; d < 3; ++d) p.kg[d] = c->kg[d];
-        p.eps = c->d_eps;
-        p.hw = c->d_hw;
-        p.T = T;
-        p.sigma = sigma;
-        p.scale = kTwoPiOverHbar / ((double)c->Nq * sigma * kSqrtPi);
-        p.out_col = c->d_col;
-        p.a = c->d_a;
-        p.b = c->d_b;
-        k_coll_coeffs<<<div_up(nnz, 256), 256, 0, c->stream>>>(p);
-        PGB_LAUNCH_CHECK(c);
-    }
+    c->coll_T = T;
+    c->coll_sigma = sigma;
+    c->coll_nb = nb;
+    if ((st = launch_coll_values(c, row, col, mode, g2, nnz)) != PGB_OK) return st;
     k_rowptr<<<div_up(ns + 1, 256), 256, 0, c->stream>>>(ns, nnz, row, c->d_rowptr);
     PGB_LAUNCH_CHECK(c);
     k_rowsum<<<div_up(ns * 32, 256), 256, 0, c->stream>>>(ns, c->d_rowptr, c->d_a, c->d_rowsum_a);
@@ -199,7 +198,8 @@ pgb_status launch_coll_coeffs(pgb_ctx *c, double T, double sigma, const int32_t 
 // so no per-entry work touches FP64: f_c is gathered from an FP32 copy written
 // by the previous stage, products and running sums are FP32 with Kahan
 // compensation, and only the per-row combination is FP64.  Stage -1 writes I; stages 0..3 fuse the RK4
-// combinations:
+// combinations (any stage can also write the diagonal of dI/df, which the
+// reverse-mode pass needs):
 //   0: acc = k1,  next = f + dt/2 k1      1: acc += 2 k2, next = f + dt/2 k2
 //   2: acc += 2 k3, next = f + dt k3      3: f = f + dt/6 (acc + k4)
 // Empty rows have I = 0 and are not launched; their stage values stay f.
@@ -218,6 +218,7 @@ struct CollArgs {
     double *acc;
     double *fnext;
     float *fnext32;       // FP32 copy of fnext (stages 0..3)
+    double *D;            // if set: dI_s/df_s = -sum a + sum f_c a - sum f_c b (any stage)
     double dt;            // seconds
     int stage;
 };
@@ -289,6 +290,7 @@ __global__ void __launch_bounds__(kCollThreads) k_collision(CollArgs p) {
         }
         const double fs = p.fin[s];
         const double I = -fs * p.rowsum_a[s] + fs * sfa + (1.0 - fs) * sfb;
+        if (p.D) p.D[s] = -p.rowsum_a[s] + sfa - sfb;
         double fn = 0.0;
         switch (p.stage) {
             case -1:
@@ -330,7 +332,7 @@ pgb_status launch_f64_to_f32(pgb_ctx *c, const double *x, float *y, int64_t n) {
 }
 
 pgb_status launch_collision(pgb_ctx *c, const double *f, const float *f32, double *I, int stage, double dt,
-                            double *acc, double *fnext, float *fnext32, const double *fbase) {
+                            double *acc, double *fnext, float *fnext32, const double *fbase, double *D) {
     if (c->nstates == 0) return PGB_OK;
     if (stage == -1) PGB_CUDA_TRY(c, cudaMemsetAsync(I, 0, 8 * (size_t)c->nstates, c->stream));
     if (c->nrows_active == 0) return PGB_OK;
@@ -349,6 +351,7 @@ pgb_status launch_collision(pgb_ctx *c, const double *f, const float *f32, doubl
     p.acc = acc;
     p.fnext = fnext;
     p.fnext32 = fnext32;
+    p.D = D;
     p.dt = dt;
     p.stage = stage;
     prof_mark(c, PGB_PROF_COLLISION);

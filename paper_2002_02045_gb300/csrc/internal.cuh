@@ -84,8 +84,20 @@ struct pgb_ctx {
     int64_t nrows_active = 0;
     double *d_f[4] = {nullptr, nullptr, nullptr, nullptr};  // RK4 stage buffers
     float *d_f32[3] = {nullptr, nullptr, nullptr};          // FP32 copies gathered by the collision kernel
-    int32_t *d_coo_row = nullptr, *d_coo_col = nullptr, *d_coo_mode = nullptr;  // list built from the grid
+    int32_t *d_coo_row = nullptr, *d_coo_col = nullptr, *d_coo_mode = nullptr;  // the list as given or built
     float *d_coo_g2 = nullptr;
+    double coll_T = 0.0, coll_sigma = 0.0;
+    int coll_nb = 0;
+
+    // transposed list for the reverse-mode pass, built on first use
+    bool adj_ready = false;
+    int64_t *d_t_colptr = nullptr;   // [nstates+1] entries with col == c
+    int32_t *d_t_src = nullptr;      // [nnz] row of each transposed entry
+    int32_t *d_t_eidx = nullptr;     // [nnz] its index in the list
+    float *d_t_a = nullptr, *d_t_b = nullptr;           // a, b of the list
+    float *d_t_alpha = nullptr, *d_t_beta = nullptr;    // a / |g|^2, b / |g|^2
+    int32_t *d_t_active = nullptr;   // columns with entries
+    int64_t t_nactive = 0;
 
     // scratch (grown on demand, freed in destroy)
     void *scratch = nullptr;
@@ -247,7 +259,17 @@ pgb_status list_sort_decode(pgb_ctx *c, int64_t n, int ns, uint64_t *keys, float
 pgb_status launch_coll_coeffs(pgb_ctx *c, double T, double sigma, const int32_t *row, const int32_t *col,
                               const int32_t *mode, const float *g2, int64_t nnz, int nb);
 pgb_status launch_collision(pgb_ctx *c, const double *f, const float *f32, double *I, int stage, double dt,
-                            double *acc, double *fnext, float *fnext32, const double *fbase);
+                            double *acc, double *fnext, float *fnext32, const double *fbase, double *D = nullptr);
+pgb_status launch_coll_values(pgb_ctx *c, const int32_t *row, const int32_t *col, const int32_t *mode,
+                              const float *g2, int64_t nnz);
+pgb_status launch_coll_rowsum(pgb_ctx *c);
+void free_adjoint(pgb_ctx *c);
+pgb_status adjoint_values_changed(pgb_ctx *c);   // a, b of the list were recomputed
+
+// reverse-mode derivatives of the collision integral and RK4 (adjoint.cu); device pointers
+pgb_status collision_vjp(pgb_ctx *c, const double *f, const double *lam, double *out_f, double *out_g2);
+pgb_status rk4_adjoint(pgb_ctx *c, const double *f0, double dt_fs, int64_t nsteps, int64_t ckpt,
+                       const double *lam_end, double *lam0, double *dg2, double *f_end);
 pgb_status launch_f64_to_f32(pgb_ctx *c, const double *x, float *y, int64_t n);
 
 }  // namespace pgb

@@ -29,9 +29,10 @@ ABI_SYMBOLS = (
     "pgb_scattering_rates", "pgb_build_collision", "pgb_collision_energies", "pgb_collision",
     "pgb_step_rk4", "pgb_launch_count", "pgb_profile", "pgb_profile_read",
     "pgb_scattering_rates_noalloc", "pgb_build_collision_grid", "pgb_collision_list",
+    "pgb_collision_set_g2", "pgb_collision_vjp", "pgb_rk4_adjoint",
 )
 PGB_NOALLOC_SCRATCH_BYTES = 64 << 20
-PROF_QSUM, PROF_RSUM, PROF_EPILOGUE, PROF_COLLISION, PROF_BANDS = 0, 1, 2, 3, 4
+PROF_QSUM, PROF_RSUM, PROF_EPILOGUE, PROF_COLLISION, PROF_BANDS, PROF_ADJOINT = 0, 1, 2, 3, 4, 5
 
 
 class PgbModel(C.Structure):
@@ -79,6 +80,9 @@ def load(path: str = LIB_PATH):
         "pgb_collision_list": (I, [P, P, P, P, P]),
         "pgb_collision": (I, [P, P, P]),
         "pgb_step_rk4": (I, [P, P, D, I64]),
+        "pgb_collision_set_g2": (I, [P, P]),
+        "pgb_collision_vjp": (I, [P, P, P, P, P]),
+        "pgb_rk4_adjoint": (I, [P, P, D, I64, I64, P, P, P, P]),
         "pgb_launch_count": (I64, [P]),
         "pgb_profile": (I, [P, I]),
         "pgb_scattering_rates_noalloc": (I, [P, P, I64, D, D, D, P]),
@@ -247,6 +251,21 @@ class Context:
     def pgb_step_rk4(self, f, dt_fs, nsteps):
         _check_dtype(f, "float64")
         self._chk(self.lib.pgb_step_rk4(self._h, _ptr(f), float(dt_fs), int(nsteps)))
+
+    def pgb_collision_set_g2(self, g2):
+        _check_dtype(g2, "float32")
+        self._chk(self.lib.pgb_collision_set_g2(self._h, _ptr(g2)))
+
+    def pgb_collision_vjp(self, f, lam, vjp_f, vjp_g2=None):
+        for a in (f, lam, vjp_f, vjp_g2):
+            _check_dtype(a, "float64")
+        self._chk(self.lib.pgb_collision_vjp(self._h, _ptr(f), _ptr(lam), _ptr(vjp_f), _ptr(vjp_g2)))
+
+    def pgb_rk4_adjoint(self, f0, dt_fs, nsteps, checkpoint, lam_end, lam_0, dL_dg2=None, f_end=None):
+        for a in (f0, lam_end, lam_0, dL_dg2, f_end):
+            _check_dtype(a, "float64")
+        self._chk(self.lib.pgb_rk4_adjoint(self._h, _ptr(f0), float(dt_fs), int(nsteps), int(checkpoint),
+                                           _ptr(lam_end), _ptr(lam_0), _ptr(dL_dg2), _ptr(f_end)))
 
     def pgb_launch_count(self):
         return int(self.lib.pgb_launch_count(self._h))
