@@ -312,6 +312,7 @@ def dynamics(ctx, model, args, world, peaks, peak_src):
     es = torch.empty((2 * nk,), dtype=torch.float64, device="cuda")
     ctx.pgb_collision_energies(es)
     f = torch.as_tensor(S.pulse_occupations(es.cpu().numpy(), emin)).cuda()
+    f_pulse = f.clone()
     n0 = float(f.sum())
     ctx.pgb_step_rk4(f, 1.0, 5)                       # warm-up
     torch.cuda.synchronize()
@@ -331,6 +332,7 @@ def dynamics(ctx, model, args, world, peaks, peak_src):
     evals = 4 * args.dyn_steps
     byte_per_entry = 12.0
     achieved = byte_per_entry * nnz * evals / (k_ms * 1e-3) / 1e9
+    adj = adjoint(ctx, f_pulse, nnz, args, world, peaks, peak_src, ms / args.dyn_steps) if args.adj_steps > 0 else None
     return {
         "metric": "collision-entry evaluations/s (RK4, 4 evaluations per step)",
         "value": world * nnz * evals / (ms * 1e-3), "unit": "entries/s",
@@ -347,6 +349,59 @@ def dynamics(ctx, model, args, world, peaks, peak_src):
                      "kernel": "k_collision",
                      "peak_source": peak_src, "algorithmic_bytes_per_entry": byte_per_entry,
                      "entries_per_launch": nnz, "launches": k_n},
+        "adjoint": adj,
+    }
+
+
+def adjoint(ctx, f, nnz, args, world, peaks, peak_src, fwd_ms_per_step):
+    """Reverse-mode RK4 on the same list: dL/df0 and dL/d|g|^2 of the mean carrier
+    energy at t_end, L = sum_s e_s f_s / sum_s f_s, through adj_steps steps from
+    the pulse (forward with checkpoints, segment recompute, four transposed-list
+    column passes per step), timed after one warm-up call that also builds the
+    transposed list.  dL/df(t_end) = (e_s - L) / sum_s f_s is the loss's own
+    derivative, formed by the caller."""
+    import torch
+    from paper_2002_02045_gb300.native import PROF_ADJOINT
+    ns = f.numel()
+    es = torch.empty(ns, dtype=torch.float64, device="cuda")
+    ctx.pgb_collision_energies(es)
+    fe = f.clone()
+    ctx.pgb_step_rk4(fe, 1.0, args.adj_steps)
+    n_end = fe.sum()
+    w = (es - (es * fe).sum() / n_end) / n_end
+    lam0 = torch.empty_like(f)
+    dg2 = torch.empty(nnz, dtype=torch.float64, device="cuda")
+    ck = args.adj_checkpoint
+    ctx.pgb_rk4_adjoint(f, 1.0, 2, ck, w, lam0, dg2)          # warm-up, transposed list
+    torch.cuda.synchronize()
+    ctx.pgb_profile(True)
+    ctx.pgb_profile_read(PROF_ADJOINT)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.pgb_rk4_adjoint(f, 1.0, args.adj_steps, ck, w, lam0, dg2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    k_ms, k_n = ctx.pgb_profile_read(PROF_ADJOINT)
+    ctx.pgb_profile(False)
+    # per entry and column pass: src, a, b, alpha, beta (4 B each) + FP64 read-modify-write of dL/d|g|^2
+    byte_per_entry = 36.0
+    achieved = byte_per_entry * nnz * k_n / (k_ms * 1e-3) / 1e9
+    return {
+        "metric": "reverse-mode RK4 steps/s (dL/df0 and dL/d|g|^2 of the final mean carrier energy, "
+                  "forward + recompute + reverse)",
+        "value": world * args.adj_steps / (ms * 1e-3), "unit": "steps/s", "steps": args.adj_steps,
+        "checkpoint": ck, "ms_per_step": ms / args.adj_steps,
+        "ratio_to_forward_step": (ms / args.adj_steps) / fwd_ms_per_step,
+        "finite": bool(torch.isfinite(lam0).all() and torch.isfinite(dg2).all()),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_adj_col",
+                     "peak_source": peak_src, "algorithmic_bytes_per_entry": byte_per_entry,
+                     "entries_per_launch": nnz, "launches": k_n,
+                     "kernel_ms_share": k_ms / ms},
     }
 
 
@@ -386,7 +441,10 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "fp64", "bf16x3", "tf32x3"])
     ap.add_argument("--no-dynamics", dest="dynamics", action="store_false",
                     help="skip the real-time BTE (collision + RK4) measurement")
-    ap.add_argument("--dyn-steps", type=int, default=200)
+    ap.add_argument("--dyn-steps", type=int, default=1000)
+    ap.add_argument("--adj-steps", type=int, default=1000,
+                    help="reverse-mode RK4 steps timed on the dynamics list (0: skip)")
+    ap.add_argument("--adj-checkpoint", type=int, default=50)
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the one-step TF32x3 and FP32 SIMT measurements")
     ap.add_argument("--shard", action="store_true",

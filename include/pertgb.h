@@ -194,8 +194,10 @@ pgb_status pgb_collision_vjp(pgb_ctx *ctx, const double *f, const double *lam, d
  *                     as computed, stage by stage),
  *   dL_dg2 [nnz]      dL/d|g|^2_e in list order, or NULL to skip it,
  *   f_end  [nstates]  f(t_end), bit-identical to pgb_step_rk4, or NULL.
- * f is kept every `checkpoint` steps (values < 1 mean 1) and each segment is
- * recomputed once during the reverse sweep, storing its stage states: device
+ * f is kept every `checkpoint` steps (values < 1 mean 1); the last segment
+ * stores its stage states during the forward pass and every other segment is
+ * recomputed once during the reverse sweep (with checkpoint >= nsteps there
+ * is no recomputation at all).  Device
  * memory is about (nsteps/checkpoint + 8 checkpoint + 12) nstates doubles,
  * plus 8 nnz bytes with dL_dg2, plus 24 nnz bytes for the transposed list.
  * All arrays host or device.                                                 */

@@ -21,10 +21,11 @@
 //   v2 = J(x2)^T (dt/3 lam + dt/2 v3)
 //   v1 = J(x1)^T (dt/6 lam + dt/2 v2)
 //   dL/df = lam + v1 + v2 + v3 + v4
-// The forward pass keeps f every `ckpt` steps.  The reverse pass recomputes one
-// segment at a time with the forward stage kernels, which also store every
-// stage state and D; the recomputed states are bit-identical to the forward
-// ones, and each reverse step is four column passes.
+// The forward pass keeps f every `ckpt` steps and runs the last segment with
+// the stage kernels storing every stage state and D.  The reverse pass
+// recomputes each earlier segment the same way from its checkpoint (the
+// recomputed states are bit-identical to the forward ones), and each reverse
+// step is four column passes.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -441,8 +442,33 @@ pgb_status rk4_adjoint(pgb_ctx *c, const double *f0, double dt_fs, int64_t nstep
     }
     if (R.acc) PGB_CUDA_TRY(c, cudaMemsetAsync(R.acc, 0, 8 * (size_t)nnz, c->stream));
 
-    // forward pass, as pgb_step_rk4, keeping f at the start of every segment.
-    // States without entries keep f0 in every buffer (their I is 0).
+    auto xs = [&](int64_t j, int i) { return X + (4 * j + i) * ns; };
+    auto ds = [&](int64_t j, int i) { return Dm + (4 * j + i) * ns; };
+    // n_in steps from xs(0, 0) (FP32 copy in g[0]) storing every stage state and
+    // D; the state after the last step goes to `tail`
+    auto stored_segment = [&](int64_t n_in) -> pgb_status {
+        pgb_status s2;
+        for (int64_t j = 0; j < n_in; ++j) {
+            double *x0 = xs(j, 0), *nxt = j + 1 < n_in ? xs(j + 1, 0) : tail;
+            if ((s2 = launch_collision(c, x0, g[0], nullptr, 0, dt, acc4, xs(j, 1), g[1], x0, ds(j, 0))) != PGB_OK)
+                return s2;
+            if ((s2 = launch_collision(c, xs(j, 1), g[1], nullptr, 1, dt, acc4, xs(j, 2), g[2], x0, ds(j, 1))) !=
+                PGB_OK)
+                return s2;
+            if ((s2 = launch_collision(c, xs(j, 2), g[2], nullptr, 2, dt, acc4, xs(j, 3), g[1], x0, ds(j, 2))) !=
+                PGB_OK)
+                return s2;
+            if ((s2 = launch_collision(c, xs(j, 3), g[1], nullptr, 3, dt, acc4, nxt, g[0], x0, ds(j, 3))) != PGB_OK)
+                return s2;
+        }
+        return PGB_OK;
+    };
+
+    // States without entries keep f0 in every buffer and slot (their I is 0), D = 0.
+    k_bcast<<<div_up(4 * ckpt * ns, 256), 256, 0, c->stream>>>(ns, 4 * ckpt, f0, X);
+    PGB_LAUNCH_CHECK(c);
+    PGB_CUDA_TRY(c, cudaMemsetAsync(Dm, 0, 4 * (size_t)ckpt * nb8, c->stream));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(tail, f0, nb8, cudaMemcpyDeviceToDevice, c->stream));
     PGB_CUDA_TRY(c, cudaMemcpyAsync(cps, f0, nb8, cudaMemcpyDeviceToDevice, c->stream));
     PGB_CUDA_TRY(c, cudaMemcpyAsync(cur, f0, nb8, cudaMemcpyDeviceToDevice, c->stream));
     PGB_CUDA_TRY(c, cudaMemcpyAsync(f1, f0, nb8, cudaMemcpyDeviceToDevice, c->stream));
@@ -450,8 +476,17 @@ pgb_status rk4_adjoint(pgb_ctx *c, const double *f0, double dt_fs, int64_t nstep
     if ((st = launch_f64_to_f32(c, f0, g[0], ns)) != PGB_OK) return st;
     PGB_CUDA_TRY(c, cudaMemcpyAsync(g[1], g[0], nb4, cudaMemcpyDeviceToDevice, c->stream));
     PGB_CUDA_TRY(c, cudaMemcpyAsync(g[2], g[0], nb4, cudaMemcpyDeviceToDevice, c->stream));
+    // forward pass with the stage kernels of pgb_step_rk4, keeping f at the
+    // start of every segment; the last segment, the first to be reversed,
+    // stores its stage states directly
     for (int64_t sg = 0; sg < nseg; ++sg) {
         const int64_t n_in = std::min<int64_t>(ckpt, nsteps - sg * ckpt);
+        if (sg == nseg - 1) {
+            PGB_CUDA_TRY(c, cudaMemcpyAsync(xs(0, 0), cur, nb8, cudaMemcpyDeviceToDevice, c->stream));
+            if ((st = stored_segment(n_in)) != PGB_OK) return st;
+            PGB_CUDA_TRY(c, cudaMemcpyAsync(cps + (sg + 1) * ns, tail, nb8, cudaMemcpyDeviceToDevice, c->stream));
+            break;
+        }
         for (int64_t j = 0; j < n_in; ++j) {
             if ((st = launch_collision(c, cur, g[0], nullptr, 0, dt, acc4, f1, g[1], cur)) != PGB_OK) return st;
             if ((st = launch_collision(c, f1, g[1], nullptr, 1, dt, acc4, f2, g[2], cur)) != PGB_OK) return st;
@@ -462,30 +497,13 @@ pgb_status rk4_adjoint(pgb_ctx *c, const double *f0, double dt_fs, int64_t nstep
     }
     if (f_end) PGB_CUDA_TRY(c, cudaMemcpyAsync(f_end, cps + nseg * ns, nb8, cudaMemcpyDeviceToDevice, c->stream));
 
-    // stage-state slots hold f0 (and D = 0) in rows without entries
-    k_bcast<<<div_up(4 * ckpt * ns, 256), 256, 0, c->stream>>>(ns, 4 * ckpt, f0, X);
-    PGB_LAUNCH_CHECK(c);
-    PGB_CUDA_TRY(c, cudaMemsetAsync(Dm, 0, 4 * (size_t)ckpt * nb8, c->stream));
     PGB_CUDA_TRY(c, cudaMemcpyAsync(lam, lam_end, nb8, cudaMemcpyDeviceToDevice, c->stream));
-    auto xs = [&](int64_t j, int i) { return X + (4 * j + i) * ns; };
-    auto ds = [&](int64_t j, int i) { return Dm + (4 * j + i) * ns; };
     for (int64_t sg = nseg - 1; sg >= 0; --sg) {
         const int64_t n_in = std::min<int64_t>(ckpt, nsteps - sg * ckpt);
-        // recompute the segment, storing every stage state and D
-        PGB_CUDA_TRY(c, cudaMemcpyAsync(xs(0, 0), cps + sg * ns, nb8, cudaMemcpyDeviceToDevice, c->stream));
-        if ((st = launch_f64_to_f32(c, xs(0, 0), g[0], ns)) != PGB_OK) return st;
-        for (int64_t j = 0; j < n_in; ++j) {
-            double *x0 = xs(j, 0), *nxt = j + 1 < n_in ? xs(j + 1, 0) : tail;
-            if ((st = launch_collision(c, x0, g[0], nullptr, 0, dt, acc4, xs(j, 1), g[1], x0, ds(j, 0))) != PGB_OK)
-                return st;
-            if ((st = launch_collision(c, xs(j, 1), g[1], nullptr, 1, dt, acc4, xs(j, 2), g[2], x0, ds(j, 1))) !=
-                PGB_OK)
-                return st;
-            if ((st = launch_collision(c, xs(j, 2), g[2], nullptr, 2, dt, acc4, xs(j, 3), g[1], x0, ds(j, 2))) !=
-                PGB_OK)
-                return st;
-            if ((st = launch_collision(c, xs(j, 3), g[1], nullptr, 3, dt, acc4, nxt, g[0], x0, ds(j, 3))) != PGB_OK)
-                return st;
+        if (sg < nseg - 1) {   // recompute the segment from its checkpoint
+            PGB_CUDA_TRY(c, cudaMemcpyAsync(xs(0, 0), cps + sg * ns, nb8, cudaMemcpyDeviceToDevice, c->stream));
+            if ((st = launch_f64_to_f32(c, xs(0, 0), g[0], ns)) != PGB_OK) return st;
+            if ((st = stored_segment(n_in)) != PGB_OK) return st;
         }
         // reverse steps
         for (int64_t j = n_in - 1; j >= 0; --j) {

@@ -134,6 +134,30 @@ def test_rk4_adjoint_matches_oracle(ctx, c1, full_list):
     assert np.array_equal(fe, f.cpu().numpy())
 
 
+def test_rk4_adjoint_with_empty_rows(ctx, c1):
+    # an energy window leaves states without entries: their f stays f0 and
+    # their derivative is lam_end, in every buffer of the checkpointed sweep
+    eps = O.collision_list_grid(c1, GRID, 0, 2)["eps"]
+    lo = float(np.quantile(eps, 0.2))
+    L = O.collision_list_grid(c1, GRID, 0, 2, window=(lo, float(eps.max())))
+    build(ctx, c1, L)
+    ns, nnz = L["nstates"], len(L["row"])
+    empty = np.setdiff1d(np.arange(ns), np.union1d(L["row"], L["col"]))
+    assert len(empty) > 0
+    f0 = S.pulse_occupations(L["eps"], L["eps"].min(), centre=3.0, width=1.0, amplitude=0.2)
+    lam_end = np.random.default_rng(45).normal(size=ns)
+    n, dt = 23, 1.0
+    lam0, dg2, fe = np.zeros(ns), np.zeros(nnz), np.zeros(ns)
+    ctx.pgb_rk4_adjoint(f0, dt, n, 5, lam_end, lam0, dg2, fe)
+    f = f0.copy()
+    ctx.pgb_step_rk4(f, dt, n)
+    assert np.array_equal(fe, f)
+    assert np.array_equal(fe[empty], f0[empty]) and np.array_equal(lam0[empty], lam_end[empty])
+    r0, rg = O.rk4_adjoint(f0, dt, n, *oracle_fns(L), lam_end)
+    assert close(lam0, r0, 1e-5)
+    assert close(dg2, rg, 1e-4)
+
+
 def test_rk4_adjoint_number_covector_and_zero_steps(ctx, c1, full_list):
     L = full_list
     build(ctx, c1, L)
@@ -213,3 +237,64 @@ def test_autograd_functions(ctx, c1, full_list):
     I_ref = I.detach().cpu().numpy()
     I2 = AG.collision(f0t.detach(), (2 * g2).detach(), lst)
     assert np.array_equal(I2.cpu().numpy(), 2 * I_ref)
+
+
+@pytest.mark.slow
+def test_rk4_adjoint_full_size_finite_differences(ctx):
+    # The real-time workload: fcc model, 30^3 grid, two lowest bands, states
+    # within 0.6 eV of the band minimum, ~1.2e8 entries; 1000 steps of 1 fs from
+    # the hot-carrier pulse; L = mean carrier energy at t_end.  At this size the
+    # oracle cannot run, so the gradients are checked against central
+    # differences of the library's own forward along random directions (the
+    # step h = 1e-3 relative keeps the FP32 rounding of the gathered f far
+    # below the perturbation), and the carrier-number covector must come back
+    # as 1.
+    m = S.model_c2()
+    ctx.pgb_set_model(m)
+    grid = (30, 30, 30)
+    ctx.pgb_set_grids(grid, grid)
+    nk = 27000
+    eps = torch.empty((nk, m.nw), dtype=torch.float64, device="cuda")
+    ctx.pgb_get_grid_energies(eps, None)
+    emin = float(eps[:, :2].min())
+    nnz = ctx.pgb_build_collision_grid(0, 2, emin, emin + 0.6, 300.0, 0.010)
+    assert nnz > 5e7
+    ns = 2 * nk
+    es = torch.empty(ns, dtype=torch.float64, device="cuda")
+    ctx.pgb_collision_energies(es)
+    f0 = torch.as_tensor(S.pulse_occupations(es.cpu().numpy(), emin)).cuda()
+    g2 = torch.empty(nnz, dtype=torch.float32, device="cuda")
+    ctx.pgb_collision_list(g2=g2)
+    n_steps, dt = 1000, 1.0
+
+    def loss(f_init):
+        f = f_init.clone()
+        ctx.pgb_step_rk4(f, dt, n_steps)
+        return float((es * f).sum() / f.sum()), f
+
+    L0, fe = loss(f0)
+    lam_end = (es - L0) / fe.sum()
+    lam0 = torch.empty_like(f0)
+    dg2 = torch.empty(nnz, dtype=torch.float64, device="cuda")
+    fe2 = torch.empty_like(f0)
+    ctx.pgb_rk4_adjoint(f0, dt, n_steps, 50, lam_end, lam0, dg2, fe2)
+    assert torch.equal(fe, fe2)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    h = 1e-3
+    for _ in range(2):
+        d = torch.randn(ns, generator=gen, device="cuda", dtype=torch.float64) * f0
+        fd = (loss(f0 + h * d)[0] - loss(f0 - h * d)[0]) / (2 * h)
+        ad = float((lam0 * d).sum())
+        assert abs(ad - fd) <= 2e-3 * abs(fd)
+    d = torch.randn(nnz, generator=gen, device="cuda", dtype=torch.float32) * g2
+    ctx.pgb_collision_set_g2((g2 + h * d).contiguous())
+    lp = loss(f0)[0]
+    ctx.pgb_collision_set_g2((g2 - h * d).contiguous())
+    lm = loss(f0)[0]
+    ctx.pgb_collision_set_g2(g2)
+    fd = (lp - lm) / (2 * h)
+    ad = float((dg2 * d.double()).sum())
+    assert abs(ad - fd) <= 2e-3 * abs(fd)
+    ones = torch.ones(ns, dtype=torch.float64, device="cuda")
+    ctx.pgb_rk4_adjoint(f0, dt, 200, 50, ones, lam0)
+    assert float((lam0 - 1.0).abs().max()) < 1e-5
