@@ -16,7 +16,8 @@
 //
 // Persistent CTAs (one per SM) walk the tiles in k-groups so that a group's
 // operands stay in L2.  Warp roles: 0 = TMA producer, 1 = TMEM owner and MMA
-// issuer, 2-5 = epilogue (one TMEM lane = one q row per thread).  With BF16x3
+// issuer, 2-9 = epilogue (warp w reads TMEM lane group w % 4, one q row per
+// thread, for one of the tile's two bands).  With BF16x3
 // the two accumulators (re, im) are double-buffered in TMEM so the epilogue of
 // one tile overlaps the mainloop of the next; TF32x3 keeps separate
 // correction accumulators (four per tile, single-buffered).
