@@ -44,6 +44,16 @@ Pins (tests/test_oracle_*.py):
   * ``rk4_adjoint``: (P(dt A)^T)^n lam on linear systems, P the degree-4
     Taylor polynomial; finite differences of ``evolve`` on a grid list; the
     carrier-number covector 1 is carried back unchanged.
+  * ``frohlich_wannier``: invariance under reciprocal-lattice shifts of q;
+    L(-q) = conj L(q); the q -> 0 closed form of the G = 0 term; a plain
+    one-G-at-a-time loop over a larger box; ``g_wannier_full`` rotated equals
+    the short-range part plus L [U^dagger(k+q) U(k)] (Eq. smooth_phase).
+  * ``velocities``: central differences of ``bands``; at a degeneracy, the
+    one-sided slopes of the split bands.
+  * ``bte_weights``: its row sums on a full list equal ``scattering_rates``;
+    ``bte_iterate``: the dense solution of (1 - tau W) F = tau v; RTA when W = 0.
+  * ``mobility``: constant-tau cosine band under Boltzmann statistics against
+    the exact aliased Bessel-function average.
 Parity unpinned: absolute Gamma of real materials (no DFT data here).
 """
 from __future__ import annotations
@@ -63,6 +73,8 @@ EV_J = 1.602176634e-19            # J
 C_OMEGA = HBAR_EVS ** 2 * EV_J / (AMU_KG * BOHR_M ** 2)
 OMEGA_MIN_EV = 1e-4
 TWO_PI_OVER_HBAR = 2.0 * np.pi / HBAR_EVS   # 1/(eV s)
+HARTREE_EV = 27.211386245988      # eV; e^2/(4 pi eps_0) = 1 hartree * bohr
+EWALD_CUT = 40.0                  # G terms with (q+G).eps.(q+G)/(4 Lambda) above this are dropped
 
 
 # ----------------------------------------------------------------------------
@@ -150,6 +162,59 @@ def g_wannier(model, kpts: np.ndarray, qpts: np.ndarray) -> np.ndarray:
     pq = phases(qpts, model.R_gp)                                                   # [nq, ngp]
     out = np.einsum("qp,kpc->kqc", pq, gk)
     return out.reshape((len(kpts), len(qpts)) + tail)
+
+
+def reciprocal_vectors(A: np.ndarray) -> np.ndarray:
+    """Rows b_i (1/bohr) with a_i . b_j = 2 pi delta_ij; a crystal point k is the Cartesian k @ B."""
+    return 2.0 * np.pi * np.linalg.inv(np.asarray(A, np.float64)).T
+
+
+def frohlich_wannier(model, qpts: np.ndarray) -> np.ndarray:
+    """Long-range coupling of Eq. e_ph_long in the Wannier gauge, [nq, nmode] complex, eV/bohr.
+
+    L^{ka}(q) = i (e^2 / (eps_0 Omega)) sum_{G, q+G != 0} [(q+G).Z*_k]_a e^{-i tau_k.(q+G)}
+                e^{-(q+G).eps.(q+G) / (4 Lambda)} / ((q+G).eps.(q+G)),
+    with every G whose exponent (q+G).eps.(q+G)/(4 Lambda) is at most EWALD_CUT.
+    With the smooth-phase bra-ket of Eq. smooth_phase the Bloch-gauge term is
+    L^{ka}(q) [U^dagger(k+q) U(k)]_mn, i.e. L^{ka}(q) delta_ij added to the
+    Wannier-gauge g before the rotation.  Zero for models without Born charges.
+    """
+    qpts = np.asarray(qpts, np.float64)
+    nm = model.nmode
+    if model.zstar is None:
+        return np.zeros((len(qpts), nm), dtype=np.complex128)
+    A = np.asarray(model.A, np.float64)
+    B = reciprocal_vectors(A)
+    omega = abs(np.linalg.det(A))
+    eps = np.asarray(model.eps_inf, np.float64)
+    lam = float(model.ewald_lambda)
+    vmax = np.sqrt(4.0 * lam * EWALD_CUT / np.linalg.eigvalsh(eps).min())
+    nmax = int(np.ceil(vmax * np.linalg.norm(A, axis=1).max() / (2 * np.pi))) + 2
+    r = np.arange(-nmax, nmax + 1)
+    n = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3).astype(np.float64)
+    pref = 4.0 * np.pi * HARTREE_EV / omega                  # e^2/(eps_0 Omega), eV/bohr^2
+    out = np.zeros((len(qpts), model.nat, 3), dtype=np.complex128)
+    for q0 in range(0, len(qpts), 1024):
+        q = qpts[q0:q0 + 1024]
+        v = (q[:, None, :] + n[None, :, :]) @ B                # q + G, Cartesian [nq, nG, 3]
+        x = np.einsum("qga,ab,qgb->qg", v, eps, v)
+        keep = (x > 0.0) & (x / (4.0 * lam) <= EWALD_CUT)
+        w = np.where(keep, np.exp(-x / (4.0 * lam)) / np.where(keep, x, 1.0), 0.0)
+        for k in range(model.nat):
+            vz = v @ np.asarray(model.zstar[k], np.float64)    # [(q+G).Z*]_a
+            ph = np.exp(-1j * (v @ np.asarray(model.tau[k], np.float64)))
+            out[q0:q0 + 1024, k] = 1j * pref * np.einsum("qg,qga->qa", w * ph, vz)
+    return out.reshape(len(qpts), nm)
+
+
+def g_wannier_full(model, kpts: np.ndarray, qpts: np.ndarray) -> np.ndarray:
+    """Wannier-gauge g of ``g_wannier`` plus the long-range term L^{ka}(q) delta_ij
+    (Sec. 2.2.4: short-range part interpolated, long-range part added)."""
+    out = g_wannier(model, kpts, qpts)
+    if model.zstar is None:
+        return out
+    L = frohlich_wannier(model, qpts)                           # [nq, nmode]
+    return out + L[None, :, :, None, None] * np.eye(model.nw)[None, None, None]
 
 
 def g_bloch(gw: np.ndarray, Uk: np.ndarray, Ukq: np.ndarray) -> np.ndarray:
@@ -250,7 +315,7 @@ def scattering_rates_grid(model, kgrid, qgrid, k_indices, T, mu, sigma, mode_res
         for q0 in range(0, nq, q_chunk):
             qs = slice(q0, min(nq, q0 + q_chunk))
             ikq = kq_row[qs]
-            gw = g_wannier(model, k, qpts[qs])[0]                  # [nq, nm, nw, nw]
+            gw = g_wannier_full(model, k, qpts[qs])[0]                  # [nq, nm, nw, nw]
             gb = g_bloch(gw, U_all[ik][None], U_all[ikq])
             gm = g_modes(gb, hw[qs], e[qs], model.mass)
             g2 = np.abs(gm) ** 2
@@ -446,7 +511,7 @@ def collision_list_grid(model, grid, band_lo, band_hi, sigma=None, screen=0.0, w
     g2_all = np.empty((nk, nk, nm, nb, nb))       # [k, q, nu, m, n]
     sel = slice(band_lo, band_hi)
     for ik in range(nk):
-        gw = g_wannier(model, pts[ik:ik + 1], pts)[0]
+        gw = g_wannier_full(model, pts[ik:ik + 1], pts)[0]
         gb = g_bloch(gw, U_all[ik][None], U_all[kq[ik]])
         gm = g_modes(gb, hw_all, e_all, model.mass)[:, :, sel, sel]
         g2_all[ik] = np.abs(gm) ** 2
@@ -519,7 +584,7 @@ def collision_rows(model, grid, band_lo, band_hi, states, f, T, sigma, window=No
     for s in states:
         ik, n = divmod(int(s), nb)
         kq = _kplusq_row(g, g, ik)
-        gw = g_wannier(model, pts[ik:ik + 1], pts)[0]
+        gw = g_wannier_full(model, pts[ik:ik + 1], pts)[0]
         gb = g_bloch(gw, U_all[ik][None], U_all[kq])
         g2 = np.abs(g_modes(gb, hw_all, e_all, model.mass)[:, :, sel, sel][:, :, :, n]) ** 2       # [q, nu, m]
         sp = kq[:, None] * nb + np.arange(nb)[None, :]              # [q, m]
@@ -533,3 +598,80 @@ def collision_rows(model, grid, band_lo, band_hi, states, f, T, sigma, window=No
         mask = live[:, :, None] & inwin[sp][:, None, :]
         out.append(-TWO_PI_OVER_HBAR / nk * np.sum(np.where(mask, term, 0.0)))
     return np.array(out)
+
+
+# ----------------------------------------------------------------------------
+# band velocities (Eqs. velocity, wannier_4), iterative BTE (Eqs. BTE_lin,
+# BTE_iter, BTE_W) and the mobility (Eq. cond), Sec. 2.1.2 and 2.2.1
+# ----------------------------------------------------------------------------
+
+def velocities(model, kpts: np.ndarray, deg_tol: float = 1e-6) -> np.ndarray:
+    """v_nk (m/s), [nk, nw, 3]: hbar v^a = [U^dagger(k) H_a(k) U(k)]_nn with
+    H_a(k) = sum_R e^{ik.R} H(R) (i R^a), R^a Cartesian (Eq. wannier_4).
+
+    For bands degenerate within ``deg_tol`` eV the velocities along each
+    Cartesian direction are the eigenvalues (ascending) of that direction's
+    matrix restricted to the degenerate subspace (the degenerate extension).
+    """
+    kpts = np.asarray(kpts, np.float64)
+    Rc = np.asarray(model.R_H, np.float64) @ np.asarray(model.A, np.float64)      # [nR, 3] bohr
+    ph = phases(kpts, model.R_H)
+    Ha = np.einsum("kr,ra,rij->kaij", ph, 1j * Rc, model.H.astype(np.complex128))   # eV bohr
+    eps, U = bands(model, kpts)
+    M = np.einsum("kin,kaij,kjm->kanm", np.conj(U), Ha, U)
+    v = np.real(np.einsum("kann->kan", M)).copy()
+    for k in range(len(kpts)):
+        n = 0
+        while n < model.nw:
+            e = n + 1
+            while e < model.nw and eps[k, e] - eps[k, e - 1] <= deg_tol:
+                e += 1
+            if e - n > 1:
+                for a in range(3):
+                    v[k, a, n:e] = np.linalg.eigvalsh(M[k, a, n:e, n:e])
+            n = e
+    return np.transpose(v, (0, 2, 1)) * (BOHR_M / HBAR_EVS)
+
+
+def bte_weights(eps, row, col, hw, g2, T, mu, sigma, nq_total):
+    """W_{nk,mk+q}^{nu q} / N_q per list entry (Eq. BTE_W), 1/s."""
+    f_m = fermi_dirac(eps[col], mu, T)
+    N = bose_einstein(hw, T)
+    live = np.asarray(hw) >= OMEGA_MIN_EV
+    d = eps[row] - eps[col]
+    W = TWO_PI_OVER_HBAR * np.asarray(g2, np.float64) * (
+        delta_gauss(d - hw, sigma) * (1.0 + N - f_m) + delta_gauss(d + hw, sigma) * (N + f_m))
+    return np.where(live, W, 0.0) / nq_total
+
+
+def bte_iterate(tau, v, row, col, w, max_iter=200, tol=1e-10):
+    """F^{i+1} = tau v + tau sum_e w_e F^i_col (Eq. BTE_iter from F^0 = tau v).
+
+    tau [ns] s, v [ns, 3] m/s, w per list entry (``bte_weights``).  Stops when
+    max |F^{i+1} - F^i| <= tol max |F^0|.  Returns (F [ns, 3] in m, iterations).
+    """
+    tau = np.asarray(tau, np.float64)
+    F0 = tau[:, None] * np.asarray(v, np.float64)
+    F = F0.copy()
+    scale = np.abs(F0).max()
+    for it in range(1, max_iter + 1):
+        S = np.zeros_like(F)
+        np.add.at(S, row, np.asarray(w, np.float64)[:, None] * F[col])
+        Fn = F0 + tau[:, None] * S
+        diff = np.abs(Fn - F).max()
+        F = Fn
+        if diff <= tol * scale:
+            return F, it
+    return F, max_iter
+
+
+def mobility(v, F, eps, T, mu):
+    """mu_ab = sigma_ab / (e n_c) (Eq. cond) in cm^2/(V s).
+
+    With n_c = (S / (N_k Omega)) sum f0 over the same states, the prefactors
+    cancel: mu_ab = sum v^a F^b (-df0/de) / sum f0, with -df0/de = f0 (1 - f0) / kT
+    in 1/eV, v in m/s and F in m.
+    """
+    f = fermi_dirac(eps, mu, T)
+    w = f * (1.0 - f) / (KB_EVK * T)
+    return 1e4 * np.einsum("s,sa,sb->ab", w, np.asarray(v), np.asarray(F)) / f.sum()

@@ -12,6 +12,7 @@ from .models import (  # noqa: F401
     mp_grid,
     model_c1,
     model_c2,
+    model_c3,
     model_sc_tight_binding,
     model_holstein,
     model_ladder,

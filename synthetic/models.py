@@ -19,6 +19,9 @@ Conventions shared by every consumer (oracle and CUDA path):
   dense product of the two R lists.  It obeys the hermiticity of the
   perturbation potential, g~_ij(R_e,R_p) = conj(g~_ji(-R_e, R_p - R_e)).
 * Masses in amu.
+* Polar models carry Born charges, the dielectric tensor and the Ewald
+  parameter of the long-range coupling (Eq. e_ph_long); the short-range g~
+  is then the part left to the Wannier sum.
 
 Nothing here evaluates the method (no Fourier sum, eigensolve or rate).
 """
@@ -45,6 +48,12 @@ class Model:
     R_gp: np.ndarray       # (ngp,3) int32
     g: np.ndarray          # (nge,ngp,nmode,nw,nw) complex64 or complex128, eV/bohr
     meta: dict = field(default_factory=dict)
+    # polar materials (Sec. 2.2.4): Born effective charges Z*[kappa][beta][alpha]
+    # (the alpha component of (q+G).Z* is sum_beta (q+G)_beta Z*[kappa][beta][alpha]),
+    # high-frequency dielectric tensor, Ewald parameter Lambda in 1/bohr^2
+    zstar: np.ndarray = None
+    eps_inf: np.ndarray = None
+    ewald_lambda: float = 0.0
 
     @property
     def nw(self) -> int:
@@ -273,6 +282,56 @@ def model_c2(seed: int = SEED_BASE + 2, rcut: float = C2_RCUT, g_dtype=np.comple
     return Model("c2_fcc_8band", A, tau, mass, R.copy(), H, R.copy(), D, R.copy(), R.copy(), g,
                  meta={"seed": seed, "T": 300.0, "sigma": 0.010, "kgrid": (40, 40, 40),
                        "qgrid": (40, 40, 40), "window_width": 0.3, "mu_below_min": 0.3})
+
+
+C3_LATTICE = 10.68
+C3_HOP = 2.0             # eV: about 2000 points of a 60^3 grid within 0.2 eV of the band minimum
+
+
+def model_c3(seed: int = SEED_BASE + 3, g_dtype=np.complex64) -> Model:
+    """Polar GaAs-like zincblende model: a = 10.68 bohr, 8 bands, 2 atoms of 69.7 and 74.9 amu.
+
+    Built like ``model_c2`` (same R sets scaled with the lattice, spring
+    network, short-range |g~| = 0.1 exp(-(|R_e|/4 + |R_p|/4))), with hoppings
+    scaled by 2.0 exp(-|R|/3 bohr) eV so that about 2000 points of a 60^3 grid lie
+    within 0.2 eV of the band minimum, and the long-range coupling of Eq. e_ph_long:
+    Z* = +2 I (cation), -2 I (anion), eps_inf = 10.9 I, Lambda = (2 pi / a)^2.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    a = C3_LATTICE
+    A = 0.5 * a * np.array([[0, 1, 1], [1, 0, 1], [1, 1, 0]], dtype=np.float64)
+    tau = np.array([[0.0, 0.0, 0.0], [0.25 * a, 0.25 * a, 0.25 * a]])
+    mass = np.array([69.7, 74.9])
+    R = _ball_vectors(A, C2_RCUT * a / C2_LATTICE)
+    nR = len(R)
+    Rd = np.linalg.norm(R @ A, axis=1)
+
+    nw = 8
+    onsite = np.array([0.0, 0.55, 1.1, 1.6, 2.2, 2.8, 3.3, 3.9])
+    H = np.zeros((nR, nw, nw), dtype=np.complex128)
+    for r in range(nR):
+        X = rng.normal(0, 1, (nw, nw)) + 1j * rng.normal(0, 1, (nw, nw))
+        if Rd[r] == 0:
+            H[r] = np.diag(onsite) + 0.05 * X * (1 - np.eye(nw))
+        else:
+            H[r] = C3_HOP * np.exp(-Rd[r] / 3.0) * X / np.sqrt(2.0)
+    H = _hermitian_symmetrise_hr(R, H)
+
+    dnn = np.sqrt(3.0) * a / 4.0
+    D = _spring_network(A, tau, R, k0=1.2, d0=dnn, ell=3.0, ktrans=0.3)
+
+    nm = 6
+    mag = (0.1 * np.exp(-(Rd[:, None] / 4.0 + Rd[None, :] / 4.0))).astype(np.float64)
+    g = np.empty((nR, nR, nm, nw, nw), dtype=np.complex128)
+    for re in range(nR):
+        ph = rng.uniform(0, 2 * np.pi, (nR, nm, nw, nw))
+        g[re] = mag[re][:, None, None, None] * np.exp(1j * ph)
+    g = _partner_symmetrise_g(R, R, g).astype(g_dtype)
+    zstar = np.stack([2.0 * np.eye(3), -2.0 * np.eye(3)])
+    return Model("c3_zincblende_polar", A, tau, mass, R.copy(), H, R.copy(), D, R.copy(), R.copy(), g,
+                 meta={"seed": seed, "T": 300.0, "sigma": 0.010, "kgrid": (60, 60, 60),
+                       "qgrid": (60, 60, 60), "window_width": 0.2},
+                 zstar=zstar, eps_inf=10.9 * np.eye(3), ewald_lambda=(2 * np.pi / a) ** 2)
 
 
 # ----------------------------------------------------------------------------
