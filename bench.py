@@ -276,6 +276,8 @@ def run_ours(args, rank, world, local):
                                      "tolerance_vs_fp64": {"tf32x3": 1e-5, "fp32": 1e-5}[name]}
     if args.dynamics:
         out["dynamics"] = dynamics(ctx, model, args, world, peaks, peak_src)
+    if args.polar:
+        out["polar"] = polar(ctx, args, world)
     if args.e2e and rank == 0:
         out["e2e"] = e2e(ctx, model, prec, steps=1)
     if args.cpu_baseline and rank == 0 and world == 1:
@@ -405,6 +407,66 @@ def adjoint(ctx, f, nnz, args, world, peaks, peak_src, fwd_ms_per_step):
     }
 
 
+POLAR_GRID = (60, 60, 60)
+POLAR_WINDOW = 0.2
+
+
+def polar(ctx, args, world):
+    """Polar zincblende model with the long-range (Froehlich) coupling: Gamma_nk of
+    the k-points within 0.2 eV of the band minimum over the 60^3 q grid (timed, the
+    same precision as the headline), then the iterative BTE and mobility on the
+    window's scattering list (list build and transport timed separately)."""
+    import torch
+    import synthetic as S
+    from paper_2002_02045_gb300 import PRECISIONS
+    m = S.model_c3()
+    prec = PRECISIONS[args.precision]
+    ctx.pgb_set_model(m)
+    ctx.pgb_set_lattice(m.A, m.tau)
+    ctx.pgb_set_polar(m.zstar, m.eps_inf, m.ewald_lambda)
+    ctx.pgb_set_grids(POLAR_GRID, POLAR_GRID)
+    nk = int(np.prod(POLAR_GRID))
+    eps = torch.empty((nk, m.nw), dtype=torch.float64, device="cuda")
+    ctx.pgb_get_grid_energies(eps, None)
+    emin = float(eps.min())
+    mu = emin - 0.3
+    kbuf = torch.empty((nk,), dtype=torch.int32, device="cuda")
+    nwin = ctx.pgb_window(emin - 1e-6, emin + POLAR_WINDOW, kbuf)
+    kw = kbuf[:nwin].clone()
+    gam = torch.empty((nwin, m.nw), dtype=torch.float64, device="cuda")
+    ctx.pgb_scattering_rates(kw, T_K, mu, SIGMA, prec, gam)     # warm-up (tables)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.pgb_scattering_rates(kw, T_K, mu, SIGMA, prec, gam)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    pairs = nwin * nk
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nnz = ctx.pgb_build_collision_grid(0, 2, emin - 1e-6, emin + POLAR_WINDOW, T_K, SIGMA)
+    torch.cuda.synchronize()
+    t_list = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mob_rta, mob, it = ctx.pgb_transport(mu, prec, 3000, 1e-6)
+    t_tr = time.perf_counter() - t0
+    return {
+        "metric": "(k,q) pairs/s, polar Gamma_nk (short-range Wannier sum + long-range Ewald term)",
+        "value": world * pairs / (ms * 1e-3), "unit": "pairs/s", "ms": ms, "pairs": pairs, "nk_window": nwin,
+        "precision": args.precision,
+        "config": {"workload": f"polar zincblende 8 bands, 2 atoms (69.7, 74.9 amu), 381 R_e x 381 R_p + 6 "
+                               f"long-range rows (Z* = +-2, eps_inf = 10.9); {POLAR_GRID[0]}^3 k = q grid, "
+                               f"k within {POLAR_WINDOW} eV of the band minimum; T = 300 K, sigma = 10 meV"},
+        "transport": {"list_entries": nnz, "list_build_s": t_list, "solve_s": t_tr, "iterations": it,
+                      "tolerance": 1e-6, "mobility_cm2_per_Vs": np.diag(mob).tolist(),
+                      "mobility_rta_cm2_per_Vs": np.diag(mob_rta).tolist(),
+                      "includes": "tau from the rates over the full q grid, velocities, W, iterations, mobility"},
+    }
+
+
 def e2e(ctx, model, prec, steps=1):
     """Same metric through the public API with host buffers: model upload,
     grids, window and rates, copies included."""
@@ -439,6 +501,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "fp64", "bf16x3", "tf32x3"])
+    ap.add_argument("--no-polar", dest="polar", action="store_false",
+                    help="skip the polar-model rates and transport measurement")
     ap.add_argument("--no-dynamics", dest="dynamics", action="store_false",
                     help="skip the real-time BTE (collision + RK4) measurement")
     ap.add_argument("--dyn-steps", type=int, default=1000)

@@ -102,6 +102,33 @@ pgb_status pgb_set_model(pgb_ctx *ctx, const pgb_model *model);
  * Each q-grid size must divide the k-grid size along the same axis.          */
 pgb_status pgb_set_grids(pgb_ctx *ctx, const int kgrid[3], const int qgrid[3]);
 
+/* Lattice of the model (Sec. 2.2): lattice[9] rows a_1, a_2, a_3 in bohr
+ * (Cartesian), tau [nat][3] atom positions in bohr (host pointers, copied).
+ * R vectors stay integer crystal coordinates (R = n_1 a_1 + n_2 a_2 + n_3 a_3).
+ * Needed by pgb_band_velocities, pgb_transport and pgb_set_polar; reset by
+ * pgb_set_model.  Re-applies an active polar term with the new positions.   */
+pgb_status pgb_set_lattice(pgb_ctx *ctx, const double lattice[9], const double *tau);
+
+/* Long-range (Froehlich) coupling of polar materials (Sec. 2.2.4, Eqs.
+ * e_ph_long, smooth_phase).  zstar [nat][3][3] Born effective charges with
+ * [(q+G).Z*_k]_a = sum_b (q+G)_b zstar[k][b][a]; eps_inf[9] the symmetric
+ * positive-definite high-frequency dielectric tensor; lambda the Ewald
+ * parameter Lambda (1/bohr^2).  In the Wannier gauge the term is
+ *   L^{ka}(q) = i (e^2/(eps_0 Omega)) sum_{G, q+G != 0} [(q+G).Z*_k]_a e^{-i tau_k.(q+G)}
+ *               e^{-(q+G).eps.(q+G)/(4 Lambda)} / ((q+G).eps.(q+G))   (eV/bohr),
+ * over every G with (q+G).eps.(q+G)/(4 Lambda) <= 40, and g~ gains
+ * L^{ka}(q) delta_ij, so that g_mn nu(k,q) gains
+ * sqrt(hbar/2 omega) sum_ka e^{ka}_nu/sqrt(M_k) L^{ka}(q) [U^dagger(k+q) U(k)]_mn in
+ * every later pgb_interpolate_g, pgb_scattering_rates(_noalloc) and
+ * pgb_build_collision_grid (a list built before keeps its |g|^2).  zstar
+ * NULL removes the term.  Host pointers, copied.  Needs pgb_set_lattice.     */
+pgb_status pgb_set_polar(pgb_ctx *ctx, const double *zstar, const double eps_inf[9], double lambda);
+
+/* L^{ka}(q) of pgb_set_polar at qpts [nq][3] (crystal coordinates, host or
+ * device): out [nq][nmode] complex as (re, im) doubles, eV/bohr (host or
+ * device).  Zero without a polar term.                                        */
+pgb_status pgb_long_range_g(pgb_ctx *ctx, const double *qpts, int64_t nq, double *out);
+
 /* Read the grid quantities computed by set_grids (host or device outputs).
  * eps [Nk][nw] eV; hw [Nq][nmode] eV.  Either pointer may be NULL.           */
 pgb_status pgb_get_grid_energies(pgb_ctx *ctx, double *eps, double *hw);
@@ -169,6 +196,36 @@ pgb_status pgb_collision(pgb_ctx *ctx, const double *f, double *I_out);
 
 /* nsteps explicit RK4 steps (Sec. 2.1.1) of df/dt = I[f], step dt_fs, in place. */
 pgb_status pgb_step_rk4(pgb_ctx *ctx, double *f, double dt_fs, int64_t nsteps);
+
+/* Band velocities (Eqs. velocity, wannier_4) at the k-grid points k_idx[0..nk)
+ * (host or device): v_out [nk][nw][3] in m/s (host or device), with
+ * hbar v^a_nk = [U^dagger(k) H_a(k) U(k)]_nn, H_a(k) = sum_R e^{ik.R} H(R) i R^a,
+ * R^a Cartesian, in FP64.  For bands degenerate within 1e-6 eV the velocities
+ * along each direction are the ascending eigenvalues of that direction's
+ * matrix restricted to the degenerate subspace.  Needs set_lattice, set_grids. */
+pgb_status pgb_band_velocities(pgb_ctx *ctx, const int32_t *k_idx, int64_t nk, double *v_out);
+
+/* Mobility from the linearised BTE (Sec. 2.1.2: Eqs. BTE_lin, BTE_iter, BTE_W,
+ * cond) on the current collision list, over its states inside its energy
+ * window (all states for a list given to pgb_build_collision), at the list's
+ * T and sigma and chemical potential mu_eV:
+ *   tau_nk = 1/Gamma_nk from pgb_scattering_rates over the whole q grid, every
+ *     final band and mode, in `precision` (states with Gamma = 0 get tau = 0);
+ *   v_nk from pgb_band_velocities;
+ *   W_e = (2 pi/hbar)(1/N_q)|g|^2 [d(e_s - hw - e_s')(1 + N - f0_s') + d(e_s + hw - e_s')(N + f0_s')]
+ *     per list entry (FP64 arithmetic, stored FP32);
+ *   F^0 = tau v, F^{i+1}_s = tau_s v_s + tau_s sum_{e in row s} W_e F^i_{col e}, until
+ *     max |F^{i+1} - F^i| <= tol max |F^0| or max_iter iterations;
+ *   mobility[a*3+b] = sum_s v^a_s F^b_s (-df0/de)_s / sum_s f0_s in cm^2/(V s),
+ *     -df0/de = f0 (1 - f0)/kT (Eq. cond divided by e n_c, the carriers of
+ *     the same states).
+ * mobility_rta [9] receives the same with F = F^0 (host or device, both
+ * required).  iterations_out (host, may be NULL): iterations run.  F_out
+ * [nstates][3] in m and tau_out [nstates] in s (host or device, may be NULL);
+ * states outside the window get 0.  Needs set_lattice.                      */
+pgb_status pgb_transport(pgb_ctx *ctx, double mu_eV, int precision, int max_iter, double tol,
+                         double *mobility_rta, double *mobility, int64_t *iterations_out, double *F_out,
+                         double *tau_out);
 
 /* Replace |g|^2 of every entry of the current list, keeping its rows,
  * columns and modes: g2 [nnz] float32 (host or device), eV^2.  a and b are

@@ -167,6 +167,7 @@ void free_grids(pgb_ctx *c) {
     if (c->d_asplit) cudaFree(c->d_asplit);
     c->d_asplit = nullptr;
     c->asplit_prec = -1;
+    dfree(&c->d_polarL);
     c->has_grids = false;
 }
 
@@ -188,6 +189,8 @@ void free_coll(pgb_ctx *c) {
     free_adjoint(c);
     c->has_coll = false;
     c->nstates = c->nnz = 0;
+    c->coll_elo = -1e300;
+    c->coll_ehi = 1e300;
 }
 
 void free_model(pgb_ctx *c) {
@@ -200,6 +203,12 @@ void free_model(pgb_ctx *c) {
     dfree(&c->d_mode_scale);
     dfree(&c->d_g64);
     dfree(&c->d_g32);
+    dfree(&c->d_Hd);
+    dfree(&c->d_polar);
+    dfree(&c->d_gvec);
+    c->has_lattice = false;
+    c->polar = false;
+    c->nG = 0;
     c->has_model = false;
 }
 
@@ -387,6 +396,7 @@ pgb_status pgb_set_model(pgb_ctx *c, const pgb_model *m) {
     c->nRD = m->nR_D;
     c->nRge = m->nR_ge;
     c->nRgp = m->nR_gp;
+    c->nKp = m->nR_gp;
     c->mass.assign(m->mass, m->mass + m->nat);
     TRY(dalloc(c, &c->d_RH, 3 * (size_t)c->nRH));
     TRY(dalloc(c, &c->d_RD, 3 * (size_t)c->nRD));
@@ -491,8 +501,124 @@ pgb_status pgb_set_grids(pgb_ctx *c, const int kgrid[3], const int qgrid[3]) {
     }
     TRY(launch_to_f32(c, c->d_coef, c->d_coef32, c->Nq * nm2));
     TRY(launch_transpose_coef(c));
-    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     c->has_grids = true;
+    TRY(polar_grid_table(c));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PGB_OK;
+}
+
+pgb_status pgb_set_lattice(pgb_ctx *c, const double lattice[9], const double *tau) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_model) return fail(c, PGB_ESTATE, "set_lattice: call set_model first");
+    if (!lattice || !tau) return fail(c, PGB_EINVAL, "set_lattice: null pointer");
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(lattice[i])) return fail(c, PGB_EINVAL, "set_lattice: non-finite lattice");
+    for (int i = 0; i < 3 * c->nat; ++i)
+        if (!std::isfinite(tau[i])) return fail(c, PGB_EINVAL, "set_lattice: non-finite tau");
+    const double *a = lattice;
+    // reciprocal rows b_i = 2 pi (a_j x a_k) / (a_1 . (a_2 x a_3))
+    auto cross = [](const double *u, const double *v, double *w) {
+        w[0] = u[1] * v[2] - u[2] * v[1];
+        w[1] = u[2] * v[0] - u[0] * v[2];
+        w[2] = u[0] * v[1] - u[1] * v[0];
+    };
+    double x23[3], x31[3], x12[3];
+    cross(a + 3, a + 6, x23);
+    cross(a + 6, a + 0, x31);
+    cross(a + 0, a + 3, x12);
+    const double vol = a[0] * x23[0] + a[1] * x23[1] + a[2] * x23[2];
+    if (!(std::fabs(vol) > 1e-12)) return fail(c, PGB_EINVAL, "set_lattice: singular lattice");
+    for (int d = 0; d < 3; ++d) {
+        c->rec[d] = 2 * kPi * x23[d] / vol;
+        c->rec[3 + d] = 2 * kPi * x31[d] / vol;
+        c->rec[6 + d] = 2 * kPi * x12[d] / vol;
+    }
+    for (int i = 0; i < 9; ++i) c->lat[i] = lattice[i];
+    c->omega = std::fabs(vol);
+    c->tau.assign(tau, tau + 3 * c->nat);
+    TRY(build_velocity_tables(c));
+    c->has_lattice = true;
+    if (c->polar) {   // atom positions enter the long-range term
+        std::vector<double> zs(c->zstar);
+        std::vector<double> e(c->eps_inf, c->eps_inf + 9);
+        TRY(pgb_set_polar(c, zs.data(), e.data(), c->ewald_lambda));
+    }
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PGB_OK;
+}
+
+pgb_status pgb_set_polar(pgb_ctx *c, const double *zstar, const double eps_inf[9], double lambda) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_lattice) return fail(c, PGB_ESTATE, "set_polar: call set_lattice first");
+    // every cached q table depends on the long-range columns
+    dfree(&c->d_phq64);
+    dfree(&c->d_phq32);
+    if (c->d_asplit) {
+        PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        cudaFree(c->d_asplit);
+        c->d_asplit = nullptr;
+    }
+    c->asplit_prec = -1;
+    dfree(&c->d_polarL);
+    if (!zstar) {
+        c->polar = false;
+        c->nKp = c->nRgp;
+        return PGB_OK;
+    }
+    if (!eps_inf) return fail(c, PGB_EINVAL, "set_polar: null eps_inf");
+    for (int i = 0; i < 9 * c->nat; ++i)
+        if (!std::isfinite(zstar[i])) return fail(c, PGB_EINVAL, "set_polar: non-finite Z*");
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            if (!std::isfinite(eps_inf[3 * i + j]) ||
+                std::fabs(eps_inf[3 * i + j] - eps_inf[3 * j + i]) > 1e-12 * (1.0 + std::fabs(eps_inf[3 * i + j])))
+                return fail(c, PGB_EINVAL, "set_polar: eps_inf must be symmetric and finite");
+    {   // positive definite: leading principal minors
+        const double *e = eps_inf;
+        const double m1 = e[0], m2 = e[0] * e[4] - e[1] * e[3];
+        const double m3 = e[0] * (e[4] * e[8] - e[5] * e[7]) - e[1] * (e[3] * e[8] - e[5] * e[6]) +
+                          e[2] * (e[3] * e[7] - e[4] * e[6]);
+        if (!(m1 > 0 && m2 > 0 && m3 > 0)) return fail(c, PGB_EINVAL, "set_polar: eps_inf must be positive definite");
+    }
+    if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(c, PGB_EINVAL, "set_polar: need Lambda > 0");
+    if (c->nRgp + c->nm > 4096) return fail(c, PGB_EINVAL, "set_polar: too many R_p vectors");
+    for (int i = 0; i < 9; ++i) c->eps_inf[i] = eps_inf[i];
+    c->ewald_lambda = lambda;
+    c->zstar.assign(zstar, zstar + 9 * c->nat);
+    std::vector<double> pol(c->tau);
+    pol.insert(pol.end(), zstar, zstar + 9 * c->nat);
+    TRY(dalloc(c, &c->d_polar, pol.size()));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_polar, pol.data(), 8 * pol.size(), cudaMemcpyHostToDevice, c->stream));
+    std::vector<int32_t> gv = ewald_candidates(c->lat, c->eps_inf, lambda);
+    c->nG = (int)(gv.size() / 3);
+    TRY(dalloc(c, &c->d_gvec, gv.size()));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_gvec, gv.data(), 4 * gv.size(), cudaMemcpyHostToDevice, c->stream));
+    c->polar = true;
+    c->nKp = c->nRgp + c->nm;
+    TRY(polar_grid_table(c));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // host vectors above go out of scope
+    return PGB_OK;
+}
+
+pgb_status pgb_long_range_g(pgb_ctx *c, const double *qpts, int64_t nq, double *out) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_model) return fail(c, PGB_ESTATE, "long_range_g: call set_model first");
+    if (nq < 0) return fail(c, PGB_EINVAL, "long_range_g: negative nq");
+    if (nq == 0) return PGB_OK;
+    if (!qpts || !out) return fail(c, PGB_EINVAL, "long_range_g: null pointer");
+    In<double> Q;
+    TRY(Q.init(c, qpts, 3 * (size_t)nq));
+    Out<double> O;
+    TRY(O.init(c, out, 2 * (size_t)nq * c->nm));
+    if (!c->polar)
+        PGB_CUDA_TRY(c, cudaMemsetAsync(O.dev, 0, 16 * (size_t)nq * c->nm, c->stream));
+    else
+        TRY(launch_ewald_pts(c, Q.dev, nq, O.dev, c->nm, 0, false));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    TRY(O.finish());
     return PGB_OK;
 }
 
@@ -582,18 +708,19 @@ pgb_status pgb_interpolate_g(pgb_ctx *c, const double *kpts, int64_t nk, const d
     }
     // g: Re-sum (GEMM), fold U(k), Rp-sum (batched GEMM), epilogue
     Tmp<char> phk, S1, G, phq, C, fullbuf;
-    const int64_t nrow = (int64_t)c->nRgp * ncol;
+    const int64_t nrow = (int64_t)c->nKp * ncol;
     TRY(phk.alloc(c, (size_t)nk * c->nRge * es));
     TRY(S1.alloc(c, (size_t)nk * nrow * es));
     TRY(G.alloc(c, (size_t)nk * nrow * es));
-    TRY(phq.alloc(c, (size_t)nq * c->nRgp * es));
+    TRY(phq.alloc(c, (size_t)nq * c->nKp * es));
     TRY(C.alloc(c, (size_t)npair * ncol * es));
     TRY(launch_phase_pts(c, K.dev, nk, c->d_Rge, c->nRge, phk.p, f32));
     const void *g = f32 ? (const void *)c->d_g32 : (const void *)c->d_g64;
-    TRY(launch_cgemm(c, f32, 1, nk, nrow, c->nRge, phk.p, c->nRge, 0, g, nrow, 0, S1.p, nrow, 0));
+    const int64_t nrowS = (int64_t)c->nRgp * ncol;   // g(k, R_p) rows before the long-range rows
+    TRY(launch_cgemm(c, f32, 1, nk, nrowS, c->nRge, phk.p, c->nRge, 0, g, nrowS, 0, S1.p, nrowS, 0));
     TRY(launch_fold_u(c, f32, nk, nullptr, c->nRgp, nm, nw, S1.p, Uk, G.p));
-    TRY(launch_phase_pts(c, Q.dev, nq, c->d_Rgp, c->nRgp, phq.p, f32));
-    TRY(launch_cgemm(c, f32, nk, nq, ncol, c->nRgp, phq.p, c->nRgp, 0, G.p, ncol, nrow, C.p, ncol, nq * ncol));
+    TRY(launch_qtable_pts(c, Q.dev, nq, phq.p, f32));
+    TRY(launch_cgemm(c, f32, nk, nq, ncol, c->nKp, phq.p, c->nKp, 0, G.p, ncol, nrow, C.p, ncol, nq * ncol));
     double *fullp = O.dev;
     if (out_mode == PGB_G_ABS) {
         TRY(fullbuf.alloc(c, full * sizeof(double)));
@@ -633,9 +760,9 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
     if (!gamma_out) return fail(c, PGB_EINVAL, "scattering_rates: null gamma_out");
     const bool f32 = precision != PGB_FP64;
     const int nw = c->nw, nm = c->nm, nw2 = nw * nw;
-    const int64_t ncol = (int64_t)nm * nw2, nrow = (int64_t)c->nRgp * ncol;
+    const int64_t ncol = (int64_t)nm * nw2, nrow = (int64_t)c->nKp * ncol, nrowS = (int64_t)c->nRgp * ncol;
     const size_t es = f32 ? sizeof(float2) : sizeof(double2);
-    const int Kp = tc_kpad(c->nRgp);
+    const int Kp = tc_kpad(c->nKp);
     const size_t tes = tf32 ? 4 : 2;
 
     // k list: validate on the host
@@ -656,13 +783,13 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
     void *phq = f32 ? (void *)c->d_phq32 : (void *)c->d_phq64;
     if (!phq) {
         if (f32) {
-            TRY(dalloc(c, &c->d_phq32, (size_t)c->Nq * c->nRgp));
+            TRY(dalloc(c, &c->d_phq32, (size_t)c->Nq * c->nKp));
             phq = c->d_phq32;
         } else {
-            TRY(dalloc(c, &c->d_phq64, (size_t)c->Nq * c->nRgp));
+            TRY(dalloc(c, &c->d_phq64, (size_t)c->Nq * c->nKp));
             phq = c->d_phq64;
         }
-        TRY(launch_phase_grid(c, c->qg, nullptr, c->Nq, c->d_Rgp, c->nRgp, phq, f32));
+        TRY(launch_qtable_grid(c, nullptr, c->Nq, phq, f32));
     }
 
     const int per = nm * nw;
@@ -725,7 +852,8 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
                 c->d_asplit = nullptr;
             }
             PGB_CUDA_TRY(c, cudaMalloc(&c->d_asplit, (size_t)4 * c->Nq * Kp * tes));
-            TRY(launch_split_phases(c, tf32, c->qg, c->Nq, c->d_Rgp, c->nRgp, Kp, c->d_asplit));
+            TRY(launch_split_phases(c, tf32, c->qg, c->Nq, c->d_Rgp, c->nRgp, Kp, c->d_asplit, c->d_polarL,
+                                    c->polar ? nm : 0));
             c->asplit_prec = precision;
         }
     }
@@ -738,11 +866,11 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
         const int32_t *kb = dk.p + b0;
         prof_mark(c, PGB_PROF_RSUM);
         TRY(launch_phase_grid(c, c->kg, kb, nb, c->d_Rge, c->nRge, phk, f32));
-        TRY(launch_cgemm(c, f32, 1, nb, nrow, c->nRge, phk, c->nRge, 0, g, nrow, 0, S1, nrow, 0));
+        TRY(launch_cgemm(c, f32, 1, nb, nrowS, c->nRge, phk, c->nRge, 0, g, nrowS, 0, S1, nrowS, 0));
         TRY(launch_fold_u(c, f32, nb, kb, c->nRgp, nm, nw, S1, U, G));
         prof_mark(c, PGB_PROF_RSUM);
         if (fused) {
-            TRY(launch_split_g6(c, tf32, nb, c->nRgp, (int)ncol, Kp, G, Bsplit));
+            TRY(launch_split_g6(c, tf32, nb, c->nKp, (int)ncol, Kp, G, Bsplit));
             FusedLaunch L;
             L.nb = nb;
             L.kidx = kb;
@@ -762,13 +890,13 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
             continue;
         }
         if (tcp) {
-            TRY(launch_split_g(c, tf32, nb, c->nRgp, (int)ncol, Kp, G, Bsplit));
+            TRY(launch_split_g(c, tf32, nb, c->nKp, (int)ncol, Kp, G, Bsplit));
             prof_mark(c, PGB_PROF_QSUM);
             TRY(launch_tc_qsum(c, tf32, nb, c->Nq, (int)ncol, Kp, c->d_asplit, Bsplit, (float2 *)Cb, c->d_err));
             prof_mark(c, PGB_PROF_QSUM);
         } else {
             prof_mark(c, PGB_PROF_QSUM);
-            TRY(launch_cgemm(c, f32, nb, c->Nq, ncol, c->nRgp, phq, c->nRgp, 0, G, ncol, nrow, Cb, ncol,
+            TRY(launch_cgemm(c, f32, nb, c->Nq, ncol, c->nKp, phq, c->nKp, 0, G, ncol, nrow, Cb, ncol,
                              c->Nq * ncol));
             prof_mark(c, PGB_PROF_QSUM);
         }
@@ -990,6 +1118,52 @@ pgb_status pgb_rk4_adjoint(pgb_ctx *c, const double *f0, double dt_fs, int64_t n
     return PGB_OK;
 }
 
+pgb_status pgb_band_velocities(pgb_ctx *c, const int32_t *k_idx, int64_t nk, double *v_out) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_grids || !c->has_lattice) return fail(c, PGB_ESTATE, "band_velocities: call set_lattice and set_grids first");
+    if (nk < 0) return fail(c, PGB_EINVAL, "band_velocities: negative nk");
+    if (nk == 0) return PGB_OK;
+    if (!k_idx || !v_out) return fail(c, PGB_EINVAL, "band_velocities: null pointer");
+    std::vector<int32_t> hk(nk);
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(hk.data(), k_idx, 4 * (size_t)nk, cudaMemcpyDefault, c->stream));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int64_t i = 0; i < nk; ++i)
+        if (hk[i] < 0 || hk[i] >= c->Nk) return fail(c, PGB_EINVAL, "band_velocities: k index out of range");
+    Tmp<int32_t> dk;
+    TRY(dk.alloc(c, (size_t)nk));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(dk.p, hk.data(), 4 * (size_t)nk, cudaMemcpyHostToDevice, c->stream));
+    Out<double> V;
+    TRY(V.init(c, v_out, (size_t)nk * c->nw * 3));
+    TRY(band_velocities(c, dk.p, nk, V.dev));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    TRY(V.finish());
+    return PGB_OK;
+}
+
+pgb_status pgb_transport(pgb_ctx *c, double mu_eV, int precision, int max_iter, double tol, double *mobility_rta,
+                         double *mobility, int64_t *iterations_out, double *F_out, double *tau_out) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_coll) return fail(c, PGB_ESTATE, "transport: build a collision list first");
+    if (!c->has_lattice) return fail(c, PGB_ESTATE, "transport: call set_lattice first");
+    if (!std::isfinite(mu_eV) || max_iter < 0 || !(tol >= 0.0))
+        return fail(c, PGB_EINVAL, "transport: need finite mu, max_iter >= 0, tol >= 0");
+    if (!mobility_rta || !mobility) return fail(c, PGB_EINVAL, "transport: null mobility output");
+    const size_t ns = (size_t)c->nstates;
+    Out<double> F, Tau;
+    TRY(F.init(c, F_out, 3 * ns));
+    TRY(Tau.init(c, tau_out, ns));
+    double mr[9], mi[9];
+    TRY(transport(c, mu_eV, precision, max_iter, tol, mr, mi, iterations_out, F.dev, Tau.dev));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(mobility_rta, mr, sizeof(mr), cudaMemcpyDefault, c->stream));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(mobility, mi, sizeof(mi), cudaMemcpyDefault, c->stream));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    TRY(F.finish());
+    TRY(Tau.finish());
+    return PGB_OK;
+}
+
 pgb_status pgb_diag_bands(pgb_ctx *c, const double *pts, int64_t n, double *Hk, double *eps, double *U) {
     if (!c) return PGB_EINVAL;
     cudaSetDevice(c->device);
@@ -1030,7 +1204,8 @@ pgb_status pgb_build_collision_grid(pgb_ctx *c, int band_lo, int band_hi, double
     if (ns > (1 << 24)) return fail(c, PGB_EINVAL, "build_collision_grid: too many states");
     free_coll(c);
     const int nw = c->nw, nm = c->nm;
-    const int64_t ncol = (int64_t)nm * nw * nw, nrow = (int64_t)c->nRgp * ncol, nsub = (int64_t)nbnd * nm * nw;
+    const int64_t ncol = (int64_t)nm * nw * nw, nrow = (int64_t)c->nKp * ncol, nsub = (int64_t)nbnd * nm * nw;
+    const int64_t nrowS = (int64_t)c->nRgp * ncol;
     // window flags and the k-points that hold at least one window state
     std::vector<double> eps((size_t)c->Nk * nw);
     PGB_CUDA_TRY(c, cudaMemcpyAsync(eps.data(), c->d_eps, 8 * eps.size(), cudaMemcpyDeviceToHost, c->stream));
@@ -1080,8 +1255,8 @@ pgb_status pgb_build_collision_grid(pgb_ctx *c, int band_lo, int band_hi, double
     PGB_CUDA_TRY(c, cudaMemsetAsync(counter.p, 0, 8, c->stream));
     // q-grid phases (FP32, kept for later calls)
     if (!c->d_phq32) {
-        TRY(dalloc(c, &c->d_phq32, (size_t)c->Nq * c->nRgp));
-        TRY(launch_phase_grid(c, c->qg, nullptr, c->Nq, c->d_Rgp, c->nRgp, c->d_phq32, true));
+        TRY(dalloc(c, &c->d_phq32, (size_t)c->Nq * c->nKp));
+        TRY(launch_qtable_grid(c, nullptr, c->Nq, c->d_phq32, true));
     }
     const size_t es = sizeof(float2);
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -1099,10 +1274,10 @@ pgb_status pgb_build_collision_grid(pgb_ctx *c, int band_lo, int band_hi, double
         const int64_t nb = std::min<int64_t>(nbmax, na - b0);
         const int32_t *kb = d_active.p + b0;
         TRY(launch_phase_grid(c, c->kg, kb, nb, c->d_Rge, c->nRge, phk, true));
-        TRY(launch_cgemm(c, true, 1, nb, nrow, c->nRge, phk, c->nRge, 0, c->d_g32, nrow, 0, S1, nrow, 0));
+        TRY(launch_cgemm(c, true, 1, nb, nrowS, c->nRge, phk, c->nRge, 0, c->d_g32, nrowS, 0, S1, nrowS, 0));
         TRY(launch_fold_u(c, true, nb, kb, c->nRgp, nm, nw, S1, c->d_U32, G));
         // q-sum over the columns of the listed bands only
-        TRY(launch_cgemm(c, true, nb, c->Nq, nsub, c->nRgp, c->d_phq32, c->nRgp, 0,
+        TRY(launch_cgemm(c, true, nb, c->Nq, nsub, c->nKp, c->d_phq32, c->nKp, 0,
                          (const float2 *)G + (int64_t)band_lo * nm * nw, ncol, nrow, Cb, nsub, c->Nq * nsub));
         ListLaunch Lb = L;
         Lb.nb = nb;
@@ -1123,6 +1298,8 @@ pgb_status pgb_build_collision_grid(pgb_ctx *c, int band_lo, int band_hi, double
     c->band_hi = band_hi;
     c->nstates = ns;
     c->nnz = (int64_t)total;
+    c->coll_elo = e_lo;
+    c->coll_ehi = e_hi;
     pgb_status st = launch_coll_coeffs(c, T, sigma, c->d_coo_row, c->d_coo_col, c->d_coo_mode, c->d_coo_g2,
                                        (int64_t)total, nbnd);
     if (st != PGB_OK) return st;

@@ -27,6 +27,8 @@ constexpr double kSqrtPi = 1.77245385090551602730;
 constexpr double kTwoPiOverHbar = 2.0 * kPi / kHbarEvS;
 constexpr double kFemto = 1e-15;
 constexpr double kDeltaCut = 7.0;                // |x|/sigma beyond which a term is skipped
+constexpr double kHartreeEv = 27.211386245988;   // eV; e^2 / (4 pi eps_0) = 1 hartree bohr
+constexpr double kEwaldCut = 40.0;               // Ewald terms with (q+G).eps.(q+G)/(4 Lambda) above this are dropped
 constexpr int kMaxNw = 16;
 constexpr int kMaxNmode = 15;
 }  // namespace pgb
@@ -51,6 +53,23 @@ struct pgb_ctx {
     double *d_mode_scale = nullptr;  // [nm] 1/sqrt(M_kappa) per ka
     double2 *d_g64 = nullptr;    // [nRge][nRgp*nm*nw*nw]
     float2 *d_g32 = nullptr;
+    int nKp = 0;                 // rows of the R_p sum: nRgp, plus nm long-range rows for polar models
+
+    // lattice (pgb_set_lattice) and long-range polar coupling (pgb_set_polar)
+    bool has_lattice = false;
+    double lat[9] = {0};         // rows a_i, bohr
+    double rec[9] = {0};         // rows b_i, 1/bohr (a_i . b_j = 2 pi delta_ij)
+    double omega = 0.0;          // cell volume, bohr^3
+    std::vector<double> tau;     // [nat][3] bohr
+    std::vector<double> zstar;   // [nat][3][3]
+    double2 *d_Hd = nullptr;     // [nRH][3][nw][nw] i R^a H(R), eV bohr (band velocities)
+    bool polar = false;
+    double eps_inf[9] = {0};
+    double ewald_lambda = 0.0;
+    double *d_polar = nullptr;   // tau [nat][3] then Z* [nat][3][3]
+    int32_t *d_gvec = nullptr;   // [nG][3] integer G candidates of the Ewald sum
+    int nG = 0;
+    double2 *d_polarL = nullptr; // [Nq][nm] long-range term on the q grid
 
     // grids
     bool has_grids = false;
@@ -88,6 +107,7 @@ struct pgb_ctx {
     float *d_coo_g2 = nullptr;
     double coll_T = 0.0, coll_sigma = 0.0;
     int coll_nb = 0;
+    double coll_elo = -1e300, coll_ehi = 1e300;   // energy window of the list's states
 
     // transposed list for the reverse-mode pass, built on first use
     bool adj_ready = false;
@@ -155,9 +175,24 @@ void dfree(T **p) {
 
 // interpolation kernels (interp.cu)
 pgb_status launch_phase_grid(pgb_ctx *c, const int grid[3], const int32_t *d_idx, int64_t npts,
-                             const int32_t *d_R, int nR, void *out, bool fp32);
+                             const int32_t *d_R, int nR, void *out, bool fp32, int64_t ld = 0);
 pgb_status launch_phase_pts(pgb_ctx *c, const double *d_pts, int64_t npts, const int32_t *d_R, int nR,
-                            void *out, bool fp32);
+                            void *out, bool fp32, int64_t ld = 0);
+
+// long-range polar coupling (polar.cu)
+pgb_status polar_grid_table(pgb_ctx *c);
+// q tables [npts][nKp]: e^{iq.Rp} for the nRgp lattice vectors, then the long-range columns
+pgb_status launch_qtable_grid(pgb_ctx *c, const int32_t *d_idx, int64_t npts, void *out, bool fp32);
+pgb_status launch_qtable_pts(pgb_ctx *c, const double *d_pts, int64_t npts, void *out, bool fp32);
+pgb_status launch_ewald_pts(pgb_ctx *c, const double *d_pts, int64_t npts, void *out, int64_t ld, int col0,
+                            bool fp32);
+std::vector<int32_t> ewald_candidates(const double lat[9], const double eps[9], double lambda);
+
+// band velocities and transport (transport.cu); device pointers
+pgb_status build_velocity_tables(pgb_ctx *c);
+pgb_status band_velocities(pgb_ctx *c, const int32_t *d_kidx, int64_t nk, double *d_v);
+pgb_status transport(pgb_ctx *c, double mu, int precision, int max_iter, double tol, double *mob_rta, double *mob,
+                     int64_t *iters_out, double *d_F, double *d_tau);
 pgb_status launch_cgemm(pgb_ctx *c, bool fp32, int64_t batch, int64_t M, int64_t N, int64_t K,
                         const void *A, int64_t lda, int64_t strideA, const void *B, int64_t ldb,
                         int64_t strideB, void *C, int64_t ldc, int64_t strideC);
@@ -215,7 +250,7 @@ pgb_status launch_window(pgb_ctx *c, const double *d_eps, int64_t Nk, int nw, do
 int tc_kpad(int nR);
 bool tc_supported(int ncol);
 pgb_status launch_split_phases(pgb_ctx *c, bool tf32, const int grid[3], int64_t Nq, const int32_t *d_R, int nR,
-                               int Kp, void *out);
+                               int Kp, void *out, const double2 *L = nullptr, int nL = 0);
 pgb_status launch_split_g(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out);
 pgb_status launch_split_g6(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out);
 pgb_status launch_tc_qsum(pgb_ctx *c, bool tf32, int64_t nb, int64_t Nq, int ncol, int Kp, void *Asplit,

@@ -20,7 +20,7 @@ static inline unsigned int div_up(int64_t a, int64_t b) { return (unsigned int)(
 // integer residues (i_d R_d mod n_d), so it carries no accumulated rounding.
 template <typename T2>
 __global__ void k_phase_grid(int n1, int n2, int n3, const int32_t *__restrict__ idx, int64_t npts,
-                             const int32_t *__restrict__ R, int nR, T2 *__restrict__ out) {
+                             const int32_t *__restrict__ R, int nR, T2 *__restrict__ out, int64_t ld) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= npts * nR) return;
     const int64_t p = t / nR;
@@ -42,12 +42,12 @@ __global__ void k_phase_grid(int n1, int n2, int n3, const int32_t *__restrict__
     T2 v;
     v.x = c;
     v.y = s;
-    out[t] = v;
+    out[p * ld + r] = v;
 }
 
 template <typename T2>
 __global__ void k_phase_pts(const double *__restrict__ pts, int64_t npts, const int32_t *__restrict__ R,
-                            int nR, T2 *__restrict__ out) {
+                            int nR, T2 *__restrict__ out, int64_t ld) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= npts * nR) return;
     const int64_t p = t / nR;
@@ -59,31 +59,33 @@ __global__ void k_phase_pts(const double *__restrict__ pts, int64_t npts, const 
     T2 v;
     v.x = c;
     v.y = s;
-    out[t] = v;
+    out[p * ld + r] = v;
 }
 
 pgb_status launch_phase_grid(pgb_ctx *c, const int grid[3], const int32_t *d_idx, int64_t npts,
-                             const int32_t *d_R, int nR, void *out, bool fp32) {
+                             const int32_t *d_R, int nR, void *out, bool fp32, int64_t ld) {
     const int64_t n = npts * nR;
     if (n == 0) return PGB_OK;
+    if (ld < nR) ld = nR;
     if (fp32)
         k_phase_grid<float2><<<div_up(n, 256), 256, 0, c->stream>>>(grid[0], grid[1], grid[2], d_idx, npts, d_R,
-                                                                     nR, (float2 *)out);
+                                                                     nR, (float2 *)out, ld);
     else
         k_phase_grid<double2><<<div_up(n, 256), 256, 0, c->stream>>>(grid[0], grid[1], grid[2], d_idx, npts,
-                                                                      d_R, nR, (double2 *)out);
+                                                                      d_R, nR, (double2 *)out, ld);
     PGB_LAUNCH_CHECK(c);
     return PGB_OK;
 }
 
 pgb_status launch_phase_pts(pgb_ctx *c, const double *d_pts, int64_t npts, const int32_t *d_R, int nR,
-                            void *out, bool fp32) {
+                            void *out, bool fp32, int64_t ld) {
     const int64_t n = npts * nR;
     if (n == 0) return PGB_OK;
+    if (ld < nR) ld = nR;
     if (fp32)
-        k_phase_pts<float2><<<div_up(n, 256), 256, 0, c->stream>>>(d_pts, npts, d_R, nR, (float2 *)out);
+        k_phase_pts<float2><<<div_up(n, 256), 256, 0, c->stream>>>(d_pts, npts, d_R, nR, (float2 *)out, ld);
     else
-        k_phase_pts<double2><<<div_up(n, 256), 256, 0, c->stream>>>(d_pts, npts, d_R, nR, (double2 *)out);
+        k_phase_pts<double2><<<div_up(n, 256), 256, 0, c->stream>>>(d_pts, npts, d_R, nR, (double2 *)out, ld);
     PGB_LAUNCH_CHECK(c);
     return PGB_OK;
 }
@@ -339,9 +341,10 @@ pgb_status launch_to_f32(pgb_ctx *c, const double2 *src, float2 *dst, int64_t n)
 // band n needs is contiguous.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_fold_u(int64_t nb, const int32_t *__restrict__ kidx, int nRgp, int nm, int nw,
+__global__ void k_fold_u(int64_t nb, const int32_t *__restrict__ kidx, int nRgp, int nKp, int nm, int nw,
                          const V2<T> *__restrict__ S1, const V2<T> *__restrict__ U, V2<T> *__restrict__ G) {
-    const int64_t per = (int64_t)nRgp * nm * nw * nw;
+    const int64_t perS = (int64_t)nRgp * nm * nw * nw;
+    const int64_t per = (int64_t)nKp * nm * nw * nw;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nb * per) return;
     const int64_t b = t / per;
@@ -351,8 +354,12 @@ __global__ void k_fold_u(int64_t nb, const int32_t *__restrict__ kidx, int nRgp,
     const int n = (int)((r / ((int64_t)nw * nm)) % nw);
     const int64_t rp = r / ((int64_t)nw * nm * nw);
     const int64_t k = kidx ? (int64_t)kidx[b] : b;
-    const V2<T> *s = S1 + b * per + ((rp * nm + ka) * nw + i) * nw;
     const V2<T> *u = U + k * nw * nw;
+    if (rp >= nRgp) {   // long-range rows: delta(ka, rp - nRgp) U_in(k)
+        G[t] = (ka == rp - nRgp) ? u[i * nw + n] : cmake<T>(0, 0);
+        return;
+    }
+    const V2<T> *s = S1 + b * perS + ((rp * nm + ka) * nw + i) * nw;
     V2<T> acc = cmake<T>(0, 0);
     for (int j = 0; j < nw; ++j) cfma(acc, s[j], u[j * nw + n]);
     G[t] = acc;
@@ -360,13 +367,14 @@ __global__ void k_fold_u(int64_t nb, const int32_t *__restrict__ kidx, int nRgp,
 
 pgb_status launch_fold_u(pgb_ctx *c, bool fp32, int64_t nb, const int32_t *d_kidx, int nRgp, int nm, int nw,
                          const void *S1, const void *U, void *G) {
-    const int64_t n = nb * (int64_t)nRgp * nm * nw * nw;
+    const int nKp = c->nKp > nRgp ? c->nKp : nRgp;
+    const int64_t n = nb * (int64_t)nKp * nm * nw * nw;
     if (n == 0) return PGB_OK;
     if (fp32)
-        k_fold_u<float><<<div_up(n, 256), 256, 0, c->stream>>>(nb, d_kidx, nRgp, nm, nw, (const float2 *)S1,
+        k_fold_u<float><<<div_up(n, 256), 256, 0, c->stream>>>(nb, d_kidx, nRgp, nKp, nm, nw, (const float2 *)S1,
                                                                (const float2 *)U, (float2 *)G);
     else
-        k_fold_u<double><<<div_up(n, 256), 256, 0, c->stream>>>(nb, d_kidx, nRgp, nm, nw, (const double2 *)S1,
+        k_fold_u<double><<<div_up(n, 256), 256, 0, c->stream>>>(nb, d_kidx, nRgp, nKp, nm, nw, (const double2 *)S1,
                                                                 (const double2 *)U, (double2 *)G);
     PGB_LAUNCH_CHECK(c);
     return PGB_OK;

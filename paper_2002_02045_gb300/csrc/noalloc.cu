@@ -93,7 +93,7 @@ extern "C" pgb_status pgb_scattering_rates_noalloc(pgb_ctx *c, const int32_t *k_
         return PGB_EINVAL;
     }
     const int nw = c->nw, nm = c->nm;
-    const int64_t ncol = (int64_t)nm * nw * nw, nrow = (int64_t)c->nRgp * ncol;
+    const int64_t ncol = (int64_t)nm * nw * nw, nrow = (int64_t)c->nKp * ncol, nrowS = (int64_t)c->nRgp * ncol;
     const size_t es = sizeof(float2);
     const int per = nm * nw;
     const int qpb = std::max(1, 256 / nw);
@@ -101,7 +101,7 @@ extern "C" pgb_status pgb_scattering_rates_noalloc(pgb_ctx *c, const int32_t *k_
     const int64_t nqblk = (c->Nq + (int64_t)qpb * qiters - 1) / ((int64_t)qpb * qiters);
 
     // fixed part: q phase table and occupation tables; per-k part: Fourier sums and partials
-    const size_t fixed = 256 + al256((size_t)c->Nq * c->nRgp * es) + al256((size_t)c->Nk * nw * 8) +
+    const size_t fixed = 256 + al256((size_t)c->Nq * c->nKp * es) + al256((size_t)c->Nk * nw * 8) +
                          al256((size_t)c->Nk * nw * 4) + al256((size_t)c->Nq * nm * 8) + al256((size_t)c->Nq * nm * 4);
     auto per_batch = [&](int64_t nb) {
         return al256((size_t)nb * c->nRge * es) + 2 * al256((size_t)nb * nrow * es) +
@@ -126,7 +126,7 @@ extern "C" pgb_status pgb_scattering_rates_noalloc(pgb_ctx *c, const int32_t *k_
         return p;
     };
     int *bad = reinterpret_cast<int *>(take(sizeof(int)));
-    float2 *phq = reinterpret_cast<float2 *>(take((size_t)c->Nq * c->nRgp * es));
+    float2 *phq = reinterpret_cast<float2 *>(take((size_t)c->Nq * c->nKp * es));
     double *focc = reinterpret_cast<double *>(take((size_t)c->Nk * nw * 8));
     float *eps32 = reinterpret_cast<float *>(take((size_t)c->Nk * nw * 4));
     double *nbe = reinterpret_cast<double *>(take((size_t)c->Nq * nm * 8));
@@ -157,18 +157,18 @@ extern "C" pgb_status pgb_scattering_rates_noalloc(pgb_ctx *c, const int32_t *k_
     }
     // every other scratch region is fully overwritten before it is read, so
     // nothing else has to be cleared between calls
-    if ((st = launch_phase_grid(c, c->qg, nullptr, c->Nq, c->d_Rgp, c->nRgp, phq, true)) != PGB_OK) return st;
+    if ((st = launch_qtable_grid(c, nullptr, c->Nq, phq, true)) != PGB_OK) return st;
     if ((st = launch_occ_tables(c, T, mu, focc, eps32, nbe, hw32)) != PGB_OK) return st;
     const double scale = kTwoPiOverHbar / ((double)c->Nq * sigma * kSqrtPi);
     for (int64_t b0 = 0; b0 < nk; b0 += nbmax) {
         const int64_t nb = std::min<int64_t>(nbmax, nk - b0);
         const int32_t *kb = k_idx + b0;
         if ((st = launch_phase_grid(c, c->kg, kb, nb, c->d_Rge, c->nRge, phk, true)) != PGB_OK) return st;
-        if ((st = launch_cgemm(c, true, 1, nb, nrow, c->nRge, phk, c->nRge, 0, c->d_g32, nrow, 0, S1, nrow, 0)) !=
+        if ((st = launch_cgemm(c, true, 1, nb, nrowS, c->nRge, phk, c->nRge, 0, c->d_g32, nrowS, 0, S1, nrowS, 0)) !=
             PGB_OK)
             return st;
         if ((st = launch_fold_u(c, true, nb, kb, c->nRgp, nm, nw, S1, c->d_U32, G)) != PGB_OK) return st;
-        if ((st = launch_cgemm(c, true, nb, c->Nq, ncol, c->nRgp, phq, c->nRgp, 0, G, ncol, nrow, Cb, ncol,
+        if ((st = launch_cgemm(c, true, nb, c->Nq, ncol, c->nKp, phq, c->nKp, 0, G, ncol, nrow, Cb, ncol,
                                c->Nq * ncol)) != PGB_OK)
             return st;
         RatesArgs ra;

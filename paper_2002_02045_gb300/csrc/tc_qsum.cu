@@ -225,13 +225,17 @@ template <> struct Split<true> {
 // A parts from the exact grid phases: [4][Nq][Kp] = (Re hi, Re lo, Im hi, Im lo), zero for p >= nR.
 template <bool TF32>
 __global__ void k_split_phases(int n1, int n2, int n3, int64_t Nq, const int32_t *__restrict__ R, int nR, int Kp,
-                               typename Split<TF32>::E *__restrict__ out) {
+                               typename Split<TF32>::E *__restrict__ out, const double2 *__restrict__ L, int nL) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= Nq * Kp) return;
     const int64_t q = t / Kp;
     const int p = (int)(t % Kp);
     double c = 0.0, s = 0.0;
-    if (p < nR) {
+    if (p >= nR && p < nR + nL) {   // long-range columns (polar coupling)
+        const double2 v = L[q * nL + (p - nR)];
+        c = v.x;
+        s = v.y;
+    } else if (p < nR) {
         const int i3 = (int)(q % n3), i2 = (int)((q / n3) % n2), i1 = (int)(q / ((int64_t)n2 * n3));
         int t1 = (int)(((int64_t)i1 * R[3 * p + 0]) % n1);
         int t2 = (int)(((int64_t)i2 * R[3 * p + 1]) % n2);
@@ -353,14 +357,16 @@ int tc_kpad(int nR) { return ((nR + 31) / 32) * 32; }
 bool tc_supported(int ncol) { return ncol % BN == 0; }
 
 pgb_status launch_split_phases(pgb_ctx *c, bool tf32, const int grid[3], int64_t Nq, const int32_t *d_R, int nR,
-                               int Kp, void *out) {
+                               int Kp, void *out, const double2 *L, int nL) {
     const int64_t n = Nq * Kp;
     const unsigned g = (unsigned)((n + 255) / 256);
+    if (!L) nL = 0;
     if (tf32)
-        k_split_phases<true><<<g, 256, 0, c->stream>>>(grid[0], grid[1], grid[2], Nq, d_R, nR, Kp, (float *)out);
+        k_split_phases<true><<<g, 256, 0, c->stream>>>(grid[0], grid[1], grid[2], Nq, d_R, nR, Kp, (float *)out, L,
+                                                       nL);
     else
         k_split_phases<false><<<g, 256, 0, c->stream>>>(grid[0], grid[1], grid[2], Nq, d_R, nR, Kp,
-                                                        (__nv_bfloat16 *)out);
+                                                        (__nv_bfloat16 *)out, L, nL);
     PGB_LAUNCH_CHECK(c);
     return PGB_OK;
 }

@@ -30,6 +30,7 @@ ABI_SYMBOLS = (
     "pgb_step_rk4", "pgb_launch_count", "pgb_profile", "pgb_profile_read",
     "pgb_scattering_rates_noalloc", "pgb_build_collision_grid", "pgb_collision_list",
     "pgb_collision_set_g2", "pgb_collision_vjp", "pgb_rk4_adjoint",
+    "pgb_set_lattice", "pgb_set_polar", "pgb_long_range_g", "pgb_band_velocities", "pgb_transport",
 )
 PGB_NOALLOC_SCRATCH_BYTES = 64 << 20
 PROF_QSUM, PROF_RSUM, PROF_EPILOGUE, PROF_COLLISION, PROF_BANDS, PROF_ADJOINT = 0, 1, 2, 3, 4, 5
@@ -83,6 +84,11 @@ def load(path: str = LIB_PATH):
         "pgb_collision_set_g2": (I, [P, P]),
         "pgb_collision_vjp": (I, [P, P, P, P, P]),
         "pgb_rk4_adjoint": (I, [P, P, D, I64, I64, P, P, P, P]),
+        "pgb_set_lattice": (I, [P, P, P]),
+        "pgb_set_polar": (I, [P, P, P, D]),
+        "pgb_long_range_g": (I, [P, P, I64, P]),
+        "pgb_band_velocities": (I, [P, P, I64, P]),
+        "pgb_transport": (I, [P, D, I, I, D, P, P, C.POINTER(I64), P, P]),
         "pgb_launch_count": (I64, [P]),
         "pgb_profile": (I, [P, I]),
         "pgb_scattering_rates_noalloc": (I, [P, P, I64, D, D, D, P]),
@@ -178,6 +184,40 @@ class Context:
         self._chk(self.lib.pgb_set_model(self._h, C.byref(m)))
         self.nw = int(model.H.shape[1])
         self.nmode = 3 * len(model.mass)
+
+    def pgb_set_lattice(self, lattice, tau):
+        lat = np.ascontiguousarray(lattice, np.float64).reshape(9)
+        t = np.ascontiguousarray(tau, np.float64).reshape(-1)
+        self._chk(self.lib.pgb_set_lattice(self._h, _ptr(lat), _ptr(t)))
+
+    def pgb_set_polar(self, zstar, eps_inf=None, ewald_lambda=0.0):
+        if zstar is None:
+            self._chk(self.lib.pgb_set_polar(self._h, None, None, 0.0))
+            return
+        z = np.ascontiguousarray(zstar, np.float64).reshape(-1)
+        e = np.ascontiguousarray(eps_inf, np.float64).reshape(9)
+        self._chk(self.lib.pgb_set_polar(self._h, _ptr(z), _ptr(e), float(ewald_lambda)))
+
+    def pgb_long_range_g(self, qpts, out):
+        _check_dtype(qpts, "float64")
+        _check_dtype(out, "float64")
+        self._chk(self.lib.pgb_long_range_g(self._h, _ptr(qpts), len(qpts), _ptr(out)))
+
+    def pgb_band_velocities(self, k_idx, v_out):
+        _check_dtype(k_idx, "int32")
+        _check_dtype(v_out, "float64")
+        self._chk(self.lib.pgb_band_velocities(self._h, _ptr(k_idx), len(k_idx), _ptr(v_out)))
+
+    def pgb_transport(self, mu, precision, max_iter, tol, F_out=None, tau_out=None):
+        """Returns (mobility_rta [3,3], mobility [3,3], iterations) in cm^2/(V s)."""
+        _check_dtype(F_out, "float64")
+        _check_dtype(tau_out, "float64")
+        mr = np.zeros(9)
+        mi = np.zeros(9)
+        it = C.c_int64(0)
+        self._chk(self.lib.pgb_transport(self._h, float(mu), int(precision), int(max_iter), float(tol), _ptr(mr),
+                                         _ptr(mi), C.byref(it), _ptr(F_out), _ptr(tau_out)))
+        return mr.reshape(3, 3), mi.reshape(3, 3), int(it.value)
 
     def pgb_set_grids(self, kgrid, qgrid):
         kg = (C.c_int * 3)(*kgrid)

@@ -288,7 +288,8 @@ C3_LATTICE = 10.68
 C3_HOP = 2.0             # eV: about 2000 points of a 60^3 grid within 0.2 eV of the band minimum
 
 
-def model_c3(seed: int = SEED_BASE + 3, g_dtype=np.complex64) -> Model:
+def model_c3(seed: int = SEED_BASE + 3, rcut: float = C2_RCUT * C3_LATTICE / C2_LATTICE,
+             g_dtype=np.complex64) -> Model:
     """Polar GaAs-like zincblende model: a = 10.68 bohr, 8 bands, 2 atoms of 69.7 and 74.9 amu.
 
     Built like ``model_c2`` (same R sets scaled with the lattice, spring
@@ -302,7 +303,7 @@ def model_c3(seed: int = SEED_BASE + 3, g_dtype=np.complex64) -> Model:
     A = 0.5 * a * np.array([[0, 1, 1], [1, 0, 1], [1, 1, 0]], dtype=np.float64)
     tau = np.array([[0.0, 0.0, 0.0], [0.25 * a, 0.25 * a, 0.25 * a]])
     mass = np.array([69.7, 74.9])
-    R = _ball_vectors(A, C2_RCUT * a / C2_LATTICE)
+    R = _ball_vectors(A, rcut)
     nR = len(R)
     Rd = np.linalg.norm(R @ A, axis=1)
 

@@ -1,0 +1,233 @@
+"""Polar coupling, band velocities and the iterative BTE on the GPU (through the
+C ABI) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import eph as O
+
+from helpers import assert_close_blocks, assert_rates_close, degenerate_sum
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_02045_gb300 import build
+    build.build()
+    from paper_2002_02045_gb300 import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def c3():
+    return S.model_c3()
+
+
+@pytest.fixture(scope="module")
+def c3s():
+    # the polar model with its 19 shortest lattice vectors (fast oracle)
+    return S.model_c3(rcut=13.0)
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x)).cuda()
+
+
+def empty(shape, dtype=torch.float64):
+    return torch.empty(shape, dtype=dtype, device="cuda")
+
+
+def set_polar_model(ctx, m):
+    ctx.pgb_set_model(m)
+    ctx.pgb_set_lattice(m.A, m.tau)
+    ctx.pgb_set_polar(m.zstar, m.eps_inf, m.ewald_lambda)
+
+
+def test_long_range_g_matches_oracle(ctx, c3s):
+    m = c3s
+    rng = np.random.default_rng(30)
+    q = np.concatenate([rng.uniform(-1, 1, (9, 3)), [[0.0, 0.0, 0.0], [1e-3, 0.0, 0.0], [0.0, -2e-4, 5e-4]]])
+    set_polar_model(ctx, m)
+    out = np.zeros((len(q), m.nmode, 2))
+    ctx.pgb_long_range_g(q, out)
+    got = out[..., 0] + 1j * out[..., 1]
+    ref = O.frohlich_wannier(m, q)
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+    ctx.pgb_set_polar(None)
+    ctx.pgb_long_range_g(q, out)
+    assert np.all(out == 0.0)
+
+
+def oracle_g2_full(m, k, q):
+    ek, Uk = O.bands(m, k)
+    hw, e = O.phonons(m, q)
+    out = np.zeros((len(k), len(q), m.nmode, m.nw, m.nw))
+    for a in range(len(k)):
+        _, Ukq = O.bands(m, k[a:a + 1] + q)
+        gw = O.g_wannier_full(m, k[a:a + 1], q)[0]
+        out[a] = np.abs(O.g_modes(O.g_bloch(gw, Uk[a][None], Ukq), hw, e, m.mass)) ** 2
+    return out, hw
+
+
+@pytest.mark.parametrize("prec,tol,floor", [("fp64", 1e-10, 1e-3), ("fp32", 1e-5, 1e-2)])
+def test_polar_interpolate_g(ctx, c3, prec, tol, floor):
+    from paper_2002_02045_gb300 import PGB_G2_FULL, PRECISIONS
+    m = c3
+    rng = np.random.default_rng(31)
+    k = rng.uniform(-0.5, 0.5, (2, 3))
+    q = np.concatenate([rng.uniform(-0.5, 0.5, (4, 3)), [[0.02, -0.01, 0.0]]])
+    set_polar_model(ctx, m)
+    out = empty((2, 5, 6, 8, 8))
+    ctx.pgb_interpolate_g(dev(k), dev(q), PRECISIONS[prec], PGB_G2_FULL, out)
+    ref, hw = oracle_g2_full(m, k, q)
+    got = out.cpu().numpy()
+    hwb = np.broadcast_to(hw[None], (2, 5, 6))
+    assert_close_blocks(degenerate_sum(got, hwb, 2), degenerate_sum(ref, hwb, 2), tol, block_axes=(2, 3, 4),
+                        floor=floor, label=f"polar g2 {prec}")
+    # the long-range term is not negligible here (small q)
+    ctx.pgb_set_polar(None)
+    ctx.pgb_interpolate_g(dev(k), dev(q), PRECISIONS[prec], PGB_G2_FULL, out)
+    assert np.abs(out.cpu().numpy() - got).max() > 0.05 * np.abs(got).max()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5), ("tf32x3", 1e-5), ("bf16x3", 1e-3)])
+def test_polar_rates(ctx, c3, prec, tol):
+    from paper_2002_02045_gb300 import PRECISIONS
+    m = c3
+    T, sig = 300.0, 0.010
+    kg, qg = (12, 12, 12), (6, 6, 6)
+    set_polar_model(ctx, m)
+    ctx.pgb_set_grids(kg, qg)
+    e_ref, _ = O.bands(m, S.mp_grid(*kg))
+    emin = e_ref.min()
+    mu = emin - 0.3
+    win = np.nonzero(((e_ref >= emin + 1e-9) & (e_ref <= emin + 0.5)).any(1))[0].astype(np.int32)
+    sample = win[:: max(1, len(win) // 5)][:5]
+    gam = empty((len(sample), 8))
+    ctx.pgb_scattering_rates(dev(sample), T, mu, sig, PRECISIONS[prec], gam)
+    ref = O.scattering_rates_grid(m, kg, qg, sample, T, mu, sig)
+    assert_rates_close(gam.cpu().numpy(), ref, tol, label=f"polar gamma {prec}")
+
+
+def test_band_velocities_match_oracle(ctx, c3):
+    m = c3
+    ctx.pgb_set_model(m)
+    ctx.pgb_set_lattice(m.A, m.tau)
+    grid = (10, 10, 10)
+    ctx.pgb_set_grids(grid, grid)
+    kidx = np.arange(0, 1000, 37, dtype=np.int32)
+    v = np.zeros((len(kidx), 8, 3))
+    ctx.pgb_band_velocities(kidx, v)
+    ref = O.velocities(m, S.mp_grid(*grid)[kidx])
+    assert np.abs(v - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_band_velocities_degenerate_point(ctx):
+    # two bands touching along k_x = 0 in an arbitrary gauge (see the oracle pin)
+    R = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0]], dtype=np.int32)
+    sz = np.diag([1.0, -1.0])
+    V = np.array([[np.cos(0.7), -np.sin(0.7)], [np.sin(0.7), np.cos(0.7)]]) * np.exp(0.3j)
+    Hp = -0.2 * np.eye(2) + 0.05 / 2j * sz
+    H = np.stack([np.zeros((2, 2)), V @ Hp @ V.conj().T, V @ Hp.conj().T @ V.conj().T]).astype(complex)
+    D = np.stack([np.eye(3), -0.5 * np.eye(3), -0.5 * np.eye(3)])
+    m = S.Model("split", 6.0 * np.eye(3), np.zeros((1, 3)), np.array([1.0]), R, H, R, D, R, R,
+                np.zeros((3, 3, 3, 2, 2), complex))
+    ctx.pgb_set_model(m)
+    ctx.pgb_set_lattice(m.A, m.tau)
+    grid = (4, 5, 5)
+    ctx.pgb_set_grids(grid, grid)
+    kidx = np.arange(100, dtype=np.int32)
+    v = np.zeros((100, 2, 3))
+    ctx.pgb_band_velocities(kidx, v)
+    ref = O.velocities(m, S.mp_grid(*grid)[kidx])
+    assert np.abs(v - ref).max() <= 1e-9 * np.abs(ref).max()
+    assert np.abs(ref[0, 1, 0] - ref[0, 0, 0]) > 0.1 * np.abs(ref[0, :, 0]).max()   # k = 0: split slopes
+
+
+def test_transport_matches_oracle(ctx, c3s):
+    from paper_2002_02045_gb300 import PGB_FP64
+    m = c3s
+    grid, T, sig = (6, 6, 6), 300.0, 0.02
+    set_polar_model(ctx, m)
+    ctx.pgb_set_grids(grid, grid)
+    pts = S.mp_grid(*grid)
+    eps_all, _ = O.bands(m, pts)
+    emin = eps_all[:, :2].min()
+    # window edges away from any state energy (membership must not hang on rounding)
+    lo, hi = emin - 1e-6, emin + 0.4
+    assert np.abs(eps_all[:, :2] - hi).min() > 1e-6
+    mu = emin - 0.2
+    ctx.pgb_build_collision_grid(0, 2, lo, hi, T, sig)
+    ns = 2 * len(pts)
+    F = np.zeros((ns, 3))
+    tau = np.zeros(ns)
+    mob_rta, mob, it = ctx.pgb_transport(mu, PGB_FP64, 5000, 1e-9, F, tau)
+    # oracle: the same steps on its own list
+    L = O.collision_list_grid(m, grid, 0, 2, window=(lo, hi))
+    es = L["eps"]
+    win = (es >= lo) & (es <= hi)
+    kw = np.unique(np.nonzero(win)[0] // 2)
+    gam = O.scattering_rates_grid(m, grid, grid, kw, T, mu, sig)
+    vel = O.velocities(m, pts[kw])
+    pos = {k: i for i, k in enumerate(kw)}
+    tau_r = np.zeros(ns)
+    v_r = np.zeros((ns, 3))
+    for s in np.nonzero(win)[0]:
+        tau_r[s] = 1.0 / gam[pos[s // 2], s % 2]
+        v_r[s] = vel[pos[s // 2], s % 2]
+    w = O.bte_weights(es, L["row"], L["col"], L["hw"], L["g2"], T, mu, sig, L["nq"])
+    F_r, it_r = O.bte_iterate(tau_r, v_r, L["row"], L["col"], w, 5000, 1e-9)
+    assert np.abs(tau - tau_r).max() <= 1e-9 * tau_r.max()
+    assert np.abs(F - F_r).max() <= 1e-5 * np.abs(F_r).max()
+    assert abs(it - it_r) <= 2 and it < 5000
+    ref_rta = O.mobility(v_r[win], (tau_r[:, None] * v_r)[win], es[win], T, mu)
+    ref = O.mobility(v_r[win], F_r[win], es[win], T, mu)
+    assert np.abs(mob_rta - ref_rta).max() <= 1e-8 * np.abs(ref_rta).max()
+    assert np.abs(mob - ref).max() <= 1e-5 * np.abs(ref).max()
+    assert np.abs(mob - mob_rta).max() > 1e-3 * np.abs(mob_rta).max()   # the iteration matters
+
+
+@pytest.mark.slow
+def test_transport_full_size_polar(ctx, c3):
+    # config-3 sizes: 60^3 k = q grid, states within 0.2 eV of the band minimum,
+    # tau from the BF16-split rates over all 216,000 q.  The oracle cannot run at
+    # this size; check properties that hold at any size.
+    from paper_2002_02045_gb300 import PGB_TC_BF16X3
+    m = c3
+    grid = (60, 60, 60)
+    set_polar_model(ctx, m)
+    ctx.pgb_set_grids(grid, grid)
+    nk = 216000
+    eps = empty((nk, 8))
+    ctx.pgb_get_grid_energies(eps, None)
+    emin = float(eps[:, :2].min())
+    nnz = ctx.pgb_build_collision_grid(0, 2, emin - 1e-6, emin + 0.2, 300.0, 0.010)
+    assert nnz > 0
+    ns = 2 * nk
+    F = empty((ns, 3))
+    tau = empty((ns,))
+    mob_rta, mob, it = ctx.pgb_transport(emin - 0.3, PGB_TC_BF16X3, 3000, 1e-6, F, tau)
+    assert it < 3000
+    assert np.all(np.isfinite(mob)) and np.all(np.diag(mob) > 0) and np.all(np.diag(mob_rta) > 0)
+    # RTA mobility from the returned tau and the velocities equals the library's
+    es = empty((ns,))
+    ctx.pgb_collision_energies(es)
+    es = es.cpu().numpy()
+    t = tau.cpu().numpy()
+    win = (es >= emin - 1e-6) & (es <= emin + 0.2)
+    assert np.all(t[win] > 0) and np.all(t[~win] == 0)
+    ks = np.unique(np.nonzero(win)[0] // 2).astype(np.int32)
+    v = np.zeros((len(ks), 8, 3))
+    ctx.pgb_band_velocities(ks, v)
+    pos = {k: i for i, k in enumerate(ks)}
+    s_w = np.nonzero(win)[0]
+    vs = np.stack([v[pos[s // 2], s % 2] for s in s_w])
+    ref_rta = O.mobility(vs, t[s_w, None] * vs, es[s_w], 300.0, emin - 0.3)
+    assert np.abs(mob_rta - ref_rta).max() <= 1e-10 * np.abs(ref_rta).max()
