@@ -213,9 +213,11 @@ pgb_status pgb_band_velocities(pgb_ctx *ctx, const int32_t *k_idx, int64_t nk, d
  *     final band and mode, in `precision` (states with Gamma = 0 get tau = 0);
  *   v_nk from pgb_band_velocities;
  *   W_e = (2 pi/hbar)(1/N_q)|g|^2 [d(e_s - hw - e_s')(1 + N - f0_s') + d(e_s + hw - e_s')(N + f0_s')]
- *     per list entry (FP64 arithmetic, stored FP32);
+ *     per list entry;
  *   F^0 = tau v, F^{i+1}_s = tau_s v_s + tau_s sum_{e in row s} W_e F^i_{col e}, until
- *     max |F^{i+1} - F^i| <= tol max |F^0| or max_iter iterations;
+ *     max |F^{i+1} - F^i| <= tol max |F^0| or max_iter iterations (W, F and
+ *     the products in FP64: the iteration matrix's spectral radius is often
+ *     within 1e-3 of one, which amplifies any error of W);
  *   mobility[a*3+b] = sum_s v^a_s F^b_s (-df0/de)_s / sum_s f0_s in cm^2/(V s),
  *     -df0/de = f0 (1 - f0)/kT (Eq. cond divided by e n_c, the carriers of
  *     the same states).

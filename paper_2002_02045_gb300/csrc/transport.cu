@@ -9,10 +9,13 @@
 //
 // BTE: the list of pgb_build_collision_grid (window states, rows sorted) gives
 // W per entry; F^{i+1}_s = tau_s v_s + tau_s sum_{e in row s} W_e F^i_{col e} is a
-// CSR product per iteration, one 256-thread block per non-empty row, FP32
-// gathers of F and FP32 products with compensated sums, FP64 per row; the
-// largest change of any component is reduced with an integer atomic max on
-// the bits of a non-negative double (order independent).
+// CSR product per iteration, one 256-thread block per non-empty row.  The
+// iteration matrix tau W of a window that keeps most of its scattering inside
+// has a spectral radius within 1e-2 .. 1e-5 of one, so F amplifies any error
+// of W by 1e2 .. 1e5: W, F and the products are FP64 here (the FP64 rate is
+// enough for one product per entry per iteration).  The largest change of
+// any component is reduced with an integer atomic max on the bits of a
+// non-negative double (order independent).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -175,7 +178,7 @@ struct WArgs {
     CoeffGeom g;
     const double *eps_state;
     double mu;
-    float *w;
+    double *w;
 };
 
 __global__ void k_bte_weights(WArgs p) {
@@ -187,14 +190,14 @@ __global__ void k_bte_weights(WArgs p) {
         const double f = 1.0 / (exp((p.eps_state[p.col[e]] - p.mu) / (kBoltzEvK * p.g.T)) + 1.0);
         w = p.g.scale * (double)p.g2[e] * (de * (1.0 + N - f) + da * (N + f));
     }
-    p.w[e] = (float)w;
+    p.w[e] = w;
 }
 
 // per state: tau, F^0 = tau v (window states with Gamma > 0), FP32 copies
 __global__ void k_bte_init(int64_t ns, int nbnd, int band_lo, int nw, const uint8_t *__restrict__ inwin,
                            const int32_t *__restrict__ kpos, const double *__restrict__ gamma,
                            const double *__restrict__ vel, double *__restrict__ tau, double *__restrict__ v,
-                           double *__restrict__ F0, double *__restrict__ F, float4 *__restrict__ F32) {
+                           double *__restrict__ F0, double *__restrict__ F) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= ns) return;
     const int64_t k = s / nbnd;
@@ -220,14 +223,6 @@ __global__ void k_bte_init(int64_t ns, int nbnd, int band_lo, int nw, const uint
     F[3 * s] = f0x;
     F[3 * s + 1] = f0y;
     F[3 * s + 2] = f0z;
-    F32[s] = make_float4((float)f0x, (float)f0y, (float)f0z, 0.f);
-}
-
-__device__ __forceinline__ void kadd(float &sum, float &comp, float x) {
-    const float y = x - comp;
-    const float t = sum + y;
-    comp = (t - sum) - y;
-    sum = t;
 }
 
 struct IterArgs {
@@ -235,13 +230,11 @@ struct IterArgs {
     const int32_t *rows;
     const int64_t *rowptr;
     const int32_t *col;
-    const float *w;
+    const double *w;
     const double *tau;
     const double *F0;
     const double *Fold;
-    const float4 *Fold32;
     double *Fnew;
-    float4 *Fnew32;
     unsigned long long *maxdiff;   // bits of a non-negative double
 };
 
@@ -254,15 +247,14 @@ __global__ void __launch_bounds__(kIterThreads) k_bte_iter(IterArgs p) {
     const int s = p.rows[r];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t beg = p.rowptr[s], end = p.rowptr[s + 1];
-    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
+    double v[3] = {0.0, 0.0, 0.0};
     for (int64_t e = beg + t; e < end; e += kIterThreads) {
-        const float w = p.w[e];
-        const float4 f = __ldg(p.Fold32 + p.col[e]);
-        kadd(sx, cx, w * f.x);
-        kadd(sy, cy, w * f.y);
-        kadd(sz, cz, w * f.z);
+        const double w = p.w[e];
+        const double *f = p.Fold + 3 * (int64_t)p.col[e];
+        v[0] = fma(w, __ldg(f), v[0]);
+        v[1] = fma(w, __ldg(f + 1), v[1]);
+        v[2] = fma(w, __ldg(f + 2), v[2]);
     }
-    double v[3] = {(double)sx - (double)cx, (double)sy - (double)cy, (double)sz - (double)cz};
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
 #pragma unroll
@@ -275,13 +267,12 @@ __global__ void __launch_bounds__(kIterThreads) k_bte_iter(IterArgs p) {
         for (int w = 0; w < kIterThreads / 32; ++w)
             for (int i = 0; i < 3; ++i) S[i] += red[i][w];
         const double ts = p.tau[s];
-        double diff = 0.0, fn[3];
+        double diff = 0.0;
         for (int i = 0; i < 3; ++i) {
-            fn[i] = p.F0[3 * s + i] + ts * S[i];
-            diff = fmax(diff, fabs(fn[i] - p.Fold[3 * s + i]));
-            p.Fnew[3 * s + i] = fn[i];
+            const double fn = p.F0[3 * s + i] + ts * S[i];
+            diff = fmax(diff, fabs(fn - p.Fold[3 * s + i]));
+            p.Fnew[3 * s + i] = fn;
         }
-        p.Fnew32[s] = make_float4((float)fn[0], (float)fn[1], (float)fn[2], 0.f);
         atomicMax(p.maxdiff, (unsigned long long)__double_as_longlong(diff));
     }
 }
@@ -431,8 +422,7 @@ pgb_status transport(pgb_ctx *c, double mu, int precision, int max_iter, double 
     double *tau = (double *)B.get(8 * (size_t)ns), *v = (double *)B.get(24 * (size_t)ns);
     double *F0 = (double *)B.get(24 * (size_t)ns);
     double *F[2] = {(double *)B.get(24 * (size_t)ns), (double *)B.get(24 * (size_t)ns)};
-    float4 *F32[2] = {(float4 *)B.get(16 * (size_t)ns), (float4 *)B.get(16 * (size_t)ns)};
-    float *w = (float *)B.get(4 * (size_t)nnz);
+    double *w = (double *)B.get(8 * (size_t)nnz);
     unsigned long long *d_max = (unsigned long long *)B.get(8);
     if (!B.ok) {
         c->err = "transport: device allocation failed";
@@ -450,10 +440,9 @@ pgb_status transport(pgb_ctx *c, double mu, int precision, int max_iter, double 
         if ((st = band_velocities(c, d_klist, nkw, d_vel)) != PGB_OK) return st;
     }
     k_bte_init<<<div_up(ns, 256), 256, 0, c->stream>>>(ns, nbnd, c->band_lo, nw, d_win, d_kpos, d_gamma, d_vel, tau, v,
-                                                       F0, F[0], F32[0]);
+                                                       F0, F[0]);
     PGB_LAUNCH_CHECK(c);
     PGB_CUDA_TRY(c, cudaMemcpyAsync(F[1], F[0], 24 * (size_t)ns, cudaMemcpyDeviceToDevice, c->stream));
-    PGB_CUDA_TRY(c, cudaMemcpyAsync(F32[1], F32[0], 16 * (size_t)ns, cudaMemcpyDeviceToDevice, c->stream));
     double nsum = 0.0;
     if ((st = mobility_sum(c, d_win, mu, v, F0, mob_rta, &nsum)) != PGB_OK) return st;
     // W per entry
@@ -492,9 +481,7 @@ pgb_status transport(pgb_ctx *c, double mu, int precision, int max_iter, double 
         p.tau = tau;
         p.F0 = F0;
         p.Fold = F[cur];
-        p.Fold32 = F32[cur];
         p.Fnew = F[1 - cur];
-        p.Fnew32 = F32[1 - cur];
         p.maxdiff = d_max;
         prof_mark(c, PGB_PROF_COLLISION);
         k_bte_iter<<<(unsigned)c->nrows_active, kIterThreads, 0, c->stream>>>(p);
