@@ -54,6 +54,13 @@ Pins (tests/test_oracle_*.py):
     ``bte_iterate``: the dense solution of (1 - tau W) F = tau v; RTA when W = 0.
   * ``mobility``: constant-tau cosine band under Boltzmann statistics against
     the exact aliased Bessel-function average.
+  * ``mc_qpoints``: the Cauchy density integrates to one and its CDF inverts
+    the map; width 1 is the uniform map; the weighted estimator integrates a
+    known function without bias.  ``scattering_rates_mc`` with the grid points
+    as samples equals ``scattering_rates_grid``.
+  * ``tetra_theta_weights``: against an independent geometric integral (iso-
+    energy slices of the tetrahedron integrated by Gauss-Legendre), continuity
+    at the corner energies; ``population_cumulative``: carrier counts.
 Parity unpinned: absolute Gamma of real materials (no DFT data here).
 """
 from __future__ import annotations
@@ -675,3 +682,149 @@ def mobility(v, F, eps, T, mu):
     f = fermi_dirac(eps, mu, T)
     w = f * (1.0 - f) / (KB_EVK * T)
     return 1e4 * np.einsum("s,sa,sb->ab", w, np.asarray(v), np.asarray(F)) / f.sum()
+
+
+# ----------------------------------------------------------------------------
+# Monte-Carlo q sampling of Gamma_nk (Sec. 4.3: random q, uniform or Cauchy)
+# ----------------------------------------------------------------------------
+
+Q_UNIFORM, Q_CAUCHY = 0, 1
+
+
+def mc_qpoints(u, sampling, width=1.0):
+    """q points (crystal coordinates) and 1/p(q) from uniforms u [nq, 3] in [0, 1).
+
+    Uniform: q_i = u_i - 1/2, p = 1.  Cauchy (reading of the paper's Cauchy
+    sampling on the periodic zone): each coordinate by the tangent map
+    q_i = atan(c tan(pi (u_i - 1/2))) / pi, whose density on [-1/2, 1/2) is
+    p(q_i) = c / (c^2 cos^2(pi q_i) + sin^2(pi q_i)) (Lorentzian of width ~c/pi
+    near q_i = 0, normalised over the zone); p(q) is the product over i.
+    """
+    u = np.asarray(u, np.float64)
+    if sampling == Q_UNIFORM:
+        return u - 0.5, np.ones(len(u))
+    c = float(width)
+    q = np.arctan(c * np.tan(np.pi * (u - 0.5))) / np.pi
+    p = c / (c * c * np.cos(np.pi * q) ** 2 + np.sin(np.pi * q) ** 2)
+    return q, 1.0 / np.prod(p, axis=1)
+
+
+def scattering_rates_mc(model, kpts, u, sampling, width, T, mu, sigma):
+    """Gamma_nk at arbitrary k (Eqs. scatter_rate, BTE_W) by Monte-Carlo q sampling.
+
+    With samples q_j of density p: Gamma = (1/N) sum_j y_j, y_j = sum_{m nu} W(q_j) / p(q_j),
+    bands at k + q_j and phonons at q_j interpolated per sample, g from the
+    short- plus long-range Wannier sum.  Returns (Gamma [nk, nw], standard error
+    [nk, nw] = sqrt(sum_j (y_j - Gamma)^2 / (N (N - 1)))).
+    """
+    q, pinv = mc_qpoints(u, sampling, width)
+    kpts = np.asarray(kpts, np.float64)
+    nq = len(q)
+    eps_k, U_k = bands(model, kpts)
+    hw, e = phonons(model, q)
+    gam = np.zeros((len(kpts), model.nw))
+    err = np.zeros((len(kpts), model.nw))
+    for a in range(len(kpts)):
+        eps_kq, U_kq = bands(model, kpts[a] + q)
+        gw = g_wannier_full(model, kpts[a:a + 1], q)[0]
+        g2 = np.abs(g_modes(g_bloch(gw, U_k[a][None], U_kq), hw, e, model.mass)) ** 2   # [q, nu, m, n]
+        f_m = fermi_dirac(eps_kq, mu, T)[:, None, :, None]
+        N = bose_einstein(hw, T)[:, :, None, None]
+        d = eps_k[a][None, None, None, :] - eps_kq[:, None, :, None]
+        w = hw[:, :, None, None]
+        live = (hw >= OMEGA_MIN_EV)[:, :, None, None]
+        W = TWO_PI_OVER_HBAR * g2 * np.where(live, delta_gauss(d - w, sigma) * (1 + N - f_m)
+                                             + delta_gauss(d + w, sigma) * (N + f_m), 0.0)
+        y = W.sum(axis=(1, 2)) * pinv[:, None]                       # [q, n]
+        gam[a] = y.mean(axis=0)
+        err[a] = np.sqrt(((y - gam[a]) ** 2).sum(axis=0) / (nq * (nq - 1))) if nq > 1 else 0.0
+    return gam, err
+
+
+# ----------------------------------------------------------------------------
+# carrier population p(E, t) by the linear tetrahedron method (Eq. pop)
+# ----------------------------------------------------------------------------
+
+def grid_tetrahedra(grid):
+    """Six tetrahedra per cell of a periodic grid, split along the cell's (0,0,0)-(1,1,1)
+    diagonal: [6 N, 4] indices of grid points (the corners of each tetrahedron)."""
+    n1, n2, n3 = grid
+    corners = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 0), (0, 0, 1), (1, 0, 1), (0, 1, 1), (1, 1, 1)]
+    # the six paths 0 -> 7 through the cube, one tetrahedron each
+    paths = [(0, 1, 3, 7), (0, 1, 5, 7), (0, 2, 3, 7), (0, 2, 6, 7), (0, 4, 5, 7), (0, 4, 6, 7)]
+    i1, i2, i3 = np.meshgrid(np.arange(n1), np.arange(n2), np.arange(n3), indexing="ij")
+    base = np.stack([i1.ravel(), i2.ravel(), i3.ravel()], -1)
+    out = []
+    for path in paths:
+        idx = []
+        for cidx in path:
+            d = np.array(corners[cidx])
+            p = (base + d) % np.array(grid)
+            idx.append((p[:, 0] * n2 + p[:, 1]) * n3 + p[:, 2])
+        out.append(np.stack(idx, -1))
+    return np.concatenate(out, 0)
+
+
+def tetra_theta_weights(e, E):
+    """Corner weights w [.., 4] with int_T f theta(E - eps) dk = V_T sum_i w_i f_i for eps and f
+    linear in the tetrahedron T (corner energies e [.., 4], any order); the weights
+    are per unit volume of T, so sum_i w_i is the fraction of T below E (Bloechl's
+    linear tetrahedron integration weights)."""
+    e = np.asarray(e, np.float64)
+    order = np.argsort(e, axis=-1, kind="stable")
+    es = np.take_along_axis(e, order, -1)
+    e1, e2, e3, e4 = (es[..., i] for i in range(4))
+    ws = np.zeros(es.shape)
+    x = E
+    with np.errstate(divide="ignore", invalid="ignore"):
+        # e1 <= E < e2
+        m = (x >= e1) & (x < e2)
+        if np.any(m):
+            d1, d21, d31, d41 = x - e1[m], e2[m] - e1[m], e3[m] - e1[m], e4[m] - e1[m]
+            C = 0.25 * d1 ** 3 / (d21 * d31 * d41)
+            ws[m, 0] = C * (4 - d1 * (1 / d21 + 1 / d31 + 1 / d41))
+            ws[m, 1] = C * d1 / d21
+            ws[m, 2] = C * d1 / d31
+            ws[m, 3] = C * d1 / d41
+        # e2 <= E < e3
+        m = (x >= e2) & (x < e3)
+        if np.any(m):
+            a1, a2, b3, b4 = x - e1[m], x - e2[m], e3[m] - x, e4[m] - x
+            d31, d41, d32, d42 = e3[m] - e1[m], e4[m] - e1[m], e3[m] - e2[m], e4[m] - e2[m]
+            C1 = 0.25 * a1 ** 2 / (d41 * d31)
+            C2 = 0.25 * a1 * a2 * b3 / (d41 * d32 * d31)
+            C3 = 0.25 * a2 ** 2 * b4 / (d42 * d32 * d41)
+            ws[m, 0] = C1 + (C1 + C2) * b3 / d31 + (C1 + C2 + C3) * b4 / d41
+            ws[m, 1] = C1 + C2 + C3 + (C2 + C3) * b3 / d32 + C3 * b4 / d42
+            ws[m, 2] = (C1 + C2) * a1 / d31 + (C2 + C3) * a2 / d32
+            ws[m, 3] = (C1 + C2 + C3) * a1 / d41 + C3 * a2 / d42
+        # e3 <= E < e4
+        m = (x >= e3) & (x < e4)
+        if np.any(m):
+            b4, d41, d42, d43 = e4[m] - x, e4[m] - e1[m], e4[m] - e2[m], e4[m] - e3[m]
+            C = 0.25 * b4 ** 3 / (d41 * d42 * d43)
+            ws[m, 0] = 0.25 - C * b4 / d41
+            ws[m, 1] = 0.25 - C * b4 / d42
+            ws[m, 2] = 0.25 - C * b4 / d43
+            ws[m, 3] = 0.25 - C * (4 - b4 * (1 / d41 + 1 / d42 + 1 / d43))
+        m = x >= e4
+        ws[m] = 0.25
+    w = np.zeros(es.shape)
+    np.put_along_axis(w, order, ws, -1)
+    return w
+
+
+def population_cumulative(eps, f, grid, E_edges):
+    """N(E) = sum_n (1/V_BZ) int f_n(k) theta(E - eps_n(k)) dk (carriers per cell below E) for
+    each E in E_edges, by the linear tetrahedron method on the k grid; eps, f [Nk, nb].
+    The carrier population of Eq. pop integrated over a bin is N(E_b) - N(E_a)."""
+    tet = grid_tetrahedra(grid)
+    ntet = len(tet)
+    eps = np.asarray(eps, np.float64)
+    f = np.asarray(f, np.float64)
+    out = np.zeros(len(E_edges))
+    for n in range(eps.shape[1]):
+        et, ft = eps[tet, n], f[tet, n]
+        for j, E in enumerate(E_edges):
+            out[j] += np.sum(tetra_theta_weights(et, E) * ft) / ntet
+    return out
