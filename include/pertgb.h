@@ -229,6 +229,34 @@ pgb_status pgb_transport(pgb_ctx *ctx, double mu_eV, int precision, int max_iter
                          double *mobility_rta, double *mobility, int64_t *iterations_out, double *F_out,
                          double *tau_out);
 
+/* Gamma_nk by Monte-Carlo q sampling (Sec. 4.3: random q in the zone, uniform
+ * or Cauchy; Eqs. scatter_rate, BTE_W) at arbitrary points kpts [nk][3]
+ * (crystal coordinates, host or device), every band.  The caller supplies the
+ * random numbers: u [nq][3] uniforms in [0, 1) (host or device; PGB_EINVAL
+ * otherwise), mapped per coordinate to
+ *   PGB_Q_UNIFORM: q_i = u_i - 1/2, density p = 1;
+ *   PGB_Q_CAUCHY:  q_i = atan(c tan(pi (u_i - 1/2)))/pi, p(q_i) = c/(c^2 cos^2(pi q_i) + sin^2(pi q_i)),
+ *                  c = width in (0, 1] (Lorentzian of width ~c/pi about q_i = 0);
+ *   Gamma_nk = (1/nq) sum_j y_j, y_j = sum_{m nu} W(k, q_j) / p(q_j),
+ * with bands at k + q_j and phonons at q_j interpolated for each sample and g
+ * including any polar term.  stderr_out (may be NULL) receives the standard
+ * error sqrt(sum_j (y_j - Gamma)^2 / (nq (nq - 1))).  precision: PGB_FP64 or
+ * PGB_FP32.  Terms with |x|/sigma > 7 are skipped.  Outputs [nk][nw], 1/s. */
+#define PGB_Q_UNIFORM 0
+#define PGB_Q_CAUCHY 1
+pgb_status pgb_scattering_rates_mc(pgb_ctx *ctx, const double *kpts, int64_t nk, const double *u, int64_t nq,
+                                   int sampling, double width, double T_K, double mu_eV, double sigma_eV,
+                                   int precision, double *gamma_out, double *stderr_out);
+
+/* Carrier population (Eq. pop) by the linear tetrahedron method on the k grid
+ * of the current collision list: for occupations f [nstates] (host or
+ * device) and energies E [nE] (eV), N_out [nE] (host or device) receives
+ *   N(E) = sum_n (1/V_BZ) int f_n(k) theta(E - e_n(k)) dk   (carriers per cell below E),
+ * with e_n and f_n linear on each of the six tetrahedra of every grid cell
+ * (cells split along their (0,0,0)-(1,1,1) diagonal), over the list's bands.
+ * p(E) integrated over [E_a, E_b) is N(E_b) - N(E_a).                      */
+pgb_status pgb_population(pgb_ctx *ctx, const double *f, const double *E, int64_t nE, double *N_out);
+
 /* Replace |g|^2 of every entry of the current list, keeping its rows,
  * columns and modes: g2 [nnz] float32 (host or device), eV^2.  a and b are
  * recomputed as in pgb_build_collision.  For fitting |g|^2 with the

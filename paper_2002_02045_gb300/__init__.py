@@ -9,6 +9,8 @@ from .native import (  # noqa: F401
     PGB_FP64,
     PGB_G2_FULL,
     PGB_G_ABS,
+    PGB_Q_CAUCHY,
+    PGB_Q_UNIFORM,
     PGB_TC_BF16X3,
     PGB_TC_TF32X3,
     PRECISIONS,

@@ -1164,6 +1164,139 @@ pgb_status pgb_transport(pgb_ctx *c, double mu_eV, int precision, int max_iter, 
     return PGB_OK;
 }
 
+pgb_status pgb_scattering_rates_mc(pgb_ctx *c, const double *kpts, int64_t nk, const double *u, int64_t nq,
+                                   int sampling, double width, double T, double mu, double sigma, int precision,
+                                   double *gamma_out, double *stderr_out) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_model) return fail(c, PGB_ESTATE, "scattering_rates_mc: call set_model first");
+    if (nk < 0 || nq < 0) return fail(c, PGB_EINVAL, "scattering_rates_mc: negative size");
+    if (!(T > 0.0) || !(sigma > 0.0) || !std::isfinite(mu))
+        return fail(c, PGB_EINVAL, "scattering_rates_mc: need T > 0, sigma > 0, finite mu");
+    if (sampling != PGB_Q_UNIFORM && sampling != PGB_Q_CAUCHY)
+        return fail(c, PGB_EINVAL, "scattering_rates_mc: unknown sampling");
+    if (sampling == PGB_Q_CAUCHY && !(width > 0.0 && width <= 1.0))
+        return fail(c, PGB_EINVAL, "scattering_rates_mc: the Cauchy width must lie in (0, 1]");
+    if (precision != PGB_FP64 && precision != PGB_FP32)
+        return fail(c, PGB_EINVAL, "scattering_rates_mc: precision must be PGB_FP64 or PGB_FP32");
+    if (nk == 0) return PGB_OK;
+    if (nq == 0) return fail(c, PGB_EINVAL, "scattering_rates_mc: need at least one q sample");
+    if (!kpts || !u || !gamma_out) return fail(c, PGB_EINVAL, "scattering_rates_mc: null pointer");
+    const bool f32 = precision == PGB_FP32;
+    const int nw = c->nw, nm = c->nm, nw2 = nw * nw, nm2 = nm * nm;
+    const int64_t ncol = (int64_t)nm * nw2, nrow = (int64_t)c->nKp * ncol, nrowS = (int64_t)c->nRgp * ncol;
+    const size_t es = f32 ? sizeof(float2) : sizeof(double2);
+    {   // uniforms must lie in [0, 1)
+        std::vector<double> hu(3 * (size_t)nq);
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(hu.data(), u, 8 * hu.size(), cudaMemcpyDefault, c->stream));
+        PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        for (double x : hu)
+            if (!(x >= 0.0 && x < 1.0)) return fail(c, PGB_EINVAL, "scattering_rates_mc: u must lie in [0, 1)");
+    }
+    In<double> K, Uin;
+    TRY(K.init(c, kpts, 3 * (size_t)nk));
+    TRY(Uin.init(c, u, 3 * (size_t)nq));
+    Out<double> Gm, Er;
+    TRY(Gm.init(c, gamma_out, (size_t)nk * nw));
+    TRY(Er.init(c, stderr_out, (size_t)nk * nw));
+    Tmp<double> q, pinv, eps_k, acc;
+    Tmp<double2> U_k;
+    TRY(q.alloc(c, 3 * (size_t)nq));
+    TRY(pinv.alloc(c, (size_t)nq));
+    TRY(eps_k.alloc(c, (size_t)nk * nw));
+    TRY(U_k.alloc(c, (size_t)nk * nw2));
+    TRY(acc.alloc(c, (size_t)nk * 2 * nw));
+    PGB_CUDA_TRY(c, cudaMemsetAsync(acc.p, 0, 16 * (size_t)nk * nw, c->stream));
+    TRY(launch_mc_qpoints(c, nq, Uin.dev, sampling, width, q.p, pinv.p));
+    TRY(bands_at(c, K.dev, nk, eps_k.p, U_k.p));
+    Tmp<float2> U_k32;
+    const void *Uk = U_k.p;
+    if (f32) {
+        TRY(U_k32.alloc(c, (size_t)nk * nw2));
+        TRY(launch_to_f32(c, U_k.p, U_k32.p, nk * nw2));
+        Uk = U_k32.p;
+    }
+    // R_e sums with U(k) folded, for every k: G [nk][nKp][ncol]
+    const int64_t kb = std::max<int64_t>(1, std::min<int64_t>(nk, 8));
+    Tmp<char> phk, S1, G;
+    TRY(phk.alloc(c, (size_t)kb * c->nRge * es));
+    TRY(S1.alloc(c, (size_t)kb * nrowS * es));
+    TRY(G.alloc(c, (size_t)nk * nrow * es));
+    const void *g = f32 ? (const void *)c->d_g32 : (const void *)c->d_g64;
+    for (int64_t k0 = 0; k0 < nk; k0 += kb) {
+        const int64_t nb = std::min(kb, nk - k0);
+        TRY(launch_phase_pts(c, K.dev + 3 * k0, nb, c->d_Rge, c->nRge, phk.p, f32));
+        TRY(launch_cgemm(c, f32, 1, nb, nrowS, c->nRge, phk.p, c->nRge, 0, g, nrowS, 0, S1.p, nrowS, 0));
+        TRY(launch_fold_u(c, f32, nb, nullptr, c->nRgp, nm, nw, S1.p,
+                          (const char *)Uk + (size_t)k0 * nw2 * es, G.p + (size_t)k0 * nrow * es));
+    }
+    // q chunks x k batches
+    const int64_t qc = std::min<int64_t>(nq, 8192);
+    Tmp<double> hw_q, kq, eps_kq, partial;
+    Tmp<double2> coef_q, U_kq;
+    Tmp<char> phq, C, coef32, Ukq32;
+    TRY(hw_q.alloc(c, (size_t)qc * nm));
+    TRY(coef_q.alloc(c, (size_t)qc * nm2));
+    TRY(phq.alloc(c, (size_t)qc * c->nKp * es));
+    TRY(kq.alloc(c, 3 * (size_t)kb * qc));
+    TRY(eps_kq.alloc(c, (size_t)kb * qc * nw));
+    TRY(U_kq.alloc(c, (size_t)kb * qc * nw2));
+    TRY(C.alloc(c, (size_t)kb * qc * ncol * es));
+    TRY(partial.alloc(c, (size_t)mc_partial_count(c, kb, qc)));
+    if (f32) {
+        TRY(coef32.alloc(c, (size_t)qc * nm2 * sizeof(float2)));
+        TRY(Ukq32.alloc(c, (size_t)kb * qc * nw2 * sizeof(float2)));
+    }
+    for (int64_t q0 = 0; q0 < nq; q0 += qc) {
+        const int64_t nqc = std::min(qc, nq - q0);
+        const double *qp = q.p + 3 * q0;
+        TRY(phonons_at(c, qp, nqc, hw_q.p, coef_q.p));
+        TRY(launch_qtable_pts(c, qp, nqc, phq.p, f32));
+        const void *cf = coef_q.p;
+        if (f32) {
+            TRY(launch_to_f32(c, coef_q.p, (float2 *)coef32.p, nqc * nm2));
+            cf = coef32.p;
+        }
+        for (int64_t k0 = 0; k0 < nk; k0 += kb) {
+            const int64_t nb = std::min(kb, nk - k0);
+            TRY(launch_kplusq_pts(c, K.dev + 3 * k0, nb, qp, nqc, kq.p));
+            TRY(bands_at(c, kq.p, nb * nqc, eps_kq.p, U_kq.p));
+            const void *Ukq = U_kq.p;
+            if (f32) {
+                TRY(launch_to_f32(c, U_kq.p, (float2 *)Ukq32.p, nb * nqc * nw2));
+                Ukq = Ukq32.p;
+            }
+            TRY(launch_cgemm(c, f32, nb, nqc, ncol, c->nKp, phq.p, c->nKp, 0, G.p + (size_t)k0 * nrow * es, ncol,
+                             nrow, C.p, ncol, nqc * ncol));
+            TRY(launch_mc_epilogue(c, f32, nb, nqc, C.p, Ukq, eps_k.p + k0 * nw, eps_kq.p, hw_q.p, cf,
+                                   pinv.p + q0, T, mu, sigma, partial.p, acc.p + k0 * 2 * nw));
+        }
+    }
+    TRY(launch_mc_finish(c, nk, nq, sigma, acc.p, Gm.dev, Er.dev));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    TRY(Gm.finish());
+    TRY(Er.finish());
+    return PGB_OK;
+}
+
+pgb_status pgb_population(pgb_ctx *c, const double *f, const double *E, int64_t nE, double *N_out) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_coll) return fail(c, PGB_ESTATE, "population: build a collision list first");
+    if (nE < 0) return fail(c, PGB_EINVAL, "population: negative nE");
+    if (nE == 0) return PGB_OK;
+    if (!f || !E || !N_out) return fail(c, PGB_EINVAL, "population: null pointer");
+    In<double> F, Ein;
+    TRY(F.init(c, f, (size_t)c->nstates));
+    TRY(Ein.init(c, E, (size_t)nE));
+    Out<double> Nn;
+    TRY(Nn.init(c, N_out, (size_t)nE));
+    TRY(launch_population(c, F.dev, Ein.dev, nE, Nn.dev));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    TRY(Nn.finish());
+    return PGB_OK;
+}
+
 pgb_status pgb_diag_bands(pgb_ctx *c, const double *pts, int64_t n, double *Hk, double *eps, double *U) {
     if (!c) return PGB_EINVAL;
     cudaSetDevice(c->device);

@@ -188,6 +188,17 @@ pgb_status launch_ewald_pts(pgb_ctx *c, const double *d_pts, int64_t npts, void 
                             bool fp32);
 std::vector<int32_t> ewald_candidates(const double lat[9], const double eps[9], double lambda);
 
+// Monte-Carlo q rates and tetrahedron populations (mcq.cu); device pointers
+pgb_status launch_mc_qpoints(pgb_ctx *c, int64_t nq, const double *u, int sampling, double width, double *q,
+                             double *pinv);
+pgb_status launch_mc_epilogue(pgb_ctx *c, bool fp32, int64_t nkb, int64_t nq, const void *C, const void *Ukq,
+                              const double *eps_k, const double *eps_kq, const double *hw, const void *coef,
+                              const double *pinv, double T, double mu, double sigma, double *partial, double *acc);
+int64_t mc_partial_count(const pgb_ctx *c, int64_t nkb, int64_t nq);
+pgb_status launch_mc_finish(pgb_ctx *c, int64_t nk, int64_t nq, double sigma, const double *acc, double *gamma,
+                            double *err);
+pgb_status launch_population(pgb_ctx *c, const double *f, const double *E, int64_t nE, double *out);
+
 // band velocities and transport (transport.cu); device pointers
 pgb_status build_velocity_tables(pgb_ctx *c);
 pgb_status band_velocities(pgb_ctx *c, const int32_t *d_kidx, int64_t nk, double *d_v);

@@ -31,7 +31,9 @@ ABI_SYMBOLS = (
     "pgb_scattering_rates_noalloc", "pgb_build_collision_grid", "pgb_collision_list",
     "pgb_collision_set_g2", "pgb_collision_vjp", "pgb_rk4_adjoint",
     "pgb_set_lattice", "pgb_set_polar", "pgb_long_range_g", "pgb_band_velocities", "pgb_transport",
+    "pgb_scattering_rates_mc", "pgb_population",
 )
+PGB_Q_UNIFORM, PGB_Q_CAUCHY = 0, 1
 PGB_NOALLOC_SCRATCH_BYTES = 64 << 20
 PROF_QSUM, PROF_RSUM, PROF_EPILOGUE, PROF_COLLISION, PROF_BANDS, PROF_ADJOINT = 0, 1, 2, 3, 4, 5
 
@@ -89,6 +91,8 @@ def load(path: str = LIB_PATH):
         "pgb_long_range_g": (I, [P, P, I64, P]),
         "pgb_band_velocities": (I, [P, P, I64, P]),
         "pgb_transport": (I, [P, D, I, I, D, P, P, C.POINTER(I64), P, P]),
+        "pgb_scattering_rates_mc": (I, [P, P, I64, P, I64, I, D, D, D, D, I, P, P]),
+        "pgb_population": (I, [P, P, P, I64, P]),
         "pgb_launch_count": (I64, [P]),
         "pgb_profile": (I, [P, I]),
         "pgb_scattering_rates_noalloc": (I, [P, P, I64, D, D, D, P]),
@@ -218,6 +222,19 @@ class Context:
         self._chk(self.lib.pgb_transport(self._h, float(mu), int(precision), int(max_iter), float(tol), _ptr(mr),
                                          _ptr(mi), C.byref(it), _ptr(F_out), _ptr(tau_out)))
         return mr.reshape(3, 3), mi.reshape(3, 3), int(it.value)
+
+    def pgb_scattering_rates_mc(self, kpts, u, sampling, width, T, mu, sigma, precision, gamma_out,
+                                stderr_out=None):
+        for a in (kpts, u, gamma_out, stderr_out):
+            _check_dtype(a, "float64")
+        self._chk(self.lib.pgb_scattering_rates_mc(self._h, _ptr(kpts), len(kpts), _ptr(u), len(u), int(sampling),
+                                                   float(width), float(T), float(mu), float(sigma), int(precision),
+                                                   _ptr(gamma_out), _ptr(stderr_out)))
+
+    def pgb_population(self, f, E, N_out):
+        for a in (f, E, N_out):
+            _check_dtype(a, "float64")
+        self._chk(self.lib.pgb_population(self._h, _ptr(f), _ptr(E), len(E), _ptr(N_out)))
 
     def pgb_set_grids(self, kgrid, qgrid):
         kg = (C.c_int * 3)(*kgrid)
