@@ -257,6 +257,33 @@ pgb_status pgb_scattering_rates_mc(pgb_ctx *ctx, const double *kpts, int64_t nk,
  * p(E) integrated over [E_a, E_b) is N(E_b) - N(E_a).                      */
 pgb_status pgb_population(pgb_ctx *ctx, const double *f, const double *E, int64_t nE, double *N_out);
 
+/* Batched scattering rates of many independent instances (contexts with
+ * their own model and grids, k grid = q grid or commensurate, on one device),
+ * in one persistent launch under a captured CUDA graph.
+ *
+ * pgb_batch_create: ctxs[0..n) (kept by pointer: they must keep their model
+ * and grids, and stay alive, while the batch exists); the batch runs on the
+ * first context's stream.
+ * pgb_batch_rates: for instance i, Gamma_nk (Eqs. scatter_rate, BTE_W; FP32
+ * products, FP64 energies, terms beyond 7 sigma skipped) of the k-grid points
+ * k_idx[i][0..nk[i]) over its whole q grid and every band and mode, at T_K,
+ * mu_eV[i] and sigma_eV, into gamma_out[i] [nk[i]][nw_i] (1/s).  k lists and
+ * outputs host or device.  The first call tunes the tile (q-points per unit
+ * and threads per block, four candidates timed once each); every call with
+ * new arguments captures the per-instance set-up (occupations, R_e sums),
+ * the persistent kernel and the reduction into a CUDA graph; calls with the
+ * same arguments replay it.  Results do not depend on the schedule.
+ * pgb_batch_tuning: chosen q tile and block size, candidate times (ms, [4],
+ * -1 where not run) and graph launches so far (any pointer may be NULL).    */
+typedef struct pgb_batch pgb_batch;
+pgb_status pgb_batch_create(pgb_batch **out, pgb_ctx *const *ctxs, int n);
+pgb_status pgb_batch_rates(pgb_batch *batch, const int32_t *const *k_idx, const int64_t *nk, double T_K,
+                           const double *mu_eV, double sigma_eV, double *const *gamma_out);
+pgb_status pgb_batch_tuning(const pgb_batch *batch, int *tile_q, int *threads, float *cand_ms,
+                            int64_t *graph_launches);
+const char *pgb_batch_last_error(const pgb_batch *batch);
+void pgb_batch_destroy(pgb_batch *batch);
+
 /* Replace |g|^2 of every entry of the current list, keeping its rows,
  * columns and modes: g2 [nnz] float32 (host or device), eV^2.  a and b are
  * recomputed as in pgb_build_collision.  For fitting |g|^2 with the

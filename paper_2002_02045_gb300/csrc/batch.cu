@@ -1,0 +1,639 @@
+// Scattering rates (Eqs. scatter_rate, BTE_W) of many independent model
+// instances of uneven band, mode and grid sizes in one persistent launch.
+//
+// Each member context holds its own model and grids.  Per call, the per-
+// instance set-up (occupation tables and the R_e sums with U(k) folded) and
+// one persistent kernel over the work units of every instance are captured in
+// a CUDA graph, which later calls with the same arguments replay.
+//
+// Work unit = (instance, k, initial band n, tile of QT q-points).  A unit
+//   1. forms its R_p-sum tile C[q][ka][i] = sum_p e^{iq.R_p} G_k[p][n][ka][i] in shared
+//      memory, K-chunk by K-chunk: the grid phases are generated exactly from
+//      integer arithmetic (the long-range rows of polar models read the q-grid
+//      table), the G_k rows of band n are contiguous (column order n, ka, i);
+//   2. runs the rates epilogue on the tile, one (q, nu) pair per thread: screen
+//      the (m) with |x| <= 7 sigma, project on nu, rotate by U(k+q), Gaussian
+//      weights with FP64 energies, FP32 products;
+//   3. writes the sum of its terms to its own partial slot.
+// Units are assigned to the persistent CTAs round-robin (every instance's
+// units are spread over all CTAs); a second kernel adds the q-tile partials of
+// each (instance, k, n) in order, so results do not depend on the schedule.
+//
+// The tile height QT and the block size are chosen by a small autotuner: on
+// the first call every candidate runs once, timed with events, and the fastest
+// is kept for the batch.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "cplx.cuh"
+#include "internal.cuh"
+
+namespace pgb {
+
+namespace {
+
+inline unsigned int div_up(int64_t a, int64_t b) { return (unsigned int)((a + b - 1) / b); }
+constexpr int KC = 16;   // K chunk of the shared-memory GEMM
+
+struct BInst {
+    int nw, nm, nRgp, nKp;
+    int qg[3], kg[3];
+    int64_t Nq;
+    int64_t unit0;             // first unit of this instance
+    int nqt;                   // q tiles
+    const int32_t *Rgp;        // [nRgp][3]
+    const double2 *polarL;     // [Nq][nm] or null
+    const float2 *G;           // [nk][nKp][nm*nw*nw]
+    const int32_t *kidx;       // [nk]
+    const double *eps;         // [Nk][nw]
+    const float2 *U;           // [Nk][nw][nw], U[i][n]
+    const float2 *coef;        // [Nq][nm][nm]
+    const double *hw;          // [Nq][nm]
+    const double *focc;        // [Nk][nw]
+    const double *nbe;         // [Nq][nm]
+    double sigma;
+};
+
+struct BArgs {
+    int ninst;
+    const BInst *inst;
+    const int32_t *unit_inst;  // [nunits] instance of each unit
+    int64_t nunits;
+    int maxc;                  // max nm*nw over the instances (shared tile width)
+    double *partial;           // [nunits]
+};
+
+__device__ __forceinline__ int64_t kq_index(int64_t k, int64_t q, const int kg[3], const int qg[3]) {
+    const int k3 = (int)(k % kg[2]), k2 = (int)((k / kg[2]) % kg[1]), k1 = (int)(k / ((int64_t)kg[1] * kg[2]));
+    const int q3 = (int)(q % qg[2]), q2 = (int)((q / qg[2]) % qg[1]), q1 = (int)(q / ((int64_t)qg[1] * qg[2]));
+    const int s1 = (k1 + q1 * (kg[0] / qg[0])) % kg[0];
+    const int s2 = (k2 + q2 * (kg[1] / qg[1])) % kg[1];
+    const int s3 = (k3 + q3 * (kg[2] / qg[2])) % kg[2];
+    return ((int64_t)s1 * kg[1] + s2) * kg[2] + s3;
+}
+
+__device__ __forceinline__ float2 grid_phase(const BInst &I, int64_t q, int p) {
+    if (p >= I.nRgp) {
+        const double2 v = I.polarL[q * I.nm + (p - I.nRgp)];
+        return make_float2((float)v.x, (float)v.y);
+    }
+    const int n1 = I.qg[0], n2 = I.qg[1], n3 = I.qg[2];
+    const int i3 = (int)(q % n3), i2 = (int)((q / n3) % n2), i1 = (int)(q / ((int64_t)n2 * n3));
+    int t1 = (int)(((int64_t)i1 * I.Rgp[3 * p + 0]) % n1);
+    int t2 = (int)(((int64_t)i2 * I.Rgp[3 * p + 1]) % n2);
+    int t3 = (int)(((int64_t)i3 * I.Rgp[3 * p + 2]) % n3);
+    if (t1 < 0) t1 += n1;
+    if (t2 < 0) t2 += n2;
+    if (t3 < 0) t3 += n3;
+    double x = (double)t1 / n1 + (double)t2 / n2 + (double)t3 / n3;
+    x -= rint(x);
+    double s, c;
+    sincospi(2.0 * x, &s, &c);
+    return make_float2((float)c, (float)s);
+}
+
+template <int QT, int NT>
+__global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
+    extern __shared__ float2 sm[];
+    float2 *Cs = sm;                         // [QT][maxc]
+    float2 *As = Cs + QT * a.maxc;           // [QT][KC]
+    float2 *Bs = As + QT * KC;               // [KC][maxc]
+    __shared__ double red[NT / 32];
+    const int t = threadIdx.x;
+    for (int64_t u = blockIdx.x; u < a.nunits; u += gridDim.x) {
+        const BInst I = a.inst[a.unit_inst[u]];
+        const int nw = I.nw, nm = I.nm, ncn = nm * nw, ncol = nm * nw * nw;
+        const int64_t r = u - I.unit0;
+        const int qt = (int)(r % I.nqt);
+        const int n = (int)((r / I.nqt) % nw);
+        const int64_t kb = r / ((int64_t)I.nqt * nw);
+        const int64_t q0 = (int64_t)qt * QT;
+        const int nq = (int)(I.Nq - q0 < QT ? I.Nq - q0 : QT);
+        const float2 *Gk = I.G + kb * (int64_t)I.nKp * ncol + (int64_t)n * ncn;
+        for (int o = t; o < QT * ncn; o += NT) Cs[(o / ncn) * a.maxc + o % ncn] = make_float2(0.f, 0.f);
+        // 1. R_p-sum tile
+        for (int p0 = 0; p0 < I.nKp; p0 += KC) {
+            __syncthreads();
+            for (int o = t; o < QT * KC; o += NT) {
+                const int qq = o / KC, kk = o % KC;
+                As[o] = (qq < nq && p0 + kk < I.nKp) ? grid_phase(I, q0 + qq, p0 + kk) : make_float2(0.f, 0.f);
+            }
+            for (int o = t; o < KC * ncn; o += NT) {
+                const int kk = o / ncn, cc = o % ncn;
+                Bs[kk * a.maxc + cc] = (p0 + kk < I.nKp) ? Gk[(int64_t)(p0 + kk) * ncol + cc] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            for (int o = t; o < QT * ncn; o += NT) {
+                const int qq = o / ncn, cc = o % ncn;
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int kk = 0; kk < KC; ++kk) cfma(acc, As[qq * KC + kk], Bs[kk * a.maxc + cc]);
+                float2 &d = Cs[qq * a.maxc + cc];
+                d.x += acc.x;
+                d.y += acc.y;
+            }
+        }
+        __syncthreads();
+        // 2. epilogue, one (q, nu) per thread
+        double part = 0.0;
+        const int64_t k = I.kidx[kb];
+        const double en = I.eps[k * nw + n];
+        const double is = 1.0 / I.sigma, ycut2 = kDeltaCut * kDeltaCut;
+        for (int o = t; o < QT * nm; o += NT) {
+            const int qq = o / nm, v = o % nm;
+            if (qq >= nq) continue;
+            const int64_t q = q0 + qq;
+            const double w = I.hw[q * nm + v];
+            if (!(w >= kOmegaMinEv)) continue;
+            const int64_t kq = kq_index(k, q, I.kg, I.qg);
+            const double *em = I.eps + kq * nw;
+            uint32_t live = 0;
+            for (int m = 0; m < nw; ++m) {
+                const double d = en - em[m];
+                const double ye = (d - w) * is, ya = (d + w) * is;
+                if (ye * ye <= ycut2 || ya * ya <= ycut2) live |= 1u << m;
+            }
+            if (!live) continue;
+            const float2 *cf = I.coef + (q * nm + v) * nm;
+            float2 gv[kMaxNw];
+#pragma unroll
+            for (int i = 0; i < kMaxNw; ++i) gv[i] = make_float2(0.f, 0.f);
+            for (int ka = 0; ka < nm; ++ka) {
+                const float2 cc = cf[ka];
+                const float2 *row = Cs + qq * a.maxc + ka * nw;
+#pragma unroll
+                for (int i = 0; i < kMaxNw; ++i)
+                    if (i < nw) cfma(gv[i], cc, row[i]);
+            }
+            const float2 *Ukq = I.U + kq * nw * nw;
+            const float N = (float)I.nbe[q * nm + v];
+            while (live) {
+                const int m = __ffs(live) - 1;
+                live &= live - 1;
+                float2 g = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < kMaxNw; ++i)
+                    if (i < nw) cfma_conj(g, Ukq[i * nw + m], gv[i]);
+                const float g2 = cabs2(g);
+                const double d = en - em[m];
+                const double ye = (d - w) * is, ya = (d + w) * is;
+                const float fm = (float)I.focc[kq * nw + m];
+                float W = 0.f;
+                if (ye * ye <= ycut2) W += expf(-(float)(ye * ye)) * (1.f + N - fm);
+                if (ya * ya <= ycut2) W += expf(-(float)(ya * ya)) * (N + fm);
+                part += (double)(g2 * W);
+            }
+        }
+        // 3. block sum into this unit's slot (fixed tree)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+        if ((t & 31) == 0) red[t >> 5] = part;
+        __syncthreads();
+        if (t == 0) {
+            double s = 0.0;
+            for (int w2 = 0; w2 < NT / 32; ++w2) s += red[w2];
+            a.partial[u] = s;
+        }
+    }
+}
+
+// Gamma rows: out[row] = scale * sum_qt partial[row * nqt + qt] for the rows of one instance
+__global__ void k_batch_reduce(int nrows, int nqt, double scale, const double *__restrict__ partial,
+                               double *__restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    double s = 0.0;
+    for (int i = 0; i < nqt; ++i) s += partial[(int64_t)r * nqt + i];
+    out[r] = scale * s;
+}
+
+struct Cand {
+    int qt, nt;
+};
+constexpr Cand kCands[4] = {{16, 128}, {32, 128}, {32, 256}, {64, 256}};
+
+size_t smem_bytes(int qt, int maxc) { return sizeof(float2) * ((size_t)qt * maxc + (size_t)qt * KC + (size_t)KC * maxc); }
+
+// CTAs per SM of a candidate (sets its shared-memory limit; call outside stream capture)
+template <int QT, int NT>
+cudaError_t prepare_one(int maxc, int *per_sm) {
+    const size_t sh = smem_bytes(QT, maxc);
+    cudaError_t e = cudaFuncSetAttribute(k_batch_rates<QT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch_rates<QT, NT>, NT, sh);
+    *per_sm = std::max(*per_sm, 1);
+    return e;
+}
+
+cudaError_t prepare_cand(int ci, int maxc, int *per_sm) {
+    switch (ci) {
+        case 0: return prepare_one<16, 128>(maxc, per_sm);
+        case 1: return prepare_one<32, 128>(maxc, per_sm);
+        case 2: return prepare_one<32, 256>(maxc, per_sm);
+        default: return prepare_one<64, 256>(maxc, per_sm);
+    }
+}
+
+// persistent grid: every SM's resident CTAs, at most one per unit
+cudaError_t launch_cand(int ci, const BArgs &a, cudaStream_t s, int nsm, int per_sm) {
+    const int64_t grid = std::min<int64_t>((int64_t)nsm * per_sm, std::max<int64_t>(a.nunits, 1));
+    const size_t sh = smem_bytes(kCands[ci].qt, a.maxc);
+    switch (ci) {
+        case 0: k_batch_rates<16, 128><<<(unsigned)grid, 128, sh, s>>>(a); break;
+        case 1: k_batch_rates<32, 128><<<(unsigned)grid, 128, sh, s>>>(a); break;
+        case 2: k_batch_rates<32, 256><<<(unsigned)grid, 256, sh, s>>>(a); break;
+        default: k_batch_rates<64, 256><<<(unsigned)grid, 256, sh, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+}  // namespace pgb
+
+// ---------------------------------------------------------------------------
+// host objects and the C ABI
+// ---------------------------------------------------------------------------
+using namespace pgb;
+
+struct pgb_batch {
+    std::vector<pgb_ctx *> ctx;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int nsm = 0;
+    int maxc = 0;
+    int cand = -1;                     // chosen candidate
+    float cand_ms[4] = {-1, -1, -1, -1};
+    int per_sm[4] = {0, 0, 0, 0};      // resident CTAs per SM of each candidate
+    int64_t graph_launches = 0;
+    // arguments the graph was captured for
+    std::vector<std::vector<int32_t>> kidx;
+    std::vector<double> mu;
+    double T = 0.0, sigma = 0.0;
+    cudaGraphExec_t exec = nullptr;
+    // device buffers owned by the batch
+    std::vector<void *> bufs;
+    BInst *d_inst = nullptr;
+    int32_t *d_unit_inst = nullptr;
+    double *d_partial = nullptr, *d_out = nullptr;
+    int64_t nunits = 0, nout = 0;
+    std::vector<int64_t> out0;         // first output row of each instance
+    std::string err;
+    void release() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        for (void *p : bufs) cudaFree(p);
+        bufs.clear();
+        d_inst = nullptr;
+        d_unit_inst = nullptr;
+        d_partial = d_out = nullptr;
+    }
+};
+
+namespace {
+
+template <typename T>
+pgb_status balloc(pgb_batch *b, T **p, size_t n) {
+    void *x = nullptr;
+    if (cudaMalloc(&x, std::max<size_t>(n * sizeof(T), 16)) != cudaSuccess) {
+        cudaGetLastError();
+        b->err = "batch: device allocation failed";
+        return PGB_ENOMEM;
+    }
+    b->bufs.push_back(x);
+    *p = static_cast<T *>(x);
+    return PGB_OK;
+}
+
+// Per-instance set-up plus the persistent kernel (and the reduction) on the
+// batch stream; candidate ci.  Enqueue only: no allocation, no synchronisation.
+struct Plan {
+    std::vector<BInst> inst;
+    struct Per {
+        int32_t *kidx;
+        void *phk, *S1, *G;
+        double *focc, *nbe;
+        float *eps32, *hw32;
+    };
+    std::vector<Per> per;
+};
+
+pgb_status enqueue(pgb_batch *b, Plan &P, int ci) {
+    const int n = (int)b->ctx.size();
+    for (int i = 0; i < n; ++i) {
+        pgb_ctx *c = b->ctx[i];
+        cudaStream_t saved = c->stream;
+        c->stream = b->stream;
+        const int64_t nk = (int64_t)b->kidx[i].size();
+        const int64_t ncol = (int64_t)c->nm * c->nw * c->nw;
+        const int64_t nrowS = (int64_t)c->nRgp * ncol;
+        Plan::Per &q = P.per[i];
+        pgb_status st = launch_occ_tables(c, b->T, b->mu[i], q.focc, q.eps32, q.nbe, q.hw32);
+        if (st == PGB_OK) st = launch_phase_grid(c, c->kg, q.kidx, nk, c->d_Rge, c->nRge, q.phk, true);
+        if (st == PGB_OK)
+            st = launch_cgemm(c, true, 1, nk, nrowS, c->nRge, q.phk, c->nRge, 0, c->d_g32, nrowS, 0, q.S1, nrowS, 0);
+        if (st == PGB_OK) st = launch_fold_u(c, true, nk, q.kidx, c->nRgp, c->nm, c->nw, q.S1, c->d_U32, q.G);
+        c->stream = saved;
+        if (st != PGB_OK) {
+            b->err = "batch: set-up of instance " + std::to_string(i) + ": " + c->err;
+            return st;
+        }
+    }
+    BArgs a;
+    a.ninst = n;
+    a.inst = b->d_inst;
+    a.unit_inst = b->d_unit_inst;
+    a.nunits = b->nunits;
+    a.maxc = b->maxc;
+    a.partial = b->d_partial;
+    cudaError_t e = launch_cand(ci, a, b->stream, b->nsm, b->per_sm[ci]);
+    if (e != cudaSuccess) {
+        b->err = std::string("batch: kernel launch: ") + cudaGetErrorString(e);
+        return PGB_ECUDA;
+    }
+    for (int i = 0; i < n; ++i) {
+        const BInst &I = P.inst[i];
+        const int nrows = (int)(b->kidx[i].size() * I.nw);
+        if (nrows == 0) continue;
+        const double scale = kTwoPiOverHbar / ((double)I.Nq * b->sigma * kSqrtPi);
+        k_batch_reduce<<<div_up(nrows, 128), 128, 0, b->stream>>>(nrows, I.nqt, scale, b->d_partial + I.unit0,
+                                                                   b->d_out + b->out0[i]);
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+            b->err = std::string("batch: reduce launch: ") + cudaGetErrorString(e);
+            return PGB_ECUDA;
+        }
+    }
+    return PGB_OK;
+}
+
+pgb_status build_plan(pgb_batch *b, Plan &P, int qt) {
+    const int n = (int)b->ctx.size();
+    P.inst.assign(n, BInst());
+    P.per.assign(n, Plan::Per());
+    int64_t unit0 = 0, out0 = 0;
+    b->out0.assign(n, 0);
+    std::vector<int32_t> unit_inst;
+    for (int i = 0; i < n; ++i) {
+        pgb_ctx *c = b->ctx[i];
+        const int64_t nk = (int64_t)b->kidx[i].size();
+        const int64_t ncol = (int64_t)c->nm * c->nw * c->nw;
+        BInst &I = P.inst[i];
+        I.nw = c->nw;
+        I.nm = c->nm;
+        I.nRgp = c->nRgp;
+        I.nKp = c->nKp;
+        for (int d = 0; d < 3; ++d) {
+            I.qg[d] = c->qg[d];
+            I.kg[d] = c->kg[d];
+        }
+        I.Nq = c->Nq;
+        I.nqt = (int)((c->Nq + qt - 1) / qt);
+        I.unit0 = unit0;
+        I.Rgp = c->d_Rgp;
+        I.polarL = c->polar ? c->d_polarL : nullptr;
+        I.eps = c->d_eps;
+        I.U = c->d_U32;
+        I.coef = c->d_coef32;
+        I.hw = c->d_hw;
+        I.sigma = b->sigma;
+        Plan::Per &q = P.per[i];
+        pgb_status st;
+        if ((st = balloc(b, &q.kidx, (size_t)std::max<int64_t>(nk, 1))) != PGB_OK) return st;
+        if (nk && cudaMemcpy(q.kidx, b->kidx[i].data(), 4 * (size_t)nk, cudaMemcpyHostToDevice) != cudaSuccess) {
+            b->err = "batch: copy of k indices failed";
+            return PGB_ECUDA;
+        }
+        char *phk, *S1, *G;
+        if ((st = balloc(b, &phk, (size_t)nk * c->nRge * 8)) != PGB_OK) return st;
+        if ((st = balloc(b, &S1, (size_t)nk * c->nRgp * ncol * 8)) != PGB_OK) return st;
+        if ((st = balloc(b, &G, (size_t)nk * c->nKp * ncol * 8)) != PGB_OK) return st;
+        q.phk = phk;
+        q.S1 = S1;
+        q.G = G;
+        if ((st = balloc(b, &q.focc, (size_t)c->Nk * c->nw)) != PGB_OK) return st;
+        if ((st = balloc(b, &q.eps32, (size_t)c->Nk * c->nw)) != PGB_OK) return st;
+        if ((st = balloc(b, &q.nbe, (size_t)c->Nq * c->nm)) != PGB_OK) return st;
+        if ((st = balloc(b, &q.hw32, (size_t)c->Nq * c->nm)) != PGB_OK) return st;
+        I.G = (const float2 *)G;
+        I.kidx = q.kidx;
+        I.focc = q.focc;
+        I.nbe = q.nbe;
+        const int64_t nu = nk * c->nw * I.nqt;
+        unit_inst.insert(unit_inst.end(), (size_t)nu, i);
+        unit0 += nu;
+        b->out0[i] = out0;
+        out0 += nk * c->nw;
+    }
+    b->nunits = unit0;
+    b->nout = out0;
+    pgb_status st;
+    if ((st = balloc(b, &b->d_inst, (size_t)n)) != PGB_OK) return st;
+    if ((st = balloc(b, &b->d_unit_inst, (size_t)std::max<int64_t>(unit0, 1))) != PGB_OK) return st;
+    if ((st = balloc(b, &b->d_partial, (size_t)std::max<int64_t>(unit0, 1))) != PGB_OK) return st;
+    if ((st = balloc(b, &b->d_out, (size_t)std::max<int64_t>(out0, 1))) != PGB_OK) return st;
+    if (cudaMemcpy(b->d_inst, P.inst.data(), sizeof(BInst) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (unit0 && cudaMemcpy(b->d_unit_inst, unit_inst.data(), 4 * (size_t)unit0, cudaMemcpyHostToDevice) !=
+                      cudaSuccess)) {
+        b->err = "batch: descriptor upload failed";
+        return PGB_ECUDA;
+    }
+    return PGB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pgb_status pgb_batch_create(pgb_batch **out, pgb_ctx *const *ctxs, int n) {
+    if (!out || !ctxs || n <= 0) return PGB_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return PGB_EINVAL;
+        if (!ctxs[i]->has_grids) {
+            ctxs[i]->err = "batch_create: every context needs set_model and set_grids";
+            return PGB_ESTATE;
+        }
+        if (ctxs[i]->device != ctxs[0]->device) {
+            ctxs[i]->err = "batch_create: contexts must share one device";
+            return PGB_EINVAL;
+        }
+    }
+    pgb_batch *b = new pgb_batch();
+    b->ctx.assign(ctxs, ctxs + n);
+    b->device = ctxs[0]->device;
+    cudaSetDevice(b->device);
+    // a stream of its own: the legacy default stream cannot be captured
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete b;
+        return PGB_ECUDA;
+    }
+    if (cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) {
+        delete b;
+        return PGB_ECUDA;
+    }
+    for (int i = 0; i < n; ++i) b->maxc = std::max(b->maxc, ctxs[i]->nm * ctxs[i]->nw);
+    for (int ci = 0; ci < 4; ++ci) {
+        b->per_sm[ci] = 0;
+        if (smem_bytes(kCands[ci].qt, b->maxc) > 220 * 1024) continue;   // does not fit: never tried
+        if (prepare_cand(ci, b->maxc, &b->per_sm[ci]) != cudaSuccess) {
+            cudaGetLastError();
+            b->per_sm[ci] = 0;
+        }
+    }
+    *out = b;
+    return PGB_OK;
+}
+
+void pgb_batch_destroy(pgb_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    b->release();
+    cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+const char *pgb_batch_last_error(const pgb_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+pgb_status pgb_batch_rates(pgb_batch *b, const int32_t *const *k_idx, const int64_t *nk, double T_K,
+                           const double *mu_eV, double sigma_eV, double *const *gamma_out) {
+    if (!b) return PGB_EINVAL;
+    cudaSetDevice(b->device);
+    const int n = (int)b->ctx.size();
+    if (!k_idx || !nk || !mu_eV || !gamma_out) {
+        b->err = "batch_rates: null pointer";
+        return PGB_EINVAL;
+    }
+    if (!(T_K > 0.0) || !(sigma_eV > 0.0)) {
+        b->err = "batch_rates: need T > 0, sigma > 0";
+        return PGB_EINVAL;
+    }
+    for (pgb_ctx *c : b->ctx)   // the members' own work (and host-side inputs) completes first
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            b->err = "batch_rates: a member stream failed";
+            return PGB_ECUDA;
+        }
+    std::vector<std::vector<int32_t>> kk(n);
+    std::vector<double> mu(mu_eV, mu_eV + n);
+    for (int i = 0; i < n; ++i) {
+        if (nk[i] < 0 || (nk[i] > 0 && (!k_idx[i] || !gamma_out[i]))) {
+            b->err = "batch_rates: bad k list of instance " + std::to_string(i);
+            return PGB_EINVAL;
+        }
+        if (!std::isfinite(mu[i])) {
+            b->err = "batch_rates: non-finite mu";
+            return PGB_EINVAL;
+        }
+        kk[i].resize(nk[i]);
+        if (nk[i] && cudaMemcpy(kk[i].data(), k_idx[i], 4 * (size_t)nk[i], cudaMemcpyDefault) != cudaSuccess) {
+            b->err = "batch_rates: k index copy failed";
+            return PGB_ECUDA;
+        }
+        for (int32_t k : kk[i])
+            if (k < 0 || k >= b->ctx[i]->Nk) {
+                b->err = "batch_rates: k index out of range in instance " + std::to_string(i);
+                return PGB_EINVAL;
+            }
+    }
+    const bool same = b->exec && kk == b->kidx && mu == b->mu && T_K == b->T && sigma_eV == b->sigma;
+    if (!same) {
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return PGB_ECUDA;
+        b->release();
+        b->kidx = kk;
+        b->mu = mu;
+        b->T = T_K;
+        b->sigma = sigma_eV;
+        // autotune on the first call: every candidate once, timed on the stream
+        if (b->cand < 0) {
+            float best = 1e30f;
+            for (int ci = 0; ci < 4; ++ci) {
+                if (b->per_sm[ci] <= 0) continue;
+                Plan P;
+                pgb_status st = build_plan(b, P, kCands[ci].qt);
+                if (st != PGB_OK) return st;
+                if ((st = enqueue(b, P, ci)) != PGB_OK) return st;   // warm-up
+                cudaEvent_t e0, e1;
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                cudaEventRecord(e0, b->stream);
+                st = enqueue(b, P, ci);
+                cudaEventRecord(e1, b->stream);
+                cudaError_t ce = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                if (st != PGB_OK) return st;
+                if (ce != cudaSuccess) {
+                    b->err = std::string("batch_rates: ") + cudaGetErrorString(ce);
+                    return PGB_ECUDA;
+                }
+                b->cand_ms[ci] = ms;
+                if (ms < best) {
+                    best = ms;
+                    b->cand = ci;
+                }
+                b->release();
+            }
+            if (b->cand < 0) {
+                b->err = "batch_rates: no tile candidate fits in shared memory";
+                return PGB_EINVAL;
+            }
+        }
+        Plan P;
+        pgb_status st = build_plan(b, P, kCands[b->cand].qt);
+        if (st != PGB_OK) return st;
+        // capture set-up, kernel and reduction in one graph
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            b->err = "batch_rates: stream capture could not start";
+            return PGB_ECUDA;
+        }
+        st = enqueue(b, P, b->cand);
+        cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+        if (st != PGB_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (ce != cudaSuccess || cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            b->err = "batch_rates: graph capture failed";
+            cudaGetLastError();
+            return PGB_ECUDA;
+        }
+        cudaGraphDestroy(g);
+    }
+    if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) {
+        b->err = "batch_rates: graph launch failed";
+        return PGB_ECUDA;
+    }
+    b->graph_launches++;
+    for (int i = 0; i < n; ++i) {
+        const size_t bytes = 8 * (size_t)kk[i].size() * b->ctx[i]->nw;
+        if (bytes && cudaMemcpyAsync(gamma_out[i], b->d_out + b->out0[i], bytes, cudaMemcpyDefault, b->stream) !=
+                         cudaSuccess) {
+            b->err = "batch_rates: output copy failed";
+            return PGB_ECUDA;
+        }
+    }
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        b->err = "batch_rates: execution failed";
+        return PGB_ECUDA;
+    }
+    return PGB_OK;
+}
+
+pgb_status pgb_batch_tuning(const pgb_batch *b, int *tile_q, int *threads, float *cand_ms, int64_t *graph_launches) {
+    if (!b) return PGB_EINVAL;
+    if (tile_q) *tile_q = b->cand >= 0 ? kCands[b->cand].qt : 0;
+    if (threads) *threads = b->cand >= 0 ? kCands[b->cand].nt : 0;
+    if (cand_ms)
+        for (int i = 0; i < 4; ++i) cand_ms[i] = b->cand_ms[i];
+    if (graph_launches) *graph_launches = b->graph_launches;
+    return PGB_OK;
+}
+
+}  // extern "C"

@@ -32,6 +32,7 @@ ABI_SYMBOLS = (
     "pgb_collision_set_g2", "pgb_collision_vjp", "pgb_rk4_adjoint",
     "pgb_set_lattice", "pgb_set_polar", "pgb_long_range_g", "pgb_band_velocities", "pgb_transport",
     "pgb_scattering_rates_mc", "pgb_population",
+    "pgb_batch_create", "pgb_batch_rates", "pgb_batch_tuning", "pgb_batch_last_error", "pgb_batch_destroy",
 )
 PGB_Q_UNIFORM, PGB_Q_CAUCHY = 0, 1
 PGB_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -93,6 +94,11 @@ def load(path: str = LIB_PATH):
         "pgb_transport": (I, [P, D, I, I, D, P, P, C.POINTER(I64), P, P]),
         "pgb_scattering_rates_mc": (I, [P, P, I64, P, I64, I, D, D, D, D, I, P, P]),
         "pgb_population": (I, [P, P, P, I64, P]),
+        "pgb_batch_create": (I, [C.POINTER(P), P, I]),
+        "pgb_batch_rates": (I, [P, P, P, D, P, D, P]),
+        "pgb_batch_tuning": (I, [P, C.POINTER(I), C.POINTER(I), P, C.POINTER(I64)]),
+        "pgb_batch_last_error": (C.c_char_p, [P]),
+        "pgb_batch_destroy": (None, [P]),
         "pgb_launch_count": (I64, [P]),
         "pgb_profile": (I, [P, I]),
         "pgb_scattering_rates_noalloc": (I, [P, P, I64, D, D, D, P]),
@@ -338,3 +344,45 @@ class Context:
         n = C.c_int64(0)
         self._chk(self.lib.pgb_profile_read(self._h, int(kernel_class), C.byref(ms), C.byref(n)))
         return float(ms.value), int(n.value)
+
+
+class Batch:
+    """pgb_batch over several Contexts (same device); rates of every instance in one graph launch."""
+
+    def __init__(self, contexts):
+        self.lib = load()
+        self._ctx = list(contexts)          # keep the contexts alive
+        arr = (C.c_void_p * len(self._ctx))(*[c._h.value for c in self._ctx])
+        self._h = C.c_void_p()
+        st = self.lib.pgb_batch_create(C.byref(self._h), arr, len(self._ctx))
+        if st != PGB_OK:
+            raise PgbError(st, "pgb_batch_create failed: " + " / ".join(
+                c.lib.pgb_last_error(c._h).decode() for c in self._ctx))
+
+    def close(self):
+        if self._h:
+            self.lib.pgb_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pgb_batch_rates(self, k_lists, T, mus, sigma, outs):
+        n = len(self._ctx)
+        keep = [np.ascontiguousarray(k, np.int32) if isinstance(k, (list, tuple)) else k for k in k_lists]
+        kp = (C.c_void_p * n)(*[_ptr(k) for k in keep])
+        nk = (C.c_int64 * n)(*[len(k) for k in keep])
+        mu = (C.c_double * n)(*[float(m) for m in mus])
+        op = (C.c_void_p * n)(*[_ptr(o) for o in outs])
+        st = self.lib.pgb_batch_rates(self._h, kp, nk, float(T), mu, float(sigma), op)
+        if st != PGB_OK:
+            raise PgbError(st, self.lib.pgb_batch_last_error(self._h).decode())
+
+    def pgb_batch_tuning(self):
+        qt, nt, gl = C.c_int(0), C.c_int(0), C.c_int64(0)
+        ms = (C.c_float * 4)()
+        self.lib.pgb_batch_tuning(self._h, C.byref(qt), C.byref(nt), ms, C.byref(gl))
+        return {"tile_q": qt.value, "threads": nt.value, "candidate_ms": list(ms), "graph_launches": gl.value}

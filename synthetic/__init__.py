@@ -13,6 +13,7 @@ from .models import (  # noqa: F401
     model_c1,
     model_c2,
     model_c3,
+    model_batch_instance,
     model_sc_tight_binding,
     model_holstein,
     model_ladder,

@@ -335,6 +335,60 @@ def model_c3(seed: int = SEED_BASE + 3, rcut: float = C2_RCUT * C3_LATTICE / C2_
                  zstar=zstar, eps_inf=10.9 * np.eye(3), ewald_lambda=(2 * np.pi / a) ** 2)
 
 
+BATCH_NW = (2, 4, 8, 12, 16)
+BATCH_GRIDS = (8, 12, 16, 24, 32)
+
+
+def model_batch_instance(i: int, seed: int = SEED_BASE + 5) -> Model:
+    """Instance i of the batched workload: a random simple-cubic model.
+
+    Drawn from its own seed: nw in {2, 4, 8, 12, 16}, nat in {1, ..., 5} atoms at
+    random positions, one R set of the lattice vectors with |n| <= r, r in {1, 2, 3}
+    (shared by H, D and both g~ indices), a grid size in {8, 12, 16, 24, 32} per
+    axis (meta "grid").  H(0) = diag of bands 0.25 eV apart + N(0, 0.02) coupling,
+    H(R != 0) complex N(0, 1) 0.3 exp(-|n|) eV; bond springs k(d) = 1.5 exp(-(d -
+    d_min)/2 bohr) eV/bohr^2 (acoustic sum rule exact); |g~| = 0.05 exp(-(|n_e| +
+    |n_p|)/2) eV/bohr with a uniform phase, partner-symmetrised, complex64.
+    """
+    rng = np.random.Generator(np.random.PCG64([seed, i]))
+    nw = int(rng.choice(BATCH_NW))
+    nat = int(rng.integers(1, 6))
+    r = int(rng.integers(1, 4))
+    ng = int(rng.choice(BATCH_GRIDS))
+    a = float(rng.uniform(5.0, 7.0))
+    A = a * np.eye(3)
+    R = _ball_vectors(A, r * a, nmax=r)
+    nR = len(R)
+    Rn = np.linalg.norm(R.astype(np.float64), axis=1)
+    while True:                               # atoms at least 1.5 bohr apart (with images)
+        tau = rng.uniform(0, a, (nat, 3))
+        dmin = np.inf
+        for k in range(nat):
+            for kp in range(nat):
+                for sh in _cube_vectors(1):
+                    if k == kp and not sh.any():
+                        continue
+                    dmin = min(dmin, np.linalg.norm(tau[kp] + sh * a - tau[k]))
+        if dmin > 1.5:
+            break
+    mass = rng.uniform(10.0, 80.0, nat)
+    H = np.zeros((nR, nw, nw), dtype=np.complex128)
+    for j in range(nR):
+        X = rng.normal(0, 1, (nw, nw)) + 1j * rng.normal(0, 1, (nw, nw))
+        if Rn[j] == 0:
+            H[j] = np.diag(0.25 * np.arange(nw)) + 0.02 * X * (1 - np.eye(nw))
+        else:
+            H[j] = 0.3 * np.exp(-Rn[j]) * X / np.sqrt(2.0)
+    H = _hermitian_symmetrise_hr(R, H)
+    D = _spring_network(A, tau, R, k0=1.5, d0=dmin, ell=2.0, ktrans=0.3)
+    nm = 3 * nat
+    mag = 0.05 * np.exp(-(Rn[:, None] + Rn[None, :]) / 2.0)
+    g = mag[:, :, None, None, None] * np.exp(1j * rng.uniform(0, 2 * np.pi, (nR, nR, nm, nw, nw)))
+    g = _partner_symmetrise_g(R, R, g).astype(np.complex64)
+    return Model(f"batch_{i}", A, tau, mass, R.copy(), H, R.copy(), D, R.copy(), R.copy(), g,
+                 meta={"seed": seed, "index": i, "grid": (ng, ng, ng), "T": 300.0, "sigma": 0.005})
+
+
 # ----------------------------------------------------------------------------
 # special models with closed forms (used as pins)
 # ----------------------------------------------------------------------------

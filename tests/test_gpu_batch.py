@@ -1,0 +1,86 @@
+"""Batched rates of uneven instances (one persistent launch under a captured
+graph) against the per-instance FP64 oracle."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import eph as O
+
+from helpers import assert_rates_close
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GRID = (8, 8, 8)
+T, SIG = 300.0, 0.05
+
+
+@pytest.fixture(scope="module")
+def members():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_02045_gb300 import build
+    build.build()
+    from paper_2002_02045_gb300 import Context
+    models = [S.model_batch_instance(i) for i in (1, 2, 3, 7, 8, 9)] + [S.model_c3(rcut=13.0)]
+    ctxs, ks, mus = [], [], []
+    rng = np.random.default_rng(60)
+    for m in models:
+        c = Context(0)
+        c.pgb_set_model(m)
+        if m.zstar is not None:
+            c.pgb_set_lattice(m.A, m.tau)
+            c.pgb_set_polar(m.zstar, m.eps_inf, m.ewald_lambda)
+        c.pgb_set_grids(GRID, GRID)
+        eps = np.zeros((512, m.nw))
+        c.pgb_get_grid_energies(eps, None)
+        ctxs.append(c)
+        ks.append(np.sort(rng.choice(512, 3, replace=False)).astype(np.int32))
+        mus.append(float(0.5 * (eps.min() + eps.max())))
+    yield models, ctxs, ks, mus
+    for c in ctxs:
+        c.close()
+
+
+def test_batch_matches_oracle_and_single_calls(members):
+    from paper_2002_02045_gb300 import Batch, PGB_FP32
+    models, ctxs, ks, mus = members
+    b = Batch(ctxs)
+    outs = [np.zeros((len(k), m.nw)) for k, m in zip(ks, models)]
+    b.pgb_batch_rates(ks, T, mus, SIG, outs)
+    tun = b.pgb_batch_tuning()
+    assert tun["tile_q"] in (16, 32, 64) and tun["threads"] in (128, 256)
+    assert min(x for x in tun["candidate_ms"] if x >= 0) > 0
+    for i, (m, c, k, mu) in enumerate(zip(models, ctxs, ks, mus)):
+        single = np.zeros((len(k), m.nw))
+        c.pgb_scattering_rates(k, T, mu, SIG, PGB_FP32, single)
+        assert_rates_close(outs[i], single, 1e-5, label=f"batch vs single {i}")
+        ref = O.scattering_rates_grid(m, GRID, GRID, k, T, mu, SIG)
+        assert_rates_close(outs[i], ref, 1e-5, label=f"batch vs oracle {i}")
+        assert np.abs(outs[i]).max() > 0
+    # the same arguments replay the captured graph, bit for bit
+    outs2 = [np.zeros_like(o) for o in outs]
+    b.pgb_batch_rates(ks, T, mus, SIG, outs2)
+    assert b.pgb_batch_tuning()["graph_launches"] == 2
+    assert all(np.array_equal(x, y) for x, y in zip(outs, outs2))
+    # new arguments re-capture (device buffers in and out)
+    k_dev = [torch.as_tensor(k[:2]).cuda() for k in ks]
+    out_dev = [torch.empty((2, m.nw), dtype=torch.float64, device="cuda") for m in models]
+    b.pgb_batch_rates(k_dev, T, mus, SIG, out_dev)
+    for o, o1 in zip(out_dev, outs):
+        assert np.array_equal(o.cpu().numpy(), o1[:2])
+    b.close()
+
+
+def test_batch_argument_errors(members):
+    from paper_2002_02045_gb300 import Batch, PgbError
+    models, ctxs, ks, mus = members
+    b = Batch(ctxs[:2])
+    outs = [np.zeros((3, m.nw)) for m in models[:2]]
+    bad = [ks[0], np.array([0, 10 ** 6], np.int32)]
+    with pytest.raises(PgbError):
+        b.pgb_batch_rates(bad, T, mus[:2], SIG, outs)
+    with pytest.raises(PgbError):
+        b.pgb_batch_rates(ks[:2], -1.0, mus[:2], SIG, outs)
+    b.close()
