@@ -278,6 +278,8 @@ def run_ours(args, rank, world, local):
         out["dynamics"] = dynamics(ctx, model, args, world, peaks, peak_src)
     if args.polar:
         out["polar"] = polar(ctx, args, world)
+    if args.batched:
+        out["batched"] = batched(args, world)
     if args.e2e and rank == 0:
         out["e2e"] = e2e(ctx, model, prec, steps=1)
     if args.cpu_baseline and rank == 0 and world == 1:
@@ -498,6 +500,63 @@ def polar(ctx, args, world):
     }
 
 
+BATCH_INSTANCES = 64
+BATCH_K = 8
+
+
+def batched(args, world):
+    """64 seeded random instances (nw in {2..16}, 1-5 atoms, R shells of radius 1-3,
+    grids 8^3..32^3), Gamma_nk of 8 k-points each over the full q grid at 300 K and
+    5 meV, all in one graph launch (persistent kernel); timed over replays after
+    the first call (tile autotuning and graph capture)."""
+    import torch
+    import synthetic as S
+    from paper_2002_02045_gb300 import Batch, Context
+    t0 = time.perf_counter()
+    models = [S.model_batch_instance(i) for i in range(BATCH_INSTANCES)]
+    t_gen = time.perf_counter() - t0
+    rng = np.random.default_rng(S.SEED_BASE + 55)
+    ctxs, ks, mus, outs = [], [], [], []
+    pairs = 0
+    t0 = time.perf_counter()
+    for m in models:
+        c = Context(torch.cuda.current_device())
+        c.pgb_set_model(m)
+        g = m.meta["grid"]
+        c.pgb_set_grids(g, g)
+        nk = int(np.prod(g))
+        eps = torch.empty((nk, m.nw), dtype=torch.float64, device="cuda")
+        c.pgb_get_grid_energies(eps, None)
+        ctxs.append(c)
+        ks.append(np.sort(rng.choice(nk, BATCH_K, replace=False)).astype(np.int32))
+        mus.append(float(0.5 * (eps.min() + eps.max())))
+        outs.append(np.zeros((BATCH_K, m.nw)))
+        pairs += BATCH_K * nk
+    t_setup = time.perf_counter() - t0
+    b = Batch(ctxs)
+    t0 = time.perf_counter()
+    b.pgb_batch_rates(ks, T_K, mus, 0.005, outs)       # autotune + capture + first run
+    t_first = time.perf_counter() - t0
+    reps = 3
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        b.pgb_batch_rates(ks, T_K, mus, 0.005, outs)
+    dt = max_over_ranks((time.perf_counter() - t0) / reps, world)
+    tun = b.pgb_batch_tuning()
+    finite = all(np.all(np.isfinite(o)) for o in outs)
+    b.close()
+    for c in ctxs:
+        c.close()
+    return {
+        "metric": "(k,q) pairs/s over 64 uneven instances in one graph launch (FP32 products, FP64 energies)",
+        "value": world * pairs / dt, "unit": "pairs/s", "ms_per_call": 1e3 * dt, "pairs": pairs,
+        "instances": BATCH_INSTANCES, "k_per_instance": BATCH_K, "first_call_s": t_first,
+        "model_generation_s": t_gen, "setup_s": t_setup, "tuning": tun, "finite": finite,
+        "timing": "host clock around pgb_batch_rates (graph replay + output copies, synchronised)",
+    }
+
+
 def e2e(ctx, model, prec, steps=1):
     """Same metric through the public API with host buffers: model upload,
     grids, window and rates, copies included."""
@@ -532,6 +591,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "fp64", "bf16x3", "tf32x3"])
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the 64-instance batched-rates measurement")
     ap.add_argument("--no-polar", dest="polar", action="store_false",
                     help="skip the polar-model rates and transport measurement")
     ap.add_argument("--no-dynamics", dest="dynamics", action="store_false",

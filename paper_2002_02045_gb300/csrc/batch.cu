@@ -8,9 +8,9 @@
 //
 // Work unit = (instance, k, initial band n, tile of QT q-points).  A unit
 //   1. forms its R_p-sum tile C[q][ka][i] = sum_p e^{iq.R_p} G_k[p][n][ka][i] in shared
-//      memory, K-chunk by K-chunk: the grid phases are generated exactly from
-//      integer arithmetic (the long-range rows of polar models read the q-grid
-//      table), the G_k rows of band n are contiguous (column order n, ka, i);
+//      memory, K-chunk by K-chunk, from the instance's FP32 q table (exact grid
+//      phases and, for polar models, the long-range columns; built once per
+//      plan) and the G_k rows of band n, which are contiguous (column order n, ka, i);
 //   2. runs the rates epilogue on the tile, one (q, nu) pair per thread: screen
 //      the (m) with |x| <= 7 sigma, project on nu, rotate by U(k+q), Gaussian
 //      weights with FP64 energies, FP32 products;
@@ -36,6 +36,7 @@ namespace {
 
 inline unsigned int div_up(int64_t a, int64_t b) { return (unsigned int)((a + b - 1) / b); }
 constexpr int KC = 16;   // K chunk of the shared-memory GEMM
+constexpr int RT = 4;    // tile rows per thread in the shared-memory GEMM
 
 struct BInst {
     int nw, nm, nRgp, nKp;
@@ -43,8 +44,7 @@ struct BInst {
     int64_t Nq;
     int64_t unit0;             // first unit of this instance
     int nqt;                   // q tiles
-    const int32_t *Rgp;        // [nRgp][3]
-    const double2 *polarL;     // [Nq][nm] or null
+    const float2 *phq;         // [Nq][nKp] q table: e^{iq.R_p}, then the long-range columns
     const float2 *G;           // [nk][nKp][nm*nw*nw]
     const int32_t *kidx;       // [nk]
     const double *eps;         // [Nk][nw]
@@ -74,26 +74,6 @@ __device__ __forceinline__ int64_t kq_index(int64_t k, int64_t q, const int kg[3
     return ((int64_t)s1 * kg[1] + s2) * kg[2] + s3;
 }
 
-__device__ __forceinline__ float2 grid_phase(const BInst &I, int64_t q, int p) {
-    if (p >= I.nRgp) {
-        const double2 v = I.polarL[q * I.nm + (p - I.nRgp)];
-        return make_float2((float)v.x, (float)v.y);
-    }
-    const int n1 = I.qg[0], n2 = I.qg[1], n3 = I.qg[2];
-    const int i3 = (int)(q % n3), i2 = (int)((q / n3) % n2), i1 = (int)(q / ((int64_t)n2 * n3));
-    int t1 = (int)(((int64_t)i1 * I.Rgp[3 * p + 0]) % n1);
-    int t2 = (int)(((int64_t)i2 * I.Rgp[3 * p + 1]) % n2);
-    int t3 = (int)(((int64_t)i3 * I.Rgp[3 * p + 2]) % n3);
-    if (t1 < 0) t1 += n1;
-    if (t2 < 0) t2 += n2;
-    if (t3 < 0) t3 += n3;
-    double x = (double)t1 / n1 + (double)t2 / n2 + (double)t3 / n3;
-    x -= rint(x);
-    double s, c;
-    sincospi(2.0 * x, &s, &c);
-    return make_float2((float)c, (float)s);
-}
-
 template <int QT, int NT>
 __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
     extern __shared__ float2 sm[];
@@ -118,21 +98,31 @@ __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
             __syncthreads();
             for (int o = t; o < QT * KC; o += NT) {
                 const int qq = o / KC, kk = o % KC;
-                As[o] = (qq < nq && p0 + kk < I.nKp) ? grid_phase(I, q0 + qq, p0 + kk) : make_float2(0.f, 0.f);
+                As[o] = (qq < nq && p0 + kk < I.nKp) ? I.phq[(q0 + qq) * I.nKp + p0 + kk] : make_float2(0.f, 0.f);
             }
             for (int o = t; o < KC * ncn; o += NT) {
                 const int kk = o / ncn, cc = o % ncn;
                 Bs[kk * a.maxc + cc] = (p0 + kk < I.nKp) ? Gk[(int64_t)(p0 + kk) * ncol + cc] : make_float2(0.f, 0.f);
             }
             __syncthreads();
-            for (int o = t; o < QT * ncn; o += NT) {
-                const int qq = o / ncn, cc = o % ncn;
-                float2 acc = make_float2(0.f, 0.f);
+            // each thread: one column, RT rows spaced QT/RT apart (one B load feeds RT products)
+            for (int o = t; o < (QT / RT) * ncn; o += NT) {
+                const int q0r = o / ncn, cc = o % ncn;
+                float2 acc[RT];
 #pragma unroll
-                for (int kk = 0; kk < KC; ++kk) cfma(acc, As[qq * KC + kk], Bs[kk * a.maxc + cc]);
-                float2 &d = Cs[qq * a.maxc + cc];
-                d.x += acc.x;
-                d.y += acc.y;
+                for (int j = 0; j < RT; ++j) acc[j] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int kk = 0; kk < KC; ++kk) {
+                    const float2 bv = Bs[kk * a.maxc + cc];
+#pragma unroll
+                    for (int j = 0; j < RT; ++j) cfma(acc[j], As[(q0r + j * (QT / RT)) * KC + kk], bv);
+                }
+#pragma unroll
+                for (int j = 0; j < RT; ++j) {
+                    float2 &d = Cs[(q0r + j * (QT / RT)) * a.maxc + cc];
+                    d.x += acc[j].x;
+                    d.y += acc[j].y;
+                }
             }
         }
         __syncthreads();
@@ -391,8 +381,7 @@ pgb_status build_plan(pgb_batch *b, Plan &P, int qt) {
         I.Nq = c->Nq;
         I.nqt = (int)((c->Nq + qt - 1) / qt);
         I.unit0 = unit0;
-        I.Rgp = c->d_Rgp;
-        I.polarL = c->polar ? c->d_polarL : nullptr;
+
         I.eps = c->d_eps;
         I.U = c->d_U32;
         I.coef = c->d_coef32;
@@ -416,6 +405,19 @@ pgb_status build_plan(pgb_batch *b, Plan &P, int qt) {
         if ((st = balloc(b, &q.eps32, (size_t)c->Nk * c->nw)) != PGB_OK) return st;
         if ((st = balloc(b, &q.nbe, (size_t)c->Nq * c->nm)) != PGB_OK) return st;
         if ((st = balloc(b, &q.hw32, (size_t)c->Nq * c->nm)) != PGB_OK) return st;
+        float2 *phq;
+        if ((st = balloc(b, &phq, (size_t)c->Nq * c->nKp)) != PGB_OK) return st;
+        {   // q table, independent of the call's arguments: built here, outside any capture
+            cudaStream_t saved = c->stream;
+            c->stream = b->stream;
+            st = launch_qtable_grid(c, nullptr, c->Nq, phq, true);
+            c->stream = saved;
+            if (st != PGB_OK || cudaStreamSynchronize(b->stream) != cudaSuccess) {
+                b->err = "batch: q table of instance " + std::to_string(i) + " failed";
+                return PGB_ECUDA;
+            }
+        }
+        I.phq = phq;
         I.G = (const float2 *)G;
         I.kidx = q.kidx;
         I.focc = q.focc;
