@@ -303,8 +303,9 @@ def dynamics(ctx, model, args, world, peaks, peak_src):
     import torch
     import synthetic as S
     from paper_2002_02045_gb300.native import PROF_COLLISION
-    ctx.pgb_set_grids(DYN_GRID, DYN_GRID)
-    nk = int(np.prod(DYN_GRID))
+    grid = (args.dyn_grid,) * 3
+    ctx.pgb_set_grids(grid, grid)
+    nk = int(np.prod(grid))
     eps = torch.empty((nk, model.nw), dtype=torch.float64, device="cuda")
     ctx.pgb_get_grid_energies(eps, None)
     emin = float(eps[:, :2].min())
@@ -351,7 +352,7 @@ def dynamics(ctx, model, args, world, peaks, peak_src):
         "value": world * nnz * evals / (ms * 1e-3), "unit": "entries/s",
         "rk4_steps_per_s": world * args.dyn_steps / (ms * 1e-3), "steps": args.dyn_steps,
         "ms_per_rk4_step": ms / args.dyn_steps, "nnz": nnz, "states": 2 * nk,
-        "config": {"workload": f"same model, {DYN_GRID[0]}^3 k = q grid, 2 lowest bands, states within "
+        "config": {"workload": f"same model, {grid[0]}^3 k = q grid, 2 lowest bands, states within "
                                f"{DYN_WINDOW} eV of the band minimum, 7 sigma screen, dt = 1 fs, hot-carrier pulse",
                    "list_build_s": build_s},
         "carrier_number_drift": abs(float(f.sum()) - n0) / n0,
@@ -513,7 +514,7 @@ def batched(args, world):
     import synthetic as S
     from paper_2002_02045_gb300 import Batch, Context
     t0 = time.perf_counter()
-    models = [S.model_batch_instance(i) for i in range(BATCH_INSTANCES)]
+    models = [S.model_batch_instance(i) for i in range(args.batch_instances)]
     t_gen = time.perf_counter() - t0
     rng = np.random.default_rng(S.SEED_BASE + 55)
     ctxs, ks, mus, outs = [], [], [], []
@@ -549,9 +550,9 @@ def batched(args, world):
     for c in ctxs:
         c.close()
     return {
-        "metric": "(k,q) pairs/s over 64 uneven instances in one graph launch (FP32 products, FP64 energies)",
+        "metric": "(k,q) pairs/s over uneven instances in one graph launch (FP32 products, FP64 energies)",
         "value": world * pairs / dt, "unit": "pairs/s", "ms_per_call": 1e3 * dt, "pairs": pairs,
-        "instances": BATCH_INSTANCES, "k_per_instance": BATCH_K, "first_call_s": t_first,
+        "instances": args.batch_instances, "k_per_instance": BATCH_K, "first_call_s": t_first,
         "model_generation_s": t_gen, "setup_s": t_setup, "tuning": tun, "finite": finite,
         "timing": "host clock around pgb_batch_rates (graph replay + output copies, synchronised)",
     }
@@ -606,6 +607,10 @@ def main():
     ap.add_argument("--shard", action="store_true",
                     help="with several ranks, split the window k-points across them (strong scaling) "
                          "instead of one full workload per rank (weak scaling)")
+    ap.add_argument("--dyn-grid", type=int, default=DYN_GRID[0],
+                    help="k = q grid of the dynamics workload (smaller for profiling runs)")
+    ap.add_argument("--batch-instances", type=int, default=BATCH_INSTANCES,
+                    help="instances of the batched workload (fewer for profiling runs)")
     ap.add_argument("--max-k", type=int, default=0,
                     help="use only the first N window k-points (small case for profiler captures)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")

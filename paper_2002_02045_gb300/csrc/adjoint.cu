@@ -12,7 +12,9 @@
 // transposed copy of the list (entries ordered by column, built once per
 // list), one block per non-empty column, with the forward kernel's arithmetic:
 // 16-byte entry vectors, FP32 gathers and products with Kahan sums, FP64 per
-// column.
+// column.  The per-entry |g|^2 derivative accumulates over all stages and
+// steps in a Kahan-compensated FP32 pair (8 bytes, no FP64 arithmetic per
+// entry: GB300's FP64 rate would otherwise bound the pass).
 //
 // RK4 reverse step (x1 = f, x2 = f + dt/2 k1, x3 = f + dt/2 k2, x4 = f + dt k3,
 // f' = f + dt/6 (k1 + 2 k2 + 2 k3 + k4)) for lam = dL/df':
@@ -123,10 +125,10 @@ __global__ void k_adj_finish(int64_t n, double *__restrict__ lam, const double *
     if (t < n) lam[t] += sumv[t] + v1[t];
 }
 
-__global__ void k_scatter_dg2(int64_t nnz, const int32_t *__restrict__ eidx, const double *__restrict__ acc,
+__global__ void k_scatter_dg2(int64_t nnz, const int32_t *__restrict__ eidx, const float2 *__restrict__ acc,
                               double *__restrict__ out) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < nnz) out[eidx[j]] = acc[j];
+    if (j < nnz) out[eidx[j]] = (double)acc[j].x - (double)acc[j].y;
 }
 
 // copies of one state into `count` consecutive state slots
@@ -145,7 +147,7 @@ struct ColArgs {
     const float2 *uw;
     const double *x;
     double *v;                // v[c] += sum over the column
-    double *acc;              // [nnz] |g|^2 derivative, transposed order (null: skipped)
+    float2 *acc;              // [nnz] |g|^2 derivative, transposed order, as (sum, compensation) (null: skipped)
 };
 
 __global__ void __launch_bounds__(kThreads) k_adj_col(ColArgs p) {
@@ -169,7 +171,11 @@ __global__ void __launch_bounds__(kThreads) k_adj_col(ColArgs p) {
         if (j >= 0) {
             const float2 q = p.uw[p.src[j]];
             kadd(s, cs, fmaf(q.x, p.a[j], q.y * p.b[j]));
-            if (p.acc) p.acc[j] += (double)(q.y * xc * p.beta[j] - q.x * omx * p.alpha[j]);
+            if (p.acc) {
+                float2 d = p.acc[j];
+                kadd(d.x, d.y, q.y * xc * p.beta[j] - q.x * omx * p.alpha[j]);
+                p.acc[j] = d;
+            }
         }
     }
     const int64_t nv = (vend - vbeg) >> 2;
@@ -186,12 +192,13 @@ __global__ void __launch_bounds__(kThreads) k_adj_col(ColArgs p) {
         if (p.acc) {
             const float4 al = __ldcs(reinterpret_cast<const float4 *>(p.alpha + j));
             const float4 be = __ldcs(reinterpret_cast<const float4 *>(p.beta + j));
-            double2 *ap = reinterpret_cast<double2 *>(p.acc + j);
-            double2 lo = ap[0], hi = ap[1];
-            lo.x += (double)(q0.y * xc * be.x - q0.x * omx * al.x);
-            lo.y += (double)(q1.y * xc * be.y - q1.x * omx * al.y);
-            hi.x += (double)(q2.y * xc * be.z - q2.x * omx * al.z);
-            hi.y += (double)(q3.y * xc * be.w - q3.x * omx * al.w);
+            // Kahan-compensated FP32 pairs: no FP64 arithmetic per entry
+            float4 *ap = reinterpret_cast<float4 *>(p.acc + j);
+            float4 lo = ap[0], hi = ap[1];   // (sum, comp) of entries j, j+1 and j+2, j+3
+            kadd(lo.x, lo.y, q0.y * xc * be.x - q0.x * omx * al.x);
+            kadd(lo.z, lo.w, q1.y * xc * be.y - q1.x * omx * al.y);
+            kadd(hi.x, hi.y, q2.y * xc * be.z - q2.x * omx * al.z);
+            kadd(hi.z, hi.w, q3.y * xc * be.w - q3.x * omx * al.w);
             ap[0] = lo;
             ap[1] = hi;
         }
@@ -322,7 +329,7 @@ struct Rev {
     int64_t ns;
     float2 *uw;
     double *sumv, *v[2];
-    double *acc;   // null: no |g|^2 derivative
+    float2 *acc;   // null: no |g|^2 derivative
 };
 
 pgb_status prep(Rev &R, const double *lam, double cl, const double *vprev, double cv, const double *x, const double *D,
@@ -388,7 +395,7 @@ pgb_status collision_vjp(pgb_ctx *c, const double *f, const double *lam, double 
     R.uw = pool.get<float2>(ns);
     R.sumv = nullptr;
     R.v[0] = R.v[1] = nullptr;
-    R.acc = out_g2 ? pool.get<double>(nnz) : nullptr;
+    R.acc = out_g2 ? pool.get<float2>(nnz) : nullptr;
     if (!pool.ok) {
         c->err = "collision_vjp: device allocation failed";
         return PGB_ENOMEM;
@@ -435,7 +442,7 @@ pgb_status rk4_adjoint(pgb_ctx *c, const double *f0, double dt_fs, int64_t nstep
     R.sumv = pool.get<double>(ns);
     R.v[0] = pool.get<double>(ns);
     R.v[1] = pool.get<double>(ns);
-    R.acc = dg2 ? pool.get<double>(nnz) : nullptr;
+    R.acc = dg2 ? pool.get<float2>(nnz) : nullptr;
     if (!pool.ok) {
         c->err = "rk4_adjoint: device allocation failed";
         return PGB_ENOMEM;

@@ -48,6 +48,7 @@ struct BInst {
     const float2 *G;           // [nk][nKp][nm*nw*nw]
     const int32_t *kidx;       // [nk]
     const double *eps;         // [Nk][nw]
+    const float *eps32;        // [Nk][nw] FP32 copy for the screen
     const float2 *U;           // [Nk][nw][nw], U[i][n]
     const float2 *coef;        // [Nq][nm][nm]
     const double *hw;          // [Nq][nm]
@@ -130,7 +131,9 @@ __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
         double part = 0.0;
         const int64_t k = I.kidx[kb];
         const double en = I.eps[k * nw + n];
+        const float en32 = I.eps32[k * nw + n];
         const double is = 1.0 / I.sigma, ycut2 = kDeltaCut * kDeltaCut;
+        const float cut32 = (float)(kDeltaCut * I.sigma) + 1e-4f;
         for (int o = t; o < QT * nm; o += NT) {
             const int qq = o / nm, v = o % nm;
             if (qq >= nq) continue;
@@ -139,11 +142,13 @@ __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
             if (!(w >= kOmegaMinEv)) continue;
             const int64_t kq = kq_index(k, q, I.kg, I.qg);
             const double *em = I.eps + kq * nw;
+            const float *em32 = I.eps32 + kq * nw;
+            // screen in FP32 with a margin (no FP64 work for the rejected terms)
+            const float w32 = (float)w;
             uint32_t live = 0;
             for (int m = 0; m < nw; ++m) {
-                const double d = en - em[m];
-                const double ye = (d - w) * is, ya = (d + w) * is;
-                if (ye * ye <= ycut2 || ya * ya <= ycut2) live |= 1u << m;
+                const float d = en32 - em32[m];
+                if (fabsf(d - w32) <= cut32 || fabsf(d + w32) <= cut32) live |= 1u << m;
             }
             if (!live) continue;
             const float2 *cf = I.coef + (q * nm + v) * nm;
@@ -418,6 +423,7 @@ pgb_status build_plan(pgb_batch *b, Plan &P, int qt) {
             }
         }
         I.phq = phq;
+        I.eps32 = q.eps32;
         I.G = (const float2 *)G;
         I.kidx = q.kidx;
         I.focc = q.focc;
