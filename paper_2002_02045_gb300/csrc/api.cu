@@ -1368,6 +1368,8 @@ pgb_status pgb_build_collision_grid(pgb_ctx *c, int band_lo, int band_hi, double
     ListLaunch L;
     L.nb = na;
     L.kidx = d_active.p;
+    L.na = na;
+    L.win = d_active.p;
     L.band_lo = band_lo;
     L.nbnd = nbnd;
     L.inwin = d_inwin.p;
@@ -1393,7 +1395,8 @@ pgb_status pgb_build_collision_grid(pgb_ctx *c, int band_lo, int band_hi, double
     }
     const size_t es = sizeof(float2);
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t per_k = al(c->nRge * es) + 2 * al(nrow * es) + al((size_t)c->Nq * nsub * es);
+    // per k: R_e phases, S1, G, the gathered q rows (only q = k' - k with k' in the window) and C
+    const size_t per_k = al(c->nRge * es) + 2 * al(nrow * es) + al((size_t)na * c->nKp * es) + al((size_t)na * nsub * es);
     int64_t nbmax = std::max<int64_t>(1, (int64_t)(((size_t)4 << 30) / per_k));
     nbmax = std::min<int64_t>(nbmax, std::max<int64_t>(na, 1));
     nbmax = std::min<int64_t>(nbmax, 65535);
@@ -1402,16 +1405,21 @@ pgb_status pgb_build_collision_grid(pgb_ctx *c, int band_lo, int band_hi, double
     char *phk = base;
     char *S1 = phk + al(nbmax * c->nRge * es);
     char *G = S1 + al(nbmax * nrow * es);
-    char *Cb = G + al(nbmax * nrow * es);
+    char *phg = G + al(nbmax * nrow * es);
+    char *Cb = phg + al(nbmax * na * c->nKp * es);
     for (int64_t b0 = 0; b0 < na; b0 += nbmax) {
         const int64_t nb = std::min<int64_t>(nbmax, na - b0);
         const int32_t *kb = d_active.p + b0;
         TRY(launch_phase_grid(c, c->kg, kb, nb, c->d_Rge, c->nRge, phk, true));
         TRY(launch_cgemm(c, true, 1, nb, nrowS, c->nRge, phk, c->nRge, 0, c->d_g32, nrowS, 0, S1, nrowS, 0));
         TRY(launch_fold_u(c, true, nb, kb, c->nRgp, nm, nw, S1, c->d_U32, G));
-        // q-sum over the columns of the listed bands only
-        TRY(launch_cgemm(c, true, nb, c->Nq, nsub, c->nKp, c->d_phq32, c->nKp, 0,
-                         (const float2 *)G + (int64_t)band_lo * nm * nw, ncol, nrow, Cb, nsub, c->Nq * nsub));
+        // q-sum over the window k' only (q = k' - k) and the columns of the listed bands only
+        ListLaunch Lg = L;
+        Lg.nb = nb;
+        Lg.kidx = kb;
+        TRY(list_gather_qrows(c, Lg, c->d_phq32, phg));
+        TRY(launch_cgemm(c, true, nb, na, nsub, c->nKp, phg, c->nKp, na * c->nKp,
+                         (const float2 *)G + (int64_t)band_lo * nm * nw, ncol, nrow, Cb, nsub, na * nsub));
         ListLaunch Lb = L;
         Lb.nb = nb;
         Lb.kidx = kb;

@@ -291,11 +291,14 @@ pgb_status launch_transpose_coef(pgb_ctx *c);
 struct ListLaunch {
     int64_t nb;
     const int32_t *kidx;
+    int64_t na;             // k-points holding a window state
+    const int32_t *win;     // [na] their grid indices (the k' = k + q of the restricted sum)
     int band_lo, nbnd;
     const uint8_t *inwin;
     double cut;
 };
 pgb_status list_count(pgb_ctx *c, const ListLaunch &L, unsigned long long *d_counter);
+pgb_status list_gather_qrows(pgb_ctx *c, const ListLaunch &L, const void *phq, void *out);
 pgb_status list_fill(pgb_ctx *c, const ListLaunch &L, const void *C, unsigned long long *d_counter, uint64_t *keys,
                      float *vals, unsigned long long cap);
 pgb_status list_sort_decode(pgb_ctx *c, int64_t n, int ns, uint64_t *keys, float *vals, uint64_t *keys_alt,

@@ -10,8 +10,9 @@
 // its Gaussian factors has |x| <= 7 sigma (the rates screen).
 //
 //   count kernel: number of kept entries (no interpolation needed);
-//   fill kernel:  per (k, q, band n) the mode projection and rotation of the
-//                 kept terms, appended with warp-aggregated atomics as
+//   fill kernel:  per (k, k' in the window, band n), q = k' - k, the mode
+//                 projection and rotation of the kept terms, appended with
+//                 warp-aggregated atomics as
 //                 (key = (s * ns + s') * nmode + nu, |g|^2);
 //   a radix sort of the keys gives the deterministic row-major order, and a
 //   decode kernel splits the keys into row, col, mode.
@@ -24,6 +25,13 @@ namespace pgb {
 
 namespace {
 inline unsigned int div_up(int64_t a, int64_t b) { return (unsigned int)((a + b - 1) / b); }
+
+// q index of k' - k on the grid (k grid = q grid)
+__device__ __forceinline__ int kdiff_grid(int kp, int k, int n0, int n1, int n2) {
+    const int k3 = k % n2, k2 = (k / n2) % n1, k1 = k / (n1 * n2);
+    const int l3 = kp % n2, l2 = (kp / n2) % n1, l1 = kp / (n1 * n2);
+    return (((l1 - k1 + n0) % n0) * n1 + (l2 - k2 + n1) % n1) * n2 + (l3 - k3 + n2) % n2;
+}
 
 __device__ __forceinline__ int kplusq_grid(int k, int q, int n0, int n1, int n2) {
     const int k3 = k % n2, k2 = (k / n2) % n1, k1 = k / (n1 * n2);
@@ -41,7 +49,9 @@ struct ListArgs {
     int Nk;                  // k grid = q grid
     int n0, n1, n2;
     int nw, nm, band_lo, nbnd;
-    const float2 *C;         // [nb][Nk][nbnd][nm][nw]  Rp-summed g with U(k) folded
+    const int32_t *win;      // [na] k-points with a window state (the only k' = k + q kept)
+    int na;
+    const float2 *C;         // [nb][na][nbnd][nm][nw]  Rp-summed g with U(k) folded, q = win[w] - k
     const float2 *U;         // [Nk][i][m] FP32
     const float2 *coef;      // [Nq][nu][ka] FP32
     const double *eps;       // [Nk][nw]
@@ -65,10 +75,11 @@ __device__ __forceinline__ bool entry_kept(const ListArgs &a, int s, int sp, dou
 __global__ void k_list_count(ListArgs a) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long cnt = 0;
-    if (t < (int64_t)a.nb * a.Nk) {
-        const int b = (int)(t / a.Nk), q = (int)(t % a.Nk);
+    if (t < (int64_t)a.nb * a.na) {
+        const int b = (int)(t / a.na), w = (int)(t % a.na);
         const int k = a.kidx[b];
-        const int kq = kplusq_grid(k, q, a.n0, a.n1, a.n2);
+        const int kq = a.win[w];
+        const int q = kdiff_grid(kq, k, a.n0, a.n1, a.n2);
         for (int nl = 0; nl < a.nbnd; ++nl) {
             const int s = k * a.nbnd + nl;
             if (!a.inwin[s]) continue;
@@ -85,22 +96,23 @@ __global__ void k_list_count(ListArgs a) {
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(a.counter, cnt);
 }
 
-// One thread per (b, q, nl).  First pass counts its entries, a warp scan and
+// One thread per (b, w, nl).  First pass counts its entries, a warp scan and
 // one atomic reserve the slots, second pass computes |g|^2 and writes.
 __global__ void k_list_fill(ListArgs a) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    const int64_t total = (int64_t)a.nb * a.Nk * a.nbnd;
-    int b = 0, q = 0, nl = 0, k = 0, kq = 0, s = 0;
+    const int64_t total = (int64_t)a.nb * a.na * a.nbnd;
+    int b = 0, q = 0, w = 0, nl = 0, k = 0, kq = 0, s = 0;
     double es = 0.0;
     unsigned cnt = 0;
     const bool act = t < total;
     if (act) {
         nl = (int)(t % a.nbnd);
-        q = (int)((t / a.nbnd) % a.Nk);
-        b = (int)(t / ((int64_t)a.nbnd * a.Nk));
+        w = (int)((t / a.nbnd) % a.na);
+        b = (int)(t / ((int64_t)a.nbnd * a.na));
         k = a.kidx[b];
-        kq = kplusq_grid(k, q, a.n0, a.n1, a.n2);
+        kq = a.win[w];
+        q = kdiff_grid(kq, k, a.n0, a.n1, a.n2);
         s = k * a.nbnd + nl;
         if (a.inwin[s]) {
             es = a.eps[(int64_t)k * a.nw + a.band_lo + nl];
@@ -127,15 +139,15 @@ __global__ void k_list_fill(ListArgs a) {
 
     const int ns = a.Nk * a.nbnd;
     const int per_n = a.nm * a.nw;
-    const float2 *Cn = a.C + (((int64_t)b * a.Nk + q) * a.nbnd + nl) * per_n;
+    const float2 *Cn = a.C + (((int64_t)b * a.na + w) * a.nbnd + nl) * per_n;
     const float2 *cf = a.coef + (int64_t)q * a.nm * a.nm;
     const float2 *U = a.U + (int64_t)kq * a.nw * a.nw;
     for (int v = 0; v < a.nm; ++v) {
-        const double w = a.hw[(int64_t)q * a.nm + v];
+        const double hw = a.hw[(int64_t)q * a.nm + v];
         bool anym = false;
         for (int ml = 0; ml < a.nbnd; ++ml) {
             const int sp = kq * a.nbnd + ml;
-            anym |= entry_kept(a, s, sp, es, a.eps[(int64_t)kq * a.nw + a.band_lo + ml], w);
+            anym |= entry_kept(a, s, sp, es, a.eps[(int64_t)kq * a.nw + a.band_lo + ml], hw);
         }
         if (!anym) continue;
         float2 gv[kMaxNw];
@@ -149,7 +161,7 @@ __global__ void k_list_fill(ListArgs a) {
         }
         for (int ml = 0; ml < a.nbnd; ++ml) {
             const int sp = kq * a.nbnd + ml;
-            if (!entry_kept(a, s, sp, es, a.eps[(int64_t)kq * a.nw + a.band_lo + ml], w)) continue;
+            if (!entry_kept(a, s, sp, es, a.eps[(int64_t)kq * a.nw + a.band_lo + ml], hw)) continue;
             const int m = a.band_lo + ml;
             float2 g = make_float2(0.f, 0.f);
 #pragma unroll
@@ -170,6 +182,19 @@ __global__ void k_list_fill(ListArgs a) {
             }
         }
     }
+}
+
+// A operand of the restricted q-sum: row w of batch b is the q-table row of
+// q = win[w] - kidx[b]
+__global__ void k_gather_qrows(int nb, const int32_t *__restrict__ kidx, int na, const int32_t *__restrict__ win,
+                               int n0, int n1, int n2, int nK, const float2 *__restrict__ phq, float2 *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nb * na * nK) return;
+    const int p = (int)(t % nK);
+    const int64_t bw = t / nK;
+    const int w = (int)(bw % na), b = (int)(bw / na);
+    const int q = kdiff_grid(win[w], kidx[b], n0, n1, n2);
+    out[t] = phq[(int64_t)q * nK + p];
 }
 
 __global__ void k_list_decode(int64_t n, int ns, int nm, const uint64_t *__restrict__ keys,
@@ -199,6 +224,8 @@ pgb_status list_count(pgb_ctx *c, const ListLaunch &L, unsigned long long *d_cou
     a.nm = c->nm;
     a.band_lo = L.band_lo;
     a.nbnd = L.nbnd;
+    a.win = L.win;
+    a.na = (int)L.na;
     a.C = nullptr;
     a.U = c->d_U32;
     a.coef = c->d_coef32;
@@ -210,7 +237,7 @@ pgb_status list_count(pgb_ctx *c, const ListLaunch &L, unsigned long long *d_cou
     a.keys = nullptr;
     a.vals = nullptr;
     a.cap = 0;
-    const int64_t n = L.nb * c->Nk;
+    const int64_t n = L.nb * L.na;
     if (n == 0) return PGB_OK;
     k_list_count<<<div_up(n, 256), 256, 0, c->stream>>>(a);
     PGB_LAUNCH_CHECK(c);
@@ -230,6 +257,8 @@ pgb_status list_fill(pgb_ctx *c, const ListLaunch &L, const void *C, unsigned lo
     a.nm = c->nm;
     a.band_lo = L.band_lo;
     a.nbnd = L.nbnd;
+    a.win = L.win;
+    a.na = (int)L.na;
     a.C = (const float2 *)C;
     a.U = c->d_U32;
     a.coef = c->d_coef32;
@@ -241,7 +270,7 @@ pgb_status list_fill(pgb_ctx *c, const ListLaunch &L, const void *C, unsigned lo
     a.keys = keys;
     a.vals = vals;
     a.cap = cap;
-    const int64_t n = L.nb * c->Nk * L.nbnd;
+    const int64_t n = L.nb * L.na * L.nbnd;
     if (n == 0) return PGB_OK;
     k_list_fill<<<div_up(n, 256), 256, 0, c->stream>>>(a);
     PGB_LAUNCH_CHECK(c);
@@ -270,4 +299,15 @@ pgb_status list_sort_decode(pgb_ctx *c, int64_t n, int ns, uint64_t *keys, float
     return PGB_OK;
 }
 
+}  // namespace pgb
+
+namespace pgb {
+pgb_status list_gather_qrows(pgb_ctx *c, const ListLaunch &L, const void *phq, void *out) {
+    const int64_t n = L.nb * L.na * (int64_t)c->nKp;
+    if (n == 0) return PGB_OK;
+    k_gather_qrows<<<div_up(n, 256), 256, 0, c->stream>>>((int)L.nb, L.kidx, (int)L.na, L.win, c->kg[0], c->kg[1],
+                                                          c->kg[2], c->nKp, (const float2 *)phq, (float2 *)out);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
 }  // namespace pgb
