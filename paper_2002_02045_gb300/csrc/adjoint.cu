@@ -150,7 +150,7 @@ struct ColArgs {
     float2 *acc;              // [nnz] |g|^2 derivative, transposed order, as (sum, compensation) (null: skipped)
 };
 
-__global__ void __launch_bounds__(kThreads) k_adj_col(ColArgs p) {
+__global__ void __launch_bounds__(kThreads, 5) k_adj_col(ColArgs p) {
     __shared__ double red[kThreads / 32];
     const int64_t r = blockIdx.x;
     if (r >= p.ncols) return;
