@@ -465,9 +465,20 @@ def polar(ctx, args, world):
     nnz = ctx.pgb_build_collision_grid(0, 2, emin - 1e-6, emin + POLAR_WINDOW, T_K, SIGMA)
     torch.cuda.synchronize()
     t_list = time.perf_counter() - t0
+    from paper_2002_02045_gb300.native import PROF_COLLISION
+    peaks, peak_src = load_peaks()
+    ctx.pgb_profile(True)
+    ctx.pgb_profile_read(PROF_COLLISION)             # reset the class: the BTE iterations are timed in it
     t0 = time.perf_counter()
     mob_rta, mob, it = ctx.pgb_transport(mu, prec, 3000, 1e-6)
     t_tr = time.perf_counter() - t0
+    it_ms, it_n = ctx.pgb_profile_read(PROF_COLLISION)
+    ctx.pgb_profile(False)
+    bte_bytes = 12.0 * nnz        # col (4 B) + W (8 B) per entry; F is gathered from L2
+    bte_gbs = bte_bytes * it_n / (it_ms * 1e-3) / 1e9 if it_ms > 0 else None
+    bte_flops = 6.0 * nnz         # three FP64 multiply-adds per entry (x, y, z)
+    bte_tf = bte_flops * it_n / (it_ms * 1e-3) / 1e12 if it_ms > 0 else None
+    FP64_PEAK = 1.25              # TFLOP/s, nominal GB300 FP64 (the iteration is FP64-bound)
     # Monte-Carlo q: Cauchy samples about q = 0 for the 16 lowest window k-points
     from paper_2002_02045_gb300 import PGB_FP32, PGB_Q_CAUCHY
     pts = torch.as_tensor(S.mp_grid(*POLAR_GRID)).cuda()
@@ -493,7 +504,16 @@ def polar(ctx, args, world):
         "transport": {"list_entries": nnz, "list_build_s": t_list, "solve_s": t_tr, "iterations": it,
                       "tolerance": 1e-6, "mobility_cm2_per_Vs": np.diag(mob).tolist(),
                       "mobility_rta_cm2_per_Vs": np.diag(mob_rta).tolist(),
-                      "includes": "tau from the rates over the full q grid, velocities, W, iterations, mobility"},
+                      "includes": "tau from the rates over the full q grid, velocities, W, iterations, mobility",
+                      "iteration_ms": it_ms / max(1, it_n),
+                      "roofline": {"bound": "alu", "kernel": "k_bte_iter (FP64)", "achieved": bte_tf,
+                                   "peak": FP64_PEAK, "unit": "TFLOP/s",
+                                   "frac": bte_tf / FP64_PEAK if bte_tf else None,
+                                   "peak_source": "nominal GB300 FP64 rate",
+                                   "algorithmic_flop_per_entry": 6.0, "launches": it_n,
+                                   "hbm_achieved_gbs": bte_gbs,
+                                   "hbm_frac": bte_gbs / peaks["hbm_gbs"] if bte_gbs else None,
+                                   "hbm_peak_source": peak_src}},
         "monte_carlo": {"metric": "(k,q) pairs/s, Gamma_nk by Cauchy-sampled random q (FP32, bands at every k+q)",
                         "value": len(kmc) * MC_SAMPLES / (ms_mc * 1e-3), "unit": "pairs/s", "ms": ms_mc,
                         "k_points": len(kmc), "samples": MC_SAMPLES, "cauchy_width": 0.1,
@@ -546,6 +566,9 @@ def batched(args, world):
     dt = max_over_ranks((time.perf_counter() - t0) / reps, world)
     tun = b.pgb_batch_tuning()
     finite = all(np.all(np.isfinite(o)) for o in outs)
+    # algorithmic q-sum work: 8 FLOP per complex multiply-add, nR_p x (nmode nw^2) per (k, q) pair
+    flops = sum(BATCH_K * int(np.prod(m.meta["grid"])) * len(m.R_gp) * m.nmode * m.nw ** 2 * 8 for m in models)
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x max clock, TFLOP/s
     b.close()
     for c in ctxs:
         c.close()
@@ -555,6 +578,10 @@ def batched(args, world):
         "instances": args.batch_instances, "k_per_instance": BATCH_K, "first_call_s": t_first,
         "model_generation_s": t_gen, "setup_s": t_setup, "tuning": tun, "finite": finite,
         "timing": "host clock around pgb_batch_rates (graph replay + output copies, synchronised)",
+        "roofline": {"bound": "alu", "kernel": "k_batch_rates (FP32 SIMT)", "achieved": flops / dt / 1e12,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": flops / dt / 1e12 / fp32_peak,
+                     "algorithmic_flop": flops,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (whole graph timed)"},
     }
 
 
