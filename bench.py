@@ -129,6 +129,40 @@ def cpu_baseline(model, n_k=2):
                       f"included), {dt:.1f} s"}
 
 
+def cpu_baseline_list(ctx, grid, nnz, es, f, n_sample=4_000_000):
+    """The FP64 oracle's I[f] and its transposed product (collision, collision_vjp) on the
+    first n_sample entries of the device-built list, timed on the host cores."""
+    import torch
+    from oracle import eph as O
+    n = int(min(nnz, n_sample))
+    dev = {k: torch.empty(nnz, dtype=dt, device="cuda")
+           for k, dt in (("row", torch.int32), ("col", torch.int32), ("mode", torch.int32), ("g2", torch.float32))}
+    ctx.pgb_collision_list(dev["row"], dev["col"], dev["mode"], dev["g2"])
+    h = {k: v[:n].cpu().numpy() for k, v in dev.items()}
+    del dev
+    nk = int(np.prod(grid))
+    hw = torch.empty((nk, ctx.nmode), dtype=torch.float64, device="cuda")
+    ctx.pgb_get_grid_energies(None, hw)
+    hw = hw.cpu().numpy()
+    k, kp = h["row"] // 2, h["col"] // 2
+    c = [np.stack([x // (grid[1] * grid[2]), (x // grid[2]) % grid[1], x % grid[2]], -1) for x in (k, kp)]
+    qv = (c[1] - c[0]) % np.array(grid)
+    q = (qv[:, 0] * grid[1] + qv[:, 1]) * grid[2] + qv[:, 2]
+    hw_e = hw[q, h["mode"]]
+    es_h, f_h = es.cpu().numpy(), f.cpu().numpy()
+    row, col, g2 = h["row"].astype(np.int64), h["col"].astype(np.int64), h["g2"].astype(np.float64)
+    t0 = time.perf_counter()
+    O.collision(f_h, es_h, row, col, hw_e, g2, T_K, SIGMA, nk)
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.collision_vjp(f_h, np.ones_like(f_h), es_h, row, col, hw_e, g2, T_K, SIGMA, nk)
+    t_vjp = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    sample = f"first {n} entries of the {nnz}-entry list, one application (FP64 NumPy oracle)"
+    return ({"value": n / t_fwd, "unit": "entries/s", "cores": cores, "kind": "oracle", "sample": sample},
+            {"value": n / t_vjp, "unit": "entries/s", "cores": cores, "kind": "oracle", "sample": sample})
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -347,6 +381,11 @@ def dynamics(ctx, model, args, world, peaks, peak_src):
     byte_per_entry = 12.0
     achieved = byte_per_entry * nnz * evals / (k_ms * 1e-3) / 1e9
     adj = adjoint(ctx, f_pulse, nnz, args, world, peaks, peak_src, ms / args.dyn_steps) if args.adj_steps > 0 else None
+    cb_fwd = cb_adj = None
+    if args.cpu_baseline and world == 1:
+        cb_fwd, cb_adj = cpu_baseline_list(ctx, grid, nnz, es, f_pulse)
+        if adj is not None:
+            adj["cpu_baseline"] = cb_adj
     return {
         "metric": "collision-entry evaluations/s (RK4, 4 evaluations per step)",
         "value": world * nnz * evals / (ms * 1e-3), "unit": "entries/s",
@@ -356,6 +395,7 @@ def dynamics(ctx, model, args, world, peaks, peak_src):
                                f"{DYN_WINDOW} eV of the band minimum, 7 sigma screen, dt = 1 fs, hot-carrier pulse",
                    "list_build_s": build_s},
         "carrier_number_drift": abs(float(f.sum()) - n0) / n0,
+        "cpu_baseline": cb_fwd,
         "population": {"energies": 401, "ms": pop_ms, "carriers_in_window_per_cell": float(Npop[-1] - Npop[0]),
                        "method": "linear tetrahedron, 6 per cell, both bands"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -494,6 +534,16 @@ def polar(ctx, args, world):
     torch.cuda.synchronize()
     ms_mc = e0.elapsed_time(e1)
     rel = (emc / gmc.clamp_min(1e-300))[gmc > 0]
+    cb = None
+    if args.cpu_baseline and world == 1:
+        from oracle import eph as O
+        ns_cpu = 2048
+        t0 = time.perf_counter()
+        O.scattering_rates_mc(m, kmc[:1].cpu().numpy(), u[:ns_cpu].cpu().numpy(), O.Q_CAUCHY, 0.1, T_K, mu, SIGMA)
+        dt_cpu = time.perf_counter() - t0
+        cb = {"value": ns_cpu / dt_cpu, "unit": "pairs/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+              "sample": f"1 k-point x {ns_cpu} Cauchy q samples of the same polar model (FP64 NumPy oracle: "
+                        f"bands at every k+q, short- and long-range g, rates), {dt_cpu:.1f} s"}
     return {
         "metric": "(k,q) pairs/s, polar Gamma_nk (short-range Wannier sum + long-range Ewald term)",
         "value": world * pairs / (ms * 1e-3), "unit": "pairs/s", "ms": ms, "pairs": pairs, "nk_window": nwin,
@@ -514,6 +564,7 @@ def polar(ctx, args, world):
                                    "hbm_achieved_gbs": bte_gbs,
                                    "hbm_frac": bte_gbs / peaks["hbm_gbs"] if bte_gbs else None,
                                    "hbm_peak_source": peak_src}},
+        "cpu_baseline": cb,
         "monte_carlo": {"metric": "(k,q) pairs/s, Gamma_nk by Cauchy-sampled random q (FP32, bands at every k+q)",
                         "value": len(kmc) * MC_SAMPLES / (ms_mc * 1e-3), "unit": "pairs/s", "ms": ms_mc,
                         "k_points": len(kmc), "samples": MC_SAMPLES, "cauchy_width": 0.1,
@@ -566,6 +617,18 @@ def batched(args, world):
     dt = max_over_ranks((time.perf_counter() - t0) / reps, world)
     tun = b.pgb_batch_tuning()
     finite = all(np.all(np.isfinite(o)) for o in outs)
+    cb = None
+    if args.cpu_baseline and world == 1:
+        from oracle import eph as O
+        small = [i for i, m in enumerate(models) if m.meta["grid"][0] == 8][:3]
+        t0 = time.perf_counter()
+        for i in small:
+            g = models[i].meta["grid"]
+            O.scattering_rates_grid(models[i], g, g, ks[i][:1], T_K, mus[i], 0.005)
+        dt_cpu = time.perf_counter() - t0
+        cb = {"value": 512 * len(small) / dt_cpu, "unit": "pairs/s", "cores": len(os.sched_getaffinity(0)),
+              "kind": "oracle", "sample": f"1 k-point x 512 q of each of the {len(small)} first 8^3 instances "
+                                          f"(FP64 NumPy oracle), {dt_cpu:.1f} s"}
     # algorithmic q-sum work: 8 FLOP per complex multiply-add, nR_p x (nmode nw^2) per (k, q) pair
     flops = sum(BATCH_K * int(np.prod(m.meta["grid"])) * len(m.R_gp) * m.nmode * m.nw ** 2 * 8 for m in models)
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x max clock, TFLOP/s
@@ -578,6 +641,7 @@ def batched(args, world):
         "instances": args.batch_instances, "k_per_instance": BATCH_K, "first_call_s": t_first,
         "model_generation_s": t_gen, "setup_s": t_setup, "tuning": tun, "finite": finite,
         "timing": "host clock around pgb_batch_rates (graph replay + output copies, synchronised)",
+        "cpu_baseline": cb,
         "roofline": {"bound": "alu", "kernel": "k_batch_rates (FP32 SIMT)", "achieved": flops / dt / 1e12,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": flops / dt / 1e12 / fp32_peak,
                      "algorithmic_flop": flops,
