@@ -7,9 +7,9 @@
 //     as four real products with hi/lo split operands (see tc_qsum.cu), FP32
 //     accumulators in TMEM;
 //   epilogue (CUDA cores, reading TMEM): per q row and band n, screen the
-//     (m, nu) with |e_n(k) - e_m(k+q) -+ hw_nu(q)| <= 7 sigma, project on the
-//     surviving modes (G^nu_i = sum_ka coef[q][nu][ka] C[q][n][ka][i]), rotate
-//     by U(k+q) for the surviving m, and accumulate
+//     (m, nu) with |e_n(k) - e_m(k+q) -+ hw_nu(q)| <= 7 sigma, rotate by U(k+q)
+//     once per surviving m (R_ka = sum_i conj(U_im) C[q][n][ka][i]), project on
+//     the surviving modes (g = sum_ka coef[q][nu][ka] R_ka), and accumulate
 //     |g|^2 [e^{-(x_em/s)^2}(1 + N - f_m) + e^{-(x_abs/s)^2}(N + f_m)].
 // The per-tile sums over q go to partial[b][q-tile][nu][n]; a second kernel
 // reduces the q-tiles in a fixed order.
@@ -316,52 +316,59 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int v = 0; v < NMF; ++v) acc[v] = 0.f;
             if (valid) {
                 const float2 en = a.ehl[(size_t)n * a.Nk + k];
+                // screen every (nu, m) first; live[nu] holds the surviving m
+                uint32_t live[NMF], any = 0;
 #pragma unroll
                 for (int v = 0; v < NMF; ++v) {
+                    live[v] = 0;
                     if (!(wv[v].x + wv[v].y >= (float)kOmegaMinEv)) continue;
-                    uint32_t bits = 0;
 #pragma unroll
                     for (int m = 0; m < NWF; ++m) {
                         // (e_n,hi - e_m,hi) is exact for every possible survivor
                         const float dh = en.x - em[m].x, dl = en.y - em[m].y;
                         const float xe = (dh - wv[v].x) + (dl - wv[v].y);
                         const float xa = (dh + wv[v].x) + (dl + wv[v].y);
-                        if (fabsf(xe) <= a.cut || fabsf(xa) <= a.cut) bits |= 1u << m;
+                        if (fabsf(xe) <= a.cut || fabsf(xa) <= a.cut) live[v] |= 1u << m;
                     }
-                    if (!bits) continue;
-                    float pr[NWF], pi[NWF];
+                    any |= live[v];
+                }
+                // g_mn^nu = sum_ka coef[nu][ka] R_ka with R_ka = sum_i conj(U_im(k+q)) C[ka][i]:
+                // the rotation runs once per surviving m, the projection once per surviving (m, nu)
+                while (any) {
+                    const int m = __ffs(any) - 1;
+                    any &= any - 1;
+                    float2 u[NWF];
 #pragma unroll
-                    for (int i = 0; i < NWF; ++i) {
-                        pr[i] = 0.f;
-                        pi[i] = 0.f;
-                    }
+                    for (int i = 0; i < NWF; ++i) u[i] = a.UT[(size_t)(m * NWF + i) * a.Nk + kq];
+                    const float f = a.focc[(size_t)m * a.Nk + kq];
+                    float rr[NMF], ri[NMF];
 #pragma unroll
                     for (int ka = 0; ka < NMF; ++ka) {
-                        const float2 c = a.coef[(size_t)(v * NMF + ka) * a.Nq + q];
+                        float sr = 0.f, si = 0.f;
 #pragma unroll
                         for (int i = 0; i < NWF; ++i) {
                             const float xr = gr[ka * NWF + i], xi = gi[ka * NWF + i];
-                            pr[i] = fmaf(c.x, xr, fmaf(-c.y, xi, pr[i]));
-                            pi[i] = fmaf(c.x, xi, fmaf(c.y, xr, pi[i]));
+                            sr = fmaf(u[i].x, xr, fmaf(u[i].y, xi, sr));
+                            si = fmaf(u[i].x, xi, fmaf(-u[i].y, xr, si));
                         }
+                        rr[ka] = sr;
+                        ri[ka] = si;
                     }
-                    const float N = nb_[v];
-                    while (bits) {
-                        const int m = __ffs(bits) - 1;
-                        bits &= bits - 1;
+                    const float dh = en.x - em[m].x, dl = en.y - em[m].y;
+#pragma unroll
+                    for (int v = 0; v < NMF; ++v) {
+                        if (!((live[v] >> m) & 1u)) continue;
                         float grr = 0.f, gii = 0.f;
 #pragma unroll
-                        for (int i = 0; i < NWF; ++i) {
-                            const float2 u = a.UT[(size_t)(m * NWF + i) * a.Nk + kq];   // U_im(k+q), conjugated below
-                            grr = fmaf(u.x, pr[i], fmaf(u.y, pi[i], grr));
-                            gii = fmaf(u.x, pi[i], fmaf(-u.y, pr[i], gii));
+                        for (int ka = 0; ka < NMF; ++ka) {
+                            const float2 c = a.coef[(size_t)(v * NMF + ka) * a.Nq + q];
+                            grr = fmaf(c.x, rr[ka], fmaf(-c.y, ri[ka], grr));
+                            gii = fmaf(c.x, ri[ka], fmaf(c.y, rr[ka], gii));
                         }
                         const float g2 = grr * grr + gii * gii;
-                        const float2 e_m = a.ehl[(size_t)m * a.Nk + kq];
-                        const float dh = en.x - e_m.x, dl = en.y - e_m.y;
                         const float xe = (dh - wv[v].x) + (dl - wv[v].y);
                         const float xa = (dh + wv[v].x) + (dl + wv[v].y);
-                        const float f = a.focc[(size_t)m * a.Nk + kq];
+                        const float N = nb_[v];
                         const float ye = xe * a.inv_sigma, ya = xa * a.inv_sigma;
                         float W = 0.f;
                         if (fabsf(xe) <= a.cut) W += expf(-ye * ye) * (1.f + N - f);
