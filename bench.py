@@ -37,7 +37,7 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu captures
 # summarised in profiles/k_tc_rates_bf16x3_fcc40.md and profiles/k_collision_rk4_30cubed.md.
 # Set an entry to None whenever its kernel changes after the capture.
-TRAFFIC = {"k_tc_rates_bf16x3_bytes_per_pair": (1.132050e9 + 17.47e6) / (64 * 64000),
+TRAFFIC = {"k_tc_rates_bf16x3_bytes_per_pair": (1.139146e9 + 23.311e6) / (64 * 64000),
            "k_collision_bytes_per_entry": (383152384 + 3583744) / 31890730}
 
 
