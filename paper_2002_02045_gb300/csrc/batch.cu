@@ -11,9 +11,10 @@
 //      memory, K-chunk by K-chunk, from the instance's FP32 q table (exact grid
 //      phases and, for polar models, the long-range columns; built once per
 //      plan) and the G_k rows of band n, which are contiguous (column order n, ka, i);
-//   2. runs the rates epilogue on the tile, one (q, nu) pair per thread: screen
-//      the (m) with |x| <= 7 sigma, project on nu, rotate by U(k+q), Gaussian
-//      weights with FP64 energies, FP32 products;
+//   2. runs the rates epilogue on the tile: screen every (q, nu) against the
+//      (m) with |x| <= 7 sigma, list the live pairs in order, then one live pair
+//      per thread: project on nu, rotate by U(k+q), Gaussian weights with FP64
+//      energies, FP32 products;
 //   3. writes the sum of its terms to its own partial slot.
 // Units are assigned to the persistent CTAs round-robin (every instance's
 // units are spread over all CTAs); a second kernel adds the q-tile partials of
@@ -49,6 +50,7 @@ struct BInst {
     const int32_t *kidx;       // [nk]
     const double *eps;         // [Nk][nw]
     const float *eps32;        // [Nk][nw] FP32 copy for the screen
+    const float *hw32;         // [Nq][nm] FP32 copy for the screen
     const float2 *U;           // [Nk][nw][nw], U[i][n]
     const float2 *coef;        // [Nq][nm][nm]
     const double *hw;          // [Nq][nm]
@@ -77,11 +79,14 @@ __device__ __forceinline__ int64_t kq_index(int64_t k, int64_t q, const int kg[3
 
 template <int QT, int NT>
 __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     float2 *Cs = sm;                         // [QT][maxc]
     float2 *As = Cs + QT * a.maxc;           // [QT][KC]
     float2 *Bs = As + QT * KC;               // [KC][maxc]
     __shared__ double red[NT / 32];
+    __shared__ int wcnt[NT / 32];
+    __shared__ int kqrow[QT];                    // k+q grid index of each tile row
+    __shared__ uint32_t items[QT * kMaxNmode];   // live (q, nu) of the tile: item << 16 | mask of m
     const int t = threadIdx.x;
     for (int64_t u = blockIdx.x; u < a.nunits; u += gridDim.x) {
         const BInst I = a.inst[a.unit_inst[u]];
@@ -113,10 +118,14 @@ __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
 #pragma unroll
                 for (int j = 0; j < RT; ++j) acc[j] = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int kk = 0; kk < KC; ++kk) {
-                    const float2 bv = Bs[kk * a.maxc + cc];
+                for (int kk = 0; kk < KC; kk += 2) {
+                    const float2 b0 = Bs[kk * a.maxc + cc], b1 = Bs[(kk + 1) * a.maxc + cc];
 #pragma unroll
-                    for (int j = 0; j < RT; ++j) cfma(acc[j], As[(q0r + j * (QT / RT)) * KC + kk], bv);
+                    for (int j = 0; j < RT; ++j) {
+                        const float4 av = *reinterpret_cast<const float4 *>(As + (q0r + j * (QT / RT)) * KC + kk);
+                        cfma(acc[j], make_float2(av.x, av.y), b0);
+                        cfma(acc[j], make_float2(av.z, av.w), b1);
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < RT; ++j) {
@@ -127,30 +136,60 @@ __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
             }
         }
         __syncthreads();
-        // 2. epilogue, one (q, nu) per thread
+        // 2. epilogue.  (a) screen every (q, nu) of the tile in FP32 (|x| <= 7 sigma plus a
+        //    margin) and list the live ones, in item order, by a block-wide scan;
+        //    (b) one live (q, nu) per thread: project on nu, rotate by U(k+q) for each
+        //    surviving m, Gaussian weights with FP64 energies, FP32 products.  The list
+        //    keeps whole warps on the projection however sparse the survivors are.
         double part = 0.0;
         const int64_t k = I.kidx[kb];
         const double en = I.eps[k * nw + n];
         const float en32 = I.eps32[k * nw + n];
         const double is = 1.0 / I.sigma, ycut2 = kDeltaCut * kDeltaCut;
         const float cut32 = (float)(kDeltaCut * I.sigma) + 1e-4f;
-        for (int o = t; o < QT * nm; o += NT) {
-            const int qq = o / nm, v = o % nm;
-            if (qq >= nq) continue;
-            const int64_t q = q0 + qq;
-            const double w = I.hw[q * nm + v];
-            if (!(w >= kOmegaMinEv)) continue;
-            const int64_t kq = kq_index(k, q, I.kg, I.qg);
-            const double *em = I.eps + kq * nw;
-            const float *em32 = I.eps32 + kq * nw;
-            // screen in FP32 with a margin (no FP64 work for the rejected terms)
-            const float w32 = (float)w;
+        for (int qq = t; qq < nq; qq += NT) kqrow[qq] = (int)kq_index(k, q0 + qq, I.kg, I.qg);
+        __syncthreads();
+        const int lane = t & 31, wid = t >> 5;
+        int nlive = 0;
+        for (int o0 = 0; o0 < QT * nm; o0 += NT) {
+            const int o = o0 + t;
             uint32_t live = 0;
-            for (int m = 0; m < nw; ++m) {
-                const float d = en32 - em32[m];
-                if (fabsf(d - w32) <= cut32 || fabsf(d + w32) <= cut32) live |= 1u << m;
+            if (o < QT * nm) {
+                const int qq = o / nm, v = o - (o / nm) * nm;
+                if (qq < nq) {
+                    const int64_t q = q0 + qq;
+                    const float w32 = I.hw32[q * nm + v];
+                    if (w32 >= (float)kOmegaMinEv) {
+                        const float *em32 = I.eps32 + (int64_t)kqrow[qq] * nw;
+                        for (int m = 0; m < nw; ++m) {
+                            const float d = en32 - em32[m];
+                            if (fabsf(d - w32) <= cut32 || fabsf(d + w32) <= cut32) live |= 1u << m;
+                        }
+                    }
+                }
             }
-            if (!live) continue;
+            const unsigned bal = __ballot_sync(0xffffffffu, live != 0);
+            if (lane == 0) wcnt[wid] = __popc(bal);
+            __syncthreads();
+            int base = nlive, tot = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < NT / 32; ++w2) {
+                base += (w2 < wid) ? wcnt[w2] : 0;
+                tot += wcnt[w2];
+            }
+            if (live) items[base + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)o << 16) | live;
+            nlive += tot;
+            __syncthreads();
+        }
+        for (int j = t; j < nlive; j += NT) {
+            const uint32_t it = items[j];
+            uint32_t live = it & 0xffffu;
+            const int o = (int)(it >> 16);
+            const int qq = o / nm, v = o - (o / nm) * nm;
+            const int64_t q = q0 + qq;
+            const int64_t kq = kqrow[qq];
+            const double w = I.hw[q * nm + v];
+            const double *em = I.eps + kq * nw;
             const float2 *cf = I.coef + (q * nm + v) * nm;
             float2 gv[kMaxNw];
 #pragma unroll
@@ -424,6 +463,7 @@ pgb_status build_plan(pgb_batch *b, Plan &P, int qt) {
         }
         I.phq = phq;
         I.eps32 = q.eps32;
+        I.hw32 = q.hw32;
         I.G = (const float2 *)G;
         I.kidx = q.kidx;
         I.focc = q.focc;
