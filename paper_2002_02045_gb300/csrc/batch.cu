@@ -8,7 +8,8 @@
 //
 // Work unit = (instance, k, initial band n, tile of QT q-points).  A unit
 //   1. forms its R_p-sum tile C[q][ka][i] = sum_p e^{iq.R_p} G_k[p][n][ka][i] in shared
-//      memory, K-chunk by K-chunk, from the instance's FP32 q table (exact grid
+//      memory, K-chunk by K-chunk (the next chunk copied by cp.async while the
+//      current one is multiplied), from the instance's FP32 q table (exact grid
 //      phases and, for polar models, the long-range columns; built once per
 //      plan) and the G_k rows of band n, which are contiguous (column order n, ka, i);
 //   2. runs the rates epilogue on the tile: screen every (q, nu) against the
@@ -36,7 +37,7 @@ namespace pgb {
 namespace {
 
 inline unsigned int div_up(int64_t a, int64_t b) { return (unsigned int)((a + b - 1) / b); }
-constexpr int KC = 16;   // K chunk of the shared-memory GEMM
+constexpr int KC = 8;    // K chunk of the shared-memory GEMM (double-buffered)
 constexpr int RT = 4;    // tile rows per thread in the shared-memory GEMM
 
 struct BInst {
@@ -77,12 +78,21 @@ __device__ __forceinline__ int64_t kq_index(int64_t k, int64_t q, const int kg[3
     return ((int64_t)s1 * kg[1] + s2) * kg[2] + s3;
 }
 
+// 8-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros (src not read)
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, int src_bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 template <int QT, int NT>
 __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
     extern __shared__ __align__(16) float2 sm[];
     float2 *Cs = sm;                         // [QT][maxc]
-    float2 *As = Cs + QT * a.maxc;           // [QT][KC]
-    float2 *Bs = As + QT * KC;               // [KC][maxc]
+    float2 *As = Cs + QT * a.maxc;           // [2][QT][KC]
+    float2 *Bs = As + 2 * QT * KC;           // [2][KC][maxc]
     __shared__ double red[NT / 32];
     __shared__ int wcnt[NT / 32];
     __shared__ int kqrow[QT];                    // k+q grid index of each tile row
@@ -99,30 +109,45 @@ __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
         const int nq = (int)(I.Nq - q0 < QT ? I.Nq - q0 : QT);
         const float2 *Gk = I.G + kb * (int64_t)I.nKp * ncol + (int64_t)n * ncn;
         for (int o = t; o < QT * ncn; o += NT) Cs[(o / ncn) * a.maxc + o % ncn] = make_float2(0.f, 0.f);
-        // 1. R_p-sum tile
-        for (int p0 = 0; p0 < I.nKp; p0 += KC) {
-            __syncthreads();
+        // 1. R_p-sum tile; K chunk c + 1 is copied (cp.async) while chunk c is multiplied
+        const int nch = (I.nKp + KC - 1) / KC;
+        auto fill = [&](int c) {
+            const int p0 = c * KC;
+            float2 *Ab = As + (c & 1) * QT * KC, *Bb = Bs + (c & 1) * KC * a.maxc;
             for (int o = t; o < QT * KC; o += NT) {
                 const int qq = o / KC, kk = o % KC;
-                As[o] = (qq < nq && p0 + kk < I.nKp) ? I.phq[(q0 + qq) * I.nKp + p0 + kk] : make_float2(0.f, 0.f);
+                const bool ok = qq < nq && p0 + kk < I.nKp;
+                cp_async8(Ab + o, ok ? I.phq + (q0 + qq) * I.nKp + p0 + kk : I.phq, ok ? 8 : 0);
             }
             for (int o = t; o < KC * ncn; o += NT) {
-                const int kk = o / ncn, cc = o % ncn;
-                Bs[kk * a.maxc + cc] = (p0 + kk < I.nKp) ? Gk[(int64_t)(p0 + kk) * ncol + cc] : make_float2(0.f, 0.f);
+                const int kk = o / ncn, cc = o - (o / ncn) * ncn;
+                const bool ok = p0 + kk < I.nKp;
+                cp_async8(Bb + kk * a.maxc + cc, ok ? Gk + (int64_t)(p0 + kk) * ncol + cc : Gk, ok ? 8 : 0);
+            }
+            cp_async_commit();
+        };
+        if (nch > 0) fill(0);
+        for (int c = 0; c < nch; ++c) {
+            if (c + 1 < nch) {
+                fill(c + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
             }
             __syncthreads();
+            const float2 *Ab = As + (c & 1) * QT * KC, *Bb = Bs + (c & 1) * KC * a.maxc;
             // each thread: one column, RT rows spaced QT/RT apart (one B load feeds RT products)
             for (int o = t; o < (QT / RT) * ncn; o += NT) {
-                const int q0r = o / ncn, cc = o % ncn;
+                const int q0r = o / ncn, cc = o - (o / ncn) * ncn;
                 float2 acc[RT];
 #pragma unroll
                 for (int j = 0; j < RT; ++j) acc[j] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int kk = 0; kk < KC; kk += 2) {
-                    const float2 b0 = Bs[kk * a.maxc + cc], b1 = Bs[(kk + 1) * a.maxc + cc];
+                    const float2 b0 = Bb[kk * a.maxc + cc], b1 = Bb[(kk + 1) * a.maxc + cc];
 #pragma unroll
                     for (int j = 0; j < RT; ++j) {
-                        const float4 av = *reinterpret_cast<const float4 *>(As + (q0r + j * (QT / RT)) * KC + kk);
+                        const float4 av = *reinterpret_cast<const float4 *>(Ab + (q0r + j * (QT / RT)) * KC + kk);
                         cfma(acc[j], make_float2(av.x, av.y), b0);
                         cfma(acc[j], make_float2(av.z, av.w), b1);
                     }
@@ -134,8 +159,8 @@ __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
                     d.y += acc[j].y;
                 }
             }
+            __syncthreads();    // buffer c & 1 is refilled by the next pass
         }
-        __syncthreads();
         // 2. epilogue.  (a) screen every (q, nu) of the tile in FP32 (|x| <= 7 sigma plus a
         //    margin) and list the live ones, in item order, by a block-wide scan;
         //    (b) one live (q, nu) per thread: project on nu, rotate by U(k+q) for each
@@ -248,7 +273,7 @@ struct Cand {
 };
 constexpr Cand kCands[4] = {{16, 128}, {32, 128}, {32, 256}, {64, 256}};
 
-size_t smem_bytes(int qt, int maxc) { return sizeof(float2) * ((size_t)qt * maxc + (size_t)qt * KC + (size_t)KC * maxc); }
+size_t smem_bytes(int qt, int maxc) { return sizeof(float2) * ((size_t)qt * maxc + 2 * ((size_t)qt * KC + (size_t)KC * maxc)); }
 
 // CTAs per SM of a candidate (sets its shared-memory limit; call outside stream capture)
 template <int QT, int NT>
