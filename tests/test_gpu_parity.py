@@ -427,16 +427,24 @@ def test_argument_errors(ctx, c1):
 # scattering list built on the device (Sec. 4.3)
 # ----------------------------------------------------------------------------
 
-def test_grid_list_matches_oracle_list(ctx, c2):
-    """The device-built list has exactly the oracle's (row, col, mode) entries
-    (7 sigma screen, energy window) and the same mode-summed |g|^2; its
-    collision integral matches the oracle's on the oracle's own list."""
+@pytest.fixture(scope="module")
+def c2_grid_list(c2):
+    """Oracle list of the C2 model on a 5^3 grid: the two lowest bands within 1.2 eV of
+    their minimum, 7 sigma screen (T = 300 K, sigma = 20 meV)."""
     T, sig = 300.0, 0.02
     grid = (5, 5, 5)
     e_ref, _ = O.bands(c2, S.mp_grid(*grid))
     emin = e_ref[:, :2].min()
     win = (emin, emin + 1.2)
     L = O.collision_list_grid(c2, grid, 0, 2, sigma=sig, screen=np.exp(-49.0), window=win)
+    return T, sig, grid, win, emin, L
+
+
+def test_grid_list_matches_oracle_list(ctx, c2, c2_grid_list):
+    """The device-built list has exactly the oracle's (row, col, mode) entries
+    (7 sigma screen, energy window) and the same mode-summed |g|^2; its
+    collision integral matches the oracle's on the oracle's own list."""
+    T, sig, grid, win, emin, L = c2_grid_list
     ctx.pgb_set_model(c2)
     ctx.pgb_set_grids(grid, grid)
     nnz = ctx.pgb_build_collision_grid(0, 2, win[0], win[1], T, sig)
@@ -465,6 +473,29 @@ def test_grid_list_matches_oracle_list(ctx, c2):
     ref = O.collision(f, L["eps"], L["row"], L["col"], L["hw"], L["g2"], T, sig, L["nq"])
     assert np.abs(I - ref).max() <= 1e-5 * np.abs(ref).max()
     assert abs(I.sum()) <= 1e-6 * np.abs(ref).max()
+
+
+def test_rk4_c2_grid_list_1000_steps(ctx, c2, c2_grid_list):
+    """1000 RK4 steps of 1 fs (Sec. 2.1.1) of a hot-carrier pulse (0.5 eV above the band
+    minimum, width 0.1 eV) on the device-built list of the C2 model, against the oracle's
+    evolution on its own FP64 list: occupations within 1e-6, carrier number conserved."""
+    T, sig, grid, win, emin, L = c2_grid_list
+    ctx.pgb_set_model(c2)
+    ctx.pgb_set_grids(grid, grid)
+    nnz = ctx.pgb_build_collision_grid(0, 2, win[0], win[1], T, sig)
+    assert nnz == len(L["row"])
+    es = np.zeros(L["nstates"])
+    assert ctx.pgb_collision_energies(es) == L["nstates"]
+    assert np.abs(es - L["eps"]).max() < 1e-11
+    f0 = S.pulse_occupations(L["eps"], emin, centre=0.5, width=0.1, amplitude=0.1)
+    f = dev(f0)
+    ctx.pgb_step_rk4(f, 1.0, 1000)
+    rhs = lambda x: O.collision(x, L["eps"], L["row"], L["col"], L["hw"], L["g2"], T, sig, L["nq"])
+    ref = O.evolve(f0, 1.0, 1000, rhs)
+    got = f.cpu().numpy()
+    assert np.abs(got - f0).max() > 1e-2       # it did evolve
+    assert np.abs(got - ref).max() <= 1e-6
+    assert abs(got.sum() - f0.sum()) <= 1e-9 * f0.sum()
 
 
 @pytest.mark.slow
