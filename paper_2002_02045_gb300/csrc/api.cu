@@ -203,6 +203,9 @@ void free_model(pgb_ctx *c) {
     dfree(&c->d_mode_scale);
     dfree(&c->d_g64);
     dfree(&c->d_g32);
+    if (c->d_gsplit) cudaFree(c->d_gsplit);
+    c->d_gsplit = nullptr;
+    c->gsplit_prec = -1;
     dfree(&c->d_Hd);
     dfree(&c->d_polar);
     dfree(&c->d_gvec);
@@ -794,13 +797,19 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
 
     const int per = nm * nw;
     const bool fused = tcp && tc_fused_supported(nw, nm);
+    // BF16x3: the R_e sum on the tensor cores too (k_tc_qsum with the batch's k phases as A
+    // and the split, transposed g~ as B) whenever its column count tiles by 96.  TF32x3 keeps
+    // the FP32 SIMT R_e sum: a second TF32x3 sum put Gamma 1.3e-5 from the oracle on the
+    // reduced fcc case, outside that path's 1e-5 bound.
+    const bool tc_rsum = tcp && !tf32 && nrowS % 96 == 0;
+    const int KpE = tc_kpad(c->nRge);
     const int qpb = std::max(1, 256 / nw);
     const int qiters = 8;
     const int64_t nqblk = fused ? (c->Nq + 127) / 128 : (c->Nq + (int64_t)qpb * qiters - 1) / ((int64_t)qpb * qiters);
     // scratch carve-up, every piece 256-byte aligned (TMA and vector loads)
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     int64_t nbmax = 0;
-    size_t o_S1 = 0, o_G = 0, o_C = 0, o_part = 0, o_gm = 0, o_B = 0, total = 0;
+    size_t o_S1 = 0, o_G = 0, o_C = 0, o_part = 0, o_gm = 0, o_B = 0, o_Ak = 0, total = 0;
     auto layout = [&](int64_t nbm) {
         o_S1 = al((size_t)nbm * c->nRge * es);
         o_G = o_S1 + al((size_t)nbm * nrow * es);
@@ -808,7 +817,8 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
         o_part = o_C + (fused ? 0 : al((size_t)nbm * c->Nq * ncol * es));
         o_gm = o_part + al((size_t)nbm * nqblk * per * sizeof(double));
         o_B = o_gm + al((size_t)nbm * per * sizeof(double));
-        total = o_B + (tcp ? al((size_t)nbm * (fused ? 6 : 4) * ncol * Kp * tes) : 0);
+        o_Ak = o_B + (tcp ? al((size_t)nbm * (fused ? 6 : 4) * ncol * Kp * tes) : 0);
+        total = o_Ak + (tc_rsum ? al((size_t)nbm * 4 * KpE * tes) : 0);
     };
     layout(1);
     const size_t budget = (size_t)4 << 30;
@@ -824,6 +834,7 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
     double *partial = (double *)(base + o_part);
     double *gmode_tmp = (double *)(base + o_gm);
     void *Bsplit = base + o_B;
+    void *Ak = base + o_Ak;
     Tmp<double> focc, nbe;
     Tmp<float> eps32, hw32;
     TRY(focc.alloc(c, (size_t)c->Nk * nw));
@@ -857,6 +868,17 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
             c->asplit_prec = precision;
         }
     }
+    if (tc_rsum && c->gsplit_prec != precision) {
+        if (c->d_gsplit) {
+            PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+            cudaFree(c->d_gsplit);
+            c->d_gsplit = nullptr;
+        }
+        c->gsplit_prec = -1;
+        PGB_CUDA_TRY(c, cudaMalloc(&c->d_gsplit, (size_t)4 * nrowS * KpE * tes));
+        TRY(launch_split_gT(c, tf32, c->nRge, nrowS, KpE, c->d_g64, c->d_gsplit));
+        c->gsplit_prec = precision;
+    }
     const void *g = f32 ? (const void *)c->d_g32 : (const void *)c->d_g64;
     const void *U = f32 ? (const void *)c->d_U32 : (const void *)c->d_U;
     const void *cf = f32 ? (const void *)c->d_coef32 : (const void *)c->d_coef;
@@ -865,8 +887,13 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
         const int64_t nb = std::min<int64_t>(nbmax, nk - b0);
         const int32_t *kb = dk.p + b0;
         prof_mark(c, PGB_PROF_RSUM);
-        TRY(launch_phase_grid(c, c->kg, kb, nb, c->d_Rge, c->nRge, phk, f32));
-        TRY(launch_cgemm(c, f32, 1, nb, nrowS, c->nRge, phk, c->nRge, 0, g, nrowS, 0, S1, nrowS, 0));
+        if (tc_rsum) {
+            TRY(launch_split_phases_pts(c, tf32, c->kg, kb, nb, c->d_Rge, c->nRge, KpE, Ak));
+            TRY(launch_tc_qsum(c, tf32, 1, nb, (int)nrowS, KpE, Ak, c->d_gsplit, (float2 *)S1, c->d_err));
+        } else {
+            TRY(launch_phase_grid(c, c->kg, kb, nb, c->d_Rge, c->nRge, phk, f32));
+            TRY(launch_cgemm(c, f32, 1, nb, nrowS, c->nRge, phk, c->nRge, 0, g, nrowS, 0, S1, nrowS, 0));
+        }
         TRY(launch_fold_u(c, f32, nb, kb, c->nRgp, nm, nw, S1, U, G));
         prof_mark(c, PGB_PROF_RSUM);
         if (fused) {

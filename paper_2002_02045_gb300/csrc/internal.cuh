@@ -88,6 +88,8 @@ struct pgb_ctx {
     float2 *d_phq32 = nullptr;
     void *d_asplit = nullptr;    // [4][Nq][Kp] hi/lo split phases for the tensor-core q-sum
     int asplit_prec = -1;        // precision the split was built for
+    void *d_gsplit = nullptr;    // [4][nRgp*nm*nw*nw][Kp(nRge)] hi/lo split g~, B of the tensor-core R_e sum
+    int gsplit_prec = -1;
     int *d_err = nullptr;        // device error word of the tensor-core kernels
 
     // collision list
@@ -262,6 +264,9 @@ int tc_kpad(int nR);
 bool tc_supported(int ncol);
 pgb_status launch_split_phases(pgb_ctx *c, bool tf32, const int grid[3], int64_t Nq, const int32_t *d_R, int nR,
                                int Kp, void *out, const double2 *L = nullptr, int nL = 0);
+pgb_status launch_split_phases_pts(pgb_ctx *c, bool tf32, const int grid[3], const int32_t *d_pts, int64_t n,
+                                   const int32_t *d_R, int nR, int Kp, void *out);
+pgb_status launch_split_gT(pgb_ctx *c, bool tf32, int nR, int64_t ncol, int Kp, const double2 *g, void *out);
 pgb_status launch_split_g(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out);
 pgb_status launch_split_g6(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out);
 pgb_status launch_tc_qsum(pgb_ctx *c, bool tf32, int64_t nb, int64_t Nq, int ncol, int Kp, void *Asplit,

@@ -223,16 +223,20 @@ template <> struct Split<true> {
 };
 
 // A parts from the exact grid phases: [4][Nq][Kp] = (Re hi, Re lo, Im hi, Im lo), zero for p >= nR.
+// Row r is grid point pts[r] (pts = null: grid point r); the long-range columns
+// (L, nL) belong to the q table only.
 template <bool TF32>
-__global__ void k_split_phases(int n1, int n2, int n3, int64_t Nq, const int32_t *__restrict__ R, int nR, int Kp,
+__global__ void k_split_phases(int n1, int n2, int n3, int64_t Nq, const int32_t *__restrict__ pts,
+                               const int32_t *__restrict__ R, int nR, int Kp,
                                typename Split<TF32>::E *__restrict__ out, const double2 *__restrict__ L, int nL) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= Nq * Kp) return;
-    const int64_t q = t / Kp;
+    const int64_t row = t / Kp;
+    const int64_t q = pts ? (int64_t)pts[row] : row;
     const int p = (int)(t % Kp);
     double c = 0.0, s = 0.0;
     if (p >= nR && p < nR + nL) {   // long-range columns (polar coupling)
-        const double2 v = L[q * nL + (p - nR)];
+        const double2 v = L[row * nL + (p - nR)];
         c = v.x;
         s = v.y;
     } else if (p < nR) {
@@ -306,6 +310,28 @@ __global__ void k_split_g6(int64_t nb, int nR, int ncol, int Kp, const float2 *_
     o[5 * per] = -l;
 }
 
+// B parts of the R_e sum (Eq. eph_mat_wann2, first factor): g~[p][c] (p < nR = R_e,
+// c < ncol = R_p x modes x bands^2) -> [4][ncol][Kp] = (re hi, re lo, im hi, im lo),
+// K = R_e fastest, zero for p >= nR.
+template <bool TF32>
+__global__ void k_split_gT(int nR, int64_t ncol, int Kp, const double2 *__restrict__ g,
+                           typename Split<TF32>::E *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = ncol * Kp;
+    if (t >= per) return;
+    const int64_t c = t / Kp;
+    const int p = (int)(t % Kp);
+    double2 v = make_double2(0.0, 0.0);
+    if (p < nR) v = g[(int64_t)p * ncol + c];
+    typename Split<TF32>::E h, l;
+    Split<TF32>::run(v.x, h, l);
+    out[0 * per + t] = h;
+    out[1 * per + t] = l;
+    Split<TF32>::run(v.y, h, l);
+    out[2 * per + t] = h;
+    out[3 * per + t] = l;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -362,11 +388,36 @@ pgb_status launch_split_phases(pgb_ctx *c, bool tf32, const int grid[3], int64_t
     const unsigned g = (unsigned)((n + 255) / 256);
     if (!L) nL = 0;
     if (tf32)
-        k_split_phases<true><<<g, 256, 0, c->stream>>>(grid[0], grid[1], grid[2], Nq, d_R, nR, Kp, (float *)out, L,
-                                                       nL);
+        k_split_phases<true><<<g, 256, 0, c->stream>>>(grid[0], grid[1], grid[2], Nq, nullptr, d_R, nR, Kp,
+                                                       (float *)out, L, nL);
     else
-        k_split_phases<false><<<g, 256, 0, c->stream>>>(grid[0], grid[1], grid[2], Nq, d_R, nR, Kp,
+        k_split_phases<false><<<g, 256, 0, c->stream>>>(grid[0], grid[1], grid[2], Nq, nullptr, d_R, nR, Kp,
                                                         (__nv_bfloat16 *)out, L, nL);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+pgb_status launch_split_phases_pts(pgb_ctx *c, bool tf32, const int grid[3], const int32_t *d_pts, int64_t n,
+                                   const int32_t *d_R, int nR, int Kp, void *out) {
+    if (n == 0) return PGB_OK;
+    const unsigned g = (unsigned)((n * Kp + 255) / 256);
+    if (tf32)
+        k_split_phases<true><<<g, 256, 0, c->stream>>>(grid[0], grid[1], grid[2], n, d_pts, d_R, nR, Kp,
+                                                       (float *)out, nullptr, 0);
+    else
+        k_split_phases<false><<<g, 256, 0, c->stream>>>(grid[0], grid[1], grid[2], n, d_pts, d_R, nR, Kp,
+                                                        (__nv_bfloat16 *)out, nullptr, 0);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+pgb_status launch_split_gT(pgb_ctx *c, bool tf32, int nR, int64_t ncol, int Kp, const double2 *g, void *out) {
+    const int64_t n = ncol * Kp;
+    const unsigned gr = (unsigned)((n + 255) / 256);
+    if (tf32)
+        k_split_gT<true><<<gr, 256, 0, c->stream>>>(nR, ncol, Kp, g, (float *)out);
+    else
+        k_split_gT<false><<<gr, 256, 0, c->stream>>>(nR, ncol, Kp, g, (__nv_bfloat16 *)out);
     PGB_LAUNCH_CHECK(c);
     return PGB_OK;
 }
