@@ -3,10 +3,12 @@
 // interpolation, rates, collision and RK4 paths.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <map>
 #include <new>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -251,6 +253,41 @@ pgb_status ensure_scratch(pgb_ctx *c, size_t bytes) {
 // ===========================================================================
 // ABI
 // ===========================================================================
+namespace {
+
+// True when none of the n IEEE values at p (bit patterns of width U) has an all-ones
+// exponent (inf or NaN).  Branch-free blocks, split over host threads for the
+// hundreds of megabytes of a g~ table.
+template <typename U, U EXP>
+bool finite_block(const U *p, size_t n) {
+    constexpr size_t B = 4096;
+    for (size_t i0 = 0; i0 < n; i0 += B) {
+        const size_t e = std::min(n, i0 + B);
+        U bad = 0;
+        for (size_t i = i0; i < e; ++i) bad |= (U)((p[i] & EXP) == EXP);
+        if (bad) return false;
+    }
+    return true;
+}
+
+template <typename U, U EXP>
+bool all_finite(const void *x, size_t n) {
+    const U *p = static_cast<const U *>(x);
+    unsigned nt = std::min(16u, std::max(1u, std::thread::hardware_concurrency()));
+    if (n < ((size_t)1 << 22)) nt = 1;
+    std::vector<char> ok(nt, 1);
+    std::vector<std::thread> th;
+    for (unsigned t = 1; t < nt; ++t) {
+        const size_t a = n * t / nt, b = n * (t + 1) / nt;
+        th.emplace_back([&ok, p, a, b, t] { ok[t] = finite_block<U, EXP>(p + a, b - a); });
+    }
+    ok[0] = finite_block<U, EXP>(p, n / nt);
+    for (auto &t : th) t.join();
+    return std::all_of(ok.begin(), ok.end(), [](char v) { return v != 0; });
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *pgb_status_string(int s) {
@@ -379,15 +416,9 @@ pgb_status pgb_set_model(pgb_ctx *c, const pgb_model *m) {
         }
     }
     const size_t ng = (size_t)m->nR_ge * m->nR_gp * nm * nw2;
-    if (m->g_is_double) {
-        const double *g = (const double *)m->g;
-        for (size_t i = 0; i < 2 * ng; ++i)
-            if (!std::isfinite(g[i])) return fail(c, PGB_EINVAL, "set_model: non-finite g");
-    } else {
-        const float *g = (const float *)m->g;
-        for (size_t i = 0; i < 2 * ng; ++i)
-            if (!std::isfinite(g[i])) return fail(c, PGB_EINVAL, "set_model: non-finite g");
-    }
+    const bool g_ok = m->g_is_double ? all_finite<uint64_t, 0x7ff0000000000000ull>(m->g, 2 * ng)
+                                     : all_finite<uint32_t, 0x7f800000u>(m->g, 2 * ng);
+    if (!g_ok) return fail(c, PGB_EINVAL, "set_model: non-finite g");
 
     free_coll(c);
     free_grids(c);

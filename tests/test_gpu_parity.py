@@ -6,6 +6,8 @@ with a 1e-6 max floor).  Per-element |g|^2 is compared only where it is
 gauge invariant: degenerate phonon modes (all three modes of the
 simple-cubic model) are summed first.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -400,7 +402,7 @@ def test_collision_edge_cases(ctx, c1):
         ctx.pgb_build_collision(1, 1, 300.0, 0.01, row, col, mode, np.array([1.0], np.float32))
 
 
-def test_argument_errors(ctx, c1):
+def test_argument_errors(ctx, c1, c2):
     from paper_2002_02045_gb300 import PGB_FP64, PGB_TC_BF16X3, PgbError
     ctx.pgb_set_model(c1)
     with pytest.raises(PgbError):
@@ -417,6 +419,16 @@ def test_argument_errors(ctx, c1):
     bad.H[3, 0, 1] += 0.1
     with pytest.raises(PgbError):
         ctx.pgb_set_model(bad)
+    # a non-finite g~ anywhere in a large table (scanned by several host threads)
+    for pos, val in ((-1, np.nan), (c2.g.size // 3 + 7, np.inf)):
+        badg = dataclasses.replace(c2, g=c2.g.copy())
+        badg.g.reshape(-1)[pos] = val
+        with pytest.raises(PgbError):
+            ctx.pgb_set_model(badg)
+    bad64 = dataclasses.replace(c1, g=c1.g.astype(np.complex128))
+    bad64.g.reshape(-1)[5] = complex(0.0, np.inf)
+    with pytest.raises(PgbError):
+        ctx.pgb_set_model(bad64)
     # empty k list is a no-op
     ctx.pgb_set_model(c1)
     ctx.pgb_set_grids((4, 4, 4), (2, 2, 2))
