@@ -632,6 +632,27 @@ def batched(args, world):
     # algorithmic q-sum work: 8 FLOP per complex multiply-add, nR_p x (nmode nw^2) per (k, q) pair
     flops = sum(BATCH_K * int(np.prod(m.meta["grid"])) * len(m.R_gp) * m.nmode * m.nw ** 2 * 8 for m in models)
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x max clock, TFLOP/s
+    # the same batch with the BF16x3 split: instances whose nmode nw^2 columns tile by 96 take
+    # their R_p sum on the tensor cores, the others stay on the CUDA cores
+    from paper_2002_02045_gb300 import PGB_TC_BF16X3
+    b.pgb_batch_set_precision(PGB_TC_BF16X3)
+    outs_tc = [np.zeros_like(o) for o in outs]
+    t0 = time.perf_counter()
+    b.pgb_batch_rates(ks, T_K, mus, 0.005, outs_tc)
+    t_first_tc = time.perf_counter() - t0
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        b.pgb_batch_rates(ks, T_K, mus, 0.005, outs_tc)
+    dt_tc = max_over_ranks((time.perf_counter() - t0) / reps, world)
+    tc_inst = [m.zstar is None and (m.nmode * m.nw ** 2) % 96 == 0 for m in models]
+    flops_tc = sum(BATCH_K * int(np.prod(m.meta["grid"])) * len(m.R_gp) * m.nmode * m.nw ** 2 * 8
+                   for m, e in zip(models, tc_inst) if e)
+    dev = max(float(np.max(np.abs(x - y) / (np.abs(y) + 1e-6 * np.abs(y).max()))) for x, y in zip(outs_tc, outs))
+    bf16 = {"value": world * pairs / dt_tc, "unit": "pairs/s", "ms_per_call": 1e3 * dt_tc,
+            "first_call_s": t_first_tc, "tensor_core_instances": int(sum(tc_inst)),
+            "tensor_core_flop_share": flops_tc / flops, "tuning": b.pgb_batch_tuning(),
+            "tolerance_vs_fp64": 1e-3, "max_rel_dev_from_fp32_batch": dev}
     b.close()
     for c in ctxs:
         c.close()
@@ -641,7 +662,7 @@ def batched(args, world):
         "instances": args.batch_instances, "k_per_instance": BATCH_K, "first_call_s": t_first,
         "model_generation_s": t_gen, "setup_s": t_setup, "tuning": tun, "finite": finite,
         "timing": "host clock around pgb_batch_rates (graph replay + output copies, synchronised)",
-        "cpu_baseline": cb,
+        "cpu_baseline": cb, "bf16x3": bf16,
         "roofline": {"bound": "alu", "kernel": "k_batch_rates (FP32 SIMT)", "achieved": flops / dt / 1e12,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": flops / dt / 1e12 / fp32_peak,
                      "algorithmic_flop": flops,

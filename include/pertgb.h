@@ -274,13 +274,23 @@ pgb_status pgb_population(pgb_ctx *ctx, const double *f, const double *E, int64_
  * the persistent kernel and the reduction into a CUDA graph; calls with the
  * same arguments replay it.  Results do not depend on the schedule.
  * pgb_batch_tuning: chosen q tile and block size, candidate times (ms, [4],
- * -1 where not run) and graph launches so far (any pointer may be NULL).    */
+ * -1 where not run) and graph launches so far (any pointer may be NULL).
+ * pgb_batch_set_precision: PGB_FP32 (default: every instance's R_p sum on
+ * the CUDA cores, FP32 products) or PGB_TC_BF16X3 / PGB_TC_TF32X3: then every
+ * non-polar instance whose nm*nw*nw columns are a multiple of 96 takes its R_p
+ * sum on the tensor cores (split operands, FP32 accumulators; a tensor-core
+ * pipeline time-out returns PGB_ETIMEOUT), written to a [nk][Nq][nm*nw*nw]
+ * FP32 buffer of the batch (8 bytes per (k, q, column)) that the persistent
+ * kernel's epilogue reads; the others keep the CUDA-core form.  A change
+ * drops the captured graph and the tuning.  Error bound against the FP64
+ * oracle: 1e-3 (BF16x3), 1e-5 (TF32x3 and FP32).  Other values: PGB_EINVAL. */
 typedef struct pgb_batch pgb_batch;
 pgb_status pgb_batch_create(pgb_batch **out, pgb_ctx *const *ctxs, int n);
 pgb_status pgb_batch_rates(pgb_batch *batch, const int32_t *const *k_idx, const int64_t *nk, double T_K,
                            const double *mu_eV, double sigma_eV, double *const *gamma_out);
 pgb_status pgb_batch_tuning(const pgb_batch *batch, int *tile_q, int *threads, float *cand_ms,
                             int64_t *graph_launches);
+pgb_status pgb_batch_set_precision(pgb_batch *batch, int precision);
 const char *pgb_batch_last_error(const pgb_batch *batch);
 void pgb_batch_destroy(pgb_batch *batch);
 

@@ -47,6 +47,7 @@ struct BInst {
     int64_t unit0;             // first unit of this instance
     int nqt;                   // q tiles
     const float2 *phq;         // [Nq][nKp] q table: e^{iq.R_p}, then the long-range columns
+    const float2 *Ctc;         // [nk][Nq][nm*nw*nw] q-sum from the tensor cores, or null (SIMT GEMM here)
     const float2 *G;           // [nk][nKp][nm*nw*nw]
     const int32_t *kidx;       // [nk]
     const double *eps;         // [Nk][nw]
@@ -108,9 +109,18 @@ __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
         const int64_t q0 = (int64_t)qt * QT;
         const int nq = (int)(I.Nq - q0 < QT ? I.Nq - q0 : QT);
         const float2 *Gk = I.G + kb * (int64_t)I.nKp * ncol + (int64_t)n * ncn;
-        for (int o = t; o < QT * ncn; o += NT) Cs[(o / ncn) * a.maxc + o % ncn] = make_float2(0.f, 0.f);
+        if (I.Ctc) {
+            // 1'. the R_p sum came from the tensor cores: copy band n's columns of the tile
+            const float2 *src = I.Ctc + (kb * I.Nq + q0) * ncol + (int64_t)n * ncn;
+            for (int o = t; o < nq * ncn; o += NT) {
+                const int qq = o / ncn, cc = o - (o / ncn) * ncn;
+                Cs[qq * a.maxc + cc] = src[(int64_t)qq * ncol + cc];
+            }
+            __syncthreads();
+        }
+        for (int o = t; o < QT * ncn && !I.Ctc; o += NT) Cs[(o / ncn) * a.maxc + o % ncn] = make_float2(0.f, 0.f);
         // 1. R_p-sum tile; K chunk c + 1 is copied (cp.async) while chunk c is multiplied
-        const int nch = (I.nKp + KC - 1) / KC;
+        const int nch = I.Ctc ? 0 : (I.nKp + KC - 1) / KC;
         auto fill = [&](int c) {
             const int p0 = c * KC;
             float2 *Ab = As + (c & 1) * QT * KC, *Bb = Bs + (c & 1) * KC * a.maxc;
@@ -324,6 +334,8 @@ struct pgb_batch {
     int nsm = 0;
     int maxc = 0;
     int cand = -1;                     // chosen candidate
+    int prec = PGB_FP32;          // q-sum precision of the instances whose columns tile by 96
+    int *d_err = nullptr;              // wait time-outs of the tensor-core q-sums
     float cand_ms[4] = {-1, -1, -1, -1};
     int per_sm[4] = {0, 0, 0, 0};      // resident CTAs per SM of each candidate
     int64_t graph_launches = 0;
@@ -375,12 +387,20 @@ struct Plan {
         void *phk, *S1, *G;
         double *focc, *nbe;
         float *eps32, *hw32;
+        bool tc = false;               // q sum on the tensor cores (k_tc_qsum)
+        int Kp = 0;
+        void *Asplit = nullptr, *Bsplit = nullptr;
+        float2 *Ctc = nullptr;
     };
     std::vector<Per> per;
 };
 
 pgb_status enqueue(pgb_batch *b, Plan &P, int ci) {
     const int n = (int)b->ctx.size();
+    if (b->prec != PGB_FP32 && cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream) != cudaSuccess) {
+        b->err = "batch: error word reset failed";
+        return PGB_ECUDA;
+    }
     for (int i = 0; i < n; ++i) {
         pgb_ctx *c = b->ctx[i];
         cudaStream_t saved = c->stream;
@@ -394,6 +414,12 @@ pgb_status enqueue(pgb_batch *b, Plan &P, int ci) {
         if (st == PGB_OK)
             st = launch_cgemm(c, true, 1, nk, nrowS, c->nRge, q.phk, c->nRge, 0, c->d_g32, nrowS, 0, q.S1, nrowS, 0);
         if (st == PGB_OK) st = launch_fold_u(c, true, nk, q.kidx, c->nRgp, c->nm, c->nw, q.S1, c->d_U32, q.G);
+        if (st == PGB_OK && q.tc) {
+            const bool tf32 = b->prec == PGB_TC_TF32X3;
+            st = launch_split_g(c, tf32, nk, c->nKp, (int)ncol, q.Kp, q.G, q.Bsplit);
+            if (st == PGB_OK)
+                st = launch_tc_qsum(c, tf32, nk, c->Nq, (int)ncol, q.Kp, q.Asplit, q.Bsplit, q.Ctc, b->d_err);
+        }
         c->stream = saved;
         if (st != PGB_OK) {
             b->err = "batch: set-up of instance " + std::to_string(i) + ": " + c->err;
@@ -474,9 +500,31 @@ pgb_status build_plan(pgb_batch *b, Plan &P, int qt) {
         if ((st = balloc(b, &q.eps32, (size_t)c->Nk * c->nw)) != PGB_OK) return st;
         if ((st = balloc(b, &q.nbe, (size_t)c->Nq * c->nm)) != PGB_OK) return st;
         if ((st = balloc(b, &q.hw32, (size_t)c->Nq * c->nm)) != PGB_OK) return st;
-        float2 *phq;
-        if ((st = balloc(b, &phq, (size_t)c->Nq * c->nKp)) != PGB_OK) return st;
-        {   // q table, independent of the call's arguments: built here, outside any capture
+        // non-polar instances whose nm*nw*nw columns tile by 96 take the tensor-core q sum
+        // when the batch runs in a split precision
+        q.tc = b->prec != PGB_FP32 && !c->polar && ncol % 96 == 0 && nk > 0;
+        float2 *phq = nullptr;
+        if (q.tc) {
+            const bool tf32 = b->prec == PGB_TC_TF32X3;
+            const size_t tes = tf32 ? 4 : 2;
+            q.Kp = tc_kpad(c->nKp);
+            char *As, *Bs;
+            if ((st = balloc(b, &As, (size_t)4 * c->Nq * q.Kp * tes)) != PGB_OK) return st;
+            if ((st = balloc(b, &Bs, (size_t)nk * 4 * ncol * q.Kp * tes)) != PGB_OK) return st;
+            if ((st = balloc(b, &q.Ctc, (size_t)nk * c->Nq * ncol)) != PGB_OK) return st;
+            q.Asplit = As;
+            q.Bsplit = Bs;
+            cudaStream_t saved = c->stream;   // split q phases: outside any capture
+            c->stream = b->stream;
+            st = launch_split_phases(c, tf32, c->qg, c->Nq, c->d_Rgp, c->nRgp, q.Kp, q.Asplit);
+            c->stream = saved;
+            if (st != PGB_OK || cudaStreamSynchronize(b->stream) != cudaSuccess) {
+                b->err = "batch: split q phases of instance " + std::to_string(i) + " failed";
+                return PGB_ECUDA;
+            }
+        } else {
+            if ((st = balloc(b, &phq, (size_t)c->Nq * c->nKp)) != PGB_OK) return st;
+            // q table, independent of the call's arguments: built here, outside any capture
             cudaStream_t saved = c->stream;
             c->stream = b->stream;
             st = launch_qtable_grid(c, nullptr, c->Nq, phq, true);
@@ -487,6 +535,7 @@ pgb_status build_plan(pgb_batch *b, Plan &P, int qt) {
             }
         }
         I.phq = phq;
+        I.Ctc = q.Ctc;
         I.eps32 = q.eps32;
         I.hw32 = q.hw32;
         I.G = (const float2 *)G;
@@ -546,6 +595,12 @@ pgb_status pgb_batch_create(pgb_batch **out, pgb_ctx *const *ctxs, int n) {
         delete b;
         return PGB_ECUDA;
     }
+    if (cudaMalloc((void **)&b->d_err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamDestroy(b->stream);
+        delete b;
+        return PGB_ENOMEM;
+    }
     for (int i = 0; i < n; ++i) b->maxc = std::max(b->maxc, ctxs[i]->nm * ctxs[i]->nw);
     for (int ci = 0; ci < 4; ++ci) {
         b->per_sm[ci] = 0;
@@ -564,8 +619,33 @@ void pgb_batch_destroy(pgb_batch *b) {
     cudaSetDevice(b->device);
     cudaStreamSynchronize(b->stream);
     b->release();
+    if (b->d_err) cudaFree(b->d_err);
     cudaStreamDestroy(b->stream);
     delete b;
+}
+
+pgb_status pgb_batch_set_precision(pgb_batch *b, int precision) {
+    if (!b) return PGB_EINVAL;
+    if (precision != PGB_FP32 && precision != PGB_TC_BF16X3 && precision != PGB_TC_TF32X3) {
+        b->err = "batch_set_precision: PGB_FP32, PGB_TC_BF16X3 or PGB_TC_TF32X3";
+        return PGB_EINVAL;
+    }
+    if (precision == b->prec) return PGB_OK;
+    cudaSetDevice(b->device);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return PGB_ECUDA;
+    if (precision != PGB_FP32) {   // function attributes are set here, outside any capture
+        const pgb_status st = tc_qsum_prepare(b->ctx[0], precision == PGB_TC_TF32X3);
+        if (st != PGB_OK) {
+            b->err = "batch_set_precision: " + b->ctx[0]->err;
+            return st;
+        }
+    }
+    b->release();                        // the next call plans, tunes and captures again
+    b->kidx.clear();
+    b->prec = precision;
+    b->cand = -1;
+    for (float &m : b->cand_ms) m = -1.f;
+    return PGB_OK;
 }
 
 const char *pgb_batch_last_error(const pgb_batch *b) { return b ? b->err.c_str() : "null batch"; }
@@ -695,6 +775,14 @@ pgb_status pgb_batch_rates(pgb_batch *b, const int32_t *const *k_idx, const int6
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
         b->err = "batch_rates: execution failed";
         return PGB_ECUDA;
+    }
+    if (b->prec != PGB_FP32) {
+        int herr = 0;
+        if (cudaMemcpy(&herr, b->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PGB_ECUDA;
+        if (herr) {
+            b->err = "batch_rates: a tensor-core pipeline wait ran out (bits " + std::to_string(herr) + ")";
+            return PGB_ETIMEOUT;
+        }
     }
     return PGB_OK;
 }

@@ -271,6 +271,7 @@ pgb_status launch_split_g(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, i
 pgb_status launch_split_g6(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out);
 pgb_status launch_tc_qsum(pgb_ctx *c, bool tf32, int64_t nb, int64_t Nq, int ncol, int Kp, void *Asplit,
                           void *Bsplit, float2 *C, int *d_err);
+pgb_status tc_qsum_prepare(pgb_ctx *c, bool tf32);
 
 // fused tensor-core rates (tc_rates.cu)
 struct FusedLaunch {

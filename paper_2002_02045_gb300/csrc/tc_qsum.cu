@@ -21,6 +21,7 @@
 // 2-5 read the two 96-column accumulators (re, im) and store C.
 #include <cstdio>
 #include <mutex>
+#include <vector>
 
 #include <cudaTypedefs.h>
 
@@ -471,14 +472,32 @@ pgb_status launch_tc_qsum(pgb_ctx *c, bool tf32, int64_t nb, int64_t Nq, int nco
     a.C = C;
     a.err = d_err;
     dim3 grid((unsigned)(ncol / BN), (unsigned)((Nq + BM - 1) / BM), (unsigned)nb);
-    if (tf32) {
-        PGB_CUDA_TRY(c, cudaFuncSetAttribute(k_tc_qsum<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    const pgb_status pst = tc_qsum_prepare(c, tf32);
+    if (pst != PGB_OK) return pst;
+    if (tf32)
         k_tc_qsum<true><<<grid, 192, SMEM_BYTES, c->stream>>>(tA, tB, a);
-    } else {
-        PGB_CUDA_TRY(c, cudaFuncSetAttribute(k_tc_qsum<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    else
         k_tc_qsum<false><<<grid, 192, SMEM_BYTES, c->stream>>>(tA, tB, a);
-    }
     PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+// Shared-memory limit of k_tc_qsum on the context's device, set once per device and
+// form (so that launches under stream capture need no attribute call).
+pgb_status tc_qsum_prepare(pgb_ctx *c, bool tf32) {
+    static std::mutex mu;
+    static std::vector<char> done[2];
+    std::lock_guard<std::mutex> lock(mu);
+    std::vector<char> &d = done[tf32 ? 1 : 0];
+    if (c->device >= 0 && (size_t)c->device < d.size() && d[c->device]) return PGB_OK;
+    if (tf32)
+        PGB_CUDA_TRY(c, cudaFuncSetAttribute(k_tc_qsum<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    else
+        PGB_CUDA_TRY(c, cudaFuncSetAttribute(k_tc_qsum<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    if (c->device >= 0) {
+        if ((size_t)c->device >= d.size()) d.resize(c->device + 1, 0);
+        d[c->device] = 1;
+    }
     return PGB_OK;
 }
 

@@ -32,7 +32,8 @@ ABI_SYMBOLS = (
     "pgb_collision_set_g2", "pgb_collision_vjp", "pgb_rk4_adjoint",
     "pgb_set_lattice", "pgb_set_polar", "pgb_long_range_g", "pgb_band_velocities", "pgb_transport",
     "pgb_scattering_rates_mc", "pgb_population",
-    "pgb_batch_create", "pgb_batch_rates", "pgb_batch_tuning", "pgb_batch_last_error", "pgb_batch_destroy",
+    "pgb_batch_create", "pgb_batch_rates", "pgb_batch_tuning", "pgb_batch_set_precision", "pgb_batch_last_error",
+    "pgb_batch_destroy",
 )
 PGB_Q_UNIFORM, PGB_Q_CAUCHY = 0, 1
 PGB_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH):
         "pgb_batch_create": (I, [C.POINTER(P), P, I]),
         "pgb_batch_rates": (I, [P, P, P, D, P, D, P]),
         "pgb_batch_tuning": (I, [P, C.POINTER(I), C.POINTER(I), P, C.POINTER(I64)]),
+        "pgb_batch_set_precision": (I, [P, I]),
         "pgb_batch_last_error": (C.c_char_p, [P]),
         "pgb_batch_destroy": (None, [P]),
         "pgb_launch_count": (I64, [P]),
@@ -379,6 +381,11 @@ class Batch:
         op = (C.c_void_p * n)(*[_ptr(o) for o in outs])
         st = self.lib.pgb_batch_rates(self._h, kp, nk, float(T), mu, float(sigma), op)
         if st != PGB_OK:
+            raise PgbError(st, self.lib.pgb_batch_last_error(self._h).decode())
+
+    def pgb_batch_set_precision(self, precision):
+        st = self.lib.pgb_batch_set_precision(self._h, int(precision))
+        if st != 0:
             raise PgbError(st, self.lib.pgb_batch_last_error(self._h).decode())
 
     def pgb_batch_tuning(self):

@@ -84,3 +84,34 @@ def test_batch_argument_errors(members):
     with pytest.raises(PgbError):
         b.pgb_batch_rates(ks[:2], -1.0, mus[:2], SIG, outs)
     b.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-3), ("tf32x3", 1e-5)])
+def test_batch_tensor_core_route(members, prec, tol):
+    """With a split precision the instances whose nm*nw*nw columns tile by 96
+    (four of the six random ones here) take the R_p sum on the tensor cores;
+    the rest, and the polar instance, keep the CUDA-core form in the same graph."""
+    from paper_2002_02045_gb300 import Batch, PGB_FP32, PRECISIONS, PgbError
+    models, ctxs, ks, mus = members
+    eligible = [m.zstar is None and (3 * len(m.mass) * m.nw ** 2) % 96 == 0 for m in models]
+    assert 0 < sum(eligible) < len(models)
+    b = Batch(ctxs)
+    with pytest.raises(PgbError):
+        b.pgb_batch_set_precision(99)
+    b.pgb_batch_set_precision(PRECISIONS[prec])
+    outs = [np.zeros((len(k), m.nw)) for k, m in zip(ks, models)]
+    b.pgb_batch_rates(ks, T, mus, SIG, outs)
+    for i, (m, k, mu) in enumerate(zip(models, ks, mus)):
+        ref = O.scattering_rates_grid(m, GRID, GRID, k, T, mu, SIG)
+        assert_rates_close(outs[i], ref, tol, label=f"batch {prec} vs oracle {i}")
+        assert np.abs(outs[i]).max() > 0
+    # replay is bit for bit; back to FP32 re-plans and re-tunes
+    outs2 = [np.zeros_like(o) for o in outs]
+    b.pgb_batch_rates(ks, T, mus, SIG, outs2)
+    assert all(np.array_equal(x, y) for x, y in zip(outs, outs2))
+    b.pgb_batch_set_precision(PGB_FP32)
+    outs3 = [np.zeros_like(o) for o in outs]
+    b.pgb_batch_rates(ks, T, mus, SIG, outs3)
+    for i in range(len(models)):
+        assert_rates_close(outs3[i], outs[i], max(tol, 1e-5), label=f"fp32 vs {prec} {i}")
+    b.close()
