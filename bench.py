@@ -632,8 +632,8 @@ def batched(args, world):
     # algorithmic q-sum work: 8 FLOP per complex multiply-add, nR_p x (nmode nw^2) per (k, q) pair
     flops = sum(BATCH_K * int(np.prod(m.meta["grid"])) * len(m.R_gp) * m.nmode * m.nw ** 2 * 8 for m in models)
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x max clock, TFLOP/s
-    # the same batch with the BF16x3 split: instances whose nmode nw^2 columns tile by 96 take
-    # their R_p sum on the tensor cores, the others stay on the CUDA cores
+    # the same batch with the BF16x3 split: every (non-polar) instance takes its R_p sum on
+    # the tensor cores
     from paper_2002_02045_gb300 import PGB_TC_BF16X3
     b.pgb_batch_set_precision(PGB_TC_BF16X3)
     outs_tc = [np.zeros_like(o) for o in outs]
@@ -645,7 +645,7 @@ def batched(args, world):
     for _ in range(reps):
         b.pgb_batch_rates(ks, T_K, mus, 0.005, outs_tc)
     dt_tc = max_over_ranks((time.perf_counter() - t0) / reps, world)
-    tc_inst = [m.zstar is None and (m.nmode * m.nw ** 2) % 96 == 0 for m in models]
+    tc_inst = [m.zstar is None for m in models]
     flops_tc = sum(BATCH_K * int(np.prod(m.meta["grid"])) * len(m.R_gp) * m.nmode * m.nw ** 2 * 8
                    for m, e in zip(models, tc_inst) if e)
     dev = max(float(np.max(np.abs(x - y) / (np.abs(y) + 1e-6 * np.abs(y).max()))) for x, y in zip(outs_tc, outs))

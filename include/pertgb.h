@@ -277,11 +277,12 @@ pgb_status pgb_population(pgb_ctx *ctx, const double *f, const double *E, int64_
  * -1 where not run) and graph launches so far (any pointer may be NULL).
  * pgb_batch_set_precision: PGB_FP32 (default: every instance's R_p sum on
  * the CUDA cores, FP32 products) or PGB_TC_BF16X3 / PGB_TC_TF32X3: then every
- * non-polar instance whose nm*nw*nw columns are a multiple of 96 takes its R_p
- * sum on the tensor cores (split operands, FP32 accumulators; a tensor-core
- * pipeline time-out returns PGB_ETIMEOUT), written to a [nk][Nq][nm*nw*nw]
- * FP32 buffer of the batch (8 bytes per (k, q, column)) that the persistent
- * kernel's epilogue reads; the others keep the CUDA-core form.  A change
+ * non-polar instance takes its R_p sum on the tensor cores (split operands,
+ * FP32 accumulators, nm*nw*nw columns padded with zeros to a multiple of 96; a
+ * tensor-core pipeline time-out returns PGB_ETIMEOUT), written to a
+ * [nk][Nq][padded columns] FP32 buffer of the batch (8 bytes per entry) that
+ * the persistent kernel's epilogue reads; polar instances keep the CUDA-core
+ * form.  A change
  * drops the captured graph and the tuning.  Error bound against the FP64
  * oracle: 1e-3 (BF16x3), 1e-5 (TF32x3 and FP32).  Other values: PGB_EINVAL. */
 typedef struct pgb_batch pgb_batch;

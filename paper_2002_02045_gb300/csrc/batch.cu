@@ -47,7 +47,8 @@ struct BInst {
     int64_t unit0;             // first unit of this instance
     int nqt;                   // q tiles
     const float2 *phq;         // [Nq][nKp] q table: e^{iq.R_p}, then the long-range columns
-    const float2 *Ctc;         // [nk][Nq][nm*nw*nw] q-sum from the tensor cores, or null (SIMT GEMM here)
+    const float2 *Ctc;         // [nk][Nq][ldc] q-sum from the tensor cores, or null (SIMT GEMM here)
+    int ldc;                   // nm*nw*nw rounded up to a multiple of 96
     const float2 *G;           // [nk][nKp][nm*nw*nw]
     const int32_t *kidx;       // [nk]
     const double *eps;         // [Nk][nw]
@@ -111,10 +112,10 @@ __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
         const float2 *Gk = I.G + kb * (int64_t)I.nKp * ncol + (int64_t)n * ncn;
         if (I.Ctc) {
             // 1'. the R_p sum came from the tensor cores: copy band n's columns of the tile
-            const float2 *src = I.Ctc + (kb * I.Nq + q0) * ncol + (int64_t)n * ncn;
+            const float2 *src = I.Ctc + (kb * I.Nq + q0) * I.ldc + (int64_t)n * ncn;
             for (int o = t; o < nq * ncn; o += NT) {
                 const int qq = o / ncn, cc = o - (o / ncn) * ncn;
-                Cs[qq * a.maxc + cc] = src[(int64_t)qq * ncol + cc];
+                Cs[qq * a.maxc + cc] = src[(int64_t)qq * I.ldc + cc];
             }
             __syncthreads();
         }
@@ -388,7 +389,7 @@ struct Plan {
         double *focc, *nbe;
         float *eps32, *hw32;
         bool tc = false;               // q sum on the tensor cores (k_tc_qsum)
-        int Kp = 0;
+        int Kp = 0, ldc = 0;
         void *Asplit = nullptr, *Bsplit = nullptr;
         float2 *Ctc = nullptr;
     };
@@ -416,9 +417,9 @@ pgb_status enqueue(pgb_batch *b, Plan &P, int ci) {
         if (st == PGB_OK) st = launch_fold_u(c, true, nk, q.kidx, c->nRgp, c->nm, c->nw, q.S1, c->d_U32, q.G);
         if (st == PGB_OK && q.tc) {
             const bool tf32 = b->prec == PGB_TC_TF32X3;
-            st = launch_split_g(c, tf32, nk, c->nKp, (int)ncol, q.Kp, q.G, q.Bsplit);
+            st = launch_split_g(c, tf32, nk, c->nKp, (int)ncol, q.Kp, q.G, q.Bsplit, q.ldc);
             if (st == PGB_OK)
-                st = launch_tc_qsum(c, tf32, nk, c->Nq, (int)ncol, q.Kp, q.Asplit, q.Bsplit, q.Ctc, b->d_err);
+                st = launch_tc_qsum(c, tf32, nk, c->Nq, q.ldc, q.Kp, q.Asplit, q.Bsplit, q.Ctc, b->d_err);
         }
         c->stream = saved;
         if (st != PGB_OK) {
@@ -500,18 +501,19 @@ pgb_status build_plan(pgb_batch *b, Plan &P, int qt) {
         if ((st = balloc(b, &q.eps32, (size_t)c->Nk * c->nw)) != PGB_OK) return st;
         if ((st = balloc(b, &q.nbe, (size_t)c->Nq * c->nm)) != PGB_OK) return st;
         if ((st = balloc(b, &q.hw32, (size_t)c->Nq * c->nm)) != PGB_OK) return st;
-        // non-polar instances whose nm*nw*nw columns tile by 96 take the tensor-core q sum
-        // when the batch runs in a split precision
-        q.tc = b->prec != PGB_FP32 && !c->polar && ncol % 96 == 0 && nk > 0;
+        // non-polar instances take the tensor-core q sum when the batch runs in a split
+        // precision, their nm*nw*nw columns padded with zeros to a multiple of 96
+        q.tc = b->prec != PGB_FP32 && !c->polar && nk > 0;
         float2 *phq = nullptr;
         if (q.tc) {
             const bool tf32 = b->prec == PGB_TC_TF32X3;
             const size_t tes = tf32 ? 4 : 2;
             q.Kp = tc_kpad(c->nKp);
+            q.ldc = (int)((ncol + 95) / 96 * 96);
             char *As, *Bs;
             if ((st = balloc(b, &As, (size_t)4 * c->Nq * q.Kp * tes)) != PGB_OK) return st;
-            if ((st = balloc(b, &Bs, (size_t)nk * 4 * ncol * q.Kp * tes)) != PGB_OK) return st;
-            if ((st = balloc(b, &q.Ctc, (size_t)nk * c->Nq * ncol)) != PGB_OK) return st;
+            if ((st = balloc(b, &Bs, (size_t)nk * 4 * q.ldc * q.Kp * tes)) != PGB_OK) return st;
+            if ((st = balloc(b, &q.Ctc, (size_t)nk * c->Nq * q.ldc)) != PGB_OK) return st;
             q.Asplit = As;
             q.Bsplit = Bs;
             cudaStream_t saved = c->stream;   // split q phases: outside any capture
@@ -536,6 +538,7 @@ pgb_status build_plan(pgb_batch *b, Plan &P, int qt) {
         }
         I.phq = phq;
         I.Ctc = q.Ctc;
+        I.ldc = q.ldc;
         I.eps32 = q.eps32;
         I.hw32 = q.hw32;
         I.G = (const float2 *)G;

@@ -267,7 +267,8 @@ pgb_status launch_split_phases(pgb_ctx *c, bool tf32, const int grid[3], int64_t
 pgb_status launch_split_phases_pts(pgb_ctx *c, bool tf32, const int grid[3], const int32_t *d_pts, int64_t n,
                                    const int32_t *d_R, int nR, int Kp, void *out);
 pgb_status launch_split_gT(pgb_ctx *c, bool tf32, int nR, int64_t ncol, int Kp, const double2 *g, void *out);
-pgb_status launch_split_g(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out);
+pgb_status launch_split_g(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out,
+                          int ncol_pad = 0);
 pgb_status launch_split_g6(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out);
 pgb_status launch_tc_qsum(pgb_ctx *c, bool tf32, int64_t nb, int64_t Nq, int ncol, int Kp, void *Asplit,
                           void *Bsplit, float2 *C, int *d_err);

@@ -262,9 +262,10 @@ __global__ void k_split_phases(int n1, int n2, int n3, int64_t Nq, const int32_t
     out[3 * part + t] = l;
 }
 
-// B parts of one k-batch: G[b][p][c] (FP32 complex) -> [b][4][ncol][Kp].
+// B parts of one k-batch: G[b][p][c] (FP32 complex, ncol_in columns) -> [b][4][ncol][Kp],
+// zero in the padding columns c >= ncol_in.
 template <bool TF32>
-__global__ void k_split_g(int64_t nb, int nR, int ncol, int Kp, const float2 *__restrict__ G,
+__global__ void k_split_g(int64_t nb, int nR, int ncol_in, int ncol, int Kp, const float2 *__restrict__ G,
                           typename Split<TF32>::E *__restrict__ out) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t per = (int64_t)ncol * Kp;
@@ -274,7 +275,7 @@ __global__ void k_split_g(int64_t nb, int nR, int ncol, int Kp, const float2 *__
     const int c = (int)(r / Kp);
     const int p = (int)(r % Kp);
     float2 v = make_float2(0.f, 0.f);
-    if (p < nR) v = G[(b * nR + p) * ncol + c];
+    if (p < nR && c < ncol_in) v = G[(b * nR + p) * ncol_in + c];
     typename Split<TF32>::E h, l;
     typename Split<TF32>::E *o = out + b * 4 * per + r;
     Split<TF32>::run((double)v.x, h, l);
@@ -423,14 +424,17 @@ pgb_status launch_split_gT(pgb_ctx *c, bool tf32, int nR, int64_t ncol, int Kp, 
     return PGB_OK;
 }
 
-pgb_status launch_split_g(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out) {
-    const int64_t n = nb * (int64_t)ncol * Kp;
+pgb_status launch_split_g(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out,
+                          int ncol_pad) {
+    const int ncol_out = ncol_pad > ncol ? ncol_pad : ncol;
+    const int64_t n = nb * (int64_t)ncol_out * Kp;
     if (n == 0) return PGB_OK;
     const unsigned g = (unsigned)((n + 255) / 256);
     if (tf32)
-        k_split_g<true><<<g, 256, 0, c->stream>>>(nb, nR, ncol, Kp, (const float2 *)G, (float *)out);
+        k_split_g<true><<<g, 256, 0, c->stream>>>(nb, nR, ncol, ncol_out, Kp, (const float2 *)G, (float *)out);
     else
-        k_split_g<false><<<g, 256, 0, c->stream>>>(nb, nR, ncol, Kp, (const float2 *)G, (__nv_bfloat16 *)out);
+        k_split_g<false><<<g, 256, 0, c->stream>>>(nb, nR, ncol, ncol_out, Kp, (const float2 *)G,
+                                                   (__nv_bfloat16 *)out);
     PGB_LAUNCH_CHECK(c);
     return PGB_OK;
 }
