@@ -12,6 +12,10 @@
 //      current one is multiplied), from the instance's FP32 q table (exact grid
 //      phases and, for polar models, the long-range columns; built once per
 //      plan) and the G_k rows of band n, which are contiguous (column order n, ka, i);
+//      in a split precision (BF16x3 / TF32x3) the non-polar instances' R_p sums
+//      come from the tensor cores instead (k_tc_qsum on split operands, inside
+//      the same graph, columns padded to a multiple of 96) and the unit copies
+//      its band's columns of that result;
 //   2. runs the rates epilogue on the tile: screen every (q, nu) against the
 //      (m) with |x| <= 7 sigma, list the live pairs in order, then one live pair
 //      per thread: project on nu, rotate by U(k+q), Gaussian weights with FP64
