@@ -58,7 +58,7 @@ struct BInst {
     const double *eps;         // [Nk][nw]
     const float *eps32;        // [Nk][nw] FP32 copy for the screen
     const float *hw32;         // [Nq][nm] FP32 copy for the screen
-    const float2 *U;           // [Nk][nw][nw], U[i][n]
+    const float2 *U;           // [Nk][nw][nw] transposed: U[k][m][i] = U_im(k) (row m contiguous)
     const float2 *coef;        // [Nq][nm][nm]
     const double *hw;          // [Nq][nm]
     const double *focc;        // [Nk][nw]
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
                 float2 g = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int i = 0; i < kMaxNw; ++i)
-                    if (i < nw) cfma_conj(g, Ukq[i * nw + m], gv[i]);
+                    if (i < nw) cfma_conj(g, Ukq[m * nw + i], gv[i]);
                 const float g2 = cabs2(g);
                 const double d = en - em[m];
                 const double ye = (d - w) * is, ya = (d + w) * is;
@@ -271,6 +271,17 @@ __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
             a.partial[u] = s;
         }
     }
+}
+
+// UT[k][m][i] = U[k][i][m]: the epilogue reads one final band m of U(k+q) per
+// surviving term, so its nw values sit in two or four 32-byte sectors
+__global__ void k_transpose_u(int64_t nk, int nw, const float2 *__restrict__ U, float2 *__restrict__ UT) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)nw * nw;
+    if (t >= nk * per) return;
+    const int64_t k = t / per;
+    const int r = (int)(t % per), m = r / nw, i = r % nw;
+    UT[t] = U[k * per + (int64_t)i * nw + m];
 }
 
 // Gamma rows: out[row] = scale * sum_qt partial[row * nqt + qt] for the rows of one instance
@@ -483,7 +494,6 @@ pgb_status build_plan(pgb_batch *b, Plan &P, int qt) {
         I.unit0 = unit0;
 
         I.eps = c->d_eps;
-        I.U = c->d_U32;
         I.coef = c->d_coef32;
         I.hw = c->d_hw;
         I.sigma = b->sigma;
@@ -539,6 +549,17 @@ pgb_status build_plan(pgb_batch *b, Plan &P, int qt) {
                 b->err = "batch: q table of instance " + std::to_string(i) + " failed";
                 return PGB_ECUDA;
             }
+        }
+        {   // transposed U table of the instance's k grid, outside any capture
+            float2 *UT;
+            if ((st = balloc(b, &UT, (size_t)c->Nk * c->nw * c->nw)) != PGB_OK) return st;
+            const int64_t nt = c->Nk * c->nw * c->nw;
+            k_transpose_u<<<div_up(nt, 256), 256, 0, b->stream>>>(c->Nk, c->nw, c->d_U32, UT);
+            if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess) {
+                b->err = "batch: U transpose of instance " + std::to_string(i) + " failed";
+                return PGB_ECUDA;
+            }
+            I.U = UT;
         }
         I.phq = phq;
         I.Ctc = q.Ctc;
