@@ -34,10 +34,11 @@ KGRID = (40, 40, 40)
 T_K, SIGMA, WIN = 300.0, 0.010, 0.3
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu captures
-# summarised in profiles/k_tc_rates_bf16x3_fcc40.md and profiles/k_collision_rk4_30cubed.md.
-# Set an entry to None whenever its kernel changes after the capture.
-TRAFFIC = {"k_tc_rates_bf16x3_bytes_per_pair": (1.139146e9 + 23.311e6) / (64 * 64000),
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of work from one
+# ncu capture of each kernel: the fused rates kernel on 64 window k x 40^3 q, the
+# collision kernel on the 30^3 list.  An entry is None while its kernel has changed
+# since the capture.
+TRAFFIC = {"k_tc_rates_bf16x3_bytes_per_pair": None,
            "k_collision_bytes_per_entry": (383152384 + 3583744) / 31890730}
 
 
@@ -111,22 +112,33 @@ def max_over_ranks(x, world):
     return _m(x)
 
 
-def cpu_baseline(model, n_k=2):
-    """The FP64 oracle as it stands on a bounded sample: n_k window k-points x all 40^3 q."""
+def cpu_baseline(model, n_k=2, with_result=False):
+    """The FP64 oracle as it stands on a bounded sample: n_k window k-points x all 40^3 q.
+    With with_result, also returns the sampled k-grid indices and their oracle Gamma."""
     from oracle import eph as O
     import synthetic as S
     t0 = time.perf_counter()
     pts = S.mp_grid(*KGRID)
     eps, _ = O.bands(model, pts)
     emin = eps.min()
-    win = np.nonzero(((eps >= emin) & (eps <= emin + WIN)).any(1))[0]
+    # k-points with a band strictly inside the window (not on an edge to rounding)
+    win = np.nonzero(((eps >= emin + 1e-9) & (eps <= emin + WIN - 1e-9)).any(1))[0]
     sample = win[np.linspace(0, len(win) - 1, n_k).astype(int)]
-    O.scattering_rates_grid(model, KGRID, KGRID, sample, T_K, emin - WIN, SIGMA, q_chunk=16000)
+    ref = O.scattering_rates_grid(model, KGRID, KGRID, sample, T_K, emin - WIN, SIGMA, q_chunk=16000)
     dt = time.perf_counter() - t0
     nq = int(np.prod(KGRID))
-    return {"value": n_k * nq / dt, "unit": "pairs/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+    info = {"value": n_k * nq / dt, "unit": "pairs/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
             "sample": f"{n_k} window k-points x {nq} q (FP64 NumPy oracle, band interpolation of the 40^3 grid "
                       f"included), {dt:.1f} s"}
+    if with_result:
+        return info, sample.astype(np.int32), ref, emin - WIN
+    return info
+
+
+def rel_err(got, ref):
+    """max over states of |got - ref| / (|ref| + 1e-6 max|ref|): the norm of the parity tests."""
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    return float(np.max(np.abs(got - ref) / (np.abs(ref) + 1e-6 * np.abs(ref).max())))
 
 
 def cpu_baseline_list(ctx, grid, nnz, es, f, n_sample=4_000_000):
@@ -259,10 +271,15 @@ def run_ours(args, rank, world, local):
     peaks, peak_src = load_peaks()
     flop_per_pair = 8.0 * len(model.R_gp) * model.nmode * model.nw ** 2
     achieved = flop_per_pair * pairs * args.steps / (q_ms * 1e-3) / 1e12
+    peak_burst = None
     if args.precision in ("bf16x3", "tf32x3"):
-        peak = peaks["bf16_tflops"] * (1.0 if args.precision == "bf16x3" else 0.5)
-        roof = {"bound": "tensor", "peak_source": f"{peak_src} bf16" + (" x 1/2 (tf32 nominal ratio)"
-                                                                        if args.precision == "tf32x3" else "")}
+        # the timed loop runs for seconds under the power cap: the sustained peak applies
+        ratio = 1.0 if args.precision == "bf16x3" else 0.5
+        peak = peaks["bf16_tflops_sustained"] * ratio
+        peak_burst = peaks["bf16_tflops"] * ratio
+        roof = {"bound": "tensor",
+                "peak_source": f"{peak_src} bf16 sustained (seconds-long loop under the power cap)" +
+                               (" x 1/2 (tf32 nominal ratio)" if args.precision == "tf32x3" else "")}
     else:
         lanes = FP32_LANES if args.precision == "fp32" else 2   # FP64 units per SM on GB300 are few
         peak = SM_COUNT * lanes * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -277,6 +294,9 @@ def run_ours(args, rank, world, local):
                  "algorithmic_flop_per_pair": flop_per_pair, "launches": q_n,
                  "pairs_per_launch": pairs * args.steps / max(1, q_n),
                  "issued_mma_achieved": achieved * issue, "issued_mma_frac": achieved * issue / peak})
+    if peak_burst:
+        roof.update({"peak_burst": peak_burst, "frac_of_burst": achieved / peak_burst,
+                     "issued_mma_frac_of_burst": achieved * issue / peak_burst})
     out = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong" if (args.shard and world > 1) else "weak",
@@ -308,6 +328,20 @@ def run_ours(args, rank, world, local):
             out["variants"][name] = {"value": pairs / (v0.elapsed_time(v1) * 1e-3), "unit": "pairs/s",
                                      "ms_per_step": v0.elapsed_time(v1),
                                      "tolerance_vs_fp64": {"tf32x3": 1e-5, "fp32": 1e-5}[name]}
+    # (before the sections below, which change the context's grids)
+    if args.cpu_baseline and rank == 0 and world == 1:
+        # the oracle's Gamma of its sample doubles as the measured error of every form
+        info, ks, ref, mu_o = cpu_baseline(model, with_result=True)
+        out["cpu_baseline"] = info
+        errs = {}
+        for name in dict.fromkeys([args.precision, "bf16x3", "tf32x3", "fp32"]):
+            g = np.zeros((len(ks), model.nw))
+            ctx.pgb_scattering_rates(ks, T_K, mu_o, SIGMA, PRECISIONS[name], g)
+            errs[name] = rel_err(g, ref)
+        out["measured_rel_err_vs_fp64"] = {
+            "value": errs[args.precision], "by_precision": errs,
+            "norm": "max over states |G - G_oracle| / (|G_oracle| + 1e-6 max G_oracle)",
+            "sample": f"Gamma_nk of the cpu_baseline k-points {ks.tolist()} (all 8 bands, every q of the 40^3 grid)"}
     if args.dynamics:
         out["dynamics"] = dynamics(ctx, model, args, world, peaks, peak_src)
     if args.polar:
@@ -316,8 +350,6 @@ def run_ours(args, rank, world, local):
         out["batched"] = batched(args, world)
     if args.e2e and rank == 0:
         out["e2e"] = e2e(ctx, model, prec, steps=1)
-    if args.cpu_baseline and rank == 0 and world == 1:
-        out["cpu_baseline"] = cpu_baseline(model)
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()

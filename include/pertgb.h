@@ -339,13 +339,19 @@ pgb_status pgb_rk4_adjoint(pgb_ctx *ctx, const double *f0, double dt_fs, int64_t
  * every temporary lives in one fixed device array of
  * PGB_NOALLOC_SCRATCH_BYTES that the library holds on each GPU until the
  * process exits; the call makes no allocation of any kind.
- *   - k_idx [nk] and gamma_out [nk][nw] must be device pointers (no host
- *     staging, since that would need a buffer); otherwise PGB_EINVAL.
+ *   - k_idx [nk] and gamma_out [nk][nw] must be device pointers on the
+ *     context's GPU (no host staging, since that would need a buffer);
+ *     otherwise PGB_EINVAL.
  *   - A grid whose scratch for a single k-point exceeds the array returns
  *     PGB_EINVAL with the required size in pgb_last_error(); larger k lists
  *     are processed in batches that fit.
- *   - The first call on each device looks up the array's device address;
- *     make that first call before any stream capture.
+ *   - The first call on each device looks up the array's device address and
+ *     keeps it until the process exits: make that first call before any
+ *     stream capture, and do not reset the device (cudaDeviceReset) while the
+ *     library is loaded.
+ *   - Each call checks the k indices on the device and reads the result back,
+ *     so it synchronises the context's stream (the host waits for the work
+ *     queued before it) before launching the rates kernels.
  *   - All calls share the array and it keeps the last call's contents: calls
  *     that overlap on the GPU race and must be serialised by the caller.    */
 #define PGB_NOALLOC_SCRATCH_BYTES (64u << 20)

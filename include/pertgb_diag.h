@@ -33,6 +33,28 @@ pgb_status pgb_selftest_heevj_device(pgb_ctx *ctx, int n, int count, const doubl
  * ran out and the kernel returned normally, which is the expected result.   */
 pgb_status pgb_selftest_wait_timeout(pgb_ctx *ctx, long long budget_cycles);
 
+/* The energy mismatch and Gaussian weight of one term exactly as the fused
+ * tensor-core rates epilogue forms them (Sec. 2.1.2, Eqs. scatter_rate,
+ * BTE_W): en, em (band energies at k and k+q) and hw (hbar*omega) [n], eV,
+ * host or device, are shifted by eps_ref and split into (hi, lo) float pairs
+ * like the epilogue's tables; out [n][4] float (host or device) receives
+ * x_em = e_n - e_m - hw, x_abs = e_n - e_m + hw and, for |x| <= 7 sigma (else
+ * 0), the weights exp(-(x/sigma)^2) of each, all in FP32 as in the kernel.   */
+pgb_status pgb_diag_delta_weights(pgb_ctx *ctx, int64_t n, const double *en, const double *em, const double *hw,
+                                  double eps_ref, double sigma, float *out);
+
+/* Device allocations.  Every device allocation the library makes (model and
+ * grid tables, scratch, per-call temporaries) goes through one internal call.
+ * pgb_diag_alloc_count returns how many it has been asked for since the
+ * library was loaded (process-wide, all contexts).  pgb_diag_fail_alloc(n)
+ * makes the n-th next one (n = 0: the next) fail on the host with
+ * cudaErrorMemoryAllocation, without touching the device, exactly once;
+ * n < 0 cancels a pending failure.  The failing entry point returns
+ * PGB_ENOMEM and its context stays usable.  Test hook, not thread safe
+ * across concurrent callers.                                                */
+int64_t pgb_diag_alloc_count(void);
+void pgb_diag_fail_alloc(int64_t n);
+
 #ifdef __cplusplus
 }
 #endif

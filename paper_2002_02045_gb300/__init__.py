@@ -6,6 +6,9 @@ The compute lives in ``libpertgb.so`` (CUDA, sm_103a) behind the C ABI of
 from .native import (  # noqa: F401
     ABI_SYMBOLS,
     Batch,
+    PGB_EINVAL,
+    PGB_ENOMEM,
+    PGB_ETIMEOUT,
     PGB_FP32,
     PGB_FP64,
     PGB_G2_FULL,

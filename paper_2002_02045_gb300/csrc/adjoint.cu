@@ -227,7 +227,7 @@ struct Pool {
     template <typename T>
     T *get(size_t count) {
         void *p = nullptr;
-        if (cudaMallocAsync(&p, std::max<size_t>(count * sizeof(T), 16), c->stream) != cudaSuccess) {
+        if (dev_malloc_async(&p, std::max<size_t>(count * sizeof(T), 16), c->stream) != cudaSuccess) {
             cudaGetLastError();
             ok = false;
             return nullptr;

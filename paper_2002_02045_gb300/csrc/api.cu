@@ -2,6 +2,7 @@
 // checks, host/device staging, memory ownership and the call sequences of the
 // interpolation, rates, collision and RK4 paths.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -47,7 +48,7 @@ struct In {
             dev = p;
             return PGB_OK;
         }
-        PGB_CUDA_TRY(c, cudaMallocAsync((void **)&tmp, n * sizeof(T), c->stream));
+        PGB_CUDA_TRY(c, dev_malloc_async((void **)&tmp, n * sizeof(T), c->stream));
         PGB_CUDA_TRY(c, cudaMemcpyAsync(tmp, p, n * sizeof(T), cudaMemcpyHostToDevice, c->stream));
         dev = tmp;
         return PGB_OK;
@@ -76,7 +77,7 @@ struct Out {
         }
         host = p;
         if (n == 0) return PGB_OK;
-        PGB_CUDA_TRY(c, cudaMallocAsync((void **)&tmp, n * sizeof(T), c->stream));
+        PGB_CUDA_TRY(c, dev_malloc_async((void **)&tmp, n * sizeof(T), c->stream));
         dev = tmp;
         return PGB_OK;
     }
@@ -100,7 +101,7 @@ struct Tmp {
     pgb_status alloc(pgb_ctx *ctx, size_t n) {
         c = ctx;
         if (n == 0) return PGB_OK;
-        PGB_CUDA_TRY(c, cudaMallocAsync((void **)&p, n * sizeof(T), c->stream));
+        PGB_CUDA_TRY(c, dev_malloc_async((void **)&p, n * sizeof(T), c->stream));
         return PGB_OK;
     }
     ~Tmp() {
@@ -225,6 +226,21 @@ __global__ void k_f32_to_f64(const float2 *s, double2 *d, int64_t n) {
 }  // namespace
 
 namespace pgb {
+namespace alloc_hook {
+std::atomic<int64_t> count{0};   // device allocations requested since the library was loaded
+std::atomic<int64_t> fail{-1};   // index of the allocation to refuse, or -1
+}  // namespace alloc_hook
+
+cudaError_t dev_malloc_raw(void **p, size_t bytes, cudaStream_t stream, bool async) {
+    const int64_t n = alloc_hook::count.fetch_add(1);
+    int64_t f = n;
+    if (alloc_hook::fail.load() == n && alloc_hook::fail.compare_exchange_strong(f, -1)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return async ? cudaMallocAsync(p, bytes, stream) : cudaMalloc(p, bytes);
+}
+
 void prof_mark(pgb_ctx *c, int id) {
     if (!c->prof) return;
     cudaEvent_t e;
@@ -244,7 +260,7 @@ pgb_status ensure_scratch(pgb_ctx *c, size_t bytes) {
         c->scratch = nullptr;
         c->scratch_bytes = 0;
     }
-    PGB_CUDA_TRY(c, cudaMalloc(&c->scratch, bytes));
+    PGB_CUDA_TRY(c, dev_malloc(&c->scratch, bytes));
     c->scratch_bytes = bytes;
     return PGB_OK;
 }
@@ -536,7 +552,11 @@ pgb_status pgb_set_grids(pgb_ctx *c, const int kgrid[3], const int qgrid[3]) {
     TRY(launch_to_f32(c, c->d_coef, c->d_coef32, c->Nq * nm2));
     TRY(launch_transpose_coef(c));
     c->has_grids = true;
-    TRY(polar_grid_table(c));
+    const pgb_status pst = polar_grid_table(c);
+    if (pst != PGB_OK) {
+        c->has_grids = false;
+        return pst;
+    }
     PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return PGB_OK;
 }
@@ -586,7 +606,28 @@ pgb_status pgb_set_polar(pgb_ctx *c, const double *zstar, const double eps_inf[9
     if (!c) return PGB_EINVAL;
     cudaSetDevice(c->device);
     if (!c->has_lattice) return fail(c, PGB_ESTATE, "set_polar: call set_lattice first");
-    // every cached q table depends on the long-range columns
+    if (zstar) {   // arguments are checked before any state changes
+        if (!eps_inf) return fail(c, PGB_EINVAL, "set_polar: null eps_inf");
+        for (int i = 0; i < 9 * c->nat; ++i)
+            if (!std::isfinite(zstar[i])) return fail(c, PGB_EINVAL, "set_polar: non-finite Z*");
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                if (!std::isfinite(eps_inf[3 * i + j]) ||
+                    std::fabs(eps_inf[3 * i + j] - eps_inf[3 * j + i]) > 1e-12 * (1.0 + std::fabs(eps_inf[3 * i + j])))
+                    return fail(c, PGB_EINVAL, "set_polar: eps_inf must be symmetric and finite");
+        {   // positive definite: leading principal minors
+            const double *e = eps_inf;
+            const double m1 = e[0], m2 = e[0] * e[4] - e[1] * e[3];
+            const double m3 = e[0] * (e[4] * e[8] - e[5] * e[7]) - e[1] * (e[3] * e[8] - e[5] * e[6]) +
+                              e[2] * (e[3] * e[7] - e[4] * e[6]);
+            if (!(m1 > 0 && m2 > 0 && m3 > 0))
+                return fail(c, PGB_EINVAL, "set_polar: eps_inf must be positive definite");
+        }
+        if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(c, PGB_EINVAL, "set_polar: need Lambda > 0");
+        if (c->nRgp + c->nm > 4096) return fail(c, PGB_EINVAL, "set_polar: too many R_p vectors");
+    }
+    // every cached q table depends on the long-range columns; until the new term
+    // is complete the context is non-polar
     dfree(&c->d_phq64);
     dfree(&c->d_phq32);
     if (c->d_asplit) {
@@ -596,28 +637,9 @@ pgb_status pgb_set_polar(pgb_ctx *c, const double *zstar, const double eps_inf[9
     }
     c->asplit_prec = -1;
     dfree(&c->d_polarL);
-    if (!zstar) {
-        c->polar = false;
-        c->nKp = c->nRgp;
-        return PGB_OK;
-    }
-    if (!eps_inf) return fail(c, PGB_EINVAL, "set_polar: null eps_inf");
-    for (int i = 0; i < 9 * c->nat; ++i)
-        if (!std::isfinite(zstar[i])) return fail(c, PGB_EINVAL, "set_polar: non-finite Z*");
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            if (!std::isfinite(eps_inf[3 * i + j]) ||
-                std::fabs(eps_inf[3 * i + j] - eps_inf[3 * j + i]) > 1e-12 * (1.0 + std::fabs(eps_inf[3 * i + j])))
-                return fail(c, PGB_EINVAL, "set_polar: eps_inf must be symmetric and finite");
-    {   // positive definite: leading principal minors
-        const double *e = eps_inf;
-        const double m1 = e[0], m2 = e[0] * e[4] - e[1] * e[3];
-        const double m3 = e[0] * (e[4] * e[8] - e[5] * e[7]) - e[1] * (e[3] * e[8] - e[5] * e[6]) +
-                          e[2] * (e[3] * e[7] - e[4] * e[6]);
-        if (!(m1 > 0 && m2 > 0 && m3 > 0)) return fail(c, PGB_EINVAL, "set_polar: eps_inf must be positive definite");
-    }
-    if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(c, PGB_EINVAL, "set_polar: need Lambda > 0");
-    if (c->nRgp + c->nm > 4096) return fail(c, PGB_EINVAL, "set_polar: too many R_p vectors");
+    c->polar = false;
+    c->nKp = c->nRgp;
+    if (!zstar) return PGB_OK;
     for (int i = 0; i < 9; ++i) c->eps_inf[i] = eps_inf[i];
     c->ewald_lambda = lambda;
     c->zstar.assign(zstar, zstar + 9 * c->nat);
@@ -631,7 +653,13 @@ pgb_status pgb_set_polar(pgb_ctx *c, const double *zstar, const double eps_inf[9
     PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_gvec, gv.data(), 4 * gv.size(), cudaMemcpyHostToDevice, c->stream));
     c->polar = true;
     c->nKp = c->nRgp + c->nm;
-    TRY(polar_grid_table(c));
+    const pgb_status st = polar_grid_table(c);
+    if (st != PGB_OK) {
+        c->polar = false;
+        c->nKp = c->nRgp;
+        dfree(&c->d_polarL);
+        return st;
+    }
     PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // host vectors above go out of scope
     return PGB_OK;
 }
@@ -696,15 +724,21 @@ pgb_status pgb_interpolate_g(pgb_ctx *c, const double *kpts, int64_t nk, const d
     cudaSetDevice(c->device);
     if (!c->has_model) return fail(c, PGB_ESTATE, "interpolate_g: call set_model first");
     if (nk < 0 || nq < 0) return fail(c, PGB_EINVAL, "interpolate_g: negative size");
-    if (precision != PGB_FP64 && precision != PGB_FP32)
-        return fail(c, PGB_EINVAL, "interpolate_g: precision must be PGB_FP64 or PGB_FP32");
+    if (precision < PGB_FP64 || precision > PGB_TC_BF16X3)
+        return fail(c, PGB_EINVAL, "interpolate_g: unknown precision");
     if (out_mode != PGB_G2_FULL && out_mode != PGB_G_ABS)
         return fail(c, PGB_EINVAL, "interpolate_g: unknown out_mode");
     if (!out && nk * nq > 0) return fail(c, PGB_EINVAL, "interpolate_g: null output");
     if (nk == 0 || nq == 0) return PGB_OK;
-    const bool f32 = precision == PGB_FP32;
+    const bool tcp = precision == PGB_TC_TF32X3 || precision == PGB_TC_BF16X3;
+    const bool tf32 = precision == PGB_TC_TF32X3;
+    const bool f32 = precision != PGB_FP64;
     const int nw = c->nw, nm = c->nm, nw2 = nw * nw, nm2 = nm * nm;
     const int64_t ncol = (int64_t)nm * nw2, npair = nk * nq;
+    // tensor-core q-sum: columns zero-padded to whole 96-column tiles
+    const int64_t ldc = tcp ? (ncol + 95) / 96 * 96 : ncol;
+    if (tcp && (nk > 65535 || (nq + 127) / 128 > 65535))
+        return fail(c, PGB_EINVAL, "interpolate_g: tensor-core forms take at most 65535 k and 65535*128 q per call");
     const size_t es = f32 ? sizeof(float2) : sizeof(double2);
     In<double> K, Q;
     TRY(K.init(c, kpts, 3 * (size_t)nk));
@@ -740,21 +774,60 @@ pgb_status pgb_interpolate_g(pgb_ctx *c, const double *kpts, int64_t nk, const d
         Ukq = U_kq32.p;
         cf = coef_q32.p;
     }
-    // g: Re-sum (GEMM), fold U(k), Rp-sum (batched GEMM), epilogue
-    Tmp<char> phk, S1, G, phq, C, fullbuf;
+    // g: Re-sum (GEMM), fold U(k), Rp-sum (batched GEMM), epilogue.  The split
+    // precisions follow pgb_scattering_rates: BF16x3 takes the R_e sum on the
+    // tensor cores (when its columns tile by 96), TF32x3 the FP32 SIMT one; both
+    // take the R_p sum on the tensor cores from phases split hi/lo in FP64.
+    const bool tc_rsum = tcp && !tf32 && ((int64_t)c->nRgp * ncol) % 96 == 0;
+    Tmp<char> phk, S1, G, phq, C, fullbuf, Asplit, Bsplit, Ak;
     const int64_t nrow = (int64_t)c->nKp * ncol;
-    TRY(phk.alloc(c, (size_t)nk * c->nRge * es));
+    const int64_t nrowS = (int64_t)c->nRgp * ncol;   // g(k, R_p) rows before the long-range rows
+    TRY(phk.alloc(c, (size_t)nk * c->nRge * (tcp ? sizeof(double2) : es)));
     TRY(S1.alloc(c, (size_t)nk * nrow * es));
     TRY(G.alloc(c, (size_t)nk * nrow * es));
-    TRY(phq.alloc(c, (size_t)nq * c->nKp * es));
-    TRY(C.alloc(c, (size_t)npair * ncol * es));
-    TRY(launch_phase_pts(c, K.dev, nk, c->d_Rge, c->nRge, phk.p, f32));
+    TRY(phq.alloc(c, (size_t)nq * c->nKp * (tcp ? sizeof(double2) : es)));
+    TRY(C.alloc(c, (size_t)npair * ldc * es));
+    if (tcp) {
+        if (!c->d_err) PGB_CUDA_TRY(c, dev_malloc((void **)&c->d_err, sizeof(int)));
+        PGB_CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    }
     const void *g = f32 ? (const void *)c->d_g32 : (const void *)c->d_g64;
-    const int64_t nrowS = (int64_t)c->nRgp * ncol;   // g(k, R_p) rows before the long-range rows
-    TRY(launch_cgemm(c, f32, 1, nk, nrowS, c->nRge, phk.p, c->nRge, 0, g, nrowS, 0, S1.p, nrowS, 0));
+    if (tc_rsum) {
+        const int KpE = tc_kpad(c->nRge);
+        const size_t tes = tf32 ? 4 : 2;
+        if (c->gsplit_prec != precision) {
+            if (c->d_gsplit) {
+                PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+                cudaFree(c->d_gsplit);
+                c->d_gsplit = nullptr;
+            }
+            c->gsplit_prec = -1;
+            PGB_CUDA_TRY(c, dev_malloc(&c->d_gsplit, (size_t)4 * nrowS * KpE * tes));
+            TRY(launch_split_gT(c, tf32, c->nRge, nrowS, KpE, c->d_g64, c->d_gsplit));
+            c->gsplit_prec = precision;
+        }
+        TRY(Ak.alloc(c, (size_t)4 * nk * KpE * tes));
+        TRY(launch_phase_pts(c, K.dev, nk, c->d_Rge, c->nRge, phk.p, false));
+        TRY(launch_split_table(c, tf32, nk, c->nRge, c->nRge, KpE, (const double2 *)phk.p, Ak.p));
+        TRY(launch_tc_qsum(c, tf32, 1, nk, (int)nrowS, KpE, Ak.p, c->d_gsplit, (float2 *)S1.p, c->d_err));
+    } else {
+        TRY(launch_phase_pts(c, K.dev, nk, c->d_Rge, c->nRge, phk.p, f32));
+        TRY(launch_cgemm(c, f32, 1, nk, nrowS, c->nRge, phk.p, c->nRge, 0, g, nrowS, 0, S1.p, nrowS, 0));
+    }
     TRY(launch_fold_u(c, f32, nk, nullptr, c->nRgp, nm, nw, S1.p, Uk, G.p));
-    TRY(launch_qtable_pts(c, Q.dev, nq, phq.p, f32));
-    TRY(launch_cgemm(c, f32, nk, nq, ncol, c->nKp, phq.p, c->nKp, 0, G.p, ncol, nrow, C.p, ncol, nq * ncol));
+    if (tcp) {
+        const int Kp = tc_kpad(c->nKp);
+        const size_t tes = tf32 ? 4 : 2;
+        TRY(Asplit.alloc(c, (size_t)4 * nq * Kp * tes));
+        TRY(Bsplit.alloc(c, (size_t)nk * 4 * ldc * Kp * tes));
+        TRY(launch_qtable_pts(c, Q.dev, nq, phq.p, false));
+        TRY(launch_split_table(c, tf32, nq, c->nKp, c->nKp, Kp, (const double2 *)phq.p, Asplit.p));
+        TRY(launch_split_g(c, tf32, nk, c->nKp, (int)ncol, Kp, G.p, Bsplit.p, (int)ldc));
+        TRY(launch_tc_qsum(c, tf32, nk, nq, (int)ldc, Kp, Asplit.p, Bsplit.p, (float2 *)C.p, c->d_err));
+    } else {
+        TRY(launch_qtable_pts(c, Q.dev, nq, phq.p, f32));
+        TRY(launch_cgemm(c, f32, nk, nq, ncol, c->nKp, phq.p, c->nKp, 0, G.p, ncol, nrow, C.p, ncol, nq * ncol));
+    }
     double *fullp = O.dev;
     if (out_mode == PGB_G_ABS) {
         TRY(fullbuf.alloc(c, full * sizeof(double)));
@@ -766,12 +839,20 @@ pgb_status pgb_interpolate_g(pgb_ctx *c, const double *kpts, int64_t nk, const d
     ga.nw = nw;
     ga.nm = nm;
     ga.C = C.p;
+    ga.ldc = ldc;
     ga.Ukq = Ukq;
     ga.coef = cf;
     ga.out_mode = out_mode;
     ga.out = fullp;
     TRY(launch_g_epilogue(c, f32, ga));
     if (out_mode == PGB_G_ABS) TRY(launch_g_abs(c, npair, nm, nw, fullp, O.dev));
+    if (tcp) {
+        int herr = 0;
+        PGB_CUDA_TRY(c, cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        if (herr) return fail(c, PGB_ETIMEOUT, "interpolate_g: a tensor-core pipeline wait ran out (bits " +
+                                                   std::to_string(herr) + ")");
+    }
     TRY(O.finish());
     return PGB_OK;
 }
@@ -884,7 +965,7 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
     }
     if (tcp) {
         if (!c->d_err) {
-            PGB_CUDA_TRY(c, cudaMalloc((void **)&c->d_err, sizeof(int)));
+            PGB_CUDA_TRY(c, dev_malloc((void **)&c->d_err, sizeof(int)));
         }
         PGB_CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
         if (c->asplit_prec != precision) {
@@ -893,7 +974,7 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
                 cudaFree(c->d_asplit);
                 c->d_asplit = nullptr;
             }
-            PGB_CUDA_TRY(c, cudaMalloc(&c->d_asplit, (size_t)4 * c->Nq * Kp * tes));
+            PGB_CUDA_TRY(c, dev_malloc(&c->d_asplit, (size_t)4 * c->Nq * Kp * tes));
             TRY(launch_split_phases(c, tf32, c->qg, c->Nq, c->d_Rgp, c->nRgp, Kp, c->d_asplit, c->d_polarL,
                                     c->polar ? nm : 0));
             c->asplit_prec = precision;
@@ -906,7 +987,7 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
             c->d_gsplit = nullptr;
         }
         c->gsplit_prec = -1;
-        PGB_CUDA_TRY(c, cudaMalloc(&c->d_gsplit, (size_t)4 * nrowS * KpE * tes));
+        PGB_CUDA_TRY(c, dev_malloc(&c->d_gsplit, (size_t)4 * nrowS * KpE * tes));
         TRY(launch_split_gT(c, tf32, c->nRge, nrowS, KpE, c->d_g64, c->d_gsplit));
         c->gsplit_prec = precision;
     }
@@ -1089,7 +1170,7 @@ pgb_status pgb_step_rk4(pgb_ctx *c, double *f, double dt_fs, int64_t nsteps) {
     double *tmp = nullptr;
     const bool host = !is_device_ptr(f);
     if (host) {
-        PGB_CUDA_TRY(c, cudaMallocAsync((void **)&tmp, 8 * ns, c->stream));
+        PGB_CUDA_TRY(c, dev_malloc_async((void **)&tmp, 8 * ns, c->stream));
         PGB_CUDA_TRY(c, cudaMemcpyAsync(tmp, f, 8 * ns, cudaMemcpyHostToDevice, c->stream));
         fd = tmp;
     }
@@ -1522,3 +1603,27 @@ pgb_status pgb_collision_list(pgb_ctx *c, int32_t *row, int32_t *col, int32_t *m
 }
 
 }  // extern "C"
+
+extern "C" pgb_status pgb_diag_delta_weights(pgb_ctx *c, int64_t n, const double *en, const double *em,
+                                             const double *hw, double eps_ref, double sigma, float *out) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (n < 0 || !(sigma > 0.0)) return fail(c, PGB_EINVAL, "diag_delta_weights: need n >= 0, sigma > 0");
+    if (n == 0) return PGB_OK;
+    In<double> E1, E2, W;
+    TRY(E1.init(c, en, (size_t)n));
+    TRY(E2.init(c, em, (size_t)n));
+    TRY(W.init(c, hw, (size_t)n));
+    Out<float> O;
+    TRY(O.init(c, out, 4 * (size_t)n));
+    if (!O.dev) return fail(c, PGB_EINVAL, "diag_delta_weights: null output");
+    TRY(diag_delta_weights(c, n, E1.dev, E2.dev, W.dev, eps_ref, sigma, O.dev));
+    TRY(O.finish());
+    return PGB_OK;
+}
+
+extern "C" int64_t pgb_diag_alloc_count(void) { return pgb::alloc_hook::count.load(); }
+
+extern "C" void pgb_diag_fail_alloc(int64_t n) {
+    pgb::alloc_hook::fail.store(n < 0 ? -1 : pgb::alloc_hook::count.load() + n);
+}

@@ -18,8 +18,8 @@
 //      its band's columns of that result;
 //   2. runs the rates epilogue on the tile: screen every (q, nu) against the
 //      (m) with |x| <= 7 sigma, list the live pairs in order, then one live pair
-//      per thread: project on nu, rotate by U(k+q), Gaussian weights with FP64
-//      energies, FP32 products;
+//      per thread: project on nu, rotate by U(k+q) (FP32 products), then the
+//      energy differences, Gaussian weights and occupation factors in FP64;
 //   3. writes the sum of its terms to its own partial slot.
 // Units are assigned to the persistent CTAs round-robin (every instance's
 // units are spread over all CTAs); a second kernel adds the q-tile partials of
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
         // 2. epilogue.  (a) screen every (q, nu) of the tile in FP32 (|x| <= 7 sigma plus a
         //    margin) and list the live ones, in item order, by a block-wide scan;
         //    (b) one live (q, nu) per thread: project on nu, rotate by U(k+q) for each
-        //    surviving m, Gaussian weights with FP64 energies, FP32 products.  The list
+        //    surviving m (FP32 products), weights and occupations in FP64.  The list
         //    keeps whole warps on the projection however sparse the survivors are.
         double part = 0.0;
         const int64_t k = I.kidx[kb];
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
                     if (i < nw) cfma(gv[i], cc, row[i]);
             }
             const float2 *Ukq = I.U + kq * nw * nw;
-            const float N = (float)I.nbe[q * nm + v];
+            const double N = I.nbe[q * nm + v];
             while (live) {
                 const int m = __ffs(live) - 1;
                 live &= live - 1;
@@ -250,14 +250,14 @@ __global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
 #pragma unroll
                 for (int i = 0; i < kMaxNw; ++i)
                     if (i < nw) cfma_conj(g, Ukq[m * nw + i], gv[i]);
-                const float g2 = cabs2(g);
+                const double g2 = (double)cabs2(g);
                 const double d = en - em[m];
                 const double ye = (d - w) * is, ya = (d + w) * is;
-                const float fm = (float)I.focc[kq * nw + m];
-                float W = 0.f;
-                if (ye * ye <= ycut2) W += expf(-(float)(ye * ye)) * (1.f + N - fm);
-                if (ya * ya <= ycut2) W += expf(-(float)(ya * ya)) * (N + fm);
-                part += (double)(g2 * W);
+                const double fm = I.focc[kq * nw + m];
+                double W = 0.0;
+                if (ye * ye <= ycut2) W += exp(-ye * ye) * (1.0 + N - fm);
+                if (ya * ya <= ycut2) W += exp(-ya * ya) * (N + fm);
+                part = fma(g2, W, part);
             }
         }
         // 3. block sum into this unit's slot (fixed tree)
@@ -384,7 +384,7 @@ namespace {
 template <typename T>
 pgb_status balloc(pgb_batch *b, T **p, size_t n) {
     void *x = nullptr;
-    if (cudaMalloc(&x, std::max<size_t>(n * sizeof(T), 16)) != cudaSuccess) {
+    if (dev_malloc(&x, std::max<size_t>(n * sizeof(T), 16)) != cudaSuccess) {
         cudaGetLastError();
         b->err = "batch: device allocation failed";
         return PGB_ENOMEM;
@@ -623,7 +623,7 @@ pgb_status pgb_batch_create(pgb_batch **out, pgb_ctx *const *ctxs, int n) {
         delete b;
         return PGB_ECUDA;
     }
-    if (cudaMalloc((void **)&b->d_err, sizeof(int)) != cudaSuccess) {
+    if (dev_malloc((void **)&b->d_err, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         cudaStreamDestroy(b->stream);
         delete b;

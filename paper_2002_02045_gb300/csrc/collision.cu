@@ -136,7 +136,7 @@ pgb_status launch_coll_coeffs(pgb_ctx *c, double T, double sigma, const int32_t 
     const int64_t ns = c->nstates;
     if (nnz > 0) {
         int *d_flag = nullptr;
-        PGB_CUDA_TRY(c, cudaMallocAsync((void **)&d_flag, sizeof(int), c->stream));
+        PGB_CUDA_TRY(c, dev_malloc_async((void **)&d_flag, sizeof(int), c->stream));
         PGB_CUDA_TRY(c, cudaMemsetAsync(d_flag, 0, sizeof(int), c->stream));
         k_coll_validate<<<div_up(nnz, 256), 256, 0, c->stream>>>(nnz, ns, c->nm, row, col, mode, d_flag);
         PGB_LAUNCH_CHECK(c);

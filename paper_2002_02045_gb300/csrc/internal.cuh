@@ -156,6 +156,20 @@ struct pgb_ctx {
 
 namespace pgb {
 
+// Every device allocation of the library goes through these calls (never
+// cudaMalloc / cudaMallocAsync directly): they count allocations and can be
+// told by pgb_diag_fail_alloc to refuse one on the host, as an out-of-memory
+// device would, so that each caller's PGB_ENOMEM path can be exercised.
+cudaError_t dev_malloc_raw(void **p, size_t bytes, cudaStream_t stream, bool async);
+template <typename T>
+cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc_raw(reinterpret_cast<void **>(p), bytes, nullptr, false);
+}
+template <typename T>
+cudaError_t dev_malloc_async(T **p, size_t bytes, cudaStream_t stream) {
+    return dev_malloc_raw(reinterpret_cast<void **>(p), bytes, stream, true);
+}
+
 pgb_status ensure_scratch(pgb_ctx *c, size_t bytes);
 // Bracket one launch of a timed kernel class with events (no-op unless enabled).
 void prof_mark(pgb_ctx *c, int id);
@@ -166,7 +180,7 @@ pgb_status dalloc(pgb_ctx *c, T **p, size_t count) {
         *p = nullptr;
     }
     if (count == 0) return PGB_OK;
-    PGB_CUDA_TRY(c, cudaMalloc((void **)p, count * sizeof(T)));
+    PGB_CUDA_TRY(c, dev_malloc((void **)p, count * sizeof(T)));
     return PGB_OK;
 }
 template <typename T>
@@ -246,7 +260,8 @@ pgb_status launch_rates_reduce(pgb_ctx *c, int64_t nb, int64_t nqblk, int nm, in
 struct GArgs {
     int64_t nk, nq;
     int nw, nm;
-    const void *C;         // [nk][nq][nm*nw*nw]
+    const void *C;         // [nk][nq][ldc]: columns (n, ka, i) of nm*nw*nw, then padding
+    int64_t ldc;           // column stride of C (>= nm*nw*nw)
     const void *Ukq;       // [nk*nq][nw][nw]
     const void *coef;      // [nq][nm][nm]
     int out_mode;
@@ -267,6 +282,8 @@ pgb_status launch_split_phases(pgb_ctx *c, bool tf32, const int grid[3], int64_t
 pgb_status launch_split_phases_pts(pgb_ctx *c, bool tf32, const int grid[3], const int32_t *d_pts, int64_t n,
                                    const int32_t *d_R, int nR, int Kp, void *out);
 pgb_status launch_split_gT(pgb_ctx *c, bool tf32, int nR, int64_t ncol, int Kp, const double2 *g, void *out);
+pgb_status launch_split_table(pgb_ctx *c, bool tf32, int64_t n, int ncols, int64_t ld, int Kp, const double2 *T,
+                              void *out);
 pgb_status launch_split_g(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out,
                           int ncol_pad = 0);
 pgb_status launch_split_g6(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out);
@@ -291,6 +308,8 @@ pgb_status launch_fp32_tables(pgb_ctx *c, const double *focc, const double *nbe,
                               float2 *whl, float *nbe32);
 bool tc_fused_supported(int nw, int nm);
 pgb_status launch_tc_rates(pgb_ctx *c, bool tf32, const FusedLaunch &L);
+pgb_status diag_delta_weights(pgb_ctx *c, int64_t n, const double *en, const double *em, const double *hw,
+                              double eps_ref, double sigma, float *out);
 pgb_status launch_transpose_u(pgb_ctx *c);
 pgb_status launch_transpose_coef(pgb_ctx *c);
 

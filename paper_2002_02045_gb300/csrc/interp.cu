@@ -7,6 +7,7 @@
 #include "cplx.cuh"
 #include "heevj.cuh"
 #include "internal.cuh"
+#include "weights.cuh"
 
 namespace pgb {
 
@@ -389,8 +390,8 @@ pgb_status launch_fold_u(pgb_ctx *c, bool fp32, int64_t nb, const int32_t *d_kid
 //        G^nu_i = sum_ka coef[q][nu][ka] C[b][q][n][ka][i];
 //   3. for each surviving m rotate, g = sum_i conj(U_im(k+q)) G^nu_i, and add
 //        |g|^2 [ e^{-(x_em/s)^2} (1 + N - f_m) + e^{-(x_abs/s)^2} (N + f_m) ]
-//      with x formed in FP64 (FP32 path: the Gaussian of the FP64 argument is
-//      taken in FP32, relative error < 3e-6).
+//      with x, the Gaussian weights and the occupation factors in FP64 in
+//      every form (the FP32 form rounds only the products that make g).
 // Per-thread sums over its q are FP64; the block reduces its q in a fixed
 // order and writes one partial per (nu, n).
 // ---------------------------------------------------------------------------
@@ -402,10 +403,6 @@ __device__ __forceinline__ int64_t kplusq_index(int64_t k, int64_t q, const int 
     const int s3 = (k3 + q3 * (kg[2] / qg[2])) % kg[2];
     return ((int64_t)s1 * kg[1] + s2) * kg[2] + s3;
 }
-
-template <typename T> __device__ __forceinline__ T gauss(double y2);
-template <> __device__ __forceinline__ float gauss<float>(double y2) { return expf(-(float)y2); }
-template <> __device__ __forceinline__ double gauss<double>(double y2) { return exp(-y2); }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_rates_epilogue(RatesArgs a) {
@@ -469,7 +466,7 @@ __global__ void __launch_bounds__(256) k_rates_epilogue(RatesArgs a) {
                         if (i < nw) cfma(gv[i], cc, Cn[ka * nw + i]);
                 }
                 const double w = a.hw[q * nm + v];
-                const T N = (T)a.nbe[q * nm + v];
+                const double N = a.nbe[q * nm + v];
                 // 3. rotation and weights for the surviving m
                 uint32_t bits = live[v];
                 while (bits) {
@@ -479,14 +476,14 @@ __global__ void __launch_bounds__(256) k_rates_epilogue(RatesArgs a) {
 #pragma unroll
                     for (int i = 0; i < kMaxNw; ++i)
                         if (i < nw) cfma_conj(g, Ukq[i * nw + m], gv[i]);
-                    const T g2 = cabs2(g);
+                    const double g2 = (double)cabs2(g);
                     const double d = en - a.eps[kq * nw + m];
                     const double ye = (d - w) * is, ya = (d + w) * is;
-                    const T fm = (T)a.focc[kq * nw + m];
-                    T W = 0;
-                    if (ye * ye <= ycut2) W += gauss<T>(ye * ye) * ((T)1 + N - fm);
-                    if (ya * ya <= ycut2) W += gauss<T>(ya * ya) * (N + fm);
-                    acc[v] += (double)(g2 * W);
+                    const double fm = a.focc[kq * nw + m];
+                    double W = 0.0;
+                    if (ye * ye <= ycut2) W += exp(-ye * ye) * (1.0 + N - fm);
+                    if (ya * ya <= ycut2) W += exp(-ya * ya) * (N + fm);
+                    acc[v] = fma(g2, W, acc[v]);
                 }
             }
         }
@@ -553,17 +550,13 @@ __global__ void k_fp32_tables(int64_t Nk, int nw, int64_t Nq, int nm, const doub
     if (t < Nk * nw) {   // t = n * Nk + k
         const int64_t k = t % Nk;
         const int n = (int)(t / Nk);
-        const double e = eps[k * nw + n] - eps_ref;
-        const float hi = (float)e;
-        ehl[t] = make_float2(hi, (float)(e - (double)hi));
+        ehl[t] = split_hl(eps[k * nw + n] - eps_ref);
         focc32[t] = (float)focc[k * nw + n];
     }
     if (t < Nq * nm) {   // t = nu * Nq + q
         const int64_t q = t % Nq;
         const int v = (int)(t / Nq);
-        const double w = hw[q * nm + v];
-        const float hi = (float)w;
-        whl[t] = make_float2(hi, (float)(w - (double)hi));
+        whl[t] = split_hl(hw[q * nm + v]);
         nbe32[t] = (float)nbe[q * nm + v];
     }
 }
@@ -631,8 +624,7 @@ __global__ void k_g_epilogue(GArgs a) {
     const int r = (int)(t % per);
     const int nu = r / a.nw, n = r % a.nw;
     const int64_t q = pair % a.nq;
-    const int ncol = per * a.nw;
-    const T2 *Cq = (const T2 *)a.C + pair * ncol;
+    const T2 *Cq = (const T2 *)a.C + pair * a.ldc;
     const T2 *cf = (const T2 *)a.coef + (q * a.nm + nu) * a.nm;
     T2 gv[kMaxNw];
 #pragma unroll
@@ -760,9 +752,9 @@ extern "C" pgb_status pgb_selftest_heevj_device(pgb_ctx *c, int n, int count, co
     double2 *dm = nullptr, *dv = nullptr;
     double *de = nullptr;
     const size_t nn = (size_t)count * n * n;
-    PGB_CUDA_TRY(c, cudaMalloc((void **)&dm, 16 * nn + 16));
-    PGB_CUDA_TRY(c, cudaMalloc((void **)&dv, 16 * nn + 16));
-    PGB_CUDA_TRY(c, cudaMalloc((void **)&de, 8 * (size_t)count * n + 8));
+    PGB_CUDA_TRY(c, dev_malloc((void **)&dm, 16 * nn + 16));
+    PGB_CUDA_TRY(c, dev_malloc((void **)&dv, 16 * nn + 16));
+    PGB_CUDA_TRY(c, dev_malloc((void **)&de, 8 * (size_t)count * n + 8));
     pgb_status st = PGB_OK;
     if (cudaMemcpy(dm, mat, 16 * nn, cudaMemcpyHostToDevice) != cudaSuccess) st = PGB_ECUDA;
     if (st == PGB_OK) st = launch_heevj(c, count, n, dm, nullptr, de, dv);

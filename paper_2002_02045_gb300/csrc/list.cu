@@ -288,7 +288,7 @@ pgb_status list_sort_decode(pgb_ctx *c, int64_t n, int ns, uint64_t *keys, float
     size_t tmp_bytes = 0;
     PGB_CUDA_TRY(c, cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, dk, dv, n, 0, end_bit, c->stream));
     void *tmp = nullptr;
-    PGB_CUDA_TRY(c, cudaMallocAsync(&tmp, tmp_bytes, c->stream));
+    PGB_CUDA_TRY(c, dev_malloc_async(&tmp, tmp_bytes, c->stream));
     cudaError_t e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, dk, dv, n, 0, end_bit, c->stream);
     cudaFreeAsync(tmp, c->stream);
     PGB_CUDA_TRY(c, e);

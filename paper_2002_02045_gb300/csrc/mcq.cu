@@ -44,11 +44,6 @@ __global__ void k_mc_qpoints(int64_t nq, const double *__restrict__ u, int sampl
     pinv[t] = w;
 }
 
-template <typename T>
-__device__ __forceinline__ T gauss_t(double y2) {
-    return (T)exp(-y2);
-}
-
 struct McArgs {
     int64_t nkb, nq;            // k-points of this batch, q samples of this chunk
     int nw, nm;
@@ -118,8 +113,8 @@ __global__ void __launch_bounds__(256) k_mc_epilogue(McArgs a) {
                 const double ye = (d - w) * is, ya = (d + w) * is;
                 const double fm = 1.0 / (exp((em[m] - a.mu) / kT) + 1.0);
                 double W = 0.0;
-                if (ye * ye <= ycut2) W += (double)gauss_t<T>(ye * ye) * (1.0 + N - fm);
-                if (ya * ya <= ycut2) W += (double)gauss_t<T>(ya * ya) * (N + fm);
+                if (ye * ye <= ycut2) W += exp(-ye * ye) * (1.0 + N - fm);
+                if (ya * ya <= ycut2) W += exp(-ya * ya) * (N + fm);
                 acc += g2 * W;
             }
         }

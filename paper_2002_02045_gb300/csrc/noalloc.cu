@@ -13,8 +13,11 @@
 // All calls share it and it keeps the previous call's contents, so calls
 // that overlap on the GPU (different streams or contexts on one device) race
 // on it and must be serialised by the caller.  The first call on each device
-// looks up the array's device address; make that first call before any
-// stream capture.
+// looks up the array's device address and keeps it for the life of the
+// process (so the device must not be reset with cudaDeviceReset while the
+// library is loaded); make that first call before any stream capture.  Every
+// call reads its k-index check back to the host, so it synchronises the
+// context's stream before it launches the rates kernels.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -54,13 +57,16 @@ pgb_status scratch_address(pgb_ctx *c, unsigned char **out) {
     return PGB_OK;
 }
 
-bool on_device(const void *p) {
+// Device (or managed) memory of the context's own GPU: a buffer on another GPU
+// would be read and written from this one.
+bool on_device(const void *p, int device) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == device;
 }
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -88,8 +94,8 @@ extern "C" pgb_status pgb_scattering_rates_noalloc(pgb_ctx *c, const int32_t *k_
         return PGB_EINVAL;
     }
     if (nk == 0) return PGB_OK;
-    if (!k_idx || !gamma_out || !on_device(k_idx) || !on_device(gamma_out)) {
-        c->err = "scattering_rates_noalloc: k_idx and gamma_out must be device pointers";
+    if (!k_idx || !gamma_out || !on_device(k_idx, c->device) || !on_device(gamma_out, c->device)) {
+        c->err = "scattering_rates_noalloc: k_idx and gamma_out must be device pointers on the context's GPU";
         return PGB_EINVAL;
     }
     const int nw = c->nw, nm = c->nm;

@@ -199,6 +199,190 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
+// TF32x3 form with chunked accumulation.  The tensor core adds each MMA's
+// products to its FP32 accumulator with truncation, ~0.6 ulp of the
+// accumulator toward zero per instruction on these sums, so a single
+// accumulator over the whole K (96 instructions per real part at K = 384)
+// shrinks |C| by a few 1e-6 (|g|^2 by ~1.4e-5).  Here every chunk of 32 K
+// elements (4 MMA K-steps) starts a fresh accumulator, double-buffered in TMEM
+// (re, im: 2 x 96 columns per buffer), and the epilogue warps add the chunk
+// values into FP32 registers with round-to-nearest while the next chunk is
+// multiplied.  Each accumulator then sees 24 instructions on a partial sum of
+// 32 terms, and the chunk errors add with random signs: about 4x less error.
+constexpr int TF_CHUNK_STAGES = 2;          // stages (16 K elements each) per chunk
+constexpr int TF_NEPI = 8;                  // epilogue warps: 4 lane groups x 2 column halves
+constexpr int TF_THREADS = 64 + 32 * TF_NEPI;
+
+__global__ void __launch_bounds__(TF_THREADS, 1)
+    k_tc_qsum_tf32(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, TcArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    // full[S], empty[S], accf[2] (chunk ready), acce[2] (chunk drained), drain
+    uint64_t *full = bars, *empty = bars + STAGES, *accf = bars + 2 * STAGES, *acce = accf + 2, *drain = acce + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    __shared__ int skip;
+    if (threadIdx.x == 0) skip = *reinterpret_cast<volatile int *>(a.err);
+    __syncthreads();
+    if (skip) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * BN;
+    const int q0 = blockIdx.y * BM;
+    const int b = blockIdx.z;
+    constexpr int EK = 16, KSTEP = 8;
+    const int nk = a.Kp / EK;
+    const int nchunk = (nk + TF_CHUNK_STAGES - 1) / TF_CHUNK_STAGES;
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < STAGES; ++st) {
+            tc::mbar_init(tc::smem_addr(full + st), 1);
+            tc::mbar_init(tc::smem_addr(empty + st), 1);
+        }
+        for (int u = 0; u < 2; ++u) {
+            tc::mbar_init(tc::smem_addr(accf + u), 1);
+            tc::mbar_init(tc::smem_addr(acce + u), TF_NEPI);
+        }
+        tc::mbar_init(tc::smem_addr(drain), 1);
+        *abort_flag = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 0 && lane == 0) {
+        tc::prefetch_tmap(&tA);
+        tc::prefetch_tmap(&tB);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tc::smem_addr(tmem_slot), TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        int issued = 0;
+        for (int kc = 0; kc < nk; ++kc) {
+            const int st = kc % STAGES;
+            if (kc >= STAGES && !tc::mbar_wait(tc::smem_addr(empty + st), ((kc / STAGES) - 1) & 1, WAIT_BUDGET)) {
+                atomicOr(a.err, 1);
+                *abort_flag = 1;
+                break;
+            }
+            if (*abort_flag) break;
+            const uint32_t fb = tc::smem_addr(full + st);
+            tc::mbar_expect_tx(fb, STAGE_BYTES);
+            uint8_t *sp = smem + st * STAGE_BYTES;
+            for (int p = 0; p < 4; ++p) tc::tma_load_3d(tc::smem_addr(sp + p * A_PART), &tA, fb, kc * EK, q0, p);
+            for (int p = 0; p < 4; ++p)
+                tc::tma_load_3d(tc::smem_addr(sp + 4 * A_PART + p * B_PART), &tB, fb, kc * EK, n0, b * 4 + p);
+            ++issued;
+        }
+        for (int kc = (issued > STAGES ? issued - STAGES : 0); kc < issued; ++kc)
+            tc::mbar_wait(tc::smem_addr(full + kc % STAGES), (kc / STAGES) & 1, WAIT_BUDGET);
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        constexpr uint32_t idp = tc::make_idesc(2u, BM, BN, false);
+        constexpr uint32_t idn = tc::make_idesc(2u, BM, BN, true);
+        bool ok = true;
+        for (int ch = 0; ch < nchunk && ok; ++ch) {
+            const int buf = ch & 1;
+            if (ch >= 2 && !tc::mbar_wait(tc::smem_addr(acce + buf), ((ch >> 1) - 1) & 1, 4 * WAIT_BUDGET)) {
+                atomicOr(a.err, 2);
+                *abort_flag = 1;
+                ok = false;
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t d_re = tbase + buf * 2 * BN, d_im = d_re + BN;
+            const int kc1 = min(nk, (ch + 1) * TF_CHUNK_STAGES);
+            for (int kc = ch * TF_CHUNK_STAGES; kc < kc1; ++kc) {
+                const int st = kc % STAGES;
+                if (!tc::mbar_wait(tc::smem_addr(full + st), (kc / STAGES) & 1, WAIT_BUDGET) || *abort_flag) {
+                    atomicOr(a.err, 2);
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t sp = tc::smem_addr(smem + st * STAGE_BYTES);
+#pragma unroll
+                for (int ks = 0; ks < EK / KSTEP; ++ks) {
+                    const uint32_t off = ks * 32;
+                    const uint64_t arh = tc::desc_sw64(sp + 0 * A_PART + off), arl = tc::desc_sw64(sp + 1 * A_PART + off);
+                    const uint64_t aih = tc::desc_sw64(sp + 2 * A_PART + off), ail = tc::desc_sw64(sp + 3 * A_PART + off);
+                    const uint32_t bb = sp + 4 * A_PART + off;
+                    const uint64_t brh = tc::desc_sw64(bb + 0 * B_PART), brl = tc::desc_sw64(bb + 1 * B_PART);
+                    const uint64_t bih = tc::desc_sw64(bb + 2 * B_PART), bil = tc::desc_sw64(bb + 3 * B_PART);
+                    const uint32_t acc = (kc > ch * TF_CHUNK_STAGES || ks > 0) ? 1u : 0u;
+                    // C_re += Ar Br - Ai Bi, C_im += Ar Bi + Ai Br (hi*hi, hi*lo, lo*hi)
+                    tc::mma<true>(d_re, arh, brh, idp, acc);
+                    tc::mma<true>(d_re, aih, bih, idn, 1);
+                    tc::mma<true>(d_re, arh, brl, idp, 1);
+                    tc::mma<true>(d_re, arl, brh, idp, 1);
+                    tc::mma<true>(d_re, aih, bil, idn, 1);
+                    tc::mma<true>(d_re, ail, bih, idn, 1);
+                    tc::mma<true>(d_im, arh, bih, idp, acc);
+                    tc::mma<true>(d_im, aih, brh, idp, 1);
+                    tc::mma<true>(d_im, arh, bil, idp, 1);
+                    tc::mma<true>(d_im, arl, bih, idp, 1);
+                    tc::mma<true>(d_im, aih, brl, idp, 1);
+                    tc::mma<true>(d_im, ail, brh, idp, 1);
+                }
+                tc::mma_commit(tc::smem_addr(empty + st));
+            }
+            if (ok) tc::mma_commit(tc::smem_addr(accf + buf));
+        }
+        tc::mma_commit(tc::smem_addr(drain));
+        tc::mbar_wait(tc::smem_addr(drain), 0, WAIT_BUDGET);
+    } else if (warp >= 2) {
+        // ---------------- epilogue: per chunk TMEM -> FP32 register sums ----------------
+        const int ew = warp - 2;
+        const int lg = warp & 3;               // TMEM lane group of this warp
+        const int half = ew >> 2;              // columns [48 half, 48 half + 48)
+        const int row = lg * 32 + lane;
+        const int64_t q = (int64_t)q0 + row;
+        const uint32_t lane_addr = tbase + ((uint32_t)(lg * 32) << 16) + half * (BN / 2);
+        float sr[BN / 2], si[BN / 2];
+#pragma unroll
+        for (int j = 0; j < BN / 2; ++j) sr[j] = si[j] = 0.f;
+        bool ok = true;
+        for (int ch = 0; ch < nchunk; ++ch) {
+            const int buf = ch & 1;
+            ok = tc::mbar_wait(tc::smem_addr(accf + buf), (ch >> 1) & 1, 4 * WAIT_BUDGET);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) atomicOr(a.err, 4);
+                break;
+            }
+            tc::fence_after_sync();
+            float v[BN / 2];
+            tc::tmem_ld48(lane_addr + buf * 2 * BN, v);
+#pragma unroll
+            for (int j = 0; j < BN / 2; ++j) sr[j] += v[j];
+            tc::tmem_ld48(lane_addr + buf * 2 * BN + BN, v);
+#pragma unroll
+            for (int j = 0; j < BN / 2; ++j) si[j] += v[j];
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(tc::smem_addr(acce + buf));
+        }
+        if (ok && q < a.Nq) {
+            float4 *dst = reinterpret_cast<float4 *>(a.C + ((int64_t)b * a.Nq + q) * a.ncol + n0 + half * (BN / 2));
+#pragma unroll
+            for (int j = 0; j < BN / 4; ++j) dst[j] = make_float4(sr[2 * j], si[2 * j], sr[2 * j + 1], si[2 * j + 1]);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tbase, TMEM_COLS);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // operand preparation
 // ---------------------------------------------------------------------------
@@ -258,6 +442,28 @@ __global__ void k_split_phases(int n1, int n2, int n3, int64_t Nq, const int32_t
     out[0 * part + t] = h;
     out[1 * part + t] = l;
     Split<TF32>::run(s, h, l);
+    out[2 * part + t] = h;
+    out[3 * part + t] = l;
+}
+
+// A parts from a complex FP64 table of arbitrary points (phases e^{i k.R} of
+// off-grid k or q, with any long-range columns appended): T[r][p] for r < n,
+// p < ncols (row stride ld) -> [4][n][Kp] = (Re hi, Re lo, Im hi, Im lo), zero
+// for p >= ncols.
+template <bool TF32>
+__global__ void k_split_table(int64_t n, int ncols, int64_t ld, int Kp, const double2 *__restrict__ T,
+                              typename Split<TF32>::E *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t part = n * Kp;
+    if (t >= part) return;
+    const int64_t r = t / Kp;
+    const int p = (int)(t % Kp);
+    const double2 v = p < ncols ? T[r * ld + p] : make_double2(0.0, 0.0);
+    typename Split<TF32>::E h, l;
+    Split<TF32>::run(v.x, h, l);
+    out[0 * part + t] = h;
+    out[1 * part + t] = l;
+    Split<TF32>::run(v.y, h, l);
     out[2 * part + t] = h;
     out[3 * part + t] = l;
 }
@@ -413,6 +619,19 @@ pgb_status launch_split_phases_pts(pgb_ctx *c, bool tf32, const int grid[3], con
     return PGB_OK;
 }
 
+pgb_status launch_split_table(pgb_ctx *c, bool tf32, int64_t n, int ncols, int64_t ld, int Kp, const double2 *T,
+                              void *out) {
+    const int64_t tot = n * Kp;
+    if (tot == 0) return PGB_OK;
+    const unsigned g = (unsigned)((tot + 255) / 256);
+    if (tf32)
+        k_split_table<true><<<g, 256, 0, c->stream>>>(n, ncols, ld, Kp, T, (float *)out);
+    else
+        k_split_table<false><<<g, 256, 0, c->stream>>>(n, ncols, ld, Kp, T, (__nv_bfloat16 *)out);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
 pgb_status launch_split_gT(pgb_ctx *c, bool tf32, int nR, int64_t ncol, int Kp, const double2 *g, void *out) {
     const int64_t n = ncol * Kp;
     const unsigned gr = (unsigned)((n + 255) / 256);
@@ -479,7 +698,7 @@ pgb_status launch_tc_qsum(pgb_ctx *c, bool tf32, int64_t nb, int64_t Nq, int nco
     const pgb_status pst = tc_qsum_prepare(c, tf32);
     if (pst != PGB_OK) return pst;
     if (tf32)
-        k_tc_qsum<true><<<grid, 192, SMEM_BYTES, c->stream>>>(tA, tB, a);
+        k_tc_qsum_tf32<<<grid, TF_THREADS, SMEM_BYTES, c->stream>>>(tA, tB, a);
     else
         k_tc_qsum<false><<<grid, 192, SMEM_BYTES, c->stream>>>(tA, tB, a);
     PGB_LAUNCH_CHECK(c);
@@ -495,7 +714,7 @@ pgb_status tc_qsum_prepare(pgb_ctx *c, bool tf32) {
     std::vector<char> &d = done[tf32 ? 1 : 0];
     if (c->device >= 0 && (size_t)c->device < d.size() && d[c->device]) return PGB_OK;
     if (tf32)
-        PGB_CUDA_TRY(c, cudaFuncSetAttribute(k_tc_qsum<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        PGB_CUDA_TRY(c, cudaFuncSetAttribute(k_tc_qsum_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     else
         PGB_CUDA_TRY(c, cudaFuncSetAttribute(k_tc_qsum<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     if (c->device >= 0) {
@@ -513,7 +732,7 @@ extern "C" pgb_status pgb_selftest_wait_timeout(pgb_ctx *c, long long budget_cyc
     if (!c || budget_cycles <= 0 || budget_cycles > (1ll << 32)) return PGB_EINVAL;
     cudaSetDevice(c->device);
     int *d = nullptr;
-    PGB_CUDA_TRY(c, cudaMalloc((void **)&d, sizeof(int)));
+    PGB_CUDA_TRY(c, dev_malloc((void **)&d, sizeof(int)));
     int h = 0;
     cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) {

@@ -28,6 +28,7 @@
 
 #include "internal.cuh"
 #include "tc.cuh"
+#include "weights.cuh"
 
 namespace pgb {
 
@@ -326,8 +327,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     for (int m = 0; m < NWF; ++m) {
                         // (e_n,hi - e_m,hi) is exact for every possible survivor
                         const float dh = en.x - em[m].x, dl = en.y - em[m].y;
-                        const float xe = (dh - wv[v].x) + (dl - wv[v].y);
-                        const float xa = (dh + wv[v].x) + (dl + wv[v].y);
+                        const float xe = mismatch32(dh, dl, wv[v], -1.f);
+                        const float xa = mismatch32(dh, dl, wv[v], 1.f);
                         if (fabsf(xe) <= a.cut || fabsf(xa) <= a.cut) live[v] |= 1u << m;
                     }
                     any |= live[v];
@@ -366,13 +367,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             gii = fmaf(c.x, ri[ka], fmaf(c.y, rr[ka], gii));
                         }
                         const float g2 = grr * grr + gii * gii;
-                        const float xe = (dh - wv[v].x) + (dl - wv[v].y);
-                        const float xa = (dh + wv[v].x) + (dl + wv[v].y);
+                        const float xe = mismatch32(dh, dl, wv[v], -1.f);
+                        const float xa = mismatch32(dh, dl, wv[v], 1.f);
                         const float N = nb_[v];
-                        const float ye = xe * a.inv_sigma, ya = xa * a.inv_sigma;
                         float W = 0.f;
-                        if (fabsf(xe) <= a.cut) W += expf(-ye * ye) * (1.f + N - f);
-                        if (fabsf(xa) <= a.cut) W += expf(-ya * ya) * (N + f);
+                        if (fabsf(xe) <= a.cut) W += gauss32(xe, a.inv_sigma) * (1.f + N - f);
+                        if (fabsf(xa) <= a.cut) W += gauss32(xa, a.inv_sigma) * (N + f);
                         acc[v] = fmaf(g2, W, acc[v]);
                     }
                 }
@@ -429,6 +429,33 @@ int make_map3(CUtensorMap *m, void *base, bool tf32, int Kp, int64_t d1, int64_t
 }  // namespace
 
 bool tc_fused_supported(int nw, int nm) { return nw == NWF && nm == NMF; }
+
+namespace {
+// The fused epilogue's arithmetic for single terms: shift and split the FP64
+// energies as the tables do, then the mismatch, the screen and the weight.
+__global__ void k_diag_delta(int64_t n, const double *__restrict__ en, const double *__restrict__ em,
+                             const double *__restrict__ hw, double eps_ref, float inv_sigma, float cut,
+                             float *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const float2 a = split_hl(en[t] - eps_ref), b = split_hl(em[t] - eps_ref), w = split_hl(hw[t]);
+    const float dh = a.x - b.x, dl = a.y - b.y;
+    const float xe = mismatch32(dh, dl, w, -1.f), xa = mismatch32(dh, dl, w, 1.f);
+    out[4 * t + 0] = xe;
+    out[4 * t + 1] = xa;
+    out[4 * t + 2] = fabsf(xe) <= cut ? gauss32(xe, inv_sigma) : 0.f;
+    out[4 * t + 3] = fabsf(xa) <= cut ? gauss32(xa, inv_sigma) : 0.f;
+}
+}  // namespace
+
+pgb_status diag_delta_weights(pgb_ctx *c, int64_t n, const double *en, const double *em, const double *hw,
+                              double eps_ref, double sigma, float *out) {
+    if (n == 0) return PGB_OK;
+    k_diag_delta<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, en, em, hw, eps_ref, (float)(1.0 / sigma),
+                                                                     (float)(kDeltaCut * sigma), out);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
 
 pgb_status launch_tc_rates(pgb_ctx *c, bool tf32, const FusedLaunch &L) {
     if (L.nb == 0) return PGB_OK;

@@ -313,7 +313,7 @@ pgb_status mobility_sum(pgb_ctx *c, const uint8_t *inwin, double mu, const doubl
     const int64_t ns = c->nstates;
     const unsigned nblk = div_up(ns, kMobThreads);
     double *part = nullptr;
-    PGB_CUDA_TRY(c, cudaMallocAsync((void **)&part, 80 * (size_t)std::max(1u, nblk), c->stream));
+    PGB_CUDA_TRY(c, dev_malloc_async((void **)&part, 80 * (size_t)std::max(1u, nblk), c->stream));
     k_mobility<<<nblk, kMobThreads, 0, c->stream>>>(ns, inwin, c->d_eps_state, mu, c->coll_T, v, F, part);
     c->launches++;
     cudaError_t e = cudaGetLastError();
@@ -353,8 +353,8 @@ pgb_status band_velocities(pgb_ctx *c, const int32_t *d_kidx, int64_t nk, double
     const int64_t nw2 = (int64_t)nw * nw;
     const int64_t chunk = 16384;
     double2 *ph = nullptr, *Hk = nullptr;
-    PGB_CUDA_TRY(c, cudaMallocAsync((void **)&ph, 16 * (size_t)std::min(nk, chunk) * c->nRH, c->stream));
-    PGB_CUDA_TRY(c, cudaMallocAsync((void **)&Hk, 16 * (size_t)std::min(nk, chunk) * 3 * nw2, c->stream));
+    PGB_CUDA_TRY(c, dev_malloc_async((void **)&ph, 16 * (size_t)std::min(nk, chunk) * c->nRH, c->stream));
+    PGB_CUDA_TRY(c, dev_malloc_async((void **)&Hk, 16 * (size_t)std::min(nk, chunk) * 3 * nw2, c->stream));
     pgb_status st = PGB_OK;
     for (int64_t k0 = 0; k0 < nk && st == PGB_OK; k0 += chunk) {
         const int64_t nb = std::min(chunk, nk - k0);
@@ -402,7 +402,7 @@ pgb_status transport(pgb_ctx *c, double mu, int precision, int max_iter, double 
         bool ok = true;
         void *get(size_t bytes) {
             void *x = nullptr;
-            if (cudaMallocAsync(&x, std::max<size_t>(bytes, 16), c->stream) != cudaSuccess) {
+            if (dev_malloc_async(&x, std::max<size_t>(bytes, 16), c->stream) != cudaSuccess) {
                 cudaGetLastError();
                 ok = false;
                 return nullptr;

@@ -22,7 +22,8 @@ PGB_FP64, PGB_FP32, PGB_TC_TF32X3, PGB_TC_BF16X3 = 0, 1, 2, 3
 PGB_G2_FULL, PGB_G_ABS = 0, 1
 PRECISIONS = {"fp64": PGB_FP64, "fp32": PGB_FP32, "tf32x3": PGB_TC_TF32X3, "bf16x3": PGB_TC_BF16X3}
 
-DIAG_SYMBOLS = ("pgb_diag_bands", "pgb_selftest_heevj", "pgb_selftest_heevj_device", "pgb_selftest_wait_timeout")
+DIAG_SYMBOLS = ("pgb_diag_bands", "pgb_selftest_heevj", "pgb_selftest_heevj_device", "pgb_selftest_wait_timeout",
+                "pgb_diag_alloc_count", "pgb_diag_fail_alloc", "pgb_diag_delta_weights")
 ABI_SYMBOLS = (
     "pgb_create", "pgb_destroy", "pgb_last_error", "pgb_status_string", "pgb_set_model",
     "pgb_set_grids", "pgb_get_grid_energies", "pgb_window", "pgb_interpolate_g",
@@ -109,6 +110,9 @@ def load(path: str = LIB_PATH):
         "pgb_selftest_heevj": (I, [I, I, P, P, P]),
         "pgb_selftest_heevj_device": (I, [P, I, I, P, P, P]),
         "pgb_selftest_wait_timeout": (I, [P, C.c_longlong]),
+        "pgb_diag_alloc_count": (I64, []),
+        "pgb_diag_fail_alloc": (None, [I64]),
+        "pgb_diag_delta_weights": (I, [P, I64, P, P, P, D, D, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -337,6 +341,13 @@ class Context:
 
     def pgb_diag_bands(self, pts, Hk=None, eps=None, U=None):
         self._chk(self.lib.pgb_diag_bands(self._h, _ptr(pts), len(pts), _ptr(Hk), _ptr(eps), _ptr(U)))
+
+    def pgb_diag_delta_weights(self, en, em, hw, eps_ref, sigma, out):
+        for a in (en, em, hw):
+            _check_dtype(a, "float64")
+        _check_dtype(out, "float32")
+        self._chk(self.lib.pgb_diag_delta_weights(self._h, len(en), _ptr(en), _ptr(em), _ptr(hw), float(eps_ref),
+                                                  float(sigma), _ptr(out)))
 
     def pgb_profile(self, enable):
         self._chk(self.lib.pgb_profile(self._h, 1 if enable else 0))

@@ -82,3 +82,26 @@ def test_host_jacobi_matches_lapack(lib, n):
     assert np.abs(rec - A).max() < 1e-12 * np.abs(A).max()
     eye = np.einsum("kin,kim->knm", np.conj(V), V)
     assert np.abs(eye - np.eye(n)).max() < 1e-13
+
+
+def test_every_device_allocation_goes_through_the_counted_call():
+    """The allocation-failure hook and the allocation-free entry point's check rely
+    on every device allocation of the library passing through one call."""
+    csrc = os.path.join(ROOT, "paper_2002_02045_gb300", "csrc")
+    offenders = []
+    for name in sorted(os.listdir(csrc)):
+        for no, line in enumerate(open(os.path.join(csrc, name)), 1):
+            code = line.split("//")[0]
+            if re.search(r"\bcudaMalloc(Async|Managed|Host|Pitch|3D|Array)?\s*\(", code) or "cudaHostAlloc" in code:
+                offenders.append(f"{name}:{no}: {line.strip()}")
+    # the one sanctioned call site, inside the wrapper itself
+    allowed = [o for o in offenders if o.startswith("api.cu:") and "async ? cudaMallocAsync" in o]
+    assert len(allowed) == 1 and len(offenders) == 1, offenders
+
+
+def test_allocation_hook_without_gpu(lib):
+    fn_count, fn_fail = lib.pgb_diag_alloc_count, lib.pgb_diag_fail_alloc
+    n0 = fn_count()
+    fn_fail(0)
+    fn_fail(-1)
+    assert fn_count() == n0

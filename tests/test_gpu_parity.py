@@ -174,6 +174,52 @@ def test_interpolate_g_c2_fp32(ctx, c2):
                         block_axes=(2, 3, 4), floor=1e-2, label="c2 g2")
 
 
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-5), ("bf16x3", 1e-3)])
+def test_interpolate_g_c2_split(ctx, c2, prec, tol):
+    """|g|^2 from the tensor-core forms (BF16x3: R_e and R_p sums on tcgen05; TF32x3:
+    R_p sum on tcgen05) at generic points of the fcc model.  300 q fill two 128-row
+    tiles and a ragged third of 44 rows; two k make two B operands.  Tolerance of the
+    tier on every element above 1e-2 of its (k, q, nu) block maximum, and normwise."""
+    from paper_2002_02045_gb300 import PGB_G2_FULL, PGB_G_ABS, PRECISIONS
+    rng = np.random.default_rng(3)
+    k = rng.uniform(-0.5, 0.5, (2, 3))
+    q = rng.uniform(-0.5, 0.5, (300, 3))
+    ctx.pgb_set_model(c2)
+    out = empty((2, 300, 6, 8, 8))
+    ctx.pgb_interpolate_g(dev(k), dev(q), PRECISIONS[prec], PGB_G2_FULL, out)
+    ref, hw = oracle_g2(c2, k, q)
+    got = out.cpu().numpy()
+    hwb = np.broadcast_to(hw[None], (2, 300, 6))
+    assert_close_blocks(degenerate_sum(got, hwb, 2), degenerate_sum(ref, hwb, 2), tol,
+                        block_axes=(2, 3, 4), floor=1e-2, label=f"c2 g2 {prec}")
+    # Eq. g_abs from the same arithmetic (host output buffer)
+    ga = np.zeros((2, 300, 6))
+    ctx.pgb_interpolate_g(k, q, PRECISIONS[prec], PGB_G_ABS, ga)
+    ref_abs2 = ref.sum((3, 4)) / 8
+    assert_close_blocks(degenerate_sum(ga ** 2, hwb, 2), degenerate_sum(ref_abs2, hwb, 2), tol,
+                        block_axes=(2,), floor=1e-2, label=f"c2 g_abs {prec}")
+
+
+def test_interpolate_g_split_padded_columns(ctx, c2):
+    """A 3-band cut of the fcc model has nmode*nw*nw = 54 columns: the tensor-core
+    q-sum pads them with zeros to one 96-column tile (and the R_e sum, 381*54
+    columns, stays on the CUDA cores)."""
+    from paper_2002_02045_gb300 import PGB_G2_FULL, PRECISIONS
+    m = dataclasses.replace(c2, H=np.ascontiguousarray(c2.H[:, :3, :3]),
+                            g=np.ascontiguousarray(c2.g[..., :3, :3]))
+    rng = np.random.default_rng(4)
+    k = rng.uniform(-0.5, 0.5, (3, 3))
+    q = rng.uniform(-0.5, 0.5, (130, 3))
+    ctx.pgb_set_model(m)
+    ref, hw = oracle_g2(m, k, q)
+    hwb = np.broadcast_to(hw[None], (3, 130, 6))
+    for prec, tol in (("tf32x3", 1e-5), ("bf16x3", 1e-3)):
+        out = empty((3, 130, 6, 3, 3))
+        ctx.pgb_interpolate_g(dev(k), dev(q), PRECISIONS[prec], PGB_G2_FULL, out)
+        assert_close_blocks(degenerate_sum(out.cpu().numpy(), hwb, 2), degenerate_sum(ref, hwb, 2), tol,
+                            block_axes=(2, 3, 4), floor=1e-2, label=f"3-band g2 {prec}")
+
+
 # ----------------------------------------------------------------------------
 # scattering rates (Eqs. scatter_rate, BTE_W)
 # ----------------------------------------------------------------------------
@@ -193,6 +239,44 @@ def test_rates_c1_full(ctx, c1, prec):
     assert_rates_close(g, ref, TOL[prec], label=f"c1 gamma {prec}")
     assert np.allclose(gmode.cpu().numpy().sum(1), g, rtol=1e-13)
     assert np.all(g >= 0)
+
+
+def test_fused_delta_weights_bound(ctx):
+    """The fused tensor-core epilogue's FP32 energy mismatch and Gaussian weight
+    (Sec. 2.1.2, Eqs. scatter_rate, BTE_W) against FP64, through the diagnostic
+    entry that runs the kernel's own arithmetic.  Energies shifted by e_ref and
+    split into float pairs make x accurate to 1e-8 eV; the weight's error is at most
+    5e-7 of the peak weight everywhere in |x| <= 7 sigma, at most 2e-6 relative for
+    |x| <= 2 sigma (where nearly all of Gamma comes from) and 2e-5 relative out to
+    the 7 sigma cut.  The FP32 screen agrees with FP64 except within 1e-8 eV of it."""
+    rng = np.random.default_rng(9)
+    n, sig, eps_ref = 1 << 20, 0.010, -8.0
+    en = rng.uniform(-7.0, -6.6, n)
+    hw = rng.uniform(1e-4, 0.09, n)
+    x = rng.uniform(-7.2 * sig, 7.2 * sig, n)
+    s = rng.choice([-1.0, 1.0], n)
+    em = en + s * hw - x
+    out = np.zeros((n, 4), np.float32)
+    ctx.pgb_diag_delta_weights(en, em, hw, eps_ref, sig, out)
+    xe64, xa64 = en - em - hw, en - em + hw
+    x32 = np.where(s < 0, out[:, 0], out[:, 1]).astype(np.float64)
+    g32 = np.where(s < 0, out[:, 2], out[:, 3]).astype(np.float64)
+    x64 = np.where(s < 0, xe64, xa64)
+    inside = np.abs(x64) <= 7 * sig
+    edge = np.abs(np.abs(x64) - 7 * sig) <= 1e-8
+    away = ~edge
+    assert np.array_equal((g32 > 0)[away], inside[away]), "screen differs from FP64 away from the cut"
+    ok = inside & ~edge
+    g64 = np.exp(-(x64[ok] / sig) ** 2)
+    err = np.abs(g32[ok] - g64)
+    assert err.max() <= 5e-7, err.max()
+    rel = err / g64
+    core = np.abs(x64[ok]) <= 2 * sig
+    assert rel[core].max() <= 2e-6, rel[core].max()
+    assert rel.max() <= 2e-5, rel.max()
+    # x of the term at hand (|x| <= 0.1 eV here) to 1e-8 eV; the other sign's x is larger and rounds coarser
+    assert np.abs(x32 - x64).max() < 1e-8
+    assert np.abs(out[:, 0] - xe64).max() < 5e-8 and np.abs(out[:, 1] - xa64).max() < 5e-8
 
 
 def test_rates_c1_ragged_and_host_buffers(ctx, c1):

@@ -76,7 +76,8 @@ def oracle_g2_full(m, k, q):
     return out, hw
 
 
-@pytest.mark.parametrize("prec,tol,floor", [("fp64", 1e-10, 1e-3), ("fp32", 1e-5, 1e-2)])
+@pytest.mark.parametrize("prec,tol,floor", [("fp64", 1e-10, 1e-3), ("fp32", 1e-5, 1e-2), ("tf32x3", 1e-5, 1e-2),
+                                            ("bf16x3", 1e-3, 1e-2)])
 def test_polar_interpolate_g(ctx, c3, prec, tol, floor):
     from paper_2002_02045_gb300 import PGB_G2_FULL, PRECISIONS
     m = c3
