@@ -228,9 +228,11 @@ def g_bloch(gw: np.ndarray, Uk: np.ndarray, Ukq: np.ndarray) -> np.ndarray:
     """g_mn = sum_ij U^dagger_mi(k+q) g_ij U_jn(k)  (Eq. eph_mat_wann2, outer sum).
 
     gw [..., nmode, nw, nw], Uk [..., nw, nw] (broadcast over the mode axis),
-    Ukq [..., nw, nw].  Returns [..., nmode, nw(m), nw(n)].
+    Ukq [..., nw, nw].  Returns [..., nmode, nw(m), nw(n)].  Evaluated as the two
+    matrix products U^dagger(k+q) g, then (U^dagger(k+q) g) U(k).
     """
-    return np.einsum("...im,...xij,...jn->...xmn", np.conj(Ukq), gw, Uk)
+    udag = np.swapaxes(np.conj(Ukq), -1, -2)[..., None, :, :]     # U^dagger(k+q), per mode
+    return (udag @ gw) @ np.asarray(Uk)[..., None, :, :]
 
 
 def g_modes(gb: np.ndarray, hw: np.ndarray, e: np.ndarray, mass: np.ndarray) -> np.ndarray:
