@@ -167,7 +167,7 @@ def g_wannier(model, kpts: np.ndarray, qpts: np.ndarray) -> np.ndarray:
     gk = phases(kpts, model.R_ge) @ g.reshape(nge, -1).astype(np.complex128)      # [nk, ngp*ncol]
     gk = gk.reshape(len(kpts), ngp, -1)
     pq = phases(qpts, model.R_gp)                                                   # [nq, ngp]
-    out = np.einsum("qp,kpc->kqc", pq, gk)
+    out = pq[None] @ gk                                                             # [nk, nq, ncol]
     return out.reshape((len(kpts), len(qpts)) + tail)
 
 
@@ -246,7 +246,10 @@ def g_modes(gb: np.ndarray, hw: np.ndarray, e: np.ndarray, mass: np.ndarray) -> 
     length = np.sqrt(C_OMEGA / (2.0 * m[..., :, None] * hw_safe[..., None, :]))   # [..., ka, nu] bohr
     length = np.where(hw[..., None, :] >= OMEGA_MIN_EV, length, 0.0)
     coef = e * length                                               # [..., ka, nu]
-    return np.einsum("...an,...amk->...nmk", coef, gb)
+    lead = gb.shape[:-3]
+    nmode, nw1, nw2 = gb.shape[-3:]
+    cT = np.broadcast_to(np.swapaxes(coef, -1, -2), lead + (coef.shape[-1], nmode))   # [..., nu, ka]
+    return (cT @ gb.reshape(lead + (nmode, nw1 * nw2))).reshape(lead + (coef.shape[-1], nw1, nw2))
 
 
 def g_abs(gm: np.ndarray) -> np.ndarray:
