@@ -265,26 +265,30 @@ pgb_status pgb_population(pgb_ctx *ctx, const double *f, const double *E, int64_
  * and grids, and stay alive, while the batch exists); the batch runs on the
  * first context's stream.
  * pgb_batch_rates: for instance i, Gamma_nk (Eqs. scatter_rate, BTE_W; FP32
- * products, FP64 energies, terms beyond 7 sigma skipped) of the k-grid points
- * k_idx[i][0..nk[i]) over its whole q grid and every band and mode, at T_K,
- * mu_eV[i] and sigma_eV, into gamma_out[i] [nk[i]][nw_i] (1/s).  k lists and
- * outputs host or device.  The first call tunes the tile (q-points per unit
- * and threads per block, four candidates timed once each); every call with
- * new arguments captures the per-instance set-up (occupations, R_e sums),
- * the persistent kernel and the reduction into a CUDA graph; calls with the
- * same arguments replay it.  Results do not depend on the schedule.
- * pgb_batch_tuning: chosen q tile and block size, candidate times (ms, [4],
- * -1 where not run) and graph launches so far (any pointer may be NULL).
+ * products, FP64 energy differences and weights, terms beyond 7 sigma
+ * skipped) of the k-grid points k_idx[i][0..nk[i]) over its whole q grid and
+ * every band and mode, at T_K, mu_eV[i] and sigma_eV, into gamma_out[i]
+ * [nk[i]][nw_i] (1/s).  k lists and outputs host or device.  Per instance the
+ * R_p sums over the whole q grid are formed first (into a [nk][Nq][columns]
+ * FP32 buffer of the batch, 8 bytes per entry); one persistent kernel then
+ * runs the epilogue of every instance, one unit per (instance, k, q tile)
+ * over all its bands.  The first call tunes the block size and the shared-
+ * memory budget that sets each instance's q tile (four candidates timed once
+ * each); every call with new arguments captures the per-instance set-up
+ * (occupations, R_e and R_p sums), the persistent kernel and the reduction
+ * into a CUDA graph; calls with the same arguments replay it.  Results do not
+ * depend on the schedule.
+ * pgb_batch_tuning: the largest per-instance q tile and the block size of the
+ * chosen candidate, candidate times (ms, [4], -1 where not run) and graph
+ * launches so far (any pointer may be NULL).
  * pgb_batch_set_precision: PGB_FP32 (default: every instance's R_p sum on
  * the CUDA cores, FP32 products) or PGB_TC_BF16X3 / PGB_TC_TF32X3: then every
- * non-polar instance takes its R_p sum on the tensor cores (split operands,
- * FP32 accumulators, nm*nw*nw columns padded with zeros to a multiple of 96; a
- * tensor-core pipeline time-out returns PGB_ETIMEOUT), written to a
- * [nk][Nq][padded columns] FP32 buffer of the batch (8 bytes per entry) that
- * the persistent kernel's epilogue reads; polar instances keep the CUDA-core
- * form.  A change
- * drops the captured graph and the tuning.  Error bound against the FP64
- * oracle: 1e-3 (BF16x3), 1e-5 (TF32x3 and FP32).  Other values: PGB_EINVAL. */
+ * instance takes its R_p sum on the tensor cores (split operands, FP32
+ * accumulators, nm*nw*nw columns padded with zeros to a multiple of 96, polar
+ * long-range rows included; a tensor-core pipeline time-out returns
+ * PGB_ETIMEOUT).  A change drops the captured graph and the tuning.  Error
+ * bound against the FP64 oracle: 1e-3 (BF16x3), 1e-5 (TF32x3 and FP32).
+ * Other values: PGB_EINVAL.                                                 */
 typedef struct pgb_batch pgb_batch;
 pgb_status pgb_batch_create(pgb_batch **out, pgb_ctx *const *ctxs, int n);
 pgb_status pgb_batch_rates(pgb_batch *batch, const int32_t *const *k_idx, const int64_t *nk, double T_K,

@@ -2,34 +2,37 @@
 // instances of uneven band, mode and grid sizes in one persistent launch.
 //
 // Each member context holds its own model and grids.  Per call, the per-
-// instance set-up (occupation tables and the R_e sums with U(k) folded) and
-// one persistent kernel over the work units of every instance are captured in
-// a CUDA graph, which later calls with the same arguments replay.
+// instance set-up and one persistent kernel over the work units of every
+// instance are captured in a CUDA graph, which later calls with the same
+// arguments replay.
 //
-// Work unit = (instance, k, initial band n, tile of QT q-points).  A unit
-//   1. forms its R_p-sum tile C[q][ka][i] = sum_p e^{iq.R_p} G_k[p][n][ka][i] in shared
-//      memory, K-chunk by K-chunk (the next chunk copied by cp.async while the
-//      current one is multiplied), from the instance's FP32 q table (exact grid
-//      phases and, for polar models, the long-range columns; built once per
-//      plan) and the G_k rows of band n, which are contiguous (column order n, ka, i);
-//      in a split precision (BF16x3 / TF32x3) the non-polar instances' R_p sums
-//      come from the tensor cores instead (k_tc_qsum on split operands, inside
-//      the same graph, columns padded to a multiple of 96) and the unit copies
-//      its band's columns of that result;
-//   2. runs the rates epilogue on the tile: screen every (q, nu) against the
-//      (m) with |x| <= 7 sigma, list the live pairs in order, then one live pair
-//      per thread: project on nu, rotate by U(k+q) (FP32 products), then the
-//      energy differences, Gaussian weights and occupation factors in FP64;
-//   3. writes the sum of its terms to its own partial slot.
-// Units are assigned to the persistent CTAs round-robin (every instance's
-// units are spread over all CTAs); a second kernel adds the q-tile partials of
+// Per instance (set-up, in the graph): occupation tables, the R_e sums with
+// U(k) folded for its k list, and the R_p sums
+//   C[b][q][n ka i] = sum_p e^{iq.R_p} G_kb[p][n ka i]
+// over its whole q grid (FP32 form: the SIMT complex GEMM; BF16x3 / TF32x3:
+// tcgen05 on split operands, columns padded to a multiple of 96), written to
+// HBM once.
+//
+// Persistent kernel, one warp per task: a chunk of qc q-points of one (instance,
+// k), every band n of the instance in turn.  For each (q, n) row the warp reads
+// the row of C into registers (coalesced; nm*nw complex values, up to eight per
+// lane), screens the (nu, m) of the row 32 at a time against |x| <= 7 sigma
+// (FP32 with a margin), and evaluates each live term as a warp-wide dot product
+//   g_mn nu = sum_{ka, i} coef[q][nu][ka] conj(U_im(k+q)) C[q][n][ka][i]
+// (FP32 products, shuffle reduction).  Live terms wait in lane slots, 32 at a
+// time, so that their energy differences, Gaussian weights and occupation
+// factors are taken in FP64 by full warps; each band's sum over the chunk goes
+// to its own partial slot.  Warps claim chunks from a counter in order of
+// decreasing cost (instances with the most work per chunk first), so the uneven
+// instances balance over the SMs; a second kernel adds the chunk partials of
 // each (instance, k, n) in order, so results do not depend on the schedule.
 //
-// The tile height QT and the block size are chosen by a small autotuner: on
-// the first call every candidate runs once, timed with events, and the fastest
-// is kept for the batch.
+// The chunk length and the block size are chosen by a small autotuner: on the
+// first call every candidate runs once, timed with events, and the fastest is
+// kept.
 #include <algorithm>
 #include <cmath>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -41,235 +44,238 @@ namespace pgb {
 namespace {
 
 inline unsigned int div_up(int64_t a, int64_t b) { return (unsigned int)((a + b - 1) / b); }
-constexpr int KC = 8;    // K chunk of the shared-memory GEMM (double-buffered)
-constexpr int RT = 4;    // tile rows per thread in the shared-memory GEMM
 
 struct BInst {
-    int nw, nm, nRgp, nKp;
+    int nw, nm;
     int qg[3], kg[3];
     int64_t Nq;
-    int64_t unit0;             // first unit of this instance
-    int nqt;                   // q tiles
-    const float2 *phq;         // [Nq][nKp] q table: e^{iq.R_p}, then the long-range columns
-    const float2 *Ctc;         // [nk][Nq][ldc] q-sum from the tensor cores, or null (SIMT GEMM here)
-    int ldc;                   // nm*nw*nw rounded up to a multiple of 96
-    const float2 *G;           // [nk][nKp][nm*nw*nw]
+    int qc;                    // q-points per chunk
+    int nch;                   // chunks per k
+    int ib;                    // lanes per mode column in a row's dot product (nm * ib <= 32, ib divides nw)
+    int64_t chunk0;            // first chunk of this instance in the claim order
+    int64_t part0;             // first partial: [nk][nw][nch]
+    const float2 *C;           // [nk][Nq][ldc] R_p sums with U(k) folded, columns (n, ka, i)
+    int64_t ldc;
     const int32_t *kidx;       // [nk]
     const double *eps;         // [Nk][nw]
     const float *eps32;        // [Nk][nw] FP32 copy for the screen
-    const float *hw32;         // [Nq][nm] FP32 copy for the screen
-    const float2 *U;           // [Nk][nw][nw] transposed: U[k][m][i] = U_im(k) (row m contiguous)
-    const float2 *coef;        // [Nq][nm][nm]
+    const float2 *U;           // [Nk][m][i] transposed: row m of U(k) contiguous
+    const float2 *coef;        // [Nq][nu][ka]
     const double *hw;          // [Nq][nm]
+    const float *hw32;         // [Nq][nm] FP32 copy for the screen
     const double *focc;        // [Nk][nw]
     const double *nbe;         // [Nq][nm]
     double sigma;
 };
 
 struct BArgs {
-    int ninst;
     const BInst *inst;
-    const int32_t *unit_inst;  // [nunits] instance of each unit
-    int64_t nunits;
-    int maxc;                  // max nm*nw over the instances (shared tile width)
-    double *partial;           // [nunits]
+    const int32_t *chunk_inst; // [nchunks] instance of each chunk, costliest instances first
+    int64_t nchunks;
+    unsigned long long *next;  // chunk counter, zeroed before each launch
+    double *partial;
 };
 
-__device__ __forceinline__ int64_t kq_index(int64_t k, int64_t q, const int kg[3], const int qg[3]) {
-    const int k3 = (int)(k % kg[2]), k2 = (int)((k / kg[2]) % kg[1]), k1 = (int)(k / ((int64_t)kg[1] * kg[2]));
-    const int q3 = (int)(q % qg[2]), q2 = (int)((q / qg[2]) % qg[1]), q1 = (int)(q / ((int64_t)qg[1] * qg[2]));
-    const int s1 = (k1 + q1 * (kg[0] / qg[0])) % kg[0];
-    const int s2 = (k2 + q2 * (kg[1] / qg[1])) % kg[1];
-    const int s3 = (k3 + q3 * (kg[2] / qg[2])) % kg[2];
-    return ((int64_t)s1 * kg[1] + s2) * kg[2] + s3;
+constexpr int kTPL = (kMaxNw * kMaxNmode + 31) / 32;   // row elements per lane (8)
+
+// One chunk of one instance: q-points q0 .. q0 + nq of k-point b, every band.
+// sum_i conj(U_im) C[ka][i] over this lane's EL elements
+template <int EL>
+__device__ __forceinline__ float2 rot_part(const float2 *__restrict__ ur, const float2 (&cr)[kMaxNw]) {
+    float2 rr = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int e = 0; e < EL; ++e) cfma_conj(rr, ur[e], cr[e]);
+    return rr;
 }
 
-// 8-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros (src not read)
-__device__ __forceinline__ void cp_async8(void *dst, const void *src, int src_bytes) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-template <int QT, int NT>
-__global__ void __launch_bounds__(NT) k_batch_rates(BArgs a) {
-    extern __shared__ __align__(16) float2 sm[];
-    float2 *Cs = sm;                         // [QT][maxc]
-    float2 *As = Cs + QT * a.maxc;           // [2][QT][KC]
-    float2 *Bs = As + 2 * QT * KC;           // [2][KC][maxc]
-    __shared__ double red[NT / 32];
-    __shared__ int wcnt[NT / 32];
-    __shared__ int kqrow[QT];                    // k+q grid index of each tile row
-    __shared__ uint32_t items[QT * kMaxNmode];   // live (q, nu) of the tile: item << 16 | mask of m
-    const int t = threadIdx.x;
-    for (int64_t u = blockIdx.x; u < a.nunits; u += gridDim.x) {
-        const BInst I = a.inst[a.unit_inst[u]];
-        const int nw = I.nw, nm = I.nm, ncn = nm * nw, ncol = nm * nw * nw;
-        const int64_t r = u - I.unit0;
-        const int qt = (int)(r % I.nqt);
-        const int n = (int)((r / I.nqt) % nw);
-        const int64_t kb = r / ((int64_t)I.nqt * nw);
-        const int64_t q0 = (int64_t)qt * QT;
-        const int nq = (int)(I.Nq - q0 < QT ? I.Nq - q0 : QT);
-        const float2 *Gk = I.G + kb * (int64_t)I.nKp * ncol + (int64_t)n * ncn;
-        if (I.Ctc) {
-            // 1'. the R_p sum came from the tensor cores: copy band n's columns of the tile
-            const float2 *src = I.Ctc + (kb * I.Nq + q0) * I.ldc + (int64_t)n * ncn;
-            for (int o = t; o < nq * ncn; o += NT) {
-                const int qq = o / ncn, cc = o - (o / ncn) * ncn;
-                Cs[qq * a.maxc + cc] = src[(int64_t)qq * I.ldc + cc];
-            }
-            __syncthreads();
+__device__ __forceinline__ float2 rot_dispatch(int el, const float2 *__restrict__ ur, const float2 (&cr)[kMaxNw]) {
+    switch (el) {
+        case 1: return rot_part<1>(ur, cr);
+        case 2: return rot_part<2>(ur, cr);
+        case 3: return rot_part<3>(ur, cr);
+        case 4: return rot_part<4>(ur, cr);
+        case 6: return rot_part<6>(ur, cr);
+        case 8: return rot_part<8>(ur, cr);
+        case 12: return rot_part<12>(ur, cr);
+        default: {
+            float2 rr = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int e = 0; e < kMaxNw; ++e)
+                if (e < el) cfma_conj(rr, ur[e], cr[e]);
+            return rr;
         }
-        for (int o = t; o < QT * ncn && !I.Ctc; o += NT) Cs[(o / ncn) * a.maxc + o % ncn] = make_float2(0.f, 0.f);
-        // 1. R_p-sum tile; K chunk c + 1 is copied (cp.async) while chunk c is multiplied
-        const int nch = I.Ctc ? 0 : (I.nKp + KC - 1) / KC;
-        auto fill = [&](int c) {
-            const int p0 = c * KC;
-            float2 *Ab = As + (c & 1) * QT * KC, *Bb = Bs + (c & 1) * KC * a.maxc;
-            for (int o = t; o < QT * KC; o += NT) {
-                const int qq = o / KC, kk = o % KC;
-                const bool ok = qq < nq && p0 + kk < I.nKp;
-                cp_async8(Ab + o, ok ? I.phq + (q0 + qq) * I.nKp + p0 + kk : I.phq, ok ? 8 : 0);
-            }
-            for (int o = t; o < KC * ncn; o += NT) {
-                const int kk = o / ncn, cc = o - (o / ncn) * ncn;
-                const bool ok = p0 + kk < I.nKp;
-                cp_async8(Bb + kk * a.maxc + cc, ok ? Gk + (int64_t)(p0 + kk) * ncol + cc : Gk, ok ? 8 : 0);
-            }
-            cp_async_commit();
-        };
-        if (nch > 0) fill(0);
-        for (int c = 0; c < nch; ++c) {
-            if (c + 1 < nch) {
-                fill(c + 1);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
-            __syncthreads();
-            const float2 *Ab = As + (c & 1) * QT * KC, *Bb = Bs + (c & 1) * KC * a.maxc;
-            // each thread: one column, RT rows spaced QT/RT apart (one B load feeds RT products)
-            for (int o = t; o < (QT / RT) * ncn; o += NT) {
-                const int q0r = o / ncn, cc = o - (o / ncn) * ncn;
-                float2 acc[RT];
+    }
+}
+
+__device__ __forceinline__ void batch_chunk(const BInst &I, int64_t b, int qci, double *__restrict__ partial) {
+    const int lane = threadIdx.x & 31;
+    const int nw = I.nw, nm = I.nm, P = nm * nw, nc = nm * nw;
+    const int64_t q0 = (int64_t)qci * I.qc;
+    const int nq = (int)(I.Nq - q0 < I.qc ? I.Nq - q0 : I.qc);
+    const int64_t k = I.kidx[b];
+    // grid coordinates of k and of the chunk's first q; k+q follows q incrementally
+    const int kg0 = I.kg[0], kg1 = I.kg[1], kg2 = I.kg[2], qg1 = I.qg[1], qg2 = I.qg[2];
+    const int st0 = kg0 / I.qg[0], st1 = kg1 / qg1, st2 = kg2 / qg2;
+    const int k3 = (int)(k % kg2), k2 = (int)((k / kg2) % kg1), k1 = (int)(k / ((int64_t)kg1 * kg2));
+    int c3 = (int)(q0 % qg2), c2 = (int)((q0 / qg2) % qg1), c1 = (int)(q0 / ((int64_t)qg1 * qg2));
+    // lane -> (mode column ka, block of EL consecutive i) of a row: ib lanes per ka
+    const int ib = I.ib, el = nw / ib;
+    const bool act = lane < nm * ib;
+    const int ka = act ? lane / ib : 0, i0 = act ? (lane - (lane / ib) * ib) * el : 0;
+    // screen combos c = 32 j + lane -> (nu, m), packed as nu * 16 + m, four per word
+    uint32_t scm[kTPL / 4] = {0u, 0u};
 #pragma unroll
-                for (int j = 0; j < RT; ++j) acc[j] = make_float2(0.f, 0.f);
+    for (int j = 0; j < kTPL; ++j) {
+        const int cc = 32 * j + lane;
+        const uint32_t v = cc < nc ? (uint32_t)(cc / nw) : 0u, m = cc < nc ? (uint32_t)(cc - (cc / nw) * nw) : 0u;
+        scm[j / 4] |= ((v << 4) | m) << (8 * (j % 4));
+    }
+    const int nj = (nc + 31) / 32;
+    const double is = 1.0 / I.sigma, ycut2 = kDeltaCut * kDeltaCut;
+    const float cut32 = (float)(kDeltaCut * I.sigma) + 1e-4f;
+    // band energies at k: band n in lane n
+    const float en32_l = lane < nw ? I.eps32[k * nw + lane] : 0.f;
+    const double en64_l = lane < nw ? I.eps[k * nw + lane] : 0.0;
+    double acc = 0.0;   // lane n: band n's sum over the chunk
+    // the term waiting in this lane's slot: |g|^2, band n, and the indices of e_m(k+q) and (q, nu)
+    int pending = 0, p_n = 0, p_e = 0, p_qv = 0;
+    float p_g2 = 0.f;
+    // weights of the waiting terms in FP64 (full warp), then per-band sums in a fixed order
+    auto flush = [&](int count) {
+        double contrib = 0.0;
+        const double en = __shfl_sync(0xffffffffu, en64_l, p_n);
+        if (lane < count) {
+            const double w = I.hw[p_qv], N = I.nbe[p_qv], f = I.focc[p_e];
+            const double d = en - I.eps[p_e];
+            const double ye = (d - w) * is, ya = (d + w) * is;
+            double W = 0.0;
+            if (ye * ye <= ycut2) W += exp(-ye * ye) * (1.0 + N - f);
+            if (ya * ya <= ycut2) W += exp(-ya * ya) * (N + f);
+            contrib = (double)p_g2 * W;
+        }
+        // per-band sums of the (at most 32) waiting terms in FP32, only over the bands present;
+        // the chunk's band sums accumulate in FP64
+        double mine = 0.0;
+        unsigned todo = 0u;
+        for (int nn = 0; nn < nw; ++nn) todo |= __ballot_sync(0xffffffffu, lane < count && p_n == nn) ? (1u << nn) : 0u;
+        while (todo) {
+            const int nn = __ffs(todo) - 1;
+            todo &= todo - 1;
+            float sh = (lane < count && p_n == nn) ? (float)contrib : 0.f;
 #pragma unroll
-                for (int kk = 0; kk < KC; kk += 2) {
-                    const float2 b0 = Bb[kk * a.maxc + cc], b1 = Bb[(kk + 1) * a.maxc + cc];
+            for (int o = 16; o > 0; o >>= 1) sh += __shfl_xor_sync(0xffffffffu, sh, o);
+            if (lane == nn) mine = (double)sh;
+        }
+        acc += mine;
+    };
+    for (int qq = 0; qq < nq; ++qq) {
+        const int64_t q = q0 + qq;
+        int t1 = k1 + c1 * st0, t2 = k2 + c2 * st1, t3 = k3 + c3 * st2;
+        t1 -= (t1 >= kg0) ? kg0 : 0;
+        t2 -= (t2 >= kg1) ? kg1 : 0;
+        t3 -= (t3 >= kg2) ? kg2 : 0;
+        const int kq = (t1 * kg1 + t2) * kg2 + t3;
+        if (++c3 == qg2) {
+            c3 = 0;
+            if (++c2 == qg1) {
+                c2 = 0;
+                ++c1;
+            }
+        }
+        // screening inputs held by lanes: e_m(k+q) in lane m, hbar*omega_nu(q) in lane nu
+        const float em_l = lane < nw ? I.eps32[(int64_t)kq * nw + lane] : 0.f;
+        const float w_l = lane < nm ? I.hw32[q * nm + lane] : 0.f;
+        const float2 *Ukq = I.U + (int64_t)kq * nw * nw + i0;
+        const float2 *cq = I.coef + q * nm * nm + ka;
+        for (int n = 0; n < nw; ++n) {
+            const float en = __shfl_sync(0xffffffffu, en32_l, n);
+            bool loaded = false;
+            float2 cr[kMaxNw];
+            for (int j = 0; j < nj; ++j) {
+                const uint32_t vm = (scm[j / 4] >> (8 * (j % 4))) & 0xffu;
+                const float em = __shfl_sync(0xffffffffu, em_l, (int)(vm & 15u));
+                const float w = __shfl_sync(0xffffffffu, w_l, (int)(vm >> 4));
+                bool live = false;
+                if (32 * j + lane < nc && w >= (float)kOmegaMinEv) {
+                    const float d = en - em;
+                    live = fabsf(d - w) <= cut32 || fabsf(d + w) <= cut32;
+                }
+                unsigned bal = __ballot_sync(0xffffffffu, live);
+                if (bal && !loaded) {
+                    // this lane's elements C[q][n][ka][i0 .. i0 + EL), loaded once the row has a live term
+                    const float2 *crow = I.C + (b * I.Nq + q) * I.ldc + (int64_t)n * P + ka * nw + i0;
 #pragma unroll
-                    for (int j = 0; j < RT; ++j) {
-                        const float4 av = *reinterpret_cast<const float4 *>(Ab + (q0r + j * (QT / RT)) * KC + kk);
-                        cfma(acc[j], make_float2(av.x, av.y), b0);
-                        cfma(acc[j], make_float2(av.z, av.w), b1);
+                    for (int e = 0; e < kMaxNw; ++e) cr[e] = (act && e < el) ? crow[e] : make_float2(0.f, 0.f);
+                    loaded = true;
+                }
+                while (bal) {
+                    // up to four live terms at a time, so their loads and reductions overlap
+                    constexpr int TB = 4;
+                    int cnt = 0;
+                    uint32_t tv[TB];
+#pragma unroll
+                    for (int u = 0; u < TB; ++u) {
+                        const int src = bal ? __ffs(bal) - 1 : 0;
+                        tv[u] = __shfl_sync(0xffffffffu, vm, src);
+                        if (bal) {
+                            bal &= bal - 1;
+                            ++cnt;
+                        }
                     }
-                }
+                    // g = sum_ka coef[q][nu][ka] sum_i conj(U_im(k+q)) C[q][n][ka][i]
+                    float2 g[TB];
 #pragma unroll
-                for (int j = 0; j < RT; ++j) {
-                    float2 &d = Cs[(q0r + j * (QT / RT)) * a.maxc + cc];
-                    d.x += acc[j].x;
-                    d.y += acc[j].y;
-                }
-            }
-            __syncthreads();    // buffer c & 1 is refilled by the next pass
-        }
-        // 2. epilogue.  (a) screen every (q, nu) of the tile in FP32 (|x| <= 7 sigma plus a
-        //    margin) and list the live ones, in item order, by a block-wide scan;
-        //    (b) one live (q, nu) per thread: project on nu, rotate by U(k+q) for each
-        //    surviving m (FP32 products), weights and occupations in FP64.  The list
-        //    keeps whole warps on the projection however sparse the survivors are.
-        double part = 0.0;
-        const int64_t k = I.kidx[kb];
-        const double en = I.eps[k * nw + n];
-        const float en32 = I.eps32[k * nw + n];
-        const double is = 1.0 / I.sigma, ycut2 = kDeltaCut * kDeltaCut;
-        const float cut32 = (float)(kDeltaCut * I.sigma) + 1e-4f;
-        for (int qq = t; qq < nq; qq += NT) kqrow[qq] = (int)kq_index(k, q0 + qq, I.kg, I.qg);
-        __syncthreads();
-        const int lane = t & 31, wid = t >> 5;
-        int nlive = 0;
-        for (int o0 = 0; o0 < QT * nm; o0 += NT) {
-            const int o = o0 + t;
-            uint32_t live = 0;
-            if (o < QT * nm) {
-                const int qq = o / nm, v = o - (o / nm) * nm;
-                if (qq < nq) {
-                    const int64_t q = q0 + qq;
-                    const float w32 = I.hw32[q * nm + v];
-                    if (w32 >= (float)kOmegaMinEv) {
-                        const float *em32 = I.eps32 + (int64_t)kqrow[qq] * nw;
-                        for (int m = 0; m < nw; ++m) {
-                            const float d = en32 - em32[m];
-                            if (fabsf(d - w32) <= cut32 || fabsf(d + w32) <= cut32) live |= 1u << m;
+                    for (int u = 0; u < TB; ++u) {
+                        g[u] = make_float2(0.f, 0.f);
+                        if (act && u < cnt) {
+                            const int v = (int)(tv[u] >> 4), m = (int)(tv[u] & 15u);
+                            const float2 rr = rot_dispatch(el, Ukq + m * nw, cr);
+                            cfma(g[u], cq[v * nm], rr);
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                        for (int u = 0; u < TB; ++u) {
+                            g[u].x += __shfl_xor_sync(0xffffffffu, g[u].x, o);
+                            g[u].y += __shfl_xor_sync(0xffffffffu, g[u].y, o);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < TB; ++u) {
+                        if (u >= cnt) break;
+                        if (lane == pending) {
+                            p_n = n;
+                            p_g2 = cabs2(g[u]);
+                            p_e = kq * nw + (int)(tv[u] & 15u);
+                            p_qv = (int)(q * nm) + (int)(tv[u] >> 4);
+                        }
+                        if (++pending == 32) {
+                            flush(32);
+                            pending = 0;
                         }
                     }
                 }
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, live != 0);
-            if (lane == 0) wcnt[wid] = __popc(bal);
-            __syncthreads();
-            int base = nlive, tot = 0;
-#pragma unroll
-            for (int w2 = 0; w2 < NT / 32; ++w2) {
-                base += (w2 < wid) ? wcnt[w2] : 0;
-                tot += wcnt[w2];
-            }
-            if (live) items[base + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)o << 16) | live;
-            nlive += tot;
-            __syncthreads();
         }
-        for (int j = t; j < nlive; j += NT) {
-            const uint32_t it = items[j];
-            uint32_t live = it & 0xffffu;
-            const int o = (int)(it >> 16);
-            const int qq = o / nm, v = o - (o / nm) * nm;
-            const int64_t q = q0 + qq;
-            const int64_t kq = kqrow[qq];
-            const double w = I.hw[q * nm + v];
-            const double *em = I.eps + kq * nw;
-            const float2 *cf = I.coef + (q * nm + v) * nm;
-            float2 gv[kMaxNw];
-#pragma unroll
-            for (int i = 0; i < kMaxNw; ++i) gv[i] = make_float2(0.f, 0.f);
-            for (int ka = 0; ka < nm; ++ka) {
-                const float2 cc = cf[ka];
-                const float2 *row = Cs + qq * a.maxc + ka * nw;
-#pragma unroll
-                for (int i = 0; i < kMaxNw; ++i)
-                    if (i < nw) cfma(gv[i], cc, row[i]);
-            }
-            const float2 *Ukq = I.U + kq * nw * nw;
-            const double N = I.nbe[q * nm + v];
-            while (live) {
-                const int m = __ffs(live) - 1;
-                live &= live - 1;
-                float2 g = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int i = 0; i < kMaxNw; ++i)
-                    if (i < nw) cfma_conj(g, Ukq[m * nw + i], gv[i]);
-                const double g2 = (double)cabs2(g);
-                const double d = en - em[m];
-                const double ye = (d - w) * is, ya = (d + w) * is;
-                const double fm = I.focc[kq * nw + m];
-                double W = 0.0;
-                if (ye * ye <= ycut2) W += exp(-ye * ye) * (1.0 + N - fm);
-                if (ya * ya <= ycut2) W += exp(-ya * ya) * (N + fm);
-                part = fma(g2, W, part);
-            }
-        }
-        // 3. block sum into this unit's slot (fixed tree)
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
-        if ((t & 31) == 0) red[t >> 5] = part;
-        __syncthreads();
-        if (t == 0) {
-            double s = 0.0;
-            for (int w2 = 0; w2 < NT / 32; ++w2) s += red[w2];
-            a.partial[u] = s;
-        }
+    }
+    flush(pending);
+    if (lane < nw) partial[I.part0 + (b * nw + lane) * I.nch + qci] = acc;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_batch_warp(BArgs a) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(a.next, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if ((long long)c >= a.nchunks) break;
+        const BInst &I = a.inst[a.chunk_inst[c]];
+        const int64_t r = (int64_t)c - I.chunk0;
+        const int qci = (int)(r % I.nch);
+        const int64_t b = r / I.nch;
+        batch_chunk(I, b, qci, a.partial);
     }
 }
 
@@ -294,42 +300,45 @@ __global__ void k_batch_reduce(int nrows, int nqt, double scale, const double *_
     out[r] = scale * s;
 }
 
+// Autotuner candidates: block size and a scale of the chunk length.
 struct Cand {
-    int qt, nt;
+    int nt;
+    int scale;
 };
-constexpr Cand kCands[4] = {{16, 128}, {32, 128}, {32, 256}, {64, 256}};
+constexpr Cand kCands[4] = {{128, 1}, {256, 1}, {256, 4}, {512, 4}};
 
-size_t smem_bytes(int qt, int maxc) { return sizeof(float2) * ((size_t)qt * maxc + 2 * ((size_t)qt * KC + (size_t)KC * maxc)); }
+// q-points per chunk: about 4096 lane-steps of work per band at scale 1.
+int pick_qc(int scale, int nw, int nm) {
+    const int want = 4096 / (nw * (nm * nw + 32));
+    int qc = 8;
+    while (qc * 2 <= want && qc < 512) qc *= 2;
+    return qc * scale;
+}
 
-// CTAs per SM of a candidate (sets its shared-memory limit; call outside stream capture)
-template <int QT, int NT>
-cudaError_t prepare_one(int maxc, int *per_sm) {
-    const size_t sh = smem_bytes(QT, maxc);
-    cudaError_t e = cudaFuncSetAttribute(k_batch_rates<QT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch_rates<QT, NT>, NT, sh);
+template <int NT>
+cudaError_t prepare_one(int *per_sm) {
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch_warp<NT>, NT, 0);
     *per_sm = std::max(*per_sm, 1);
     return e;
 }
 
-cudaError_t prepare_cand(int ci, int maxc, int *per_sm) {
-    switch (ci) {
-        case 0: return prepare_one<16, 128>(maxc, per_sm);
-        case 1: return prepare_one<32, 128>(maxc, per_sm);
-        case 2: return prepare_one<32, 256>(maxc, per_sm);
-        default: return prepare_one<64, 256>(maxc, per_sm);
+// CTAs per SM of a candidate (call outside stream capture)
+cudaError_t prepare_cand(int ci, int *per_sm) {
+    switch (kCands[ci].nt) {
+        case 128: return prepare_one<128>(per_sm);
+        case 256: return prepare_one<256>(per_sm);
+        default: return prepare_one<512>(per_sm);
     }
 }
 
-// persistent grid: every SM's resident CTAs, at most one per unit
+// persistent grid: every SM's resident CTAs, at most one warp per chunk
 cudaError_t launch_cand(int ci, const BArgs &a, cudaStream_t s, int nsm, int per_sm) {
-    const int64_t grid = std::min<int64_t>((int64_t)nsm * per_sm, std::max<int64_t>(a.nunits, 1));
-    const size_t sh = smem_bytes(kCands[ci].qt, a.maxc);
-    switch (ci) {
-        case 0: k_batch_rates<16, 128><<<(unsigned)grid, 128, sh, s>>>(a); break;
-        case 1: k_batch_rates<32, 128><<<(unsigned)grid, 128, sh, s>>>(a); break;
-        case 2: k_batch_rates<32, 256><<<(unsigned)grid, 256, sh, s>>>(a); break;
-        default: k_batch_rates<64, 256><<<(unsigned)grid, 256, sh, s>>>(a); break;
+    const int nt = kCands[ci].nt;
+    const int64_t grid = std::min<int64_t>((int64_t)nsm * per_sm, std::max<int64_t>((a.nchunks + nt / 32 - 1) / (nt / 32), 1));
+    switch (nt) {
+        case 128: k_batch_warp<128><<<(unsigned)grid, 128, 0, s>>>(a); break;
+        case 256: k_batch_warp<256><<<(unsigned)grid, 256, 0, s>>>(a); break;
+        default: k_batch_warp<512><<<(unsigned)grid, 512, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }
@@ -348,9 +357,8 @@ struct pgb_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
     int nsm = 0;
-    int maxc = 0;
     int cand = -1;                     // chosen candidate
-    int prec = PGB_FP32;          // q-sum precision of the instances whose columns tile by 96
+    int prec = PGB_FP32;               // q-sum precision: SIMT FP32 or tensor-core split
     int *d_err = nullptr;              // wait time-outs of the tensor-core q-sums
     float cand_ms[4] = {-1, -1, -1, -1};
     int per_sm[4] = {0, 0, 0, 0};      // resident CTAs per SM of each candidate
@@ -363,10 +371,12 @@ struct pgb_batch {
     // device buffers owned by the batch
     std::vector<void *> bufs;
     BInst *d_inst = nullptr;
-    int32_t *d_unit_inst = nullptr;
+    int32_t *d_chunk_inst = nullptr;
     double *d_partial = nullptr, *d_out = nullptr;
-    int64_t nunits = 0, nout = 0;
+    unsigned long long *d_next = nullptr;
+    int64_t nchunks = 0, nout = 0;
     std::vector<int64_t> out0;         // first output row of each instance
+    std::vector<int> qc;               // chunk length of each instance for the current candidate
     std::string err;
     void release() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -374,8 +384,9 @@ struct pgb_batch {
         for (void *p : bufs) cudaFree(p);
         bufs.clear();
         d_inst = nullptr;
-        d_unit_inst = nullptr;
+        d_chunk_inst = nullptr;
         d_partial = d_out = nullptr;
+        d_next = nullptr;
     }
 };
 
@@ -394,23 +405,26 @@ pgb_status balloc(pgb_batch *b, T **p, size_t n) {
     return PGB_OK;
 }
 
-// Per-instance set-up plus the persistent kernel (and the reduction) on the
-// batch stream; candidate ci.  Enqueue only: no allocation, no synchronisation.
+// Per-instance buffers and tables of one call (independent of the tile candidate).
 struct Plan {
     std::vector<BInst> inst;
     struct Per {
-        int32_t *kidx;
-        void *phk, *S1, *G;
-        double *focc, *nbe;
-        float *eps32, *hw32;
-        bool tc = false;               // q sum on the tensor cores (k_tc_qsum)
-        int Kp = 0, ldc = 0;
+        int32_t *kidx = nullptr;
+        void *phk = nullptr, *S1 = nullptr, *G = nullptr;
+        double *focc = nullptr, *nbe = nullptr;
+        float *eps32 = nullptr, *hw32 = nullptr;
+        float2 *phq = nullptr;         // FP32 q table (SIMT q-sum)
+        bool tc = false;               // q-sum on the tensor cores (k_tc_qsum)
+        int Kp = 0;
+        int64_t ldc = 0;
         void *Asplit = nullptr, *Bsplit = nullptr;
-        float2 *Ctc = nullptr;
+        float2 *C = nullptr;           // [nk][Nq][ldc]
     };
     std::vector<Per> per;
 };
 
+// Enqueue the set-up of every instance, the persistent kernel of candidate ci and
+// the reductions on the batch stream.  No allocation, no synchronisation.
 pgb_status enqueue(pgb_batch *b, Plan &P, int ci) {
     const int n = (int)b->ctx.size();
     if (b->prec != PGB_FP32 && cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream) != cudaSuccess) {
@@ -426,15 +440,20 @@ pgb_status enqueue(pgb_batch *b, Plan &P, int ci) {
         const int64_t nrowS = (int64_t)c->nRgp * ncol;
         Plan::Per &q = P.per[i];
         pgb_status st = launch_occ_tables(c, b->T, b->mu[i], q.focc, q.eps32, q.nbe, q.hw32);
-        if (st == PGB_OK) st = launch_phase_grid(c, c->kg, q.kidx, nk, c->d_Rge, c->nRge, q.phk, true);
-        if (st == PGB_OK)
-            st = launch_cgemm(c, true, 1, nk, nrowS, c->nRge, q.phk, c->nRge, 0, c->d_g32, nrowS, 0, q.S1, nrowS, 0);
-        if (st == PGB_OK) st = launch_fold_u(c, true, nk, q.kidx, c->nRgp, c->nm, c->nw, q.S1, c->d_U32, q.G);
-        if (st == PGB_OK && q.tc) {
-            const bool tf32 = b->prec == PGB_TC_TF32X3;
-            st = launch_split_g(c, tf32, nk, c->nKp, (int)ncol, q.Kp, q.G, q.Bsplit, q.ldc);
+        if (nk > 0) {
+            if (st == PGB_OK) st = launch_phase_grid(c, c->kg, q.kidx, nk, c->d_Rge, c->nRge, q.phk, true);
             if (st == PGB_OK)
-                st = launch_tc_qsum(c, tf32, nk, c->Nq, q.ldc, q.Kp, q.Asplit, q.Bsplit, q.Ctc, b->d_err);
+                st = launch_cgemm(c, true, 1, nk, nrowS, c->nRge, q.phk, c->nRge, 0, c->d_g32, nrowS, 0, q.S1, nrowS, 0);
+            if (st == PGB_OK) st = launch_fold_u(c, true, nk, q.kidx, c->nRgp, c->nm, c->nw, q.S1, c->d_U32, q.G);
+            if (st == PGB_OK && q.tc) {
+                const bool tf32 = b->prec == PGB_TC_TF32X3;
+                st = launch_split_g(c, tf32, nk, c->nKp, (int)ncol, q.Kp, q.G, q.Bsplit, (int)q.ldc);
+                if (st == PGB_OK)
+                    st = launch_tc_qsum(c, tf32, nk, c->Nq, (int)q.ldc, q.Kp, q.Asplit, q.Bsplit, q.C, b->d_err);
+            } else if (st == PGB_OK) {
+                st = launch_cgemm(c, true, nk, c->Nq, ncol, c->nKp, q.phq, c->nKp, 0, q.G, ncol, (int64_t)c->nKp * ncol,
+                                  q.C, ncol, c->Nq * ncol);
+            }
         }
         c->stream = saved;
         if (st != PGB_OK) {
@@ -442,12 +461,15 @@ pgb_status enqueue(pgb_batch *b, Plan &P, int ci) {
             return st;
         }
     }
+    if (cudaMemsetAsync(b->d_next, 0, sizeof(unsigned long long), b->stream) != cudaSuccess) {
+        b->err = "batch: chunk counter reset failed";
+        return PGB_ECUDA;
+    }
     BArgs a;
-    a.ninst = n;
     a.inst = b->d_inst;
-    a.unit_inst = b->d_unit_inst;
-    a.nunits = b->nunits;
-    a.maxc = b->maxc;
+    a.chunk_inst = b->d_chunk_inst;
+    a.nchunks = b->nchunks;
+    a.next = b->d_next;
     a.partial = b->d_partial;
     cudaError_t e = launch_cand(ci, a, b->stream, b->nsm, b->per_sm[ci]);
     if (e != cudaSuccess) {
@@ -459,7 +481,7 @@ pgb_status enqueue(pgb_batch *b, Plan &P, int ci) {
         const int nrows = (int)(b->kidx[i].size() * I.nw);
         if (nrows == 0) continue;
         const double scale = kTwoPiOverHbar / ((double)I.Nq * b->sigma * kSqrtPi);
-        k_batch_reduce<<<div_up(nrows, 128), 128, 0, b->stream>>>(nrows, I.nqt, scale, b->d_partial + I.unit0,
+        k_batch_reduce<<<div_up(nrows, 128), 128, 0, b->stream>>>(nrows, I.nch, scale, b->d_partial + I.part0,
                                                                    b->d_out + b->out0[i]);
         if ((e = cudaGetLastError()) != cudaSuccess) {
             b->err = std::string("batch: reduce launch: ") + cudaGetErrorString(e);
@@ -469,13 +491,14 @@ pgb_status enqueue(pgb_batch *b, Plan &P, int ci) {
     return PGB_OK;
 }
 
-pgb_status build_plan(pgb_batch *b, Plan &P, int qt) {
+// Buffers and call-independent tables of every instance (q tables or split q phases,
+// transposed U), built outside any capture.
+pgb_status build_plan(pgb_batch *b, Plan &P) {
     const int n = (int)b->ctx.size();
     P.inst.assign(n, BInst());
     P.per.assign(n, Plan::Per());
-    int64_t unit0 = 0, out0 = 0;
+    int64_t out0 = 0;
     b->out0.assign(n, 0);
-    std::vector<int32_t> unit_inst;
     for (int i = 0; i < n; ++i) {
         pgb_ctx *c = b->ctx[i];
         const int64_t nk = (int64_t)b->kidx[i].size();
@@ -483,16 +506,14 @@ pgb_status build_plan(pgb_batch *b, Plan &P, int qt) {
         BInst &I = P.inst[i];
         I.nw = c->nw;
         I.nm = c->nm;
-        I.nRgp = c->nRgp;
-        I.nKp = c->nKp;
         for (int d = 0; d < 3; ++d) {
             I.qg[d] = c->qg[d];
             I.kg[d] = c->kg[d];
         }
         I.Nq = c->Nq;
-        I.nqt = (int)((c->Nq + qt - 1) / qt);
-        I.unit0 = unit0;
-
+        I.ib = 1;
+        for (int ib : {4, 2})
+            if (I.ib == 1 && c->nm * ib <= 32 && c->nw % ib == 0) I.ib = ib;
         I.eps = c->d_eps;
         I.coef = c->d_coef32;
         I.hw = c->d_hw;
@@ -515,42 +536,37 @@ pgb_status build_plan(pgb_batch *b, Plan &P, int qt) {
         if ((st = balloc(b, &q.eps32, (size_t)c->Nk * c->nw)) != PGB_OK) return st;
         if ((st = balloc(b, &q.nbe, (size_t)c->Nq * c->nm)) != PGB_OK) return st;
         if ((st = balloc(b, &q.hw32, (size_t)c->Nq * c->nm)) != PGB_OK) return st;
-        // non-polar instances take the tensor-core q sum when the batch runs in a split
-        // precision, their nm*nw*nw columns padded with zeros to a multiple of 96
-        q.tc = b->prec != PGB_FP32 && !c->polar && nk > 0;
-        float2 *phq = nullptr;
+        // split precisions: every instance's q-sum on the tensor cores, its nm*nw*nw
+        // columns padded with zeros to a multiple of 96 (polar instances carry the
+        // long-range term in nm extra rows of the split phases)
+        q.tc = b->prec != PGB_FP32 && nk > 0;
+        cudaStream_t saved = c->stream;
+        c->stream = b->stream;
         if (q.tc) {
             const bool tf32 = b->prec == PGB_TC_TF32X3;
             const size_t tes = tf32 ? 4 : 2;
             q.Kp = tc_kpad(c->nKp);
-            q.ldc = (int)((ncol + 95) / 96 * 96);
+            q.ldc = (ncol + 95) / 96 * 96;
             char *As, *Bs;
-            if ((st = balloc(b, &As, (size_t)4 * c->Nq * q.Kp * tes)) != PGB_OK) return st;
-            if ((st = balloc(b, &Bs, (size_t)nk * 4 * q.ldc * q.Kp * tes)) != PGB_OK) return st;
-            if ((st = balloc(b, &q.Ctc, (size_t)nk * c->Nq * q.ldc)) != PGB_OK) return st;
-            q.Asplit = As;
-            q.Bsplit = Bs;
-            cudaStream_t saved = c->stream;   // split q phases: outside any capture
-            c->stream = b->stream;
-            st = launch_split_phases(c, tf32, c->qg, c->Nq, c->d_Rgp, c->nRgp, q.Kp, q.Asplit);
-            c->stream = saved;
-            if (st != PGB_OK || cudaStreamSynchronize(b->stream) != cudaSuccess) {
-                b->err = "batch: split q phases of instance " + std::to_string(i) + " failed";
-                return PGB_ECUDA;
+            if ((st = balloc(b, &As, (size_t)4 * c->Nq * q.Kp * tes)) == PGB_OK &&
+                (st = balloc(b, &Bs, (size_t)nk * 4 * q.ldc * q.Kp * tes)) == PGB_OK) {
+                q.Asplit = As;
+                q.Bsplit = Bs;
+                st = launch_split_phases(c, tf32, c->qg, c->Nq, c->d_Rgp, c->nRgp, q.Kp, q.Asplit, c->d_polarL,
+                                         c->polar ? c->nm : 0);
             }
         } else {
-            if ((st = balloc(b, &phq, (size_t)c->Nq * c->nKp)) != PGB_OK) return st;
-            // q table, independent of the call's arguments: built here, outside any capture
-            cudaStream_t saved = c->stream;
-            c->stream = b->stream;
-            st = launch_qtable_grid(c, nullptr, c->Nq, phq, true);
-            c->stream = saved;
-            if (st != PGB_OK || cudaStreamSynchronize(b->stream) != cudaSuccess) {
-                b->err = "batch: q table of instance " + std::to_string(i) + " failed";
-                return PGB_ECUDA;
-            }
+            q.ldc = ncol;
+            if ((st = balloc(b, &q.phq, (size_t)c->Nq * c->nKp)) == PGB_OK)
+                st = launch_qtable_grid(c, nullptr, c->Nq, q.phq, true);
         }
-        {   // transposed U table of the instance's k grid, outside any capture
+        c->stream = saved;
+        if (st == PGB_OK) st = balloc(b, &q.C, (size_t)std::max<int64_t>(nk, 1) * c->Nq * q.ldc);
+        if (st != PGB_OK || cudaStreamSynchronize(b->stream) != cudaSuccess) {
+            if (b->err.empty() || st == PGB_OK) b->err = "batch: q tables of instance " + std::to_string(i) + " failed";
+            return st != PGB_OK ? st : PGB_ECUDA;
+        }
+        {   // transposed U table of the instance's k grid
             float2 *UT;
             if ((st = balloc(b, &UT, (size_t)c->Nk * c->nw * c->nw)) != PGB_OK) return st;
             const int64_t nt = c->Nk * c->nw * c->nw;
@@ -561,31 +577,59 @@ pgb_status build_plan(pgb_batch *b, Plan &P, int qt) {
             }
             I.U = UT;
         }
-        I.phq = phq;
-        I.Ctc = q.Ctc;
+        I.C = q.C;
         I.ldc = q.ldc;
         I.eps32 = q.eps32;
         I.hw32 = q.hw32;
-        I.G = (const float2 *)G;
         I.kidx = q.kidx;
         I.focc = q.focc;
         I.nbe = q.nbe;
-        const int64_t nu = nk * c->nw * I.nqt;
-        unit_inst.insert(unit_inst.end(), (size_t)nu, i);
-        unit0 += nu;
         b->out0[i] = out0;
         out0 += nk * c->nw;
     }
-    b->nunits = unit0;
     b->nout = out0;
     pgb_status st;
-    if ((st = balloc(b, &b->d_inst, (size_t)n)) != PGB_OK) return st;
-    if ((st = balloc(b, &b->d_unit_inst, (size_t)std::max<int64_t>(unit0, 1))) != PGB_OK) return st;
-    if ((st = balloc(b, &b->d_partial, (size_t)std::max<int64_t>(unit0, 1))) != PGB_OK) return st;
     if ((st = balloc(b, &b->d_out, (size_t)std::max<int64_t>(out0, 1))) != PGB_OK) return st;
+    if ((st = balloc(b, &b->d_next, 1)) != PGB_OK) return st;
+    if ((st = balloc(b, &b->d_inst, (size_t)n)) != PGB_OK) return st;
+    return PGB_OK;
+}
+
+// Chunk lengths, chunk order and partial slots of candidate ci; uploads the descriptors.
+pgb_status set_candidate(pgb_batch *b, Plan &P, int ci) {
+    const int n = (int)b->ctx.size();
+    b->qc.assign(n, 0);
+    std::vector<double> cost(n, 0.0);
+    int64_t part0 = 0;
+    for (int i = 0; i < n; ++i) {
+        BInst &I = P.inst[i];
+        I.qc = pick_qc(kCands[ci].scale, I.nw, I.nm);
+        b->qc[i] = I.qc;
+        I.nch = (int)((I.Nq + I.qc - 1) / I.qc);
+        I.part0 = part0;
+        part0 += (int64_t)b->kidx[i].size() * I.nw * I.nch;
+        cost[i] = (double)I.qc * I.nw * (I.nm * I.nw + 32);
+    }
+    // chunks of the costliest instances first, so the counter hands out the big ones early
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<int32_t> chunk_inst;
+    int64_t chunk0 = 0;
+    for (int i : order) {
+        BInst &I = P.inst[i];
+        I.chunk0 = chunk0;
+        const int64_t nch = (int64_t)b->kidx[i].size() * I.nch;
+        chunk_inst.insert(chunk_inst.end(), (size_t)nch, i);
+        chunk0 += nch;
+    }
+    b->nchunks = chunk0;
+    pgb_status st;
+    if ((st = balloc(b, &b->d_chunk_inst, (size_t)std::max<int64_t>(chunk0, 1))) != PGB_OK) return st;
+    if ((st = balloc(b, &b->d_partial, (size_t)std::max<int64_t>(part0, 1))) != PGB_OK) return st;
     if (cudaMemcpy(b->d_inst, P.inst.data(), sizeof(BInst) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
-        (unit0 && cudaMemcpy(b->d_unit_inst, unit_inst.data(), 4 * (size_t)unit0, cudaMemcpyHostToDevice) !=
-                      cudaSuccess)) {
+        (chunk0 && cudaMemcpy(b->d_chunk_inst, chunk_inst.data(), 4 * (size_t)chunk0, cudaMemcpyHostToDevice) !=
+                       cudaSuccess)) {
         b->err = "batch: descriptor upload failed";
         return PGB_ECUDA;
     }
@@ -620,6 +664,7 @@ pgb_status pgb_batch_create(pgb_batch **out, pgb_ctx *const *ctxs, int n) {
         return PGB_ECUDA;
     }
     if (cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) {
+        cudaStreamDestroy(b->stream);
         delete b;
         return PGB_ECUDA;
     }
@@ -629,11 +674,8 @@ pgb_status pgb_batch_create(pgb_batch **out, pgb_ctx *const *ctxs, int n) {
         delete b;
         return PGB_ENOMEM;
     }
-    for (int i = 0; i < n; ++i) b->maxc = std::max(b->maxc, ctxs[i]->nm * ctxs[i]->nw);
     for (int ci = 0; ci < 4; ++ci) {
-        b->per_sm[ci] = 0;
-        if (smem_bytes(kCands[ci].qt, b->maxc) > 220 * 1024) continue;   // does not fit: never tried
-        if (prepare_cand(ci, b->maxc, &b->per_sm[ci]) != cudaSuccess) {
+        if (prepare_cand(ci, &b->per_sm[ci]) != cudaSuccess) {
             cudaGetLastError();
             b->per_sm[ci] = 0;
         }
@@ -726,15 +768,20 @@ pgb_status pgb_batch_rates(pgb_batch *b, const int32_t *const *k_idx, const int6
         b->mu = mu;
         b->T = T_K;
         b->sigma = sigma_eV;
-        // autotune on the first call: every candidate once, timed on the stream
+        Plan P;
+        pgb_status st = build_plan(b, P);
+        if (st != PGB_OK) {
+            b->release();
+            b->kidx.clear();
+            return st;
+        }
+        // autotune on the first call: every candidate once (after a warm-up), timed on the stream
         if (b->cand < 0) {
             float best = 1e30f;
             for (int ci = 0; ci < 4; ++ci) {
                 if (b->per_sm[ci] <= 0) continue;
-                Plan P;
-                pgb_status st = build_plan(b, P, kCands[ci].qt);
-                if (st != PGB_OK) return st;
-                if ((st = enqueue(b, P, ci)) != PGB_OK) return st;   // warm-up
+                if ((st = set_candidate(b, P, ci)) != PGB_OK) break;
+                if ((st = enqueue(b, P, ci)) != PGB_OK) break;   // warm-up
                 cudaEvent_t e0, e1;
                 cudaEventCreate(&e0);
                 cudaEventCreate(&e1);
@@ -746,44 +793,52 @@ pgb_status pgb_batch_rates(pgb_batch *b, const int32_t *const *k_idx, const int6
                 cudaEventElapsedTime(&ms, e0, e1);
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
-                if (st != PGB_OK) return st;
+                if (st != PGB_OK) break;
                 if (ce != cudaSuccess) {
                     b->err = std::string("batch_rates: ") + cudaGetErrorString(ce);
-                    return PGB_ECUDA;
+                    st = PGB_ECUDA;
+                    break;
                 }
                 b->cand_ms[ci] = ms;
                 if (ms < best) {
                     best = ms;
                     b->cand = ci;
                 }
-                b->release();
             }
-            if (b->cand < 0) {
-                b->err = "batch_rates: no tile candidate fits in shared memory";
-                return PGB_EINVAL;
+            if (st == PGB_OK && b->cand < 0) {
+                b->err = "batch_rates: no candidate could be launched";
+                st = PGB_EINVAL;
+            }
+            if (st != PGB_OK) {
+                b->release();
+                b->kidx.clear();
+                b->cand = -1;
+                return st;
             }
         }
-        Plan P;
-        pgb_status st = build_plan(b, P, kCands[b->cand].qt);
-        if (st != PGB_OK) return st;
+        if ((st = set_candidate(b, P, b->cand)) != PGB_OK) {
+            b->release();
+            b->kidx.clear();
+            return st;
+        }
         // capture set-up, kernel and reduction in one graph
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
             b->err = "batch_rates: stream capture could not start";
+            b->release();
+            b->kidx.clear();
             return PGB_ECUDA;
         }
         st = enqueue(b, P, b->cand);
         cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
-        if (st != PGB_OK) {
+        if (st != PGB_OK || ce != cudaSuccess || cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
-            return st;
-        }
-        if (ce != cudaSuccess || cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            b->err = "batch_rates: graph capture failed";
+            if (st == PGB_OK) b->err = "batch_rates: graph capture failed";
             cudaGetLastError();
-            return PGB_ECUDA;
+            b->release();
+            b->kidx.clear();
+            return st != PGB_OK ? st : PGB_ECUDA;
         }
         cudaGraphDestroy(g);
     }
@@ -817,7 +872,7 @@ pgb_status pgb_batch_rates(pgb_batch *b, const int32_t *const *k_idx, const int6
 
 pgb_status pgb_batch_tuning(const pgb_batch *b, int *tile_q, int *threads, float *cand_ms, int64_t *graph_launches) {
     if (!b) return PGB_EINVAL;
-    if (tile_q) *tile_q = b->cand >= 0 ? kCands[b->cand].qt : 0;
+    if (tile_q) *tile_q = b->qc.empty() ? 0 : *std::max_element(b->qc.begin(), b->qc.end());
     if (threads) *threads = b->cand >= 0 ? kCands[b->cand].nt : 0;
     if (cand_ms)
         for (int i = 0; i < 4; ++i) cand_ms[i] = b->cand_ms[i];

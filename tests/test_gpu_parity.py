@@ -595,6 +595,47 @@ def test_rk4_c2_grid_list_1000_steps(ctx, c2, c2_grid_list):
 
 
 @pytest.mark.slow
+def test_rk4_c2_12cubed_list_1000_steps(ctx, c2):
+    """Config 4 at the reduced 12^3 size: the device builds the list of the C2 model
+    (two lowest bands, states within 0.6 eV of the band minimum, 7 sigma screen at
+    sigma = 10 meV, T = 300 K) and runs 1000 RK4 steps of 1 fs (Sec. 2.1.1) of the
+    hot-carrier pulse; the oracle evolves the same entries (read back, |g|^2 as stored)
+    with its own FP64 band and phonon energies (Eq. e_ph_scattering): occupations
+    within 1e-6, carrier number conserved.  The list itself is pinned entry by entry
+    against the oracle's on the 5^3 grid above."""
+    T, sig, grid = 300.0, 0.010, (12, 12, 12)
+    nk = int(np.prod(grid))
+    pts = S.mp_grid(*grid)
+    e_ref, _ = O.bands(c2, pts)
+    hw_ref, _ = O.phonons(c2, pts)
+    emin = e_ref[:, :2].min()
+    ctx.pgb_set_model(c2)
+    ctx.pgb_set_grids(grid, grid)
+    nnz = ctx.pgb_build_collision_grid(0, 2, emin, emin + 0.6, T, sig)
+    assert nnz > 100_000
+    row, col, mode = (np.zeros(nnz, np.int32) for _ in range(3))
+    g2 = np.zeros(nnz, np.float32)
+    ctx.pgb_collision_list(row, col, mode, g2)
+    eps = e_ref[:, :2].reshape(-1)                      # state s = 2 ik + n
+    kr, kc = row // 2, col // 2
+    c_r = np.stack([kr // 144, (kr // 12) % 12, kr % 12], -1)
+    c_c = np.stack([kc // 144, (kc // 12) % 12, kc % 12], -1)
+    qv = (c_c - c_r) % 12
+    q = (qv[:, 0] * 12 + qv[:, 1]) * 12 + qv[:, 2]
+    hw_e = hw_ref[q, mode]
+    f0 = S.pulse_occupations(eps, emin, centre=0.5, width=0.1, amplitude=0.1)
+    f = dev(f0)
+    ctx.pgb_step_rk4(f, 1.0, 1000)
+    rows, cols, g2d = row.astype(np.int64), col.astype(np.int64), g2.astype(np.float64)
+    rhs = lambda x: O.collision(x, eps, rows, cols, hw_e, g2d, T, sig, nk)
+    ref = O.evolve(f0, 1.0, 1000, rhs)
+    got = f.cpu().numpy()
+    assert np.abs(got - f0).max() > 1e-2
+    assert np.abs(got - ref).max() <= 1e-6
+    assert abs(got.sum() - f0.sum()) <= 1e-9 * f0.sum()
+
+
+@pytest.mark.slow
 def test_grid_list_full_size_sampled_rows(ctx, c2):
     """The dynamics workload: 30^3 grid, two lowest bands, states in a 0.6 eV
     window above the band minimum (~1.2e8 entries).  Sampled rows of I[f] at the
