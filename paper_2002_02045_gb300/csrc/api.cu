@@ -869,8 +869,6 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
         return fail(c, PGB_EINVAL, "scattering_rates: unknown precision");
     const bool tcp = precision == PGB_TC_TF32X3 || precision == PGB_TC_BF16X3;
     const bool tf32 = precision == PGB_TC_TF32X3;
-    if (tcp && !tc_supported(c->nm * c->nw * c->nw))
-        return fail(c, PGB_EINVAL, "scattering_rates: tensor-core path needs nmode*nw*nw to be a multiple of 96");
     if (nk == 0) return PGB_OK;
     if (!gamma_out) return fail(c, PGB_EINVAL, "scattering_rates: null gamma_out");
     const bool f32 = precision != PGB_FP64;
@@ -909,6 +907,11 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
 
     const int per = nm * nw;
     const bool fused = tcp && tc_fused_supported(nw, nm);
+    // other shapes on the tensor cores: columns padded to whole 96-column tiles, the
+    // q-sum in q slabs small enough to stay in L2 (kSlabBytes) until the epilogue
+    // has read them
+    const int64_t ldc = (ncol + 95) / 96 * 96;
+    constexpr int64_t kSlabBytes = (int64_t)48 << 20;
     // BF16x3: the R_e sum on the tensor cores too (k_tc_qsum with the batch's k phases as A
     // and the split, transposed g~ as B) whenever its column count tiles by 96.  TF32x3 keeps
     // the FP32 SIMT R_e sum: a second TF32x3 sum put Gamma 1.3e-5 from the oracle on the
@@ -917,7 +920,10 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
     const int KpE = tc_kpad(c->nRge);
     const int qpb = std::max(1, 256 / nw);
     const int qiters = 8;
-    const int64_t nqblk = fused ? (c->Nq + 127) / 128 : (c->Nq + (int64_t)qpb * qiters - 1) / ((int64_t)qpb * qiters);
+    const int wqc = 16;   // q-points per warp task of the slab epilogue (tensor-core route, other shapes)
+    const int64_t nqblk = fused ? (c->Nq + 127) / 128
+                          : tcp ? (c->Nq + wqc - 1) / wqc
+                                : (c->Nq + (int64_t)qpb * qiters - 1) / ((int64_t)qpb * qiters);
     // scratch carve-up, every piece 256-byte aligned (TMA and vector loads)
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     int64_t nbmax = 0;
@@ -926,16 +932,18 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
         o_S1 = al((size_t)nbm * c->nRge * es);
         o_G = o_S1 + al((size_t)nbm * nrow * es);
         o_C = o_G + al((size_t)nbm * nrow * es);
-        o_part = o_C + (fused ? 0 : al((size_t)nbm * c->Nq * ncol * es));
+        o_part = o_C + (fused ? 0 : tcp ? al((size_t)kSlabBytes) : al((size_t)nbm * c->Nq * ncol * es));
         o_gm = o_part + al((size_t)nbm * nqblk * per * sizeof(double));
         o_B = o_gm + al((size_t)nbm * per * sizeof(double));
-        o_Ak = o_B + (tcp ? al((size_t)nbm * (fused ? 6 : 4) * ncol * Kp * tes) : 0);
+        o_Ak = o_B + (tcp ? al((size_t)nbm * (fused ? 6 * ncol : 4 * ldc) * Kp * tes) : 0);
         total = o_Ak + (tc_rsum ? al((size_t)nbm * 4 * KpE * tes) : 0);
     };
     layout(1);
     const size_t budget = (size_t)4 << 30;
     nbmax = std::max<int64_t>(1, (int64_t)(budget / total));
     nbmax = std::min<int64_t>(nbmax, std::min<int64_t>(nk, 65535));
+    if (tcp && !fused)   // a slab holds at least 128 q-points of every k of the batch
+        nbmax = std::max<int64_t>(1, std::min<int64_t>(nbmax, kSlabBytes / (128 * ldc * (int64_t)sizeof(float2))));
     layout(nbmax);
     TRY(ensure_scratch(c, total));
     char *base = (char *)c->scratch;
@@ -1028,17 +1036,6 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
                                     Gmm.dev ? Gmm.dev + b0 * nm * nw : gmode_tmp));
             continue;
         }
-        if (tcp) {
-            TRY(launch_split_g(c, tf32, nb, c->nKp, (int)ncol, Kp, G, Bsplit));
-            prof_mark(c, PGB_PROF_QSUM);
-            TRY(launch_tc_qsum(c, tf32, nb, c->Nq, (int)ncol, Kp, c->d_asplit, Bsplit, (float2 *)Cb, c->d_err));
-            prof_mark(c, PGB_PROF_QSUM);
-        } else {
-            prof_mark(c, PGB_PROF_QSUM);
-            TRY(launch_cgemm(c, f32, nb, c->Nq, ncol, c->nKp, phq, c->nKp, 0, G, ncol, nrow, Cb, ncol,
-                             c->Nq * ncol));
-            prof_mark(c, PGB_PROF_QSUM);
-        }
         RatesArgs ra;
         ra.nb = nb;
         ra.kidx = kb;
@@ -1065,9 +1062,57 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
         ra.nqblk = nqblk;
         ra.qpb = qpb;
         ra.qiters = qiters;
-        prof_mark(c, PGB_PROF_EPILOGUE);
-        TRY(launch_rates_epilogue(c, f32, ra));
-        prof_mark(c, PGB_PROF_EPILOGUE);
+        if (tcp) {
+            // q slabs: tensor-core q-sum into the L2-sized buffer, then the warp epilogue on that slab
+            TRY(launch_split_g(c, tf32, nb, c->nKp, (int)ncol, Kp, G, Bsplit, (int)ldc));
+            const int64_t sq = std::max<int64_t>(128, kSlabBytes / (nb * ldc * (int64_t)sizeof(float2)) / 128 * 128);
+            WarpRatesArgs wa;
+            wa.nw = nw;
+            wa.nm = nm;
+            wa.ib = warp_rates_ib(nw, nm);
+            for (int d = 0; d < 3; ++d) {
+                wa.kg[d] = c->kg[d];
+                wa.qg[d] = c->qg[d];
+            }
+            wa.qc = wqc;
+            wa.nb = nb;
+            wa.C = (const float2 *)Cb;
+            wa.ldc = ldc;
+            wa.kidx = kb;
+            wa.eps = c->d_eps;
+            wa.eps32 = eps32.p;
+            wa.U = c->d_U32;
+            wa.coef = c->d_coef32;
+            wa.hw = c->d_hw;
+            wa.hw32 = hw32.p;
+            wa.focc = focc.p;
+            wa.nbe = nbe.p;
+            wa.sigma = sigma;
+            wa.partial = partial;
+            wa.nqblk = nqblk;
+            for (int64_t qs = 0; qs < c->Nq; qs += sq) {
+                const int64_t nqs = std::min(sq, c->Nq - qs);
+                prof_mark(c, PGB_PROF_QSUM);
+                TRY(launch_tc_qsum(c, tf32, nb, nqs, (int)ldc, Kp, c->d_asplit, Bsplit, (float2 *)Cb, c->d_err, c->Nq,
+                                   qs));
+                prof_mark(c, PGB_PROF_QSUM);
+                wa.q_off = qs;
+                wa.nqs = nqs;
+                wa.nch = (int)((nqs + wqc - 1) / wqc);
+                wa.blk0 = qs / wqc;
+                prof_mark(c, PGB_PROF_EPILOGUE);
+                TRY(launch_rates_warp(c, wa));
+                prof_mark(c, PGB_PROF_EPILOGUE);
+            }
+        } else {
+            prof_mark(c, PGB_PROF_QSUM);
+            TRY(launch_cgemm(c, f32, nb, c->Nq, ncol, c->nKp, phq, c->nKp, 0, G, ncol, nrow, Cb, ncol,
+                             c->Nq * ncol));
+            prof_mark(c, PGB_PROF_QSUM);
+            prof_mark(c, PGB_PROF_EPILOGUE);
+            TRY(launch_rates_epilogue(c, f32, ra));
+            prof_mark(c, PGB_PROF_EPILOGUE);
+        }
         TRY(launch_rates_reduce(c, nb, nqblk, nm, nw, scale, partial, Gm.dev + b0 * nw,
                                 Gmm.dev ? Gmm.dev + b0 * nm * nw : gmode_tmp));
     }

@@ -305,7 +305,7 @@ struct Cand {
     int nt;
     int scale;
 };
-constexpr Cand kCands[4] = {{128, 1}, {256, 1}, {256, 4}, {512, 4}};
+constexpr Cand kCands[4] = {{256, 1}, {256, 4}, {512, 4}, {512, 16}};
 
 // q-points per chunk: about 4096 lane-steps of work per band at scale 1.
 int pick_qc(int scale, int nw, int nm) {

@@ -287,9 +287,35 @@ pgb_status launch_split_table(pgb_ctx *c, bool tf32, int64_t n, int ncols, int64
 pgb_status launch_split_g(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out,
                           int ncol_pad = 0);
 pgb_status launch_split_g6(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, int Kp, const void *G, void *out);
+// C[b][q][c] for q < Nq from rows q_off .. q_off + Nq of an A table of nqA rows (nqA <= 0: Nq)
 pgb_status launch_tc_qsum(pgb_ctx *c, bool tf32, int64_t nb, int64_t Nq, int ncol, int Kp, void *Asplit,
-                          void *Bsplit, float2 *C, int *d_err);
+                          void *Bsplit, float2 *C, int *d_err, int64_t nqA = 0, int64_t q_off = 0);
 pgb_status tc_qsum_prepare(pgb_ctx *c, bool tf32);
+
+// warp-per-row rates epilogue over a q slab of tensor-core q-sums (rates_warp.cu)
+struct WarpRatesArgs {
+    int nw, nm, ib;        // ib: lanes per mode column of a row (warp_rates_ib)
+    int kg[3], qg[3];
+    int64_t q_off, nqs;    // q-grid index of the slab's first row, rows in the slab
+    int qc, nch;           // q-points per task, tasks per k in the slab
+    int64_t nb;            // k-points of the batch
+    const float2 *C;       // [nb][nqs][ldc] R_p sums, columns (n, ka, i)
+    int64_t ldc;
+    const int32_t *kidx;   // [nb] k-grid indices
+    const double *eps;     // [Nk][nw]
+    const float *eps32;    // [Nk][nw]
+    const float2 *U;       // [Nk][i][m] FP32
+    const float2 *coef;    // [Nq][nu][ka] FP32
+    const double *hw;      // [Nq][nm]
+    const float *hw32;     // [Nq][nm]
+    const double *focc;    // [Nk][nw]
+    const double *nbe;     // [Nq][nm]
+    double sigma;
+    double *partial;       // [nb][nqblk][nm][nw]; this slab writes blocks blk0 .. blk0 + nch
+    int64_t nqblk, blk0;
+};
+int warp_rates_ib(int nw, int nm);
+pgb_status launch_rates_warp(pgb_ctx *c, const WarpRatesArgs &a);
 
 // fused tensor-core rates (tc_rates.cu)
 struct FusedLaunch {

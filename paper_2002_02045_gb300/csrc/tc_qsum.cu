@@ -19,6 +19,7 @@
 // One CTA computes a 128 (q) x 96 (c) complex tile of one k: warp 0 issues
 // TMA loads into a 3-stage ring, warp 1 owns TMEM and issues the MMAs, warps
 // 2-5 read the two 96-column accumulators (re, im) and store C.
+#include <climits>
 #include <cstdio>
 #include <mutex>
 #include <vector>
@@ -44,7 +45,8 @@ constexpr long long WAIT_BUDGET = 1ll << 31;           // ~1 s of clock cycles
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 
 struct TcArgs {
-    int64_t Nq;
+    int64_t Nq;       // rows of C (q-points of this launch)
+    int q_off;        // first row of the A table that this launch multiplies
     int Kp;
     int ncol;
     int nb;
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(192, 1)
             tc::mbar_expect_tx(full, STAGE_BYTES);
             uint8_t *st = smem + s * STAGE_BYTES;
             for (int p = 0; p < 4; ++p)
-                tc::tma_load_3d(tc::smem_addr(st + p * A_PART), &tA, full, kc * EK, q0, p);
+                tc::tma_load_3d(tc::smem_addr(st + p * A_PART), &tA, full, kc * EK, a.q_off + q0, p);
             for (int p = 0; p < 4; ++p)
                 tc::tma_load_3d(tc::smem_addr(st + 4 * A_PART + p * B_PART), &tB, full, kc * EK, n0, b * 4 + p);
             ++issued;
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
             const uint32_t fb = tc::smem_addr(full + st);
             tc::mbar_expect_tx(fb, STAGE_BYTES);
             uint8_t *sp = smem + st * STAGE_BYTES;
-            for (int p = 0; p < 4; ++p) tc::tma_load_3d(tc::smem_addr(sp + p * A_PART), &tA, fb, kc * EK, q0, p);
+            for (int p = 0; p < 4; ++p) tc::tma_load_3d(tc::smem_addr(sp + p * A_PART), &tA, fb, kc * EK, a.q_off + q0, p);
             for (int p = 0; p < 4; ++p)
                 tc::tma_load_3d(tc::smem_addr(sp + 4 * A_PART + p * B_PART), &tB, fb, kc * EK, n0, b * 4 + p);
             ++issued;
@@ -673,14 +675,19 @@ pgb_status launch_split_g6(pgb_ctx *c, bool tf32, int64_t nb, int nR, int ncol, 
 // C[b][q][c] for b < nb from the split operands; err (device int) collects
 // wait time-outs and is checked by the caller.
 pgb_status launch_tc_qsum(pgb_ctx *c, bool tf32, int64_t nb, int64_t Nq, int ncol, int Kp, void *Asplit,
-                          void *Bsplit, float2 *C, int *d_err) {
-    if (nb == 0) return PGB_OK;
+                          void *Bsplit, float2 *C, int *d_err, int64_t nqA, int64_t q_off) {
+    if (nb == 0 || Nq == 0) return PGB_OK;
+    if (nqA <= 0) nqA = Nq;
+    if (q_off < 0 || q_off + Nq > nqA || nqA > INT32_MAX) {
+        c->err = "tensor-core q-sum: q rows outside the A table";
+        return PGB_EINVAL;
+    }
     if (ncol % BN != 0 || Kp % 32 != 0 || nb > 65535 || (Nq + BM - 1) / BM > 65535) {
         c->err = "tensor-core q-sum: unsupported shape (needs nmode*nw*nw a multiple of 96)";
         return PGB_EINVAL;
     }
     CUtensorMap tA, tB;
-    const int ra = make_map(&tA, Asplit, tf32, Kp, Nq, 4, BM);
+    const int ra = make_map(&tA, Asplit, tf32, Kp, nqA, 4, BM);
     const int rb = ra == 0 ? make_map(&tB, Bsplit, tf32, Kp, ncol, nb * 4, BN) : 0;
     if (ra != 0 || rb != 0) {
         c->err = "tensor-core q-sum: cuTensorMapEncodeTiled failed (A " + std::to_string(ra) + ", B " +
@@ -689,6 +696,7 @@ pgb_status launch_tc_qsum(pgb_ctx *c, bool tf32, int64_t nb, int64_t Nq, int nco
     }
     TcArgs a;
     a.Nq = Nq;
+    a.q_off = (int)q_off;
     a.Kp = Kp;
     a.ncol = ncol;
     a.nb = (int)nb;

@@ -363,6 +363,37 @@ def test_rates_unfused_tensor_core_4band(ctx, c2):
         assert_rates_close(gam.cpu().numpy(), ref, tol, label=f"4-band {prec}")
 
 
+@pytest.mark.parametrize("inst,grid", [(17, 12), (1, 8), ("c2-3band", 10)])
+def test_rates_general_shape_tensor_core(ctx, inst, grid):
+    """Shapes the fused kernel does not cover (16 bands x 15 modes, 12 bands x 12
+    modes, an odd 3-band cut with 54 columns padded to 96): the tensor-core q-sum in
+    L2-sized q slabs followed by the warp epilogue, against the oracle in both split
+    precisions, mode-resolved sums equal to the total."""
+    from paper_2002_02045_gb300 import PRECISIONS
+    if inst == "c2-3band":
+        c2m = S.model_c2()
+        m = dataclasses.replace(c2m, H=np.ascontiguousarray(c2m.H[:, :3, :3]), g=np.ascontiguousarray(c2m.g[..., :3, :3]))
+    else:
+        m = S.model_batch_instance(inst)
+    g = (grid,) * 3
+    T, sig = 300.0, 0.005
+    ctx.pgb_set_model(m)
+    ctx.pgb_set_grids(g, g)
+    nk = grid ** 3
+    eps = np.zeros((nk, m.nw))
+    ctx.pgb_get_grid_energies(eps, None)
+    mu = float(0.5 * (eps.min() + eps.max()))
+    ks = np.array([0, nk // 3, nk - 1], np.int32)
+    ref = O.scattering_rates_grid(m, g, g, ks, T, mu, sig, q_chunk=4096)
+    assert np.abs(ref).max() > 0
+    for prec, tol in (("bf16x3", 1e-3), ("tf32x3", 1e-5)):
+        gam = empty((3, m.nw))
+        gmode = empty((3, m.nmode, m.nw))
+        ctx.pgb_scattering_rates(dev(ks), T, mu, sig, PRECISIONS[prec], gam, gmode)
+        assert_rates_close(gam.cpu().numpy(), ref, tol, label=f"instance {inst} {prec}")
+        assert np.allclose(gmode.cpu().numpy().sum(1), gam.cpu().numpy(), rtol=1e-12)
+
+
 @pytest.mark.slow
 def test_rates_c2_full_size_sampled(ctx, c2):
     """Full 40^3 x 40^3 workload over the whole 0.3 eV window, as the bench runs
