@@ -619,7 +619,8 @@ def batched(args, world):
     import synthetic as S
     from paper_2002_02045_gb300 import Batch, Context
     t0 = time.perf_counter()
-    models = [S.model_batch_instance(i) for i in range(args.batch_instances)]
+    ids = [int(x) for x in args.batch_ids.split(",")] if args.batch_ids else list(range(args.batch_instances))
+    models = [S.model_batch_instance(i) for i in ids]
     t_gen = time.perf_counter() - t0
     rng = np.random.default_rng(S.SEED_BASE + 55)
     ctxs, ks, mus, outs = [], [], [], []
@@ -693,7 +694,7 @@ def batched(args, world):
     return {
         "metric": "(k,q) pairs/s over uneven instances in one graph launch (FP32 products, FP64 energies)",
         "value": world * pairs / dt, "unit": "pairs/s", "ms_per_call": 1e3 * dt, "pairs": pairs,
-        "instances": args.batch_instances, "k_per_instance": BATCH_K, "first_call_s": t_first,
+        "instances": len(models), "k_per_instance": BATCH_K, "first_call_s": t_first,
         "model_generation_s": t_gen, "setup_s": t_setup, "tuning": tun, "finite": finite,
         "timing": "host clock around pgb_batch_rates (graph replay + output copies, synchronised)",
         "cpu_baseline": cb, "bf16x3": bf16,
@@ -825,6 +826,8 @@ def main():
     ap.add_argument("--max-k", type=int, default=0,
                     help="use only the first N window k-points (small case for profiler captures)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--batch-ids", default="",
+                    help="comma-separated instance indices for the batched section (profiling subsets)")
     ap.add_argument("--no-general", dest="general", action="store_false",
                     help="skip the 16-band, 15-mode shape outside the fused kernel")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
