@@ -38,7 +38,7 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # ncu capture of each kernel: the fused rates kernel on 64 window k x 40^3 q, the
 # collision kernel on the 30^3 list.  An entry is None while its kernel has changed
 # since the capture.
-TRAFFIC = {"k_tc_rates_bf16x3_bytes_per_pair": None,
+TRAFFIC = {"k_tc_rates_bf16x3_bytes_per_pair": (1.134679e9 + 23.895552e6) / (64 * 64000),
            "k_collision_bytes_per_entry": (383152384 + 3583744) / 31890730}
 
 

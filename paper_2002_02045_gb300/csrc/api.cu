@@ -911,7 +911,7 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
     // q-sum in q slabs small enough to stay in L2 (kSlabBytes) until the epilogue
     // has read them
     const int64_t ldc = (ncol + 95) / 96 * 96;
-    constexpr int64_t kSlabBytes = (int64_t)48 << 20;
+    constexpr int64_t kSlabBytes = (int64_t)64 << 20;
     // BF16x3: the R_e sum on the tensor cores too (k_tc_qsum with the batch's k phases as A
     // and the split, transposed g~ as B) whenever its column count tiles by 96.  TF32x3 keeps
     // the FP32 SIMT R_e sum: a second TF32x3 sum put Gamma 1.3e-5 from the oracle on the
@@ -920,7 +920,7 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
     const int KpE = tc_kpad(c->nRge);
     const int qpb = std::max(1, 256 / nw);
     const int qiters = 8;
-    const int wqc = 16;   // q-points per warp task of the slab epilogue (tensor-core route, other shapes)
+    const int wqc = 8;    // q-points per warp task of the slab epilogue (tensor-core route, other shapes)
     const int64_t nqblk = fused ? (c->Nq + 127) / 128
                           : tcp ? (c->Nq + wqc - 1) / wqc
                                 : (c->Nq + (int64_t)qpb * qiters - 1) / ((int64_t)qpb * qiters);

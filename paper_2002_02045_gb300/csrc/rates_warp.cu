@@ -3,7 +3,7 @@
 // and BTE_W), fed by the tensor-core q-sum in q slabs that stay in L2.
 //
 // The q-sum writes C[b][q][n ka i] = sum_p e^{iq.R_p} G_kb[p][n ka i] for one slab
-// of q-points (at most ~48 MB, so the slab is still in L2 when it is read here).
+// of q-points (at most 64 MB, so the slab is still in L2 when it is read here).
 // One warp per task = (k of the batch, chunk of qc q-points of the slab, band n):
 // slabs of wide shapes hold few q-points, so the bands supply the parallelism.
 // For each q of the chunk (k+q followed incrementally on the grid) the warp
