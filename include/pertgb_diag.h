@@ -43,6 +43,12 @@ pgb_status pgb_selftest_wait_timeout(pgb_ctx *ctx, long long budget_cycles);
 pgb_status pgb_diag_delta_weights(pgb_ctx *ctx, int64_t n, const double *en, const double *em, const double *hw,
                                   double eps_ref, double sigma, float *out);
 
+/* Measured FP64 arithmetic rate of the context's device in TFLOP/s (*tflops):
+ * every thread runs sixteen independent chains of dependent FMAs, 2 FLOP each,
+ * timed with events (best of three runs after a warm-up).  The denominator of
+ * the FP64-bound kernels' rooflines.                                         */
+pgb_status pgb_diag_fp64_rate(pgb_ctx *ctx, double *tflops);
+
 /* Device allocations.  Every device allocation the library makes (model and
  * grid tables, scratch, per-call temporaries) goes through one internal call.
  * pgb_diag_alloc_count returns how many it has been asked for since the

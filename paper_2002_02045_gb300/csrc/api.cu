@@ -135,7 +135,9 @@ pgb_status bands_at(pgb_ctx *c, const double *d_pts, int64_t np, double *d_eps, 
     TRY(ph.alloc(c, (size_t)np * c->nRH));
     TRY(hk.alloc(c, (size_t)np * nw2));
     TRY(launch_phase_pts(c, d_pts, np, c->d_RH, c->nRH, ph.p, false));
+    prof_mark(c, PGB_PROF_BANDS);
     TRY(launch_cgemm(c, false, 1, np, nw2, c->nRH, ph.p, c->nRH, 0, c->d_H, nw2, 0, hk.p, nw2, 0));
+    prof_mark(c, PGB_PROF_BANDS);
     TRY(launch_heevj(c, np, c->nw, hk.p, nullptr, d_eps, d_U));
     return PGB_OK;
 }

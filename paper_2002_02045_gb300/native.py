@@ -23,7 +23,8 @@ PGB_G2_FULL, PGB_G_ABS = 0, 1
 PRECISIONS = {"fp64": PGB_FP64, "fp32": PGB_FP32, "tf32x3": PGB_TC_TF32X3, "bf16x3": PGB_TC_BF16X3}
 
 DIAG_SYMBOLS = ("pgb_diag_bands", "pgb_selftest_heevj", "pgb_selftest_heevj_device", "pgb_selftest_wait_timeout",
-                "pgb_diag_alloc_count", "pgb_diag_fail_alloc", "pgb_diag_delta_weights")
+                "pgb_diag_alloc_count", "pgb_diag_fail_alloc", "pgb_diag_delta_weights",
+                "pgb_diag_fp64_rate")
 ABI_SYMBOLS = (
     "pgb_create", "pgb_destroy", "pgb_last_error", "pgb_status_string", "pgb_set_model",
     "pgb_set_grids", "pgb_get_grid_energies", "pgb_window", "pgb_interpolate_g",
@@ -113,6 +114,7 @@ def load(path: str = LIB_PATH):
         "pgb_diag_alloc_count": (I64, []),
         "pgb_diag_fail_alloc": (None, [I64]),
         "pgb_diag_delta_weights": (I, [P, I64, P, P, P, D, D, P]),
+        "pgb_diag_fp64_rate": (I, [P, C.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -348,6 +350,11 @@ class Context:
         _check_dtype(out, "float32")
         self._chk(self.lib.pgb_diag_delta_weights(self._h, len(en), _ptr(en), _ptr(em), _ptr(hw), float(eps_ref),
                                                   float(sigma), _ptr(out)))
+
+    def pgb_diag_fp64_rate(self):
+        t = C.c_double(0.0)
+        self._chk(self.lib.pgb_diag_fp64_rate(self._h, C.byref(t)))
+        return float(t.value)
 
     def pgb_profile(self, enable):
         self._chk(self.lib.pgb_profile(self._h, 1 if enable else 0))
