@@ -715,7 +715,7 @@ def batched(args, world):
         "timing": "host clock around pgb_batch_rates (graph replay + output copies, synchronised)",
         "cpu_baseline": cb, "bf16x3": bf16,
         "roofline": {"bound": "alu", "kernel": "batched graph (FP32): per-instance R_p sums on k_cgemm + the "
-                                               "persistent epilogue k_batch_epi", "achieved": flops / dt / 1e12,
+                                               "persistent warp epilogue k_batch_warp", "achieved": flops / dt / 1e12,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": flops / dt / 1e12 / fp32_peak,
                      "algorithmic_flop": flops,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (whole graph timed)"},
