@@ -18,6 +18,16 @@ extern "C" {
  * U [n][nw][nw] complex128 (columns are eigenvectors).  Any output may be NULL. */
 pgb_status pgb_diag_bands(pgb_ctx *ctx, const double *pts, int64_t n, double *Hk, double *eps, double *U);
 
+/* Bands at n points (crystal coordinates [n][3], host or device) by the path the
+ * FP32 Monte-Carlo rates use (Sec. 2.2.1, Eq. wannier_3): the packed Hermitian
+ * H(k) [n][nw*nw] float64 (nw real diagonal entries, then (re, im) of the
+ * entries (i, j), i < j, row by row) from the real cos/sin Fourier sum over one
+ * representative of each {R, -R}; eps [n][nw] float64 ascending, refined in
+ * FP64; U [n][nw][nw] complex64 (interleaved floats, column n the eigenvector of
+ * band n) from the FP32 parallel Jacobi.  Outputs host or device, any may be
+ * NULL.  Needs nw >= 2 (PGB_EINVAL otherwise).                               */
+pgb_status pgb_diag_bands_mixed(pgb_ctx *ctx, const double *pts, int64_t n, double *Hp, double *eps, float *U);
+
 /* The device eigensolver template run on the host for `count` Hermitian
  * n x n complex128 matrices: eval [count][n], evec [count][n][n].
  * Returns 0, or -1 for an unsupported n (supported: 1, 2, 3, 6, 8, 16).     */

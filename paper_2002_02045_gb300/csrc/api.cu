@@ -142,6 +142,20 @@ pgb_status bands_at(pgb_ctx *c, const double *d_pts, int64_t np, double *d_eps, 
     return PGB_OK;
 }
 
+// Bands at arbitrary points for the FP32 paths: real cos/sin Fourier sum of the
+// packed Hermitian H(k), FP32 Jacobi eigenvectors, FP64-refined eigenvalues.
+pgb_status bands_at_mixed(pgb_ctx *c, const double *d_pts, int64_t np, double *d_eps, float2 *d_U32,
+                          double2 *d_U64) {
+    if (c->nw < 2) return fail(c, PGB_EINVAL, "bands_at_mixed: needs nw >= 2");
+    Tmp<double> hp;
+    TRY(hp.alloc(c, (size_t)np * c->nw * c->nw));
+    prof_mark(c, PGB_PROF_BANDS);
+    TRY(launch_herm_sum(c, d_pts, np, hp.p));
+    prof_mark(c, PGB_PROF_BANDS);
+    TRY(launch_heev_mixed(c, np, c->nw, hp.p, d_eps, d_U32, d_U64));
+    return PGB_OK;
+}
+
 // Interpolate phonons at arbitrary points: hbar*omega and mode coefficients.
 pgb_status phonons_at(pgb_ctx *c, const double *d_pts, int64_t np, double *d_hw, double2 *d_coef) {
     const int nm2 = c->nm * c->nm;
@@ -204,6 +218,9 @@ void free_model(pgb_ctx *c) {
     dfree(&c->d_Rge);
     dfree(&c->d_Rgp);
     dfree(&c->d_H);
+    dfree(&c->d_Hrep);
+    dfree(&c->d_Hcs);
+    c->nHrep = c->HrepM = 0;
     dfree(&c->d_D);
     dfree(&c->d_mode_scale);
     dfree(&c->d_g64);
@@ -464,6 +481,7 @@ pgb_status pgb_set_model(pgb_ctx *c, const pgb_model *m) {
     PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_Rge, m->R_ge, 12 * (size_t)c->nRge, cudaMemcpyHostToDevice, c->stream));
     PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_Rgp, m->R_gp, 12 * (size_t)c->nRgp, cudaMemcpyHostToDevice, c->stream));
     PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_H, m->H, 16 * (size_t)c->nRH * nw2, cudaMemcpyHostToDevice, c->stream));
+    TRY(build_band_table(c, m->R_H, m->H, c->nRH, nw));
     std::vector<double> D2((size_t)2 * c->nRD * nm2, 0.0);
     for (size_t i = 0; i < (size_t)c->nRD * nm2; ++i) D2[2 * i] = m->D[i];
     PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_D, D2.data(), 8 * D2.size(), cudaMemcpyHostToDevice, c->stream));
@@ -1426,7 +1444,7 @@ pgb_status pgb_scattering_rates_mc(pgb_ctx *c, const double *kpts, int64_t nk, c
     TRY(phq.alloc(c, (size_t)qc * c->nKp * es));
     TRY(kq.alloc(c, 3 * (size_t)kb * qc));
     TRY(eps_kq.alloc(c, (size_t)kb * qc * nw));
-    TRY(U_kq.alloc(c, (size_t)kb * qc * nw2));
+    if (!f32 || nw < 2) TRY(U_kq.alloc(c, (size_t)kb * qc * nw2));
     TRY(C.alloc(c, (size_t)kb * qc * ncol * es));
     TRY(partial.alloc(c, (size_t)mc_partial_count(c, kb, qc)));
     if (f32) {
@@ -1446,11 +1464,16 @@ pgb_status pgb_scattering_rates_mc(pgb_ctx *c, const double *kpts, int64_t nk, c
         for (int64_t k0 = 0; k0 < nk; k0 += kb) {
             const int64_t nb = std::min(kb, nk - k0);
             TRY(launch_kplusq_pts(c, K.dev + 3 * k0, nb, qp, nqc, kq.p));
-            TRY(bands_at(c, kq.p, nb * nqc, eps_kq.p, U_kq.p));
             const void *Ukq = U_kq.p;
-            if (f32) {
-                TRY(launch_to_f32(c, U_kq.p, (float2 *)Ukq32.p, nb * nqc * nw2));
+            if (f32 && nw >= 2) {
+                TRY(bands_at_mixed(c, kq.p, nb * nqc, eps_kq.p, (float2 *)Ukq32.p, nullptr));
                 Ukq = Ukq32.p;
+            } else {
+                TRY(bands_at(c, kq.p, nb * nqc, eps_kq.p, U_kq.p));
+                if (f32) {
+                    TRY(launch_to_f32(c, U_kq.p, (float2 *)Ukq32.p, nb * nqc * nw2));
+                    Ukq = Ukq32.p;
+                }
             }
             TRY(launch_cgemm(c, f32, nb, nqc, ncol, c->nKp, phq.p, c->nKp, 0, G.p + (size_t)k0 * nrow * es, ncol,
                              nrow, C.p, ncol, nqc * ncol));
@@ -1503,6 +1526,31 @@ pgb_status pgb_diag_bands(pgb_ctx *c, const double *pts, int64_t n, double *Hk, 
     TRY(launch_heevj(c, n, c->nw, hk.p, nullptr, e.p, u.p));
     if (eps) PGB_CUDA_TRY(c, cudaMemcpyAsync(eps, e.p, 8 * (size_t)n * c->nw, cudaMemcpyDefault, c->stream));
     if (U) PGB_CUDA_TRY(c, cudaMemcpyAsync(U, u.p, 16 * (size_t)n * nw2, cudaMemcpyDefault, c->stream));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PGB_OK;
+}
+
+pgb_status pgb_diag_bands_mixed(pgb_ctx *c, const double *pts, int64_t n, double *Hp, double *eps, float *U) {
+    if (!c) return PGB_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->has_model) return fail(c, PGB_ESTATE, "diag_bands_mixed: call set_model first");
+    if (c->nw < 2) return fail(c, PGB_EINVAL, "diag_bands_mixed: needs nw >= 2");
+    if (n < 0) return fail(c, PGB_EINVAL, "diag_bands_mixed: negative n");
+    if (n == 0) return PGB_OK;
+    if (!pts) return fail(c, PGB_EINVAL, "diag_bands_mixed: null pts");
+    const int nw2 = c->nw * c->nw;
+    In<double> P;
+    TRY(P.init(c, pts, 3 * (size_t)n));
+    Tmp<double> hp, e;
+    Tmp<float2> u;
+    TRY(hp.alloc(c, (size_t)n * nw2));
+    TRY(e.alloc(c, (size_t)n * c->nw));
+    TRY(u.alloc(c, (size_t)n * nw2));
+    TRY(launch_herm_sum(c, P.dev, n, hp.p));
+    if (Hp) PGB_CUDA_TRY(c, cudaMemcpyAsync(Hp, hp.p, 8 * (size_t)n * nw2, cudaMemcpyDefault, c->stream));
+    TRY(launch_heev_mixed(c, n, c->nw, hp.p, e.p, u.p, nullptr));
+    if (eps) PGB_CUDA_TRY(c, cudaMemcpyAsync(eps, e.p, 8 * (size_t)n * c->nw, cudaMemcpyDefault, c->stream));
+    if (U) PGB_CUDA_TRY(c, cudaMemcpyAsync(U, u.p, 8 * (size_t)n * nw2, cudaMemcpyDefault, c->stream));
     PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return PGB_OK;
 }

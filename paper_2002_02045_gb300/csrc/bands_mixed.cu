@@ -1,0 +1,571 @@
+// Band interpolation at arbitrary points for the FP32 paths: a real form of the
+// Fourier sum and a mixed-precision Jacobi eigensolver (Sec. 2.2.1, Eq.
+// wannier_3: H(k) = sum_R e^{ik.R} H(R), H(k) = U(k) diag(eps_k) U(k)^dagger).
+//
+// Fourier sum.  The eigensolver uses the Hermitian part of H(k), which is, for any
+// set of R closed under inversion,
+//   H(k) = sum_{R in S} cos(k.R) C_R + sin(k.R) S_R,
+//   C_R = A(R) + A(-R),  S_R = B(R) - B(-R)   (C_0 = A(0), S_0 = 0),
+//   A(X) = (H(X) + H(X)^dagger) / 2,  B(X) = i (H(X) - H(X)^dagger) / 2,
+// over one representative R of each pair {R, -R}.  C_R and S_R are Hermitian,
+// so only the upper triangle is summed: nw real diagonal entries and the real
+// and imaginary parts of the nw (nw - 1) / 2 entries above it, nw^2 real
+// columns.  That is a real GEMM with K = 2 |S| ~ nR rows, a quarter of the real
+// multiply-adds of the complex form.  The phases come from per-point 1-D tables
+// e^{2 pi i k_d m}: e^{ik.R} = prod_d e^{2 pi i k_d R_d}.
+//
+// Eigensolver.  A parallel cyclic Jacobi with one lane per matrix row: in each
+// round the n/2 disjoint pairs of a round-robin schedule are rotated at once
+// (columns in every lane, rows by exchanging the two rows of each pair).  The
+// rotation is the one of the FP64 thread-per-matrix solver (phase of the pivot
+// removed, then the real rotation that zeroes it).  It runs
+//   1. in FP32 with eigenvectors, to convergence at FP32 rounding (V);
+//   2. in FP64 without eigenvectors on A'' below, for the eigenvalues:
+//        A' = V^dagger H V,  E = V^dagger V - I,
+//        A''_ij = A'_ij - E_ij (A'_ii + A'_jj) / 2,
+//      the congruence of A' by (I + E)^{-1/2} (symmetric orthonormalisation of
+//      V) to first order in E; the terms left out are O(|E|^2 |H|) and
+//      O(|E| |A'_ij, i != j|), below 1e-11 of |H| for |E| ~ 1e-7.  A'' is nearly
+//      diagonal, so the FP64 sweeps converge in one or two sweeps.
+// The eigenvalues are those of H to FP64 rounding; the eigenvectors returned are
+// the FP32 V (orthonormal to ~1e-7), which is what the FP32 |g|^2 products use.
+// Within a cluster of eigenvalues closer than ~1e-7 |H| the FP32 vectors are an
+// orthonormal basis of the cluster's subspace in an arbitrary gauge, as at an
+// exact degeneracy: sums over the bands of a cluster are unaffected.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "cplx.cuh"
+#include "internal.cuh"
+
+namespace pgb {
+
+namespace {
+
+inline unsigned int div_up(int64_t a, int64_t b) { return (unsigned int)((a + b - 1) / b); }
+
+constexpr int kHermMaxM = 7;      // per-point 1-D phase tables for |R_d| <= 7, else one sincospi per (point, R)
+constexpr int HS_P = 64;          // points per block of the Fourier sum
+constexpr int HS_C = 64;          // real columns per block
+constexpr int HS_K = 16;          // K rows (8 representatives) per stage
+
+// Real Fourier sum: out[p][c] = sum_k phase_k(p) T[k][c], phase_{2r} = cos(2 pi k.R_r),
+// phase_{2r+1} = sin(2 pi k.R_r).  Block: 64 points x 64 columns, 4 x 4 per thread.
+__global__ void __launch_bounds__(256) k_herm_sum(int64_t np, const double *__restrict__ pts, int nrep,
+                                                  const int32_t *__restrict__ Rrep, int M, int ncol,
+                                                  const double *__restrict__ T, double *__restrict__ out) {
+    extern __shared__ double2 t1d[];   // [3][2M+1][HS_P] e^{2 pi i k_d m}, when M <= kHermMaxM
+    __shared__ double As[HS_K][HS_P];
+    __shared__ double Bs[HS_K][HS_C];
+    const int tid = threadIdx.x;
+    const int64_t p0 = (int64_t)blockIdx.x * HS_P;
+    const int c0 = blockIdx.y * HS_C;
+    const int W = 2 * M + 1;
+    const bool tab = M <= kHermMaxM;
+    if (tab) {
+        for (int x = tid; x < 3 * W * HS_P; x += blockDim.x) {
+            const int pl = x % HS_P, dm = x / HS_P, d = dm / W, mm = dm - d * W - M;
+            const int64_t p = p0 + pl;
+            double s = 0.0, c = 1.0;
+            if (p < np) sincospi(2.0 * pts[3 * p + d] * (double)mm, &s, &c);
+            t1d[x] = make_double2(c, s);
+        }
+    }
+    __syncthreads();
+    const int tx = tid & 15, ty = tid >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    const int K = 2 * nrep;
+    for (int k0 = 0; k0 < K; k0 += HS_K) {
+        for (int x = tid; x < (HS_K / 2) * HS_P; x += blockDim.x) {
+            const int pl = x % HS_P, rl = x / HS_P;
+            const int rep = k0 / 2 + rl;
+            const int64_t p = p0 + pl;
+            double c = 0.0, s = 0.0;
+            if (rep < nrep && p < np) {
+                const int R1 = Rrep[3 * rep], R2 = Rrep[3 * rep + 1], R3 = Rrep[3 * rep + 2];
+                if (tab) {
+                    const double2 e = cmul(cmul(t1d[(R1 + M) * HS_P + pl], t1d[(W + R2 + M) * HS_P + pl]),
+                                           t1d[(2 * W + R3 + M) * HS_P + pl]);
+                    c = e.x;
+                    s = e.y;
+                } else {
+                    double x3 = pts[3 * p] * R1 + pts[3 * p + 1] * R2 + pts[3 * p + 2] * R3;
+                    x3 -= rint(x3);
+                    sincospi(2.0 * x3, &s, &c);
+                }
+            }
+            As[2 * rl][pl] = c;
+            As[2 * rl + 1][pl] = s;
+        }
+        for (int x = tid; x < HS_K * HS_C; x += blockDim.x) {
+            const int cl = x % HS_C, kl = x / HS_C;
+            const int kr = k0 + kl, col = c0 + cl;
+            Bs[kl][cl] = (kr < K && col < ncol) ? T[(int64_t)kr * ncol + col] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < HS_K; ++kk) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t p = p0 + ty * 4 + i;
+        if (p >= np) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int col = c0 + tx * 4 + j;
+            if (col < ncol) out[p * ncol + col] = acc[i][j];
+        }
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Parallel Jacobi, one lane per row
+// ---------------------------------------------------------------------------
+template <int N>
+struct JShape {
+    static constexpr int L = N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : 16;   // lanes per matrix (one per row)
+    static constexpr int NE = N + (N & 1);   // indices of the round-robin schedule (one dummy when N is odd)
+    static constexpr int NR = NE - 1;        // rounds per sweep
+    static constexpr int NP = NE / 2;        // pairs per round
+};
+
+// Circle schedule over ne indices: in round t index ne-1 meets t, and t+k meets
+// t-k (mod ne-1) for k = 1 .. ne/2-1.  Partner of index r in round t:
+__device__ __forceinline__ int rr_partner(int ne, int t, int r) {
+    const int m = ne - 1;
+    if (r == m) return t;
+    if (r == t) return m;
+    const int x = (2 * t - r) % m;
+    return x < 0 ? x + m : x;
+}
+
+template <typename T2, int N>
+__device__ __forceinline__ T2 pick(const T2 (&a)[N], int idx) {
+    T2 v = a[0];
+#pragma unroll
+    for (int e = 1; e < N; ++e)
+        if (e == idx) v = a[e];
+    return v;
+}
+
+// Rotation that zeroes the pivot b = A_pq of the Hermitian 2x2 block
+// [[app, b], [conj b, aqq]]: with e = conj(b)/|b|, z = (aqq - app) / (2|b|),
+// t = sgn(z) / (|z| + sqrt(z^2 + 1)), c = 1/sqrt(1 + t^2), s = t c, the
+// columns (p, q) of J are (c, -s e) and (s, c e).  Returns the identity for b = 0.
+// |b| and e are formed from b scaled by max(|Re b|, |Im b|): inside a degenerate
+// cluster the pivots become tiny, and an unscaled |b|^2 would underflow and
+// leave |e| != 1 (J no longer unitary).
+template <typename T>
+__device__ __forceinline__ void rot_params(T app, T aqq, T br, T bi, T &c, T &s, T &pr, T &pi, T &qr, T &qi) {
+    const T mx = fmax(fabs(br), fabs(bi));
+    if (!(mx > T(0))) return;
+    const T im = T(1) / mx;
+    const T xr = br * im, xi = bi * im;
+    const T nn = sqrt(xr * xr + xi * xi);
+    const T inn = T(1) / nn;
+    const T er = xr * inn, ei = -xi * inn;
+    const T ab = mx * nn;
+    const T z = (aqq - app) / (T(2) * ab);
+    T t;
+    if (fabs(z) > T(1e18))
+        t = T(0.5) / z;
+    else
+        t = (z >= T(0) ? T(1) : T(-1)) / (fabs(z) + sqrt(z * z + T(1)));
+    c = T(1) / sqrt(T(1) + t * t);
+    s = t * c;
+    pr = -s * er;
+    pi = -s * ei;
+    qr = c * er;
+    qi = c * ei;
+}
+
+// (x, y) <- (c x + vp y, s x + vq y): entries p, q of one row of A J
+template <typename T2, typename T>
+__device__ __forceinline__ void rot_cols(T2 &x, T2 &y, T c, T s, T pr, T pi, T qr, T qi) {
+    const T2 x0 = x, y0 = y;
+    x.x = c * x0.x + (pr * y0.x - pi * y0.y);
+    x.y = c * x0.y + (pr * y0.y + pi * y0.x);
+    y.x = s * x0.x + (qr * y0.x - qi * y0.y);
+    y.y = s * x0.y + (qr * y0.y + qi * y0.x);
+}
+
+// Sweeps of the parallel Jacobi on the N x N Hermitian matrix whose row r lane r
+// holds in a (lanes base .. base + L - 1 hold one matrix; lanes r >= N hold
+// zeros).  With VEC the rows of V (initially I) are rotated too, so that
+// A_in = V A_out V^dagger.  Stops when every matrix of the warp has
+// sum_{i != j} |A_ij|^2 <= tol * sum |A_ij|^2, or after max_sweeps.
+template <typename T, int N, bool VEC>
+__device__ __forceinline__ void jacobi_rows(V2<T> (&a)[N], V2<T> (&v)[N], int r, int base, T tol,
+                                            int max_sweeps) {
+    using S = JShape<N>;
+    using T2 = V2<T>;
+    constexpr unsigned FULL = 0xffffffffu;
+    const bool row = r < N;
+#pragma unroll 1
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        T off = T(0), tot = T(0);
+#pragma unroll
+        for (int e = 0; e < N; ++e) {
+            const T w = a[e].x * a[e].x + a[e].y * a[e].y;
+            tot += w;
+            if (e != r) off += w;
+        }
+#pragma unroll
+        for (int o = 1; o < S::L; o <<= 1) {
+            off += __shfl_xor_sync(FULL, off, o);
+            tot += __shfl_xor_sync(FULL, tot, o);
+        }
+        if (__all_sync(FULL, !(off > tol * tot))) break;
+#pragma unroll
+        for (int t = 0; t < S::NR; ++t) {
+            const int pt = row ? rr_partner(S::NE, t, r) : r;
+            const bool paired = row && pt < N;
+            const int src = base + (paired ? pt : r);
+            // pivots of this lane's pair: lane p holds A_pp and A_pq, lane q holds A_qq
+            const T dg = pick(a, r).x;
+            const T2 of = pick(a, pt);
+            const T dg_o = __shfl_sync(FULL, dg, src);
+            const T ofx_o = __shfl_sync(FULL, of.x, src), ofy_o = __shfl_sync(FULL, of.y, src);
+            const bool is_p = r < pt;
+            T c = T(1), s = T(0), pr = T(0), pi = T(0), qr = T(1), qi = T(0);
+            if (paired)
+                rot_params<T>(is_p ? dg : dg_o, is_p ? dg_o : dg, is_p ? of.x : ofx_o, is_p ? of.y : ofy_o, c, s,
+                              pr, pi, qr, qi);
+            // A <- A J (and V <- V J): every lane rotates the column pairs of its row
+#pragma unroll
+            for (int k = 0; k < S::NP; ++k) {
+                const int ia = k == 0 ? S::NE - 1 : (t + k) % S::NR;
+                const int ib = k == 0 ? t : (t - k + S::NR) % S::NR;
+                const int p = ia < ib ? ia : ib, q = ia < ib ? ib : ia;
+                if (q >= N) continue;
+                const int lp = base + p;
+                const T kc = __shfl_sync(FULL, c, lp), ks = __shfl_sync(FULL, s, lp);
+                const T kpr = __shfl_sync(FULL, pr, lp), kpi = __shfl_sync(FULL, pi, lp);
+                const T kqr = __shfl_sync(FULL, qr, lp), kqi = __shfl_sync(FULL, qi, lp);
+                rot_cols(a[p], a[q], kc, ks, kpr, kpi, kqr, kqi);
+                if (VEC) rot_cols(v[p], v[q], kc, ks, kpr, kpi, kqr, kqi);
+            }
+            // A <- J^dagger A: row p' = c row p + conj(vp) row q, row q' = s row p + conj(vq) row q
+            T2 al, be;   // new row = al * own + be * partner
+            al.x = T(1), al.y = T(0), be.x = T(0), be.y = T(0);
+            if (paired) {
+                if (is_p) {
+                    al.x = c;
+                    be.x = pr;
+                    be.y = -pi;
+                } else {
+                    al.x = qr;
+                    al.y = -qi;
+                    be.x = s;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < N; ++e) {
+                T2 o;
+                o.x = __shfl_sync(FULL, a[e].x, src);
+                o.y = __shfl_sync(FULL, a[e].y, src);
+                const T2 x = a[e];
+                a[e].x = (al.x * x.x - al.y * x.y) + (be.x * o.x - be.y * o.y);
+                a[e].y = (al.x * x.y + al.y * x.x) + (be.x * o.y + be.y * o.x);
+            }
+            // the rotated pivots are zero and the diagonal real, exactly
+#pragma unroll
+            for (int k = 0; k < S::NP; ++k) {
+                const int ia = k == 0 ? S::NE - 1 : (t + k) % S::NR;
+                const int ib = k == 0 ? t : (t - k + S::NR) % S::NR;
+                const int p = ia < ib ? ia : ib, q = ia < ib ? ib : ia;
+                if (q >= N) continue;
+                if (r == p) {
+                    a[q].x = T(0);
+                    a[q].y = T(0);
+                    a[p].y = T(0);
+                }
+                if (r == q) {
+                    a[p].x = T(0);
+                    a[p].y = T(0);
+                    a[q].y = T(0);
+                }
+            }
+        }
+    }
+}
+
+// entry (r, l) of the Hermitian matrix from its packed upper triangle
+// (diagonal reals first, then (re, im) of (i, j), i < j, row by row)
+template <int N>
+__device__ __forceinline__ double2 packed_entry(const double *__restrict__ H, int r, int l) {
+    if (l == r) return make_double2(H[r], 0.0);
+    const int i = r < l ? r : l, j = r < l ? l : r;
+    const int idx = N + 2 * (i * N - (i * (i + 1)) / 2 + (j - i - 1));
+    return make_double2(H[idx], r < l ? H[idx + 1] : -H[idx + 1]);
+}
+
+// Eigenpairs of count packed Hermitian N x N matrices: eigenvalues ascending
+// (FP64-refined), eigenvector columns (FP32) in U[i][n] order.
+template <int N>
+__global__ void __launch_bounds__(64) k_heev_mixed(int64_t count, const double *__restrict__ Hp,
+                                                   double *__restrict__ eval, float2 *__restrict__ U32,
+                                                   double2 *__restrict__ U64) {
+    using S = JShape<N>;
+    constexpr int MPB = 64 / S::L;   // matrices per block
+    constexpr int NC = N * N;
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ float2 Vs[MPB][N][N];
+    __shared__ double2 Ws[MPB][N][N];
+    const int lane = threadIdx.x & 31;
+    const int r = lane & (S::L - 1), base = lane & ~(S::L - 1);
+    const int ms = threadIdx.x / S::L;
+    const int64_t pt = (int64_t)blockIdx.x * MPB + ms;
+    const bool row = r < N;
+    const bool live = row && pt < count;
+    const int rc = row ? r : 0;
+    const double *H = Hp + (pt < count ? pt : 0) * (int64_t)NC;
+    // 1. FP32 Jacobi with eigenvectors
+    float2 a[N], v[N];
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+        const double2 x = live ? packed_entry<N>(H, r, l) : make_double2(0.0, 0.0);
+        a[l] = make_float2((float)x.x, (float)x.y);
+        v[l] = make_float2(live && l == r ? 1.f : 0.f, 0.f);
+    }
+    jacobi_rows<float, N, true>(a, v, r, base, 1e-12f, 15);
+    if (row) {
+#pragma unroll
+        for (int e = 0; e < N; ++e) Vs[ms][r][e] = v[e];
+    }
+    __syncwarp();
+    // 2. W = H V (row r), FP64
+    {
+        double2 w[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) w[j] = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+            const double2 h = live ? packed_entry<N>(H, r, l) : make_double2(0.0, 0.0);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const float2 vl = Vs[ms][l][j];
+                cfma(w[j], h, make_double2(vl.x, vl.y));
+            }
+        }
+        if (row) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) Ws[ms][r][j] = w[j];
+        }
+    }
+    __syncwarp();
+    // 3. A' = V^dagger W and E = V^dagger V - I (row r), then A'' (first-order congruence)
+    double2 a64[N];
+    {
+        double2 ap[N], ee[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            ap[j] = make_double2(0.0, 0.0);
+            ee[j] = make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+            const float2 vs = Vs[ms][s][rc];
+            const double2 vd = make_double2(vs.x, vs.y);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                cfma_conj(ap[j], vd, Ws[ms][s][j]);
+                const float2 vj = Vs[ms][s][j];
+                cfma_conj(ee[j], vd, make_double2(vj.x, vj.y));
+            }
+        }
+        double lam = 0.0;
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+            if (j == r) {
+                ee[j].x -= 1.0;
+                lam = ap[j].x;
+            }
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const double lj = __shfl_sync(FULL, lam, base + j);
+            const double f = 0.5 * (lam + lj);
+            a64[j] = live ? make_double2(ap[j].x - f * ee[j].x, ap[j].y - f * ee[j].y) : make_double2(0.0, 0.0);
+        }
+    }
+    // 4. FP64 Jacobi on A'' for the eigenvalues
+    double2 unused[N];
+    jacobi_rows<double, N, false>(a64, unused, r, base, 1e-30, 20);
+    const double lam = pick(a64, r).x;
+    int rank = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const double lj = __shfl_sync(FULL, lam, base + j);
+        rank += (lj < lam || (lj == lam && j < r)) ? 1 : 0;
+    }
+    if (live) {
+        eval[pt * N + rank] = lam;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const float2 u = Vs[ms][i][r];
+            if (U32) U32[pt * NC + i * N + rank] = u;
+            if (U64) U64[pt * NC + i * N + rank] = make_double2(u.x, u.y);
+        }
+    }
+}
+
+}  // namespace
+
+// Cos/sin coefficient table of H(k) (see the top of this file), built on the host
+// when the model is set: representatives R = 0 and every R that is
+// lexicographically positive; T[2r][c] = C_R, T[2r+1][c] = S_R in the packed
+// column order.
+pgb_status build_band_table(pgb_ctx *c, const int32_t *R, const double *H, int nR, int nw) {
+    using Key = std::tuple<int, int, int>;
+    std::map<Key, int> idx;
+    for (int r = 0; r < nR; ++r) idx[Key(R[3 * r], R[3 * r + 1], R[3 * r + 2])] = r;
+    const int ncol = nw * nw;
+    std::vector<int32_t> reps;
+    std::vector<double> T;
+    int M = 0;
+    // entry (i, j) of H(X) and of its adjoint-based parts A(X), B(X)
+    auto hx = [&](int X, int i, int j, double &re, double &im) {
+        re = H[2 * ((size_t)X * ncol + i * nw + j)];
+        im = H[2 * ((size_t)X * ncol + i * nw + j) + 1];
+    };
+    auto parts = [&](int X, int i, int j, double A[2], double B[2]) {
+        double hr, hi, tr, ti;
+        hx(X, i, j, hr, hi);
+        hx(X, j, i, tr, ti);               // conj(H_ji) = (tr, -ti)
+        A[0] = 0.5 * (hr + tr);
+        A[1] = 0.5 * (hi - ti);
+        const double dr = hr - tr, di = hi + ti;   // H_ij - conj(H_ji)
+        B[0] = -0.5 * di;                  // i * d / 2
+        B[1] = 0.5 * dr;
+    };
+    for (int r = 0; r < nR; ++r) {
+        const int x = R[3 * r], y = R[3 * r + 1], z = R[3 * r + 2];
+        const bool zero = x == 0 && y == 0 && z == 0;
+        const bool pos = x > 0 || (x == 0 && (y > 0 || (y == 0 && z > 0)));
+        if (!zero && !pos) continue;
+        int rn = r;
+        if (!zero) {
+            auto it = idx.find(Key(-x, -y, -z));
+            if (it == idx.end()) {
+                c->err = "set_model: R_H is not closed under inversion";
+                return PGB_EINVAL;
+            }
+            rn = it->second;
+        }
+        reps.push_back(x);
+        reps.push_back(y);
+        reps.push_back(z);
+        M = std::max(M, std::max(std::abs(x), std::max(std::abs(y), std::abs(z))));
+        std::vector<double> Cr(ncol), Sr(ncol);
+        for (int i = 0; i < nw; ++i)
+            for (int j = i; j < nw; ++j) {
+                double Ap[2], Bp[2], An[2], Bn[2];
+                parts(r, i, j, Ap, Bp);
+                double C[2], Sv[2];
+                if (zero) {
+                    C[0] = Ap[0];
+                    C[1] = Ap[1];
+                    Sv[0] = Sv[1] = 0.0;
+                } else {
+                    parts(rn, i, j, An, Bn);
+                    C[0] = Ap[0] + An[0];
+                    C[1] = Ap[1] + An[1];
+                    Sv[0] = Bp[0] - Bn[0];
+                    Sv[1] = Bp[1] - Bn[1];
+                }
+                if (i == j) {
+                    Cr[i] = C[0];
+                    Sr[i] = Sv[0];
+                } else {
+                    const int pidx = nw + 2 * (i * nw - (i * (i + 1)) / 2 + (j - i - 1));
+                    Cr[pidx] = C[0];
+                    Cr[pidx + 1] = C[1];
+                    Sr[pidx] = Sv[0];
+                    Sr[pidx + 1] = Sv[1];
+                }
+            }
+        T.insert(T.end(), Cr.begin(), Cr.end());
+        T.insert(T.end(), Sr.begin(), Sr.end());
+    }
+    c->nHrep = (int)(reps.size() / 3);
+    c->HrepM = M;
+    pgb_status st = dalloc(c, &c->d_Hrep, reps.size());
+    if (st == PGB_OK) st = dalloc(c, &c->d_Hcs, T.size());
+    if (st != PGB_OK) return st;
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_Hrep, reps.data(), 4 * reps.size(), cudaMemcpyHostToDevice, c->stream));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_Hcs, T.data(), 8 * T.size(), cudaMemcpyHostToDevice, c->stream));
+    PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // the host vectors go out of scope
+    return PGB_OK;
+}
+
+// Packed Hermitian H(k) [np][nw^2] at np points (crystal coordinates).
+pgb_status launch_herm_sum(pgb_ctx *c, const double *d_pts, int64_t np, double *d_out) {
+    if (np == 0) return PGB_OK;
+    const int ncol = c->nw * c->nw;
+    const int M = c->HrepM;
+    const size_t smem = M <= kHermMaxM ? (size_t)3 * (2 * M + 1) * HS_P * sizeof(double2) : 0;
+    const dim3 grid(div_up(np, HS_P), div_up(ncol, HS_C));
+    if (smem > 48 * 1024)
+        PGB_CUDA_TRY(c, cudaFuncSetAttribute(k_herm_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_herm_sum<<<grid, 256, smem, c->stream>>>(np, d_pts, c->nHrep, c->d_Hrep, M, ncol, c->d_Hcs, d_out);
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+// Eigenpairs of count packed Hermitian n x n matrices (2 <= n <= 16): eigenvalues
+// ascending in FP64, eigenvectors in FP32 (U32) and/or widened to FP64 (U64).
+pgb_status launch_heev_mixed(pgb_ctx *c, int64_t count, int n, const double *d_Hp, double *d_eval, float2 *d_U32,
+                             double2 *d_U64) {
+    if (count == 0) return PGB_OK;
+#define PGB_HEEVM_CASE(NN)                                                                                    \
+    case NN: {                                                                                                \
+        constexpr int mpb = 64 / JShape<NN>::L;                                                               \
+        k_heev_mixed<NN><<<div_up(count, mpb), 64, 0, c->stream>>>(count, d_Hp, d_eval, d_U32,  \
+                                                                                 d_U64);                      \
+        break;                                                                                                \
+    }
+    switch (n) {
+        PGB_HEEVM_CASE(2)
+        PGB_HEEVM_CASE(3)
+        PGB_HEEVM_CASE(4)
+        PGB_HEEVM_CASE(5)
+        PGB_HEEVM_CASE(6)
+        PGB_HEEVM_CASE(7)
+        PGB_HEEVM_CASE(8)
+        PGB_HEEVM_CASE(9)
+        PGB_HEEVM_CASE(10)
+        PGB_HEEVM_CASE(11)
+        PGB_HEEVM_CASE(12)
+        PGB_HEEVM_CASE(13)
+        PGB_HEEVM_CASE(14)
+        PGB_HEEVM_CASE(15)
+        PGB_HEEVM_CASE(16)
+        default:
+            c->err = "heev_mixed: n must be 2..16";
+            return PGB_EINVAL;
+    }
+#undef PGB_HEEVM_CASE
+    PGB_LAUNCH_CHECK(c);
+    return PGB_OK;
+}
+
+}  // namespace pgb

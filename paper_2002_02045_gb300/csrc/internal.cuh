@@ -49,6 +49,9 @@ struct pgb_ctx {
     std::vector<double> mass;
     int32_t *d_RH = nullptr, *d_RD = nullptr, *d_Rge = nullptr, *d_Rgp = nullptr;
     double2 *d_H = nullptr;      // [nRH][nw*nw]
+    int nHrep = 0, HrepM = 0;    // cos/sin form of H(k): representatives of {R, -R} and max |R_d|
+    int32_t *d_Hrep = nullptr;   // [nHrep][3]
+    double *d_Hcs = nullptr;     // [2 nHrep][nw*nw] C_R, S_R rows, packed upper-triangle columns
     double2 *d_D = nullptr;      // [nRD][nm*nm] (imaginary part 0)
     double *d_mode_scale = nullptr;  // [nm] 1/sqrt(M_kappa) per ka
     double2 *d_g64 = nullptr;    // [nRge][nRgp*nm*nw*nw]
@@ -225,6 +228,11 @@ pgb_status launch_cgemm(pgb_ctx *c, bool fp32, int64_t batch, int64_t M, int64_t
                         int64_t strideB, void *C, int64_t ldc, int64_t strideC);
 pgb_status launch_heevj(pgb_ctx *c, int64_t count, int n, double2 *d_mat, const double *d_scale,
                         double *d_eval, double2 *d_evec);
+// band interpolation for the FP32 paths (bands_mixed.cu)
+pgb_status build_band_table(pgb_ctx *c, const int32_t *R, const double *H, int nR, int nw);
+pgb_status launch_herm_sum(pgb_ctx *c, const double *d_pts, int64_t np, double *d_out);
+pgb_status launch_heev_mixed(pgb_ctx *c, int64_t count, int n, const double *d_Hp, double *d_eval, float2 *d_U32,
+                             double2 *d_U64);
 pgb_status launch_phonon_coef(pgb_ctx *c, int64_t nq, int nm, const double *d_eval,
                               const double2 *d_evec, const double *d_mode_scale, double *d_hw,
                               double2 *d_coef);
