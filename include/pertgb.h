@@ -240,8 +240,14 @@ pgb_status pgb_transport(pgb_ctx *ctx, double mu_eV, int precision, int max_iter
  *   Gamma_nk = (1/nq) sum_j y_j, y_j = sum_{m nu} W(k, q_j) / p(q_j),
  * with bands at k + q_j and phonons at q_j interpolated for each sample and g
  * including any polar term.  stderr_out (may be NULL) receives the standard
- * error sqrt(sum_j (y_j - Gamma)^2 / (nq (nq - 1))).  precision: PGB_FP64 or
- * PGB_FP32.  Terms with |x|/sigma > 7 are skipped.  Outputs [nk][nw], 1/s. */
+ * error sqrt(sum_j (y_j - Gamma)^2 / (nq (nq - 1))).  precision: PGB_FP64
+ * (everything FP64); PGB_FP32 (FP32 products; bands at k + q_j and phonons at
+ * q_j from the cos/sin Fourier sums in double-float and a mixed-precision
+ * Jacobi: FP64-refined eigenvalues and phonon modes, FP32 band eigenvectors;
+ * energies and weights FP64); PGB_TC_TF32X3 or
+ * PGB_TC_BF16X3 (as PGB_FP32, with the R_p sum on the tensor cores in the split
+ * precision).  Terms with |x|/sigma > 7 are skipped.  Outputs [nk][nw], 1/s.
+ * PGB_ETIMEOUT if a tensor-core pipeline wait ran out (no result).           */
 #define PGB_Q_UNIFORM 0
 #define PGB_Q_CAUCHY 1
 pgb_status pgb_scattering_rates_mc(pgb_ctx *ctx, const double *kpts, int64_t nk, const double *u, int64_t nq,

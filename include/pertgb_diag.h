@@ -28,6 +28,12 @@ pgb_status pgb_diag_bands(pgb_ctx *ctx, const double *pts, int64_t n, double *Hk
  * NULL.  Needs nw >= 2 (PGB_EINVAL otherwise).                               */
 pgb_status pgb_diag_bands_mixed(pgb_ctx *ctx, const double *pts, int64_t n, double *Hp, double *eps, float *U);
 
+/* The same for the phonons of the FP32 Monte-Carlo rates (Sec. 2.2.2, Eq. IFC2):
+ * Dp [n][nm*nm] the packed mass-scaled D(q) = sum_R e^{iq.R} D(R)/sqrt(M M'),
+ * w2 [n][nm] its eigenvalues omega^2 ascending (eV/bohr^2/amu), e [n][nm][nm]
+ * complex64 the modes (column nu), refined in FP64 like the eigenvalues.    */
+pgb_status pgb_diag_phonons_mixed(pgb_ctx *ctx, const double *pts, int64_t n, double *Dp, double *w2, float *e);
+
 /* The device eigensolver template run on the host for `count` Hermitian
  * n x n complex128 matrices: eval [count][n], evec [count][n][n].
  * Returns 0, or -1 for an unsupported n (supported: 1, 2, 3, 6, 8, 16).     */

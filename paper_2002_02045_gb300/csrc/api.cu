@@ -150,9 +150,24 @@ pgb_status bands_at_mixed(pgb_ctx *c, const double *d_pts, int64_t np, double *d
     Tmp<double> hp;
     TRY(hp.alloc(c, (size_t)np * c->nw * c->nw));
     prof_mark(c, PGB_PROF_BANDS);
-    TRY(launch_herm_sum(c, d_pts, np, hp.p));
+    TRY(launch_herm_sum(c, c->htH, d_pts, np, hp.p));
     prof_mark(c, PGB_PROF_BANDS);
-    TRY(launch_heev_mixed(c, np, c->nw, hp.p, d_eps, d_U32, d_U64));
+    TRY(launch_heev_mixed(c, np, c->nw, hp.p, d_eps, d_U32, d_U64, false));
+    return PGB_OK;
+}
+
+// Phonons at arbitrary points for the FP32 paths: cos/sin Fourier sum of the
+// mass-scaled D(q), mixed-precision Jacobi (FP64-refined omega^2, FP32 modes).
+pgb_status phonons_at_mixed(pgb_ctx *c, const double *d_pts, int64_t np, double *d_hw, double2 *d_coef) {
+    const int nm2 = c->nm * c->nm;
+    Tmp<double> dp, lam;
+    Tmp<double2> ev;
+    TRY(dp.alloc(c, (size_t)np * nm2));
+    TRY(lam.alloc(c, (size_t)np * c->nm));
+    TRY(ev.alloc(c, (size_t)np * nm2));
+    TRY(launch_herm_sum(c, c->htD, d_pts, np, dp.p));
+    TRY(launch_heev_mixed(c, np, c->nm, dp.p, lam.p, nullptr, ev.p, true));
+    TRY(launch_phonon_coef(c, np, c->nm, lam.p, ev.p, c->d_mode_scale, d_hw, d_coef));
     return PGB_OK;
 }
 
@@ -218,9 +233,8 @@ void free_model(pgb_ctx *c) {
     dfree(&c->d_Rge);
     dfree(&c->d_Rgp);
     dfree(&c->d_H);
-    dfree(&c->d_Hrep);
-    dfree(&c->d_Hcs);
-    c->nHrep = c->HrepM = 0;
+    free_herm_table(&c->htH);
+    free_herm_table(&c->htD);
     dfree(&c->d_D);
     dfree(&c->d_mode_scale);
     dfree(&c->d_g64);
@@ -481,13 +495,20 @@ pgb_status pgb_set_model(pgb_ctx *c, const pgb_model *m) {
     PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_Rge, m->R_ge, 12 * (size_t)c->nRge, cudaMemcpyHostToDevice, c->stream));
     PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_Rgp, m->R_gp, 12 * (size_t)c->nRgp, cudaMemcpyHostToDevice, c->stream));
     PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_H, m->H, 16 * (size_t)c->nRH * nw2, cudaMemcpyHostToDevice, c->stream));
-    TRY(build_band_table(c, m->R_H, m->H, c->nRH, nw));
+    TRY(build_herm_table(c, &c->htH, m->R_H, m->H, c->nRH, nw));
     std::vector<double> D2((size_t)2 * c->nRD * nm2, 0.0);
     for (size_t i = 0; i < (size_t)c->nRD * nm2; ++i) D2[2 * i] = m->D[i];
     PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_D, D2.data(), 8 * D2.size(), cudaMemcpyHostToDevice, c->stream));
     std::vector<double> sc(nm);
     for (int ka = 0; ka < nm; ++ka) sc[ka] = 1.0 / std::sqrt(m->mass[ka / 3]);
     PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_mode_scale, sc.data(), 8 * (size_t)nm, cudaMemcpyHostToDevice, c->stream));
+    {   // the mass-scaled D(R) / sqrt(M M') as complex entries, for the cos/sin form of D(q)
+        std::vector<double> Ds((size_t)2 * c->nRD * nm2, 0.0);
+        for (size_t r = 0; r < (size_t)c->nRD; ++r)
+            for (int i = 0; i < nm; ++i)
+                for (int j = 0; j < nm; ++j) Ds[2 * (r * nm2 + i * nm + j)] = m->D[r * nm2 + i * nm + j] * sc[i] * sc[j];
+        TRY(build_herm_table(c, &c->htD, m->R_D, Ds.data(), c->nRD, nm));
+    }
     if (m->g_is_double) {
         PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_g64, m->g, 16 * ng, cudaMemcpyHostToDevice, c->stream));
         TRY(launch_to_f32(c, c->d_g64, c->d_g32, (int64_t)ng));
@@ -1381,14 +1402,19 @@ pgb_status pgb_scattering_rates_mc(pgb_ctx *c, const double *kpts, int64_t nk, c
         return fail(c, PGB_EINVAL, "scattering_rates_mc: unknown sampling");
     if (sampling == PGB_Q_CAUCHY && !(width > 0.0 && width <= 1.0))
         return fail(c, PGB_EINVAL, "scattering_rates_mc: the Cauchy width must lie in (0, 1]");
-    if (precision != PGB_FP64 && precision != PGB_FP32)
-        return fail(c, PGB_EINVAL, "scattering_rates_mc: precision must be PGB_FP64 or PGB_FP32");
+    if (precision != PGB_FP64 && precision != PGB_FP32 && precision != PGB_TC_TF32X3 && precision != PGB_TC_BF16X3)
+        return fail(c, PGB_EINVAL, "scattering_rates_mc: unknown precision");
     if (nk == 0) return PGB_OK;
     if (nq == 0) return fail(c, PGB_EINVAL, "scattering_rates_mc: need at least one q sample");
     if (!kpts || !u || !gamma_out) return fail(c, PGB_EINVAL, "scattering_rates_mc: null pointer");
-    const bool f32 = precision == PGB_FP32;
+    const bool tcp = precision == PGB_TC_TF32X3 || precision == PGB_TC_BF16X3;
+    const bool tf32 = precision == PGB_TC_TF32X3;
+    const bool f32 = precision != PGB_FP64;   // FP32 epilogue for the FP32 and split forms
     const int nw = c->nw, nm = c->nm, nw2 = nw * nw, nm2 = nm * nm;
     const int64_t ncol = (int64_t)nm * nw2, nrow = (int64_t)c->nKp * ncol, nrowS = (int64_t)c->nRgp * ncol;
+    const int64_t ldc = tcp ? (ncol + 95) / 96 * 96 : ncol;   // row stride of the q-sum result
+    const int Kp = tcp ? tc_kpad(c->nKp) : 0;
+    const size_t tes = tf32 ? 4 : 2;
     const size_t es = f32 ? sizeof(float2) : sizeof(double2);
     {   // uniforms must lie in [0, 1)
         std::vector<double> hu(3 * (size_t)nq);
@@ -1441,11 +1467,18 @@ pgb_status pgb_scattering_rates_mc(pgb_ctx *c, const double *kpts, int64_t nk, c
     Tmp<char> phq, C, coef32, Ukq32;
     TRY(hw_q.alloc(c, (size_t)qc * nm));
     TRY(coef_q.alloc(c, (size_t)qc * nm2));
-    TRY(phq.alloc(c, (size_t)qc * c->nKp * es));
+    Tmp<char> Asplit, Bsplit;
+    TRY(phq.alloc(c, (size_t)qc * c->nKp * (tcp ? sizeof(double2) : es)));
     TRY(kq.alloc(c, 3 * (size_t)kb * qc));
     TRY(eps_kq.alloc(c, (size_t)kb * qc * nw));
     if (!f32 || nw < 2) TRY(U_kq.alloc(c, (size_t)kb * qc * nw2));
-    TRY(C.alloc(c, (size_t)kb * qc * ncol * es));
+    TRY(C.alloc(c, (size_t)kb * qc * ldc * es));
+    if (tcp) {
+        TRY(Asplit.alloc(c, (size_t)4 * qc * Kp * tes));
+        TRY(Bsplit.alloc(c, (size_t)kb * 4 * ldc * Kp * tes));
+        if (!c->d_err) PGB_CUDA_TRY(c, dev_malloc((void **)&c->d_err, sizeof(int)));
+        PGB_CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    }
     TRY(partial.alloc(c, (size_t)mc_partial_count(c, kb, qc)));
     if (f32) {
         TRY(coef32.alloc(c, (size_t)qc * nm2 * sizeof(float2)));
@@ -1454,8 +1487,12 @@ pgb_status pgb_scattering_rates_mc(pgb_ctx *c, const double *kpts, int64_t nk, c
     for (int64_t q0 = 0; q0 < nq; q0 += qc) {
         const int64_t nqc = std::min(qc, nq - q0);
         const double *qp = q.p + 3 * q0;
-        TRY(phonons_at(c, qp, nqc, hw_q.p, coef_q.p));
-        TRY(launch_qtable_pts(c, qp, nqc, phq.p, f32));
+        if (f32)
+            TRY(phonons_at_mixed(c, qp, nqc, hw_q.p, coef_q.p));
+        else
+            TRY(phonons_at(c, qp, nqc, hw_q.p, coef_q.p));
+        TRY(launch_qtable_pts(c, qp, nqc, phq.p, f32 && !tcp));
+        if (tcp) TRY(launch_split_table(c, tf32, nqc, c->nKp, c->nKp, Kp, (const double2 *)phq.p, Asplit.p));
         const void *cf = coef_q.p;
         if (f32) {
             TRY(launch_to_f32(c, coef_q.p, (float2 *)coef32.p, nqc * nm2));
@@ -1475,14 +1512,26 @@ pgb_status pgb_scattering_rates_mc(pgb_ctx *c, const double *kpts, int64_t nk, c
                     Ukq = Ukq32.p;
                 }
             }
-            TRY(launch_cgemm(c, f32, nb, nqc, ncol, c->nKp, phq.p, c->nKp, 0, G.p + (size_t)k0 * nrow * es, ncol,
-                             nrow, C.p, ncol, nqc * ncol));
-            TRY(launch_mc_epilogue(c, f32, nb, nqc, C.p, Ukq, eps_k.p + k0 * nw, eps_kq.p, hw_q.p, cf,
+            if (tcp) {
+                TRY(launch_split_g(c, tf32, nb, c->nKp, (int)ncol, Kp, (const float2 *)(G.p + (size_t)k0 * nrow * es),
+                                   Bsplit.p, (int)ldc));
+                TRY(launch_tc_qsum(c, tf32, nb, nqc, (int)ldc, Kp, Asplit.p, Bsplit.p, (float2 *)C.p, c->d_err));
+            } else {
+                TRY(launch_cgemm(c, f32, nb, nqc, ncol, c->nKp, phq.p, c->nKp, 0, G.p + (size_t)k0 * nrow * es,
+                                 ncol, nrow, C.p, ncol, nqc * ncol));
+            }
+            TRY(launch_mc_epilogue(c, f32, nb, nqc, C.p, ldc, Ukq, eps_k.p + k0 * nw, eps_kq.p, hw_q.p, cf,
                                    pinv.p + q0, T, mu, sigma, partial.p, acc.p + k0 * 2 * nw));
         }
     }
     TRY(launch_mc_finish(c, nk, nq, sigma, acc.p, Gm.dev, Er.dev));
     PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (tcp) {
+        int herr = 0;
+        PGB_CUDA_TRY(c, cudaMemcpy(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (herr) return fail(c, PGB_ETIMEOUT, "scattering_rates_mc: a tensor-core pipeline wait ran out (bits " +
+                                                   std::to_string(herr) + ")");
+    }
     TRY(Gm.finish());
     TRY(Er.finish());
     return PGB_OK;
@@ -1530,29 +1579,41 @@ pgb_status pgb_diag_bands(pgb_ctx *c, const double *pts, int64_t n, double *Hk, 
     return PGB_OK;
 }
 
-pgb_status pgb_diag_bands_mixed(pgb_ctx *c, const double *pts, int64_t n, double *Hp, double *eps, float *U) {
+// shared body of pgb_diag_bands_mixed (H, nw bands) and pgb_diag_phonons_mixed (mass-scaled D, nm modes)
+static pgb_status diag_mixed(pgb_ctx *c, const HermTab &tab, int nn, bool refine, const char *who, const double *pts,
+                             int64_t n, double *Hp, double *eps, float *U) {
     if (!c) return PGB_EINVAL;
     cudaSetDevice(c->device);
-    if (!c->has_model) return fail(c, PGB_ESTATE, "diag_bands_mixed: call set_model first");
-    if (c->nw < 2) return fail(c, PGB_EINVAL, "diag_bands_mixed: needs nw >= 2");
-    if (n < 0) return fail(c, PGB_EINVAL, "diag_bands_mixed: negative n");
+    if (!c->has_model) return fail(c, PGB_ESTATE, std::string(who) + ": call set_model first");
+    if (nn < 2) return fail(c, PGB_EINVAL, std::string(who) + ": needs matrices of size >= 2");
+    if (n < 0) return fail(c, PGB_EINVAL, std::string(who) + ": negative n");
     if (n == 0) return PGB_OK;
-    if (!pts) return fail(c, PGB_EINVAL, "diag_bands_mixed: null pts");
-    const int nw2 = c->nw * c->nw;
+    if (!pts) return fail(c, PGB_EINVAL, std::string(who) + ": null pts");
+    const int nw2 = nn * nn;
     In<double> P;
     TRY(P.init(c, pts, 3 * (size_t)n));
     Tmp<double> hp, e;
     Tmp<float2> u;
     TRY(hp.alloc(c, (size_t)n * nw2));
-    TRY(e.alloc(c, (size_t)n * c->nw));
+    TRY(e.alloc(c, (size_t)n * nn));
     TRY(u.alloc(c, (size_t)n * nw2));
-    TRY(launch_herm_sum(c, P.dev, n, hp.p));
+    TRY(launch_herm_sum(c, tab, P.dev, n, hp.p));
     if (Hp) PGB_CUDA_TRY(c, cudaMemcpyAsync(Hp, hp.p, 8 * (size_t)n * nw2, cudaMemcpyDefault, c->stream));
-    TRY(launch_heev_mixed(c, n, c->nw, hp.p, e.p, u.p, nullptr));
-    if (eps) PGB_CUDA_TRY(c, cudaMemcpyAsync(eps, e.p, 8 * (size_t)n * c->nw, cudaMemcpyDefault, c->stream));
+    TRY(launch_heev_mixed(c, n, nn, hp.p, e.p, u.p, nullptr, refine));
+    if (eps) PGB_CUDA_TRY(c, cudaMemcpyAsync(eps, e.p, 8 * (size_t)n * nn, cudaMemcpyDefault, c->stream));
     if (U) PGB_CUDA_TRY(c, cudaMemcpyAsync(U, u.p, 8 * (size_t)n * nw2, cudaMemcpyDefault, c->stream));
     PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return PGB_OK;
+}
+
+pgb_status pgb_diag_bands_mixed(pgb_ctx *c, const double *pts, int64_t n, double *Hp, double *eps, float *U) {
+    if (!c) return PGB_EINVAL;
+    return diag_mixed(c, c->htH, c->nw, false, "diag_bands_mixed", pts, n, Hp, eps, U);
+}
+
+pgb_status pgb_diag_phonons_mixed(pgb_ctx *c, const double *pts, int64_t n, double *Dp, double *w2, float *e) {
+    if (!c) return PGB_EINVAL;
+    return diag_mixed(c, c->htD, c->nm, true, "diag_phonons_mixed", pts, n, Dp, w2, e);
 }
 
 pgb_status pgb_build_collision_grid(pgb_ctx *c, int band_lo, int band_hi, double e_lo, double e_hi, double T,

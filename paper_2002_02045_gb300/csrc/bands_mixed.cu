@@ -12,7 +12,8 @@
 // and imaginary parts of the nw (nw - 1) / 2 entries above it, nw^2 real
 // columns.  That is a real GEMM with K = 2 |S| ~ nR rows, a quarter of the real
 // multiply-adds of the complex form.  The phases come from per-point 1-D tables
-// e^{2 pi i k_d m}: e^{ik.R} = prod_d e^{2 pi i k_d R_d}.
+// e^{2 pi i k_d m}: e^{ik.R} = prod_d e^{2 pi i k_d R_d}.  The sum runs in
+// double-float arithmetic on the FP32 pipe (see k_herm_sum).
 //
 // Eigensolver.  A parallel cyclic Jacobi with one lane per matrix row: in each
 // round the n/2 disjoint pairs of a round-robin schedule are rotated at once
@@ -26,7 +27,10 @@
 //      the congruence of A' by (I + E)^{-1/2} (symmetric orthonormalisation of
 //      V) to first order in E; the terms left out are O(|E|^2 |H|) and
 //      O(|E| |A'_ij, i != j|), below 1e-11 of |H| for |E| ~ 1e-7.  A'' is nearly
-//      diagonal, so the FP64 sweeps converge in one or two sweeps.
+//      diagonal (off-diagonals ~1e-7 |H|): one sweep, quadratically convergent,
+//      leaves couplings b ~ 1e-12 |H| or below, which move an eigenvalue by at
+//      most min(|b|, |b|^2 / gap).  The sweeps stop once the off-diagonal mass
+//      is below 1e-22 of the total.
 // The eigenvalues are those of H to FP64 rounding; the eigenvectors returned are
 // the FP32 V (orthonormal to ~1e-7), which is what the FP32 |g|^2 products use.
 // Within a cluster of eigenvalues closer than ~1e-7 |H| the FP32 vectors are an
@@ -52,75 +56,165 @@ constexpr int HS_P = 64;          // points per block of the Fourier sum
 constexpr int HS_C = 64;          // real columns per block
 constexpr int HS_K = 16;          // K rows (8 representatives) per stage
 
+// Double-float arithmetic on the FP32 pipe (a value is an unevaluated sum h + l of
+// two floats, ~48 significant bits).  Every step uses the explicitly rounded
+// intrinsics so that the compiler cannot contract a product and a sum into an FMA
+// (the error-free transforms below depend on each rounding).
+__device__ __forceinline__ float2 df_split(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+// h + l = a + b exactly, |l| <= ulp(h)/2, for |a| >= |b| or a = 0
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {
+    const float h = __fadd_rn(a, b);
+    return make_float2(h, __fsub_rn(b, __fsub_rn(h, a)));
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float s = __fadd_rn(a.x, b.x);
+    const float z = __fsub_rn(s, a.x);
+    float t = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, z)), __fsub_rn(b.x, z));
+    t = __fadd_rn(t, __fadd_rn(a.y, b.y));
+    return fast_two_sum(s, t);
+}
+struct cdf {   // complex double-float
+    float2 re, im;
+};
+__device__ __forceinline__ cdf cdf_mul(const cdf &x, const cdf &y) {
+    cdf r;
+    const float2 a = df_mul(x.re, y.re), b = df_mul(x.im, y.im), c = df_mul(x.re, y.im), d = df_mul(x.im, y.re);
+    r.re = df_add(a, make_float2(-b.x, -b.y));
+    r.im = df_add(c, d);
+    return r;
+}
+// (sh, sl) += (ah + al)(bh + bl): exact leading product and its error, TwoSum into sh;
+// the al bl term (2^-48 relative) is dropped
+__device__ __forceinline__ void df_fma(float &sh, float &sl, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    const float t = __fadd_rn(sh, p);
+    const float z = __fsub_rn(t, sh);
+    const float r = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
+    sl = __fadd_rn(sl, __fadd_rn(r, e));
+    sh = t;
+}
+
 // Real Fourier sum: out[p][c] = sum_k phase_k(p) T[k][c], phase_{2r} = cos(2 pi k.R_r),
-// phase_{2r+1} = sin(2 pi k.R_r).  Block: 64 points x 64 columns, 4 x 4 per thread.
+// phase_{2r+1} = sin(2 pi k.R_r), in double-float (products and sums on the FP32
+// pipe, ~2^-44 relative to the largest partial sum; FP64 would be FP64-pipe bound).
+// Block: 64 points x 64 columns, 4 x 4 per thread.  The phases are products of
+// per-point 1-D tables e^{2 pi i k_d m} (powers of sincospi(2 k_d) in
+// double-float) when every |R_d| <= kHermMaxM, else one FP64 sincospi each.
 __global__ void __launch_bounds__(256) k_herm_sum(int64_t np, const double *__restrict__ pts, int nrep,
                                                   const int32_t *__restrict__ Rrep, int M, int ncol,
-                                                  const double *__restrict__ T, double *__restrict__ out) {
-    extern __shared__ double2 t1d[];   // [3][2M+1][HS_P] e^{2 pi i k_d m}, when M <= kHermMaxM
-    __shared__ double As[HS_K][HS_P];
-    __shared__ double Bs[HS_K][HS_C];
+                                                  const float2 *__restrict__ T2, double *__restrict__ out) {
+    extern __shared__ float4 t1d[];   // [3][2M+1][HS_P] (re_h, re_l, im_h, im_l), when M <= kHermMaxM
+    __shared__ __align__(16) float Ah[HS_K][HS_P];
+    __shared__ __align__(16) float Al[HS_K][HS_P];
+    __shared__ __align__(16) float Bh[HS_K][HS_C];
+    __shared__ __align__(16) float Bl[HS_K][HS_C];
     const int tid = threadIdx.x;
     const int64_t p0 = (int64_t)blockIdx.x * HS_P;
     const int c0 = blockIdx.y * HS_C;
     const int W = 2 * M + 1;
     const bool tab = M <= kHermMaxM;
     if (tab) {
-        for (int x = tid; x < 3 * W * HS_P; x += blockDim.x) {
-            const int pl = x % HS_P, dm = x / HS_P, d = dm / W, mm = dm - d * W - M;
+        for (int x = tid; x < 3 * HS_P; x += blockDim.x) {
+            const int pl = x % HS_P, d = x / HS_P;
             const int64_t p = p0 + pl;
-            double s = 0.0, c = 1.0;
-            if (p < np) sincospi(2.0 * pts[3 * p + d] * (double)mm, &s, &c);
-            t1d[x] = make_double2(c, s);
+            double sn = 0.0, cs = 1.0;
+            if (p < np) sincospi(2.0 * pts[3 * p + d], &sn, &cs);
+            cdf b, pw;
+            b.re = df_split(cs);
+            b.im = df_split(sn);
+            pw.re = make_float2(1.f, 0.f);
+            pw.im = make_float2(0.f, 0.f);
+            float4 *row = t1d + (size_t)d * W * HS_P + pl;
+            row[M * HS_P] = make_float4(1.f, 0.f, 0.f, 0.f);
+            for (int m = 1; m <= M; ++m) {
+                pw = cdf_mul(pw, b);
+                row[(M + m) * HS_P] = make_float4(pw.re.x, pw.re.y, pw.im.x, pw.im.y);
+                row[(M - m) * HS_P] = make_float4(pw.re.x, pw.re.y, -pw.im.x, -pw.im.y);
+            }
         }
     }
     __syncthreads();
     const int tx = tid & 15, ty = tid >> 4;
-    double acc[4][4];
+    float sh[4][4], sl[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
     const int K = 2 * nrep;
     for (int k0 = 0; k0 < K; k0 += HS_K) {
         for (int x = tid; x < (HS_K / 2) * HS_P; x += blockDim.x) {
             const int pl = x % HS_P, rl = x / HS_P;
             const int rep = k0 / 2 + rl;
             const int64_t p = p0 + pl;
-            double c = 0.0, s = 0.0;
+            cdf e;
+            e.re = e.im = make_float2(0.f, 0.f);
             if (rep < nrep && p < np) {
                 const int R1 = Rrep[3 * rep], R2 = Rrep[3 * rep + 1], R3 = Rrep[3 * rep + 2];
                 if (tab) {
-                    const double2 e = cmul(cmul(t1d[(R1 + M) * HS_P + pl], t1d[(W + R2 + M) * HS_P + pl]),
-                                           t1d[(2 * W + R3 + M) * HS_P + pl]);
-                    c = e.x;
-                    s = e.y;
+                    const float4 f1 = t1d[(R1 + M) * HS_P + pl], f2 = t1d[(W + R2 + M) * HS_P + pl],
+                                 f3 = t1d[(2 * W + R3 + M) * HS_P + pl];
+                    cdf a1, a2, a3;
+                    a1.re = make_float2(f1.x, f1.y), a1.im = make_float2(f1.z, f1.w);
+                    a2.re = make_float2(f2.x, f2.y), a2.im = make_float2(f2.z, f2.w);
+                    a3.re = make_float2(f3.x, f3.y), a3.im = make_float2(f3.z, f3.w);
+                    e = cdf_mul(cdf_mul(a1, a2), a3);
                 } else {
                     double x3 = pts[3 * p] * R1 + pts[3 * p + 1] * R2 + pts[3 * p + 2] * R3;
                     x3 -= rint(x3);
-                    sincospi(2.0 * x3, &s, &c);
+                    double sn, cs;
+                    sincospi(2.0 * x3, &sn, &cs);
+                    e.re = df_split(cs);
+                    e.im = df_split(sn);
                 }
             }
-            As[2 * rl][pl] = c;
-            As[2 * rl + 1][pl] = s;
+            Ah[2 * rl][pl] = e.re.x;
+            Al[2 * rl][pl] = e.re.y;
+            Ah[2 * rl + 1][pl] = e.im.x;
+            Al[2 * rl + 1][pl] = e.im.y;
         }
         for (int x = tid; x < HS_K * HS_C; x += blockDim.x) {
             const int cl = x % HS_C, kl = x / HS_C;
             const int kr = k0 + kl, col = c0 + cl;
-            Bs[kl][cl] = (kr < K && col < ncol) ? T[(int64_t)kr * ncol + col] : 0.0;
+            const float2 v = (kr < K && col < ncol) ? T2[(int64_t)kr * ncol + col] : make_float2(0.f, 0.f);
+            Bh[kl][cl] = v.x;
+            Bl[kl][cl] = v.y;
         }
         __syncthreads();
-#pragma unroll
+#pragma unroll 2
         for (int kk = 0; kk < HS_K; ++kk) {
-            double av[4], bv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+            const float4 ah = *reinterpret_cast<const float4 *>(&Ah[kk][ty * 4]);
+            const float4 al = *reinterpret_cast<const float4 *>(&Al[kk][ty * 4]);
+            const float4 bh = *reinterpret_cast<const float4 *>(&Bh[kk][tx * 4]);
+            const float4 bl = *reinterpret_cast<const float4 *>(&Bl[kk][tx * 4]);
+            const float ahv[4] = {ah.x, ah.y, ah.z, ah.w}, alv[4] = {al.x, al.y, al.z, al.w};
+            const float bhv[4] = {bh.x, bh.y, bh.z, bh.w}, blv[4] = {bl.x, bl.y, bl.z, bl.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) df_fma(sh[i][j], sl[i][j], ahv[i], alv[i], bhv[j], blv[j]);
+            if (kk & 1) {   // renormalise every second step: |sl| stays near ulp(sh)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float2 n = fast_two_sum(sh[i][j], sl[i][j]);
+                        sh[i][j] = n.x;
+                        sl[i][j] = n.y;
+                    }
+            }
         }
         __syncthreads();
     }
@@ -131,11 +225,10 @@ __global__ void __launch_bounds__(256) k_herm_sum(int64_t np, const double *__re
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int col = c0 + tx * 4 + j;
-            if (col < ncol) out[p * ncol + col] = acc[i][j];
+            if (col < ncol) out[p * ncol + col] = (double)sh[i][j] + (double)sl[i][j];
         }
     }
 }
-
 
 // ---------------------------------------------------------------------------
 // Parallel Jacobi, one lane per row
@@ -173,11 +266,13 @@ __device__ __forceinline__ T2 pick(const T2 (&a)[N], int idx) {
 // columns (p, q) of J are (c, -s e) and (s, c e).  Returns the identity for b = 0.
 // |b| and e are formed from b scaled by max(|Re b|, |Im b|): inside a degenerate
 // cluster the pivots become tiny, and an unscaled |b|^2 would underflow and
-// leave |e| != 1 (J no longer unitary).
+// leave |e| != 1 (J no longer unitary).  Pivots below 1e-30 (where 1/max could
+// overflow in FP32) are left to the exact zeroing that follows every rotation,
+// which moves the eigenvalues by at most |b|.
 template <typename T>
 __device__ __forceinline__ void rot_params(T app, T aqq, T br, T bi, T &c, T &s, T &pr, T &pi, T &qr, T &qi) {
     const T mx = fmax(fabs(br), fabs(bi));
-    if (!(mx > T(0))) return;
+    if (!(mx > T(1e-30))) return;
     const T im = T(1) / mx;
     const T xr = br * im, xi = bi * im;
     const T nn = sqrt(xr * xr + xi * xi);
@@ -191,6 +286,35 @@ __device__ __forceinline__ void rot_params(T app, T aqq, T br, T bi, T &c, T &s,
     else
         t = (z >= T(0) ? T(1) : T(-1)) / (fabs(z) + sqrt(z * z + T(1)));
     c = T(1) / sqrt(T(1) + t * t);
+    s = t * c;
+    pr = -s * er;
+    pi = -s * ei;
+    qr = c * er;
+    qi = c * ei;
+}
+
+// FP64 form for the eigenvalue stage (pivots far above underflow there): rsqrt and a
+// correctly rounded reciprocal instead of divides; c^2 + s^2 = 1 and |e| = 1 to a
+// few ulp, so J stays unitary to FP64 rounding.  A pivot below 1e-140 is left to
+// the exact zeroing that follows every rotation (its effect on the eigenvalues is
+// below |b|^2 / gap).
+__device__ __forceinline__ void rot_params64(double app, double aqq, double br, double bi, double &c, double &s,
+                                             double &pr, double &pi, double &qr, double &qi) {
+    const double b2 = fma(br, br, bi * bi);
+    if (!(b2 > 1e-280)) return;
+    const double inv = rsqrt(b2);
+    const double er = br * inv, ei = -bi * inv;
+    const double z = (aqq - app) * (0.5 * inv);
+    const double az = fabs(z);
+    double t;
+    if (az > 1e18) {
+        t = __drcp_rn(2.0 * z);
+    } else {
+        const double z2 = fma(z, z, 1.0);
+        const double rt = z2 * rsqrt(z2);
+        t = copysign(__drcp_rn(az + rt), z);
+    }
+    c = rsqrt(fma(t, t, 1.0));
     s = t * c;
     pr = -s * er;
     pi = -s * ei;
@@ -247,9 +371,14 @@ __device__ __forceinline__ void jacobi_rows(V2<T> (&a)[N], V2<T> (&v)[N], int r,
             const T ofx_o = __shfl_sync(FULL, of.x, src), ofy_o = __shfl_sync(FULL, of.y, src);
             const bool is_p = r < pt;
             T c = T(1), s = T(0), pr = T(0), pi = T(0), qr = T(1), qi = T(0);
-            if (paired)
-                rot_params<T>(is_p ? dg : dg_o, is_p ? dg_o : dg, is_p ? of.x : ofx_o, is_p ? of.y : ofy_o, c, s,
-                              pr, pi, qr, qi);
+            if (paired) {
+                if constexpr (sizeof(T) == 8)
+                    rot_params64(is_p ? dg : dg_o, is_p ? dg_o : dg, is_p ? of.x : ofx_o, is_p ? of.y : ofy_o, c, s,
+                                 pr, pi, qr, qi);
+                else
+                    rot_params<T>(is_p ? dg : dg_o, is_p ? dg_o : dg, is_p ? of.x : ofx_o, is_p ? of.y : ofy_o, c,
+                                  s, pr, pi, qr, qi);
+            }
             // A <- A J (and V <- V J): every lane rotates the column pairs of its row
 #pragma unroll
             for (int k = 0; k < S::NP; ++k) {
@@ -264,28 +393,24 @@ __device__ __forceinline__ void jacobi_rows(V2<T> (&a)[N], V2<T> (&v)[N], int r,
                 rot_cols(a[p], a[q], kc, ks, kpr, kpi, kqr, kqi);
                 if (VEC) rot_cols(v[p], v[q], kc, ks, kpr, kpi, kqr, kqi);
             }
-            // A <- J^dagger A: row p' = c row p + conj(vp) row q, row q' = s row p + conj(vq) row q
-            T2 al, be;   // new row = al * own + be * partner
-            al.x = T(1), al.y = T(0), be.x = T(0), be.y = T(0);
+            // A <- J^dagger A: row p' = c row p + conj(vp) row q, row q' = s row p + conj(vq) row q,
+            // i.e. new row = ar X + conj(b) Y with (ar, b, X, Y) = (c, vp, own, partner) in lane p
+            // and (s, vq, partner, own) in lane q: one real and one complex coefficient
+            T ar = T(1), bx = T(0), by = T(0);
             if (paired) {
-                if (is_p) {
-                    al.x = c;
-                    be.x = pr;
-                    be.y = -pi;
-                } else {
-                    al.x = qr;
-                    al.y = -qi;
-                    be.x = s;
-                }
+                ar = is_p ? c : s;
+                bx = is_p ? pr : qr;
+                by = is_p ? pi : qi;
             }
+            const bool swap = paired && !is_p;
 #pragma unroll
             for (int e = 0; e < N; ++e) {
                 T2 o;
                 o.x = __shfl_sync(FULL, a[e].x, src);
                 o.y = __shfl_sync(FULL, a[e].y, src);
-                const T2 x = a[e];
-                a[e].x = (al.x * x.x - al.y * x.y) + (be.x * o.x - be.y * o.y);
-                a[e].y = (al.x * x.y + al.y * x.x) + (be.x * o.y + be.y * o.x);
+                const T2 X = swap ? o : a[e], Y = swap ? a[e] : o;
+                a[e].x = fma(ar, X.x, fma(bx, Y.x, by * Y.y));
+                a[e].y = fma(ar, X.y, fma(bx, Y.y, -(by * Y.x)));
             }
             // the rotated pivots are zero and the diagonal real, exactly
 #pragma unroll
@@ -320,8 +445,13 @@ __device__ __forceinline__ double2 packed_entry(const double *__restrict__ H, in
 }
 
 // Eigenpairs of count packed Hermitian N x N matrices: eigenvalues ascending
-// (FP64-refined), eigenvector columns (FP32) in U[i][n] order.
-template <int N>
+// (FP64-refined), eigenvector columns in U[i][n] order: the FP32 V, or with VREF
+// refined in FP64 as well, U = V (I - E/2) J with J the FP64 rotations (the
+// orthonormalised basis times the eigenvectors of A'').  VREF serves the phonon
+// modes: near q = 0 the acoustic omega^2 are ~1e-6 of |D| apart, below what the
+// FP32 vectors resolve, and the mode coefficients sqrt(hbar / 2 M omega) differ
+// between those branches.
+template <int N, bool VREF>
 __global__ void __launch_bounds__(64) k_heev_mixed(int64_t count, const double *__restrict__ Hp,
                                                    double *__restrict__ eval, float2 *__restrict__ U32,
                                                    double2 *__restrict__ U64) {
@@ -374,7 +504,7 @@ __global__ void __launch_bounds__(64) k_heev_mixed(int64_t count, const double *
     }
     __syncwarp();
     // 3. A' = V^dagger W and E = V^dagger V - I (row r), then A'' (first-order congruence)
-    double2 a64[N];
+    double2 a64[N], v64[N];
     {
         double2 ap[N], ee[N];
 #pragma unroll
@@ -406,10 +536,33 @@ __global__ void __launch_bounds__(64) k_heev_mixed(int64_t count, const double *
             const double f = 0.5 * (lam + lj);
             a64[j] = live ? make_double2(ap[j].x - f * ee[j].x, ap[j].y - f * ee[j].y) : make_double2(0.0, 0.0);
         }
+        if (VREF) {   // row r of V (I - E/2), E from every lane's row
+            __syncwarp();
+            if (row) {
+#pragma unroll
+                for (int j = 0; j < N; ++j) Ws[ms][r][j] = ee[j];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const float2 vj = Vs[ms][rc][j];
+                v64[j] = make_double2(vj.x, vj.y);
+            }
+#pragma unroll
+            for (int l = 0; l < N; ++l) {
+                const float2 vl = Vs[ms][rc][l];
+                const double2 h = make_double2(-0.5 * vl.x, -0.5 * vl.y);
+#pragma unroll
+                for (int j = 0; j < N; ++j) cfma(v64[j], h, Ws[ms][l][j]);
+            }
+            if (!live) {
+#pragma unroll
+                for (int j = 0; j < N; ++j) v64[j] = make_double2(0.0, 0.0);
+            }
+        }
     }
-    // 4. FP64 Jacobi on A'' for the eigenvalues
-    double2 unused[N];
-    jacobi_rows<double, N, false>(a64, unused, r, base, 1e-30, 20);
+    // 4. FP64 Jacobi on A'' for the eigenvalues (and with VREF the vectors)
+    jacobi_rows<double, N, VREF>(a64, v64, r, base, 1e-22, 20);
     const double lam = pick(a64, r).x;
     int rank = 0;
 #pragma unroll
@@ -417,8 +570,17 @@ __global__ void __launch_bounds__(64) k_heev_mixed(int64_t count, const double *
         const double lj = __shfl_sync(FULL, lam, base + j);
         rank += (lj < lam || (lj == lam && j < r)) ? 1 : 0;
     }
-    if (live) {
-        eval[pt * N + rank] = lam;
+    if (live) eval[pt * N + rank] = lam;
+    if (VREF) {   // lane r holds row r of U: column j goes to position rank_j
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const int rj = __shfl_sync(FULL, rank, base + j);
+            if (live) {
+                if (U32) U32[pt * NC + r * N + rj] = make_float2((float)v64[j].x, (float)v64[j].y);
+                if (U64) U64[pt * NC + r * N + rj] = v64[j];
+            }
+        }
+    } else if (live) {
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             const float2 u = Vs[ms][i][r];
@@ -430,11 +592,12 @@ __global__ void __launch_bounds__(64) k_heev_mixed(int64_t count, const double *
 
 }  // namespace
 
-// Cos/sin coefficient table of H(k) (see the top of this file), built on the host
-// when the model is set: representatives R = 0 and every R that is
-// lexicographically positive; T[2r][c] = C_R, T[2r+1][c] = S_R in the packed
-// column order.
-pgb_status build_band_table(pgb_ctx *c, const int32_t *R, const double *H, int nR, int nw) {
+// Cos/sin coefficient table of X(k) = sum_R e^{ik.R} X(R) (see the top of this
+// file; X = H or the mass-scaled D), built on the host when the model is set:
+// representatives R = 0 and every R that is lexicographically positive;
+// T[2r][c] = C_R, T[2r+1][c] = S_R in the packed column order.  X is complex
+// [nR][n][n], interleaved (re, im).
+pgb_status build_herm_table(pgb_ctx *c, HermTab *tab, const int32_t *R, const double *H, int nR, int nw) {
     using Key = std::tuple<int, int, int>;
     std::map<Key, int> idx;
     for (int r = 0; r < nR; ++r) idx[Key(R[3 * r], R[3 * r + 1], R[3 * r + 2])] = r;
@@ -466,7 +629,7 @@ pgb_status build_band_table(pgb_ctx *c, const int32_t *R, const double *H, int n
         if (!zero) {
             auto it = idx.find(Key(-x, -y, -z));
             if (it == idx.end()) {
-                c->err = "set_model: R_H is not closed under inversion";
+                c->err = "set_model: an R list is not closed under inversion";
                 return PGB_EINVAL;
             }
             rn = it->second;
@@ -506,27 +669,51 @@ pgb_status build_band_table(pgb_ctx *c, const int32_t *R, const double *H, int n
         T.insert(T.end(), Cr.begin(), Cr.end());
         T.insert(T.end(), Sr.begin(), Sr.end());
     }
-    c->nHrep = (int)(reps.size() / 3);
-    c->HrepM = M;
-    pgb_status st = dalloc(c, &c->d_Hrep, reps.size());
-    if (st == PGB_OK) st = dalloc(c, &c->d_Hcs, T.size());
-    if (st != PGB_OK) return st;
-    PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_Hrep, reps.data(), 4 * reps.size(), cudaMemcpyHostToDevice, c->stream));
-    PGB_CUDA_TRY(c, cudaMemcpyAsync(c->d_Hcs, T.data(), 8 * T.size(), cudaMemcpyHostToDevice, c->stream));
+    free_herm_table(tab);
+    std::vector<float> T2(2 * T.size());
+    for (size_t x = 0; x < T.size(); ++x) {
+        const float h = (float)T[x];
+        T2[2 * x] = h;
+        T2[2 * x + 1] = (float)(T[x] - (double)h);
+    }
+    pgb_status st = dalloc(c, &tab->d_R, reps.size());
+    if (st == PGB_OK) st = dalloc(c, &tab->d_T, T.size());
+    if (st == PGB_OK) st = dalloc(c, &tab->d_T2, T.size());
+    if (st != PGB_OK) {
+        free_herm_table(tab);
+        return st;
+    }
+    tab->n = nw;
+    tab->nrep = (int)(reps.size() / 3);
+    tab->M = M;
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(tab->d_R, reps.data(), 4 * reps.size(), cudaMemcpyHostToDevice, c->stream));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(tab->d_T, T.data(), 8 * T.size(), cudaMemcpyHostToDevice, c->stream));
+    PGB_CUDA_TRY(c, cudaMemcpyAsync(tab->d_T2, T2.data(), 4 * T2.size(), cudaMemcpyHostToDevice, c->stream));
     PGB_CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // the host vectors go out of scope
     return PGB_OK;
 }
 
-// Packed Hermitian H(k) [np][nw^2] at np points (crystal coordinates).
-pgb_status launch_herm_sum(pgb_ctx *c, const double *d_pts, int64_t np, double *d_out) {
+void free_herm_table(HermTab *t) {
+    dfree(&t->d_R);
+    dfree(&t->d_T);
+    dfree(&t->d_T2);
+    t->n = t->nrep = t->M = 0;
+}
+
+// Packed Hermitian X(k) [np][n^2] at np points (crystal coordinates).
+pgb_status launch_herm_sum(pgb_ctx *c, const HermTab &t, const double *d_pts, int64_t np, double *d_out) {
     if (np == 0) return PGB_OK;
-    const int ncol = c->nw * c->nw;
-    const int M = c->HrepM;
-    const size_t smem = M <= kHermMaxM ? (size_t)3 * (2 * M + 1) * HS_P * sizeof(double2) : 0;
+    if (!t.d_T) {
+        c->err = "herm_sum: no cos/sin table";
+        return PGB_ESTATE;
+    }
+    const int ncol = t.n * t.n;
+    const int M = t.M;
+    const size_t smem = M <= kHermMaxM ? (size_t)3 * (2 * M + 1) * HS_P * sizeof(float4) : 0;
     const dim3 grid(div_up(np, HS_P), div_up(ncol, HS_C));
     if (smem > 48 * 1024)
         PGB_CUDA_TRY(c, cudaFuncSetAttribute(k_herm_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_herm_sum<<<grid, 256, smem, c->stream>>>(np, d_pts, c->nHrep, c->d_Hrep, M, ncol, c->d_Hcs, d_out);
+    k_herm_sum<<<grid, 256, smem, c->stream>>>(np, d_pts, t.nrep, t.d_R, M, ncol, t.d_T2, d_out);
     PGB_LAUNCH_CHECK(c);
     return PGB_OK;
 }
@@ -534,13 +721,15 @@ pgb_status launch_herm_sum(pgb_ctx *c, const double *d_pts, int64_t np, double *
 // Eigenpairs of count packed Hermitian n x n matrices (2 <= n <= 16): eigenvalues
 // ascending in FP64, eigenvectors in FP32 (U32) and/or widened to FP64 (U64).
 pgb_status launch_heev_mixed(pgb_ctx *c, int64_t count, int n, const double *d_Hp, double *d_eval, float2 *d_U32,
-                             double2 *d_U64) {
+                             double2 *d_U64, bool refine_vectors) {
     if (count == 0) return PGB_OK;
 #define PGB_HEEVM_CASE(NN)                                                                                    \
     case NN: {                                                                                                \
         constexpr int mpb = 64 / JShape<NN>::L;                                                               \
-        k_heev_mixed<NN><<<div_up(count, mpb), 64, 0, c->stream>>>(count, d_Hp, d_eval, d_U32,  \
-                                                                                 d_U64);                      \
+        if (refine_vectors)                                                                                   \
+            k_heev_mixed<NN, true><<<div_up(count, mpb), 64, 0, c->stream>>>(count, d_Hp, d_eval, d_U32, d_U64); \
+        else                                                                                                  \
+            k_heev_mixed<NN, false><<<div_up(count, mpb), 64, 0, c->stream>>>(count, d_Hp, d_eval, d_U32, d_U64); \
         break;                                                                                                \
     }
     switch (n) {

@@ -33,6 +33,19 @@ constexpr int kMaxNw = 16;
 constexpr int kMaxNmode = 15;
 }  // namespace pgb
 
+namespace pgb {
+// Real cos/sin form of a Hermitian Fourier sum X(k) = sum_R e^{ik.R} X(R) over
+// one representative R of each {R, -R}: rows 2r (cos) and 2r+1 (sin) of T hold
+// the packed upper triangle (n real diagonal entries, then (re, im) of (i, j),
+// i < j, row by row) of C_R and S_R.
+struct HermTab {
+    int n = 0, nrep = 0, M = 0;   // matrix size, representatives, max |R_d|
+    int32_t *d_R = nullptr;       // [nrep][3]
+    double *d_T = nullptr;        // [2 nrep][n*n]
+    float2 *d_T2 = nullptr;       // the same split into (hi, lo) floats
+};
+}  // namespace pgb
+
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
@@ -49,11 +62,10 @@ struct pgb_ctx {
     std::vector<double> mass;
     int32_t *d_RH = nullptr, *d_RD = nullptr, *d_Rge = nullptr, *d_Rgp = nullptr;
     double2 *d_H = nullptr;      // [nRH][nw*nw]
-    int nHrep = 0, HrepM = 0;    // cos/sin form of H(k): representatives of {R, -R} and max |R_d|
-    int32_t *d_Hrep = nullptr;   // [nHrep][3]
-    double *d_Hcs = nullptr;     // [2 nHrep][nw*nw] C_R, S_R rows, packed upper-triangle columns
+    pgb::HermTab htH;            // cos/sin form of H(k) (bands_mixed.cu)
     double2 *d_D = nullptr;      // [nRD][nm*nm] (imaginary part 0)
     double *d_mode_scale = nullptr;  // [nm] 1/sqrt(M_kappa) per ka
+    pgb::HermTab htD;            // cos/sin form of the mass-scaled D(q)
     double2 *d_g64 = nullptr;    // [nRge][nRgp*nm*nw*nw]
     float2 *d_g32 = nullptr;
     int nKp = 0;                 // rows of the R_p sum: nRgp, plus nm long-range rows for polar models
@@ -210,9 +222,10 @@ std::vector<int32_t> ewald_candidates(const double lat[9], const double eps[9], 
 // Monte-Carlo q rates and tetrahedron populations (mcq.cu); device pointers
 pgb_status launch_mc_qpoints(pgb_ctx *c, int64_t nq, const double *u, int sampling, double width, double *q,
                              double *pinv);
-pgb_status launch_mc_epilogue(pgb_ctx *c, bool fp32, int64_t nkb, int64_t nq, const void *C, const void *Ukq,
-                              const double *eps_k, const double *eps_kq, const double *hw, const void *coef,
-                              const double *pinv, double T, double mu, double sigma, double *partial, double *acc);
+pgb_status launch_mc_epilogue(pgb_ctx *c, bool fp32, int64_t nkb, int64_t nq, const void *C, int64_t ldc,
+                              const void *Ukq, const double *eps_k, const double *eps_kq, const double *hw,
+                              const void *coef, const double *pinv, double T, double mu, double sigma, double *partial,
+                              double *acc);
 int64_t mc_partial_count(const pgb_ctx *c, int64_t nkb, int64_t nq);
 pgb_status launch_mc_finish(pgb_ctx *c, int64_t nk, int64_t nq, double sigma, const double *acc, double *gamma,
                             double *err);
@@ -229,10 +242,11 @@ pgb_status launch_cgemm(pgb_ctx *c, bool fp32, int64_t batch, int64_t M, int64_t
 pgb_status launch_heevj(pgb_ctx *c, int64_t count, int n, double2 *d_mat, const double *d_scale,
                         double *d_eval, double2 *d_evec);
 // band interpolation for the FP32 paths (bands_mixed.cu)
-pgb_status build_band_table(pgb_ctx *c, const int32_t *R, const double *H, int nR, int nw);
-pgb_status launch_herm_sum(pgb_ctx *c, const double *d_pts, int64_t np, double *d_out);
+pgb_status build_herm_table(pgb_ctx *c, HermTab *t, const int32_t *R, const double *X, int nR, int n);
+void free_herm_table(HermTab *t);
+pgb_status launch_herm_sum(pgb_ctx *c, const HermTab &t, const double *d_pts, int64_t np, double *d_out);
 pgb_status launch_heev_mixed(pgb_ctx *c, int64_t count, int n, const double *d_Hp, double *d_eval, float2 *d_U32,
-                             double2 *d_U64);
+                             double2 *d_U64, bool refine_vectors);
 pgb_status launch_phonon_coef(pgb_ctx *c, int64_t nq, int nm, const double *d_eval,
                               const double2 *d_evec, const double *d_mode_scale, double *d_hw,
                               double2 *d_coef);

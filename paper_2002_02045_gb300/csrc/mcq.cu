@@ -47,7 +47,8 @@ __global__ void k_mc_qpoints(int64_t nq, const double *__restrict__ u, int sampl
 struct McArgs {
     int64_t nkb, nq;            // k-points of this batch, q samples of this chunk
     int nw, nm;
-    const void *C;              // [nkb][nq][nm*nw*nw]
+    const void *C;              // [nkb][nq][ldc], columns (n, ka, i) first
+    int64_t ldc;
     const void *Ukq;            // [nkb*nq][nw][nw]
     const double *eps_k;        // [nkb][nw]
     const double *eps_kq;       // [nkb*nq][nw]
@@ -67,7 +68,6 @@ __global__ void __launch_bounds__(256) k_mc_epilogue(McArgs a) {
     const int ql = threadIdx.x / nw;
     const int n = threadIdx.x % nw;
     const int64_t b = blockIdx.y;
-    const int ncol = nm * nw * nw;
     const int64_t q = (int64_t)blockIdx.x * a.qpb + ql;
     double y = 0.0;
     if (ql < a.qpb && q < a.nq) {
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) k_mc_epilogue(McArgs a) {
         const double en = a.eps_k[b * nw + n];
         const double is = 1.0 / a.sigma, ycut2 = kDeltaCut * kDeltaCut;
         const double kT = kBoltzEvK * a.T;
-        const T2 *Cn = (const T2 *)a.C + pr * ncol + (int64_t)n * nm * nw;
+        const T2 *Cn = (const T2 *)a.C + pr * a.ldc + (int64_t)n * nm * nw;
         const T2 *U = (const T2 *)a.Ukq + pr * nw * nw;
         const double *em = a.eps_kq + pr * nw;
         double acc = 0.0;
@@ -260,9 +260,10 @@ pgb_status launch_mc_qpoints(pgb_ctx *c, int64_t nq, const double *u, int sampli
     return PGB_OK;
 }
 
-pgb_status launch_mc_epilogue(pgb_ctx *c, bool fp32, int64_t nkb, int64_t nq, const void *C, const void *Ukq,
-                              const double *eps_k, const double *eps_kq, const double *hw, const void *coef,
-                              const double *pinv, double T, double mu, double sigma, double *partial, double *acc) {
+pgb_status launch_mc_epilogue(pgb_ctx *c, bool fp32, int64_t nkb, int64_t nq, const void *C, int64_t ldc,
+                              const void *Ukq, const double *eps_k, const double *eps_kq, const double *hw,
+                              const void *coef, const double *pinv, double T, double mu, double sigma, double *partial,
+                              double *acc) {
     if (nkb == 0 || nq == 0) return PGB_OK;
     McArgs a;
     a.nkb = nkb;
@@ -270,6 +271,7 @@ pgb_status launch_mc_epilogue(pgb_ctx *c, bool fp32, int64_t nkb, int64_t nq, co
     a.nw = c->nw;
     a.nm = c->nm;
     a.C = C;
+    a.ldc = ldc;
     a.Ukq = Ukq;
     a.eps_k = eps_k;
     a.eps_kq = eps_kq;

@@ -24,7 +24,7 @@ PRECISIONS = {"fp64": PGB_FP64, "fp32": PGB_FP32, "tf32x3": PGB_TC_TF32X3, "bf16
 
 DIAG_SYMBOLS = ("pgb_diag_bands", "pgb_selftest_heevj", "pgb_selftest_heevj_device", "pgb_selftest_wait_timeout",
                 "pgb_diag_alloc_count", "pgb_diag_fail_alloc", "pgb_diag_delta_weights",
-                "pgb_diag_fp64_rate", "pgb_diag_bands_mixed")
+                "pgb_diag_fp64_rate", "pgb_diag_bands_mixed", "pgb_diag_phonons_mixed")
 ABI_SYMBOLS = (
     "pgb_create", "pgb_destroy", "pgb_last_error", "pgb_status_string", "pgb_set_model",
     "pgb_set_grids", "pgb_get_grid_energies", "pgb_window", "pgb_interpolate_g",
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
         "pgb_profile_read": (I, [P, I, C.POINTER(D), C.POINTER(I64)]),
         "pgb_diag_bands": (I, [P, P, I64, P, P, P]),
         "pgb_diag_bands_mixed": (I, [P, P, I64, P, P, P]),
+        "pgb_diag_phonons_mixed": (I, [P, P, I64, P, P, P]),
         "pgb_selftest_heevj": (I, [I, I, P, P, P]),
         "pgb_selftest_heevj_device": (I, [P, I, I, P, P, P]),
         "pgb_selftest_wait_timeout": (I, [P, C.c_longlong]),
@@ -347,6 +348,9 @@ class Context:
 
     def pgb_diag_bands_mixed(self, pts, Hp=None, eps=None, U=None):
         self._chk(self.lib.pgb_diag_bands_mixed(self._h, _ptr(pts), len(pts), _ptr(Hp), _ptr(eps), _ptr(U)))
+
+    def pgb_diag_phonons_mixed(self, pts, Dp=None, w2=None, e=None):
+        self._chk(self.lib.pgb_diag_phonons_mixed(self._h, _ptr(pts), len(pts), _ptr(Dp), _ptr(w2), _ptr(e)))
 
     def pgb_diag_delta_weights(self, en, em, hw, eps_ref, sigma, out):
         for a in (en, em, hw):

@@ -44,7 +44,7 @@ def test_mc_uniform_on_grid_points_equals_grid_rates(ctx):
 
 
 @pytest.mark.parametrize("sampling,width", [(0, 1.0), (1, 0.2)])
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5), ("tf32x3", 1e-5), ("bf16x3", 1e-3)])
 def test_mc_random_matches_oracle(ctx, sampling, width, prec, tol):
     from paper_2002_02045_gb300 import PRECISIONS
     m = S.model_c1()
@@ -61,8 +61,9 @@ def test_mc_random_matches_oracle(ctx, sampling, width, prec, tol):
     assert np.abs(err - ref_err).max() <= 1e3 * tol * ref_err.max() + 1e-300
 
 
-def test_mc_polar_c3_fp32(ctx):
-    from paper_2002_02045_gb300 import PGB_FP32, PGB_Q_CAUCHY
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("tf32x3", 1e-5), ("bf16x3", 1e-3)])
+def test_mc_polar_c3(ctx, prec, tol):
+    from paper_2002_02045_gb300 import PRECISIONS, PGB_Q_CAUCHY
     m = S.model_c3(rcut=13.0)
     ctx.pgb_set_model(m)
     ctx.pgb_set_lattice(m.A, m.tau)
@@ -74,18 +75,18 @@ def test_mc_polar_c3_fp32(ctx):
     mu = eps_k.min() - 0.3
     u = rng.uniform(size=(700, 3))
     got = np.zeros((2, 8))
-    ctx.pgb_scattering_rates_mc(k, u, PGB_Q_CAUCHY, 0.1, T, mu, sig, PGB_FP32, got)
+    ctx.pgb_scattering_rates_mc(k, u, PGB_Q_CAUCHY, 0.1, T, mu, sig, PRECISIONS[prec], got)
     ref, _ = O.scattering_rates_mc(m, k, u, O.Q_CAUCHY, 0.1, T, mu, sig)
-    assert_rates_close(got, ref, 1e-5, label="mc polar")
+    assert_rates_close(got, ref, tol, label=f"mc polar {prec}")
 
 
 def test_mc_argument_errors(ctx):
-    from paper_2002_02045_gb300 import PgbError, PGB_FP64, PGB_TC_BF16X3
+    from paper_2002_02045_gb300 import PgbError, PGB_FP64
     ctx.pgb_set_model(S.model_c1())
     k = np.zeros((1, 3))
     out = np.zeros((1, 2))
     for u, samp, w, prec in ((np.full((4, 3), 1.0), 0, 1.0, PGB_FP64), (np.full((4, 3), 0.2), 1, 0.0, PGB_FP64),
-                             (np.full((4, 3), 0.2), 0, 1.0, PGB_TC_BF16X3), (np.full((4, 3), 0.2), 7, 1.0, PGB_FP64)):
+                             (np.full((4, 3), 0.2), 0, 1.0, 99), (np.full((4, 3), 0.2), 7, 1.0, PGB_FP64)):
         with pytest.raises(PgbError):
             ctx.pgb_scattering_rates_mc(k, u, samp, w, 300.0, 0.5, 0.02, prec, out)
 
