@@ -1438,13 +1438,19 @@ pgb_status pgb_scattering_rates_mc(pgb_ctx *c, const double *kpts, int64_t nk, c
     TRY(acc.alloc(c, (size_t)nk * 2 * nw));
     PGB_CUDA_TRY(c, cudaMemsetAsync(acc.p, 0, 16 * (size_t)nk * nw, c->stream));
     TRY(launch_mc_qpoints(c, nq, Uin.dev, sampling, width, q.p, pinv.p));
-    TRY(bands_at(c, K.dev, nk, eps_k.p, U_k.p));
     Tmp<float2> U_k32;
     const void *Uk = U_k.p;
     if (f32) {
         TRY(U_k32.alloc(c, (size_t)nk * nw2));
-        TRY(launch_to_f32(c, U_k.p, U_k32.p, nk * nw2));
+        if (nw >= 2) {
+            TRY(bands_at_mixed(c, K.dev, nk, eps_k.p, U_k32.p, nullptr));
+        } else {
+            TRY(bands_at(c, K.dev, nk, eps_k.p, U_k.p));
+            TRY(launch_to_f32(c, U_k.p, U_k32.p, nk * nw2));
+        }
         Uk = U_k32.p;
+    } else {
+        TRY(bands_at(c, K.dev, nk, eps_k.p, U_k.p));
     }
     // R_e sums with U(k) folded, for every k: G [nk][nKp][ncol]
     const int64_t kb = std::max<int64_t>(1, std::min<int64_t>(nk, 8));

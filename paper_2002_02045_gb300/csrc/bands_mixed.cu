@@ -27,10 +27,12 @@
 //      the congruence of A' by (I + E)^{-1/2} (symmetric orthonormalisation of
 //      V) to first order in E; the terms left out are O(|E|^2 |H|) and
 //      O(|E| |A'_ij, i != j|), below 1e-11 of |H| for |E| ~ 1e-7.  A'' is nearly
-//      diagonal (off-diagonals ~1e-7 |H|): one sweep, quadratically convergent,
-//      leaves couplings b ~ 1e-12 |H| or below, which move an eigenvalue by at
-//      most min(|b|, |b|^2 / gap).  The sweeps stop once the off-diagonal mass
-//      is below 1e-22 of the total.
+//      diagonal (off-diagonals ~1e-7 |H|): where every coupling is below 1e-4 of
+//      its gap, second-order perturbation theory gives the eigenvalues (see the
+//      kernel); otherwise one sweep, quadratically convergent, leaves couplings
+//      b ~ 1e-12 |H| or below, which move an eigenvalue by at most
+//      min(|b|, |b|^2 / gap).  The sweeps stop once the off-diagonal mass is
+//      below 1e-22 of the total.
 // The eigenvalues are those of H to FP64 rounding; the eigenvectors returned are
 // the FP32 V (orthonormal to ~1e-7), which is what the FP32 |g|^2 products use.
 // Within a cluster of eigenvalues closer than ~1e-7 |H| the FP32 vectors are an
@@ -561,9 +563,35 @@ __global__ void __launch_bounds__(64) k_heev_mixed(int64_t count, const double *
             }
         }
     }
-    // 4. FP64 Jacobi on A'' for the eigenvalues (and with VREF the vectors)
-    jacobi_rows<double, N, VREF>(a64, v64, r, base, 1e-22, 20);
-    const double lam = pick(a64, r).x;
+    // 4. Eigenvalues of A''.  Without VREF, when every coupling is small against its
+    // gap (|a_ij| <= 1e-4 |a_ii - a_jj| and <= 1e-5 max|a_jj| for all pairs of the
+    // warp's matrices), second-order perturbation theory:
+    //   lambda_i = a_ii + sum_{j != i} |a_ij|^2 / (a_ii - a_jj),
+    // whose third-order remainder is at most (N-1)^2 1e-8 max|a_ij| < 5e-12 of
+    // max|a_jj|.  Otherwise (near-degenerate pairs) FP64 Jacobi sweeps on A''.
+    bool fast = false;
+    double lam_pt = 0.0;
+    if constexpr (!VREF) {
+        const double dr = pick(a64, r).x;
+        double sc = fabs(dr);
+#pragma unroll
+        for (int o = 1; o < S::L; o <<= 1) sc = fmax(sc, __shfl_xor_sync(FULL, sc, o));
+        bool ok = true;
+        double corr = 0.0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const double dj = __shfl_sync(FULL, dr, base + j);
+            if (j == r) continue;
+            const double gap = dr - dj;
+            const double a2 = fma(a64[j].x, a64[j].x, a64[j].y * a64[j].y);
+            ok = ok && a2 <= 1e-8 * gap * gap && a2 <= 1e-10 * sc * sc;
+            if (a2 > 0.0) corr = fma(a2, __drcp_rn(gap), corr);
+        }
+        fast = __all_sync(FULL, ok || !live);
+        lam_pt = dr + corr;
+    }
+    if (!fast) jacobi_rows<double, N, VREF>(a64, v64, r, base, 1e-22, 20);
+    const double lam = fast ? lam_pt : pick(a64, r).x;
     int rank = 0;
 #pragma unroll
     for (int j = 0; j < N; ++j) {

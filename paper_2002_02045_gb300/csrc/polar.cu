@@ -43,9 +43,19 @@ struct EwaldArgs {
     int fp32;
 };
 
-__global__ void k_ewald(EwaldArgs p) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= p.npts) return;
+// One warp per point.  The candidates G are screened 32 at a time in FP32 (the
+// exponent with a relative margin of 1e-4, far above the FP32 error of ~1e-6), the
+// survivors (~60 of the 1331 candidates of config 3) are compacted into a per-warp
+// list by ballot, and the list is evaluated 32 terms at a time in FP64 (every
+// lane busy), so the FP64 work is that of the surviving terms only.  Each lane
+// sums its terms; the lanes' sums are then added by a butterfly.
+constexpr int kEwWarps = 8;
+__global__ void __launch_bounds__(32 * kEwWarps) k_ewald(EwaldArgs p) {
+    __shared__ int list_s[kEwWarps][64];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int *list = list_s[wid];
+    const int64_t t = (int64_t)blockIdx.x * kEwWarps + wid;
+    if (t >= p.npts) return;   // warp-uniform
     double q[3];
     if (p.pts) {
         q[0] = p.pts[3 * t];
@@ -59,35 +69,89 @@ __global__ void k_ewald(EwaldArgs p) {
         q[1] = (double)i2 / p.grid[1];
         q[2] = (double)i3 / p.grid[2];
     }
+    const int nm = 3 * p.nat;
     double ar[kMaxNmode], ai[kMaxNmode];
-    for (int j = 0; j < 3 * p.nat; ++j) {
+#pragma unroll
+    for (int j = 0; j < kMaxNmode; ++j) {
         ar[j] = 0.0;
         ai[j] = 0.0;
     }
-    for (int g = 0; g < p.nG; ++g) {
+    float Bf[9], Ef[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        Bf[i] = (float)p.B[i];
+        Ef[i] = (float)p.eps[i];
+    }
+    const float cutf = (float)(p.cut4lam * (1.0 + 1e-4));
+    // one surviving term, exactly as the FP64 definition
+    auto term = [&](int g) {
         const double m0 = q[0] + p.gvec[3 * g], m1 = q[1] + p.gvec[3 * g + 1], m2 = q[2] + p.gvec[3 * g + 2];
         double v[3];
         for (int a = 0; a < 3; ++a) v[a] = m0 * p.B[a] + m1 * p.B[3 + a] + m2 * p.B[6 + a];
         double x = 0.0;
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) x += v[a] * p.eps[3 * a + b] * v[b];
-        if (!(x > 0.0) || x > p.cut4lam) continue;
+        if (!(x > 0.0) || x > p.cut4lam) return;
         const double w = exp(-x * p.inv4lam) / x;
-        for (int k = 0; k < p.nat; ++k) {
+#pragma unroll
+        for (int k = 0; k < kMaxNmode / 3; ++k) {
+            if (k >= p.nat) break;
             const double th = v[0] * p.tau[3 * k] + v[1] * p.tau[3 * k + 1] + v[2] * p.tau[3 * k + 2];
             double s, c;
             sincos(th, &s, &c);
             const double wr = w * c, wi = -w * s;       // w e^{-i th}
             const double *Z = p.zstar + 9 * k;
+#pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const double vz = v[0] * Z[a] + v[1] * Z[3 + a] + v[2] * Z[6 + a];
                 ar[3 * k + a] += wr * vz;
                 ai[3 * k + a] += wi * vz;
             }
         }
+    };
+    const float q0 = (float)q[0], q1 = (float)q[1], q2 = (float)q[2];
+    int cnt = 0;   // warp-uniform length of the survivor list
+    for (int g0 = 0; g0 < p.nG; g0 += 32) {
+        const int g = g0 + lane;
+        bool keep = false;
+        if (g < p.nG) {
+            const float m0 = q0 + (float)p.gvec[3 * g], m1 = q1 + (float)p.gvec[3 * g + 1],
+                        m2 = q2 + (float)p.gvec[3 * g + 2];
+            float v[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) v[a] = m0 * Bf[a] + m1 * Bf[3 + a] + m2 * Bf[6 + a];
+            float x = 0.f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) x += v[a] * Ef[3 * a + b] * v[b];
+            keep = x <= cutf;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) list[cnt + __popc(bal & ((1u << lane) - 1u))] = g;
+        cnt += __popc(bal);
+        __syncwarp();
+        if (cnt >= 32) {
+            term(list[cnt - 32 + lane]);
+            cnt -= 32;
+        }
+        __syncwarp();
     }
-    // multiply by i pref
-    for (int j = 0; j < 3 * p.nat; ++j) {
+    if (lane < cnt) term(list[lane]);
+    // warp sums, then i * pref
+#pragma unroll
+    for (int j = 0; j < kMaxNmode; ++j) {
+        if (j >= nm) break;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ar[j] += __shfl_xor_sync(0xffffffffu, ar[j], o);
+            ai[j] += __shfl_xor_sync(0xffffffffu, ai[j], o);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxNmode; ++j) {
+        if (j >= nm) break;
+        if (lane != j) continue;
         const double re = -p.pref * ai[j], im = p.pref * ar[j];
         if (p.fp32)
             reinterpret_cast<float2 *>(p.out)[t * p.ld + p.col0 + j] = make_float2((float)re, (float)im);
@@ -147,7 +211,7 @@ pgb_status launch_ewald_pts(pgb_ctx *c, const double *d_pts, int64_t npts, void 
     a.ld = ld;
     a.col0 = col0;
     a.fp32 = fp32 ? 1 : 0;
-    k_ewald<<<div_up(npts, 128), 128, 0, c->stream>>>(a);
+    k_ewald<<<div_up(npts, kEwWarps), 32 * kEwWarps, 0, c->stream>>>(a);
     PGB_LAUNCH_CHECK(c);
     return PGB_OK;
 }
@@ -162,7 +226,7 @@ pgb_status polar_grid_table(pgb_ctx *c) {
     for (int d = 0; d < 3; ++d) a.grid[d] = c->qg[d];
     a.out = c->d_polarL;
     a.ld = c->nm;
-    k_ewald<<<div_up(c->Nq, 128), 128, 0, c->stream>>>(a);
+    k_ewald<<<div_up(c->Nq, kEwWarps), 32 * kEwWarps, 0, c->stream>>>(a);
     PGB_LAUNCH_CHECK(c);
     return PGB_OK;
 }
