@@ -79,15 +79,23 @@ __global__ void __launch_bounds__(256) k_mc_epilogue(McArgs a) {
         const T2 *U = (const T2 *)a.Ukq + pr * nw * nw;
         const double *em = a.eps_kq + pr * nw;
         double acc = 0.0;
+        // FP32 copies for the screen: |x| <= 7 sigma with a margin of 1e-4 eV (FP32
+        // rounding of energies of a few eV is ~1e-6 eV); survivors take the exact FP64 test
+        float em32[kMaxNw];
+#pragma unroll
+        for (int m = 0; m < kMaxNw; ++m) em32[m] = m < nw ? (float)em[m] : 0.f;
+        const float en32 = (float)en, cut32 = (float)(kDeltaCut * a.sigma) + 1e-4f;
         for (int v = 0; v < nm; ++v) {
             const double w = a.hw[q * nm + v];
             if (!(w >= kOmegaMinEv)) continue;
+            const float w32 = (float)w;
             // screen before the projection
             uint32_t live = 0;
-            for (int m = 0; m < nw; ++m) {
-                const double d = en - em[m];
-                const double ye = (d - w) * is, ya = (d + w) * is;
-                if (ye * ye <= ycut2 || ya * ya <= ycut2) live |= 1u << m;
+#pragma unroll
+            for (int m = 0; m < kMaxNw; ++m) {
+                if (m >= nw) break;
+                const float d = en32 - em32[m];
+                if (fabsf(d - w32) <= cut32 || fabsf(d + w32) <= cut32) live |= 1u << m;
             }
             if (!live) continue;
             const T2 *cf = (const T2 *)a.coef + (q * nm + v) * nm;
