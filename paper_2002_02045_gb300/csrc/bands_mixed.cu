@@ -22,7 +22,7 @@
 // removed, then the real rotation that zeroes it).  It runs
 //   1. in FP32 with eigenvectors, to convergence at FP32 rounding (V);
 //   2. in FP64 without eigenvectors on A'' below, for the eigenvalues:
-//        A' = V^dagger H V,  E = V^dagger V - I,
+//        A' = V^dagger H V,  E = V^dagger V - I   (both in double-float),
 //        A''_ij = A'_ij - E_ij (A'_ii + A'_jj) / 2,
 //      the congruence of A' by (I + E)^{-1/2} (symmetric orthonormalisation of
 //      V) to first order in E; the terms left out are O(|E|^2 |H|) and
@@ -107,6 +107,33 @@ __device__ __forceinline__ void df_fma(float &sh, float &sl, float ah, float al,
     const float r = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
     sl = __fadd_rn(sl, __fadd_rn(r, e));
     sh = t;
+}
+
+// (sh, sl) += (xh + xl) y: the product exact to ~2^-48, TwoSum into sh
+__device__ __forceinline__ void df_acc_mulf(float &sh, float &sl, float2 x, float y) {
+    const float p = __fmul_rn(x.x, y);
+    float e = __fmaf_rn(x.x, y, -p);
+    e = __fmaf_rn(x.y, y, e);
+    const float t = __fadd_rn(sh, p);
+    const float z = __fsub_rn(t, sh);
+    const float r = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
+    sl = __fadd_rn(sl, __fadd_rn(r, e));
+    sh = t;
+}
+// (sh, sl) += x y for floats: the product exact as p + e
+__device__ __forceinline__ void df_acc_ff(float &sh, float &sl, float x, float y) {
+    const float p = __fmul_rn(x, y);
+    const float e = __fmaf_rn(x, y, -p);
+    const float t = __fadd_rn(sh, p);
+    const float z = __fsub_rn(t, sh);
+    const float r = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
+    sl = __fadd_rn(sl, __fadd_rn(r, e));
+    sh = t;
+}
+__device__ __forceinline__ void df_renorm(float &sh, float &sl) {
+    const float2 n = fast_two_sum(sh, sl);
+    sh = n.x;
+    sl = n.y;
 }
 
 // Real Fourier sum: out[p][c] = sum_k phase_k(p) T[k][c], phase_{2r} = cos(2 pi k.R_r),
@@ -485,44 +512,85 @@ __global__ void __launch_bounds__(64) k_heev_mixed(int64_t count, const double *
         for (int e = 0; e < N; ++e) Vs[ms][r][e] = v[e];
     }
     __syncwarp();
-    // 2. W = H V (row r), FP64
+    // 2. W = H V (row r) in double-float: H split into (hi, lo) floats, V exact
+    //    floats; each product exact to ~2^-48, TwoSum accumulation renormalised
+    //    every fourth term (the FP64 form of stages 2-3 was most of the FP64 work)
     {
-        double2 w[N];
+        float4 *Wd = reinterpret_cast<float4 *>(&Ws[ms][0][0]);
+        float wrh[N], wrl[N], wih[N], wil[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) w[j] = make_double2(0.0, 0.0);
+        for (int j = 0; j < N; ++j) wrh[j] = wrl[j] = wih[j] = wil[j] = 0.f;
 #pragma unroll
         for (int l = 0; l < N; ++l) {
             const double2 h = live ? packed_entry<N>(H, r, l) : make_double2(0.0, 0.0);
+            const float2 hr = df_split(h.x), hi = df_split(h.y);
 #pragma unroll
             for (int j = 0; j < N; ++j) {
                 const float2 vl = Vs[ms][l][j];
-                cfma(w[j], h, make_double2(vl.x, vl.y));
+                df_acc_mulf(wrh[j], wrl[j], hr, vl.x);   // re = hr vx - hi vy
+                df_acc_mulf(wrh[j], wrl[j], hi, -vl.y);
+                df_acc_mulf(wih[j], wil[j], hr, vl.y);   // im = hr vy + hi vx
+                df_acc_mulf(wih[j], wil[j], hi, vl.x);
+            }
+            if ((l & 3) == 3) {
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    df_renorm(wrh[j], wrl[j]);
+                    df_renorm(wih[j], wil[j]);
+                }
             }
         }
         if (row) {
 #pragma unroll
-            for (int j = 0; j < N; ++j) Ws[ms][r][j] = w[j];
+            for (int j = 0; j < N; ++j) {
+                df_renorm(wrh[j], wrl[j]);
+                df_renorm(wih[j], wil[j]);
+                Wd[r * N + j] = make_float4(wrh[j], wrl[j], wih[j], wil[j]);
+            }
         }
     }
     __syncwarp();
-    // 3. A' = V^dagger W and E = V^dagger V - I (row r), then A'' (first-order congruence)
+    // 3. A' = V^dagger W and E = V^dagger V - I (row r) in double-float, then A''
+    //    (first-order congruence) in FP64
     double2 a64[N], v64[N];
     {
         double2 ap[N], ee[N];
+        {
+            const float4 *Wd = reinterpret_cast<const float4 *>(&Ws[ms][0][0]);
+            float arh[N], arl[N], aih[N], ail[N], erh[N], erl[N], eih[N], eil[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            ap[j] = make_double2(0.0, 0.0);
-            ee[j] = make_double2(0.0, 0.0);
-        }
+            for (int j = 0; j < N; ++j) arh[j] = arl[j] = aih[j] = ail[j] = erh[j] = erl[j] = eih[j] = eil[j] = 0.f;
 #pragma unroll
-        for (int s = 0; s < N; ++s) {
-            const float2 vs = Vs[ms][s][rc];
-            const double2 vd = make_double2(vs.x, vs.y);
+            for (int s = 0; s < N; ++s) {
+                const float2 v = Vs[ms][s][rc];
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    const float4 w = Wd[s * N + j];
+                    const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
+                    df_acc_mulf(arh[j], arl[j], wr, v.x);    // conj(v) w: re = vx wr + vy wi
+                    df_acc_mulf(arh[j], arl[j], wi, v.y);
+                    df_acc_mulf(aih[j], ail[j], wi, v.x);    //            im = vx wi - vy wr
+                    df_acc_mulf(aih[j], ail[j], wr, -v.y);
+                    const float2 vj = Vs[ms][s][j];
+                    df_acc_ff(erh[j], erl[j], v.x, vj.x);    // conj(v) vj, products exact
+                    df_acc_ff(erh[j], erl[j], v.y, vj.y);
+                    df_acc_ff(eih[j], eil[j], v.x, vj.y);
+                    df_acc_ff(eih[j], eil[j], -v.y, vj.x);
+                }
+                if ((s & 3) == 3) {
+#pragma unroll
+                    for (int j = 0; j < N; ++j) {
+                        df_renorm(arh[j], arl[j]);
+                        df_renorm(aih[j], ail[j]);
+                        df_renorm(erh[j], erl[j]);
+                        df_renorm(eih[j], eil[j]);
+                    }
+                }
+            }
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                cfma_conj(ap[j], vd, Ws[ms][s][j]);
-                const float2 vj = Vs[ms][s][j];
-                cfma_conj(ee[j], vd, make_double2(vj.x, vj.y));
+                ap[j] = make_double2((double)arh[j] + (double)arl[j], (double)aih[j] + (double)ail[j]);
+                ee[j] = make_double2((double)erh[j] + (double)erl[j], (double)eih[j] + (double)eil[j]);
             }
         }
         double lam = 0.0;
