@@ -520,8 +520,8 @@ __global__ void __launch_bounds__(64) k_heev_mixed(int64_t count, const double *
         float wrh[N], wrl[N], wih[N], wil[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) wrh[j] = wrl[j] = wih[j] = wil[j] = 0.f;
-#pragma unroll
-        for (int l = 0; l < N; ++l) {
+#pragma unroll 1
+        for (int l = 0; l < N; ++l) {   // outer loops rolled: the unrolled body overflowed the instruction cache
             const double2 h = live ? packed_entry<N>(H, r, l) : make_double2(0.0, 0.0);
             const float2 hr = df_split(h.x), hi = df_split(h.y);
 #pragma unroll
@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(64) k_heev_mixed(int64_t count, const double *
             float arh[N], arl[N], aih[N], ail[N], erh[N], erl[N], eih[N], eil[N];
 #pragma unroll
             for (int j = 0; j < N; ++j) arh[j] = arl[j] = aih[j] = ail[j] = erh[j] = erl[j] = eih[j] = eil[j] = 0.f;
-#pragma unroll
+#pragma unroll 1
             for (int s = 0; s < N; ++s) {
                 const float2 v = Vs[ms][s][rc];
 #pragma unroll

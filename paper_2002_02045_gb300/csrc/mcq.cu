@@ -63,18 +63,31 @@ struct McArgs {
 template <typename T>
 __global__ void __launch_bounds__(256) k_mc_epilogue(McArgs a) {
     using T2 = V2<T>;
-    extern __shared__ double red[];                 // [qpb][nw][2]
+    extern __shared__ double red[];                 // [qpb][nw][2], then f [qpb][nw], then N [qpb][nm]
     const int nw = a.nw, nm = a.nm;
     const int ql = threadIdx.x / nw;
     const int n = threadIdx.x % nw;
     const int64_t b = blockIdx.y;
     const int64_t q = (int64_t)blockIdx.x * a.qpb + ql;
+    const double kT = kBoltzEvK * a.T;
+    // occupations f(e_m(k+q)) and Bose factors N(omega_nu(q)) of the block's q-points,
+    // once each (every thread of a q-point uses them)
+    double *sf = red + 2 * a.qpb * nw, *sN = sf + a.qpb * nw;
+    for (int x = threadIdx.x; x < a.qpb * nw; x += blockDim.x) {
+        const int64_t qq = (int64_t)blockIdx.x * a.qpb + x / nw;
+        sf[x] = qq < a.nq ? 1.0 / (exp((a.eps_kq[(b * a.nq + qq) * nw + x % nw] - a.mu) / kT) + 1.0) : 0.0;
+    }
+    for (int x = threadIdx.x; x < a.qpb * nm; x += blockDim.x) {
+        const int64_t qq = (int64_t)blockIdx.x * a.qpb + x / nm;
+        const double w = qq < a.nq ? a.hw[qq * nm + x % nm] : 0.0;
+        sN[x] = w >= kOmegaMinEv ? 1.0 / expm1(w / kT) : 0.0;
+    }
+    __syncthreads();
     double y = 0.0;
     if (ql < a.qpb && q < a.nq) {
         const int64_t pr = b * a.nq + q;            // pair index
         const double en = a.eps_k[b * nw + n];
         const double is = 1.0 / a.sigma, ycut2 = kDeltaCut * kDeltaCut;
-        const double kT = kBoltzEvK * a.T;
         const T2 *Cn = (const T2 *)a.C + pr * a.ldc + (int64_t)n * nm * nw;
         const T2 *U = (const T2 *)a.Ukq + pr * nw * nw;
         const double *em = a.eps_kq + pr * nw;
@@ -108,7 +121,7 @@ __global__ void __launch_bounds__(256) k_mc_epilogue(McArgs a) {
                 for (int i = 0; i < kMaxNw; ++i)
                     if (i < nw) cfma(gv[i], cc, Cn[ka * nw + i]);
             }
-            const double N = 1.0 / expm1(w / kT);
+            const double N = sN[ql * nm + v];
             while (live) {
                 const int m = __ffs(live) - 1;
                 live &= live - 1;
@@ -119,7 +132,7 @@ __global__ void __launch_bounds__(256) k_mc_epilogue(McArgs a) {
                 const double g2 = (double)cabs2(g);
                 const double d = en - em[m];
                 const double ye = (d - w) * is, ya = (d + w) * is;
-                const double fm = 1.0 / (exp((em[m] - a.mu) / kT) + 1.0);
+                const double fm = sf[ql * nw + m];
                 double W = 0.0;
                 if (ye * ye <= ycut2) W += exp(-ye * ye) * (1.0 + N - fm);
                 if (ya * ya <= ycut2) W += exp(-ya * ya) * (N + fm);
@@ -293,7 +306,7 @@ pgb_status launch_mc_epilogue(pgb_ctx *c, bool fp32, int64_t nkb, int64_t nq, co
     a.partial = partial;
     const int nblk = (int)((nq + a.qpb - 1) / a.qpb);
     dim3 grid((unsigned)nblk, (unsigned)nkb);
-    const size_t sh = (size_t)a.qpb * c->nw * 2 * sizeof(double);
+    const size_t sh = (size_t)a.qpb * (3 * c->nw + c->nm) * sizeof(double);
     if (fp32)
         k_mc_epilogue<float><<<grid, a.qpb * c->nw, sh, c->stream>>>(a);
     else
