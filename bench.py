@@ -500,6 +500,78 @@ POLAR_WINDOW = 0.2
 MC_SAMPLES = 65536
 
 
+def monte_carlo(ctx, args, world, m, kw, mu, stream, e0, e1):
+    """Monte-Carlo q rates on the polar model: Cauchy samples about q = 0 for the 16 lowest
+    window k-points, TF32x3 (the FP32 tier's tensor-core form) timed with the FP32 SIMT form
+    beside it, and the oracle on a bounded sample of the same call."""
+    import torch
+    import synthetic as S
+    # Monte-Carlo q: Cauchy samples about q = 0 for the 16 lowest window k-points
+    from paper_2002_02045_gb300 import PGB_FP32, PGB_TC_TF32X3, PGB_Q_CAUCHY
+    pts = torch.as_tensor(S.mp_grid(*POLAR_GRID)).cuda()
+    kmc = pts[kw[:16].long()].contiguous()
+    u = torch.as_tensor(np.random.default_rng(S.SEED_BASE + 33).uniform(size=(MC_SAMPLES, 3))).cuda()
+    gmc = torch.empty((len(kmc), m.nw), dtype=torch.float64, device="cuda")
+    emc = torch.empty_like(gmc)
+    from paper_2002_02045_gb300.native import PROF_BANDS
+
+    def mc_run(prec):
+        ctx.pgb_scattering_rates_mc(kmc, u[:1024].contiguous(), PGB_Q_CAUCHY, 0.1, T_K, mu, SIGMA, prec, gmc, emc)
+        torch.cuda.synchronize()
+        ctx.pgb_profile(True)
+        ctx.pgb_profile_read(PROF_BANDS)
+        e0.record(stream)
+        ctx.pgb_scattering_rates_mc(kmc, u, PGB_Q_CAUCHY, 0.1, T_K, mu, SIGMA, prec, gmc, emc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = ctx.pgb_profile_read(PROF_BANDS)
+        ctx.pgb_profile(False)
+        return e0.elapsed_time(e1), prof, gmc.clone()
+
+    ms_mc32, _, g32 = mc_run(PGB_FP32)
+    ms_mc, (hk_ms, hk_n), _ = mc_run(PGB_TC_TF32X3)   # TF32x3: the FP32 tier (1e-5) on the tensor cores
+    dev_mc = float(((gmc - g32).abs() / (g32.abs() + 1e-6 * g32.abs().max())).max())
+    # the k+q points' H(k) Fourier sums: real cos/sin form over one representative of each
+    # {R, -R} (K = 2 n_rep rows) into the nw^2 packed Hermitian columns, 2 FLOP per term, in
+    # double-float on the FP32 pipe: 13.5 FP32 instructions per term (the product and its error in
+    # 4, TwoSum and the low-part update in 8, a renormalisation of 3 every second term), so its ALU
+    # peak is the FP32 instruction rate / 13.5
+    n_rep = (len(m.R_H) + 1) // 2
+    hk_flop_pt = 2.0 * (2 * n_rep) * m.nw ** 2
+    hk_flop = hk_flop_pt * len(kmc) * MC_SAMPLES
+    hk_tf = hk_flop / (hk_ms * 1e-3) / 1e12 if hk_ms > 0 else None
+    df_peak = 152 * 128 * 2.07e9 / 13.5 * 2 / 1e12      # TFLOP/s of double-float multiply-adds
+    rel = (emc / gmc.clamp_min(1e-300))[gmc > 0]
+    cb = None
+    if args.cpu_baseline and world == 1:
+        from oracle import eph as O
+        ns_cpu = 2048
+        t0 = time.perf_counter()
+        O.scattering_rates_mc(m, kmc[:1].cpu().numpy(), u[:ns_cpu].cpu().numpy(), O.Q_CAUCHY, 0.1, T_K, mu, SIGMA)
+        dt_cpu = time.perf_counter() - t0
+        cb = {"value": ns_cpu / dt_cpu, "unit": "pairs/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+              "sample": f"1 k-point x {ns_cpu} Cauchy q samples of the same polar model (FP64 NumPy oracle: "
+                        f"bands at every k+q, short- and long-range g, rates), {dt_cpu:.1f} s"}
+    mc = {"metric": "(k,q) pairs/s, Gamma_nk by Cauchy-sampled random q (FP32 tier: TF32x3 R_p sums, "
+                                  "FP32 epilogue, bands and phonons at every sample with FP64-refined energies)",
+                        "value": len(kmc) * MC_SAMPLES / (ms_mc * 1e-3), "unit": "pairs/s", "ms": ms_mc,
+                        "precision": "tf32x3", "k_points": len(kmc), "samples": MC_SAMPLES, "cauchy_width": 0.1,
+                        "median_relative_stderr": float(rel.median()) if rel.numel() else None,
+                        "fp32_simt": {"value": len(kmc) * MC_SAMPLES / (ms_mc32 * 1e-3), "unit": "pairs/s",
+                                      "ms": ms_mc32, "max_rel_dev_tf32x3_vs_fp32": dev_mc},
+                        "roofline": {"bound": "alu", "kernel": "k_herm_sum: packed Hermitian H(k+q) = sum_R "
+                                                                "cos(k.R) C_R + sin(k.R) S_R at every sample "
+                                                                "(double-float on the FP32 pipe)",
+                                     "achieved": hk_tf, "peak": df_peak, "unit": "TFLOP/s",
+                                     "frac": hk_tf / df_peak if hk_tf else None,
+                                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 13.5 FP32 "
+                                                    "instructions per double-float multiply-add, x 2 FLOP",
+                                     "algorithmic_flop_per_sample_point": hk_flop_pt,
+                                     "kernel_ms": hk_ms, "launches": hk_n,
+                                     "share_of_call": hk_ms / ms_mc if ms_mc > 0 else None}}
+    return mc, cb
+
+
 def polar(ctx, args, world):
     """Polar zincblende model with the long-range (Froehlich) coupling: Gamma_nk of
     the k-points within 0.2 eV of the band minimum over the 60^3 q grid (timed, the
@@ -522,10 +594,13 @@ def polar(ctx, args, world):
     kbuf = torch.empty((nk,), dtype=torch.int32, device="cuda")
     nwin = ctx.pgb_window(emin - 1e-6, emin + POLAR_WINDOW, kbuf)
     kw = kbuf[:nwin].clone()
-    gam = torch.empty((nwin, m.nw), dtype=torch.float64, device="cuda")
-    ctx.pgb_scattering_rates(kw, T_K, mu, SIGMA, prec, gam)     # warm-up (tables)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.mc_only:     # the Monte-Carlo part alone (profiling)
+        mc, cb = monte_carlo(ctx, args, world, m, kw, mu, stream, e0, e1)
+        return {"monte_carlo": mc, "cpu_baseline": cb}
+    gam = torch.empty((nwin, m.nw), dtype=torch.float64, device="cuda")
+    ctx.pgb_scattering_rates(kw, T_K, mu, SIGMA, prec, gam)     # warm-up (tables)
     barrier(world)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -553,52 +628,7 @@ def polar(ctx, args, world):
     bte_flops = 6.0 * nnz         # three FP64 multiply-adds per entry (x, y, z)
     bte_tf = bte_flops * it_n / (it_ms * 1e-3) / 1e12 if it_ms > 0 else None
     FP64_PEAK = ctx.pgb_diag_fp64_rate()   # TFLOP/s, measured on this device (the iteration is FP64-bound)
-    # Monte-Carlo q: Cauchy samples about q = 0 for the 16 lowest window k-points
-    from paper_2002_02045_gb300 import PGB_FP32, PGB_TC_TF32X3, PGB_Q_CAUCHY
-    pts = torch.as_tensor(S.mp_grid(*POLAR_GRID)).cuda()
-    kmc = pts[kw[:16].long()].contiguous()
-    u = torch.as_tensor(np.random.default_rng(S.SEED_BASE + 33).uniform(size=(MC_SAMPLES, 3))).cuda()
-    gmc = torch.empty((len(kmc), m.nw), dtype=torch.float64, device="cuda")
-    emc = torch.empty_like(gmc)
-    from paper_2002_02045_gb300.native import PROF_BANDS
-
-    def mc_run(prec):
-        ctx.pgb_scattering_rates_mc(kmc, u[:1024].contiguous(), PGB_Q_CAUCHY, 0.1, T_K, mu, SIGMA, prec, gmc, emc)
-        torch.cuda.synchronize()
-        ctx.pgb_profile(True)
-        ctx.pgb_profile_read(PROF_BANDS)
-        e0.record(stream)
-        ctx.pgb_scattering_rates_mc(kmc, u, PGB_Q_CAUCHY, 0.1, T_K, mu, SIGMA, prec, gmc, emc)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        prof = ctx.pgb_profile_read(PROF_BANDS)
-        ctx.pgb_profile(False)
-        return e0.elapsed_time(e1), prof, gmc.clone()
-
-    ms_mc32, _, g32 = mc_run(PGB_FP32)
-    ms_mc, (hk_ms, hk_n), _ = mc_run(PGB_TC_TF32X3)   # the FP32 tier's tensor-core form (reading 12)
-    dev_mc = float(((gmc - g32).abs() / (g32.abs() + 1e-6 * g32.abs().max())).max())
-    # the k+q points' H(k) Fourier sums: real cos/sin form over one representative of each
-    # {R, -R} (K = 2 n_rep rows) into the nw^2 packed Hermitian columns, 2 FLOP per term, in
-    # double-float on the FP32 pipe: 13.5 FP32 instructions per term (the product and its error in
-    # 4, TwoSum and the low-part update in 8, a renormalisation of 3 every second term), so its ALU
-    # peak is the FP32 instruction rate / 13.5
-    n_rep = (len(m.R_H) + 1) // 2
-    hk_flop_pt = 2.0 * (2 * n_rep) * m.nw ** 2
-    hk_flop = hk_flop_pt * len(kmc) * MC_SAMPLES
-    hk_tf = hk_flop / (hk_ms * 1e-3) / 1e12 if hk_ms > 0 else None
-    df_peak = 152 * 128 * 2.07e9 / 13.5 * 2 / 1e12      # TFLOP/s of double-float multiply-adds
-    rel = (emc / gmc.clamp_min(1e-300))[gmc > 0]
-    cb = None
-    if args.cpu_baseline and world == 1:
-        from oracle import eph as O
-        ns_cpu = 2048
-        t0 = time.perf_counter()
-        O.scattering_rates_mc(m, kmc[:1].cpu().numpy(), u[:ns_cpu].cpu().numpy(), O.Q_CAUCHY, 0.1, T_K, mu, SIGMA)
-        dt_cpu = time.perf_counter() - t0
-        cb = {"value": ns_cpu / dt_cpu, "unit": "pairs/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-              "sample": f"1 k-point x {ns_cpu} Cauchy q samples of the same polar model (FP64 NumPy oracle: "
-                        f"bands at every k+q, short- and long-range g, rates), {dt_cpu:.1f} s"}
+    mc, cb = monte_carlo(ctx, args, world, m, kw, mu, stream, e0, e1)
     return {
         "metric": "(k,q) pairs/s, polar Gamma_nk (short-range Wannier sum + long-range Ewald term)",
         "value": world * pairs / (ms * 1e-3), "unit": "pairs/s", "ms": ms, "pairs": pairs, "nk_window": nwin,
@@ -620,23 +650,7 @@ def polar(ctx, args, world):
                                    "hbm_frac": bte_gbs / peaks["hbm_gbs"] if bte_gbs else None,
                                    "hbm_peak_source": peak_src}},
         "cpu_baseline": cb,
-        "monte_carlo": {"metric": "(k,q) pairs/s, Gamma_nk by Cauchy-sampled random q (FP32 tier: TF32x3 R_p sums, "
-                                  "FP32 epilogue, bands and phonons at every sample with FP64-refined energies)",
-                        "value": len(kmc) * MC_SAMPLES / (ms_mc * 1e-3), "unit": "pairs/s", "ms": ms_mc,
-                        "precision": "tf32x3", "k_points": len(kmc), "samples": MC_SAMPLES, "cauchy_width": 0.1,
-                        "median_relative_stderr": float(rel.median()) if rel.numel() else None,
-                        "fp32_simt": {"value": len(kmc) * MC_SAMPLES / (ms_mc32 * 1e-3), "unit": "pairs/s",
-                                      "ms": ms_mc32, "max_rel_dev_tf32x3_vs_fp32": dev_mc},
-                        "roofline": {"bound": "alu", "kernel": "k_herm_sum: packed Hermitian H(k+q) = sum_R "
-                                                                "cos(k.R) C_R + sin(k.R) S_R at every sample "
-                                                                "(double-float on the FP32 pipe)",
-                                     "achieved": hk_tf, "peak": df_peak, "unit": "TFLOP/s",
-                                     "frac": hk_tf / df_peak if hk_tf else None,
-                                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 13.5 FP32 "
-                                                    "instructions per double-float multiply-add, x 2 FLOP",
-                                     "algorithmic_flop_per_sample_point": hk_flop_pt,
-                                     "kernel_ms": hk_ms, "launches": hk_n,
-                                     "share_of_call": hk_ms / ms_mc if ms_mc > 0 else None}},
+        "monte_carlo": mc,
     }
 
 
@@ -865,6 +879,8 @@ def main():
     ap.add_argument("--no-general", dest="general", action="store_false",
                     help="skip the 16-band, 15-mode shape outside the fused kernel")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--mc-only", action="store_true",
+                    help="in the polar section, run only the Monte-Carlo rates (profiling)")
     ap.add_argument("--kgrid", type=int, default=40, help="grid size per axis (40 = the workload; smaller "
                     "values give the small case used for profiler captures)")
     args = ap.parse_args()
