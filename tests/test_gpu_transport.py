@@ -169,6 +169,7 @@ def _oracle_transport(m, grid, T, mu, sig, L, win, n_iter):
     F, it = O.bte_iterate(tau, v, L["row"], L["col"], w, n_iter, 0.0)
     mob_rta = O.mobility(v[win], (tau[:, None] * v)[win], es[win], T, mu)
     mob = O.mobility(v[win], F[win], es[win], T, mu)
+    _oracle_transport.last = {"v": v, "w": w}
     return tau, F, it, mob_rta, mob
 
 
@@ -214,20 +215,52 @@ def test_transport_grid_list_window(ctx, c3s):
     lo, hi = emin - 1e-6, emin + 0.4
     assert np.abs(eps_all[:, :2] - hi).min() > 1e-6
     mu = emin - 0.2
-    ctx.pgb_build_collision_grid(0, 2, lo, hi, T, sig)
+    nnz = ctx.pgb_build_collision_grid(0, 2, lo, hi, T, sig)
     ns = 2 * len(pts)
     F = np.zeros((ns, 3))
     tau = np.zeros(ns)
     mob_rta, mob, it = ctx.pgb_transport(mu, PGB_FP64, 200, 0.0, F, tau)
     L = O.collision_list_grid(m, grid, 0, 2, window=(lo, hi))
     win = (L["eps"] >= lo) & (L["eps"] <= hi)
-    tau_r, F_r, it_r, mr_r, m_r = _oracle_transport(m, grid, T, mu, sig, L, win, 200)
-    assert it == it_r == 200
+    n_it = 200
+    tau_r, F_r, it_r, mr_r, m_r = _oracle_transport(m, grid, T, mu, sig, L, win, n_it)
+    assert it == it_r == n_it
     assert np.abs(tau - tau_r).max() <= 1e-9 * tau_r.max()
     assert np.all(tau[~win] == 0.0) and np.all(F[~win] == 0.0)
     assert np.abs(mob_rta - mr_r).max() <= 1e-8 * np.abs(mr_r).max()
     assert np.abs(F - F_r).max() <= 1e-3 * np.abs(F_r).max()
     assert np.abs(mob - m_r).max() <= 1e-3 * np.abs(m_r).max()
+    # A bound from the conditioning of the iteration F <- tau (v + W F) (Eq. BTE_iter): the
+    # device list's |g|^2 (FP32 interpolation) give W + dW, and after n iterations
+    #   |dF|_inf <= sum_{j<n} r^j |tau dW|_inf max_i |F_i|_inf  (first order),
+    # r = |tau W|_inf <= 1 since the row sums of W over a full list are the rates 1/tau.
+    # W, tau and F are the oracle's; dW is the weights of the device list's |g|^2 minus the
+    # oracle's, entry by entry (the keys are equal; checked by the list tests).
+    row = np.zeros(nnz, np.int32)
+    col = np.zeros(nnz, np.int32)
+    mode = np.zeros(nnz, np.int32)
+    g2 = np.zeros(nnz, np.float32)
+    ctx.pgb_collision_list(row, col, mode, g2)
+    nm = m.D.shape[1]
+    key_d = (row.astype(np.int64) * ns + col) * nm + mode
+    key_o = (L["row"].astype(np.int64) * ns + L["col"]) * nm + L["mode"]
+    od, oo = np.argsort(key_d), np.argsort(key_o)
+    assert np.array_equal(key_d[od], key_o[oo])
+    g2_dev = np.empty(len(oo))
+    g2_dev[oo] = g2[od].astype(np.float64)
+    w_o = _oracle_transport.last["w"]
+    w_d = O.bte_weights(L["eps"], L["row"], L["col"], L["hw"], g2_dev, T, mu, sig, L["nq"])
+    rs = L["row"]
+    r_inf = np.bincount(rs, weights=tau_r[rs] * w_o, minlength=ns).max()
+    dW_inf = np.bincount(rs, weights=tau_r[rs] * np.abs(w_d - w_o), minlength=ns).max()
+    amp = float(n_it) if r_inf >= 1.0 else (1.0 - r_inf ** n_it) / (1.0 - r_inf)
+    # plus the tau deviation (<= 1e-9 relative, checked above), which enters F^0 and tau W
+    bound_F = 2.0 * amp * (dW_inf + 2e-9) * np.abs(F_r).max() + 1e-10 * np.abs(F_r).max()
+    err_F = np.abs(F - F_r).max()
+    assert err_F <= bound_F, f"F: {err_F:.3g} > conditioning bound {bound_F:.3g} (r = {r_inf:.6f})"
+    v_r = _oracle_transport.last["v"]
+    bound_mob = O.mobility(np.abs(v_r[win]), np.full((int(win.sum()), 3), bound_F), L["eps"][win], T, mu)
+    assert np.all(np.abs(mob - m_r) <= bound_mob + 1e-10 * np.abs(m_r).max())
 
 
 @pytest.mark.slow
