@@ -40,11 +40,10 @@
 // exact degeneracy: sums over the bands of a cluster are unaffected.
 #include <algorithm>
 #include <cmath>
-#include <map>
-#include <tuple>
 #include <vector>
 
 #include "cplx.cuh"
+#include "herm_table.h"
 #include "internal.cuh"
 
 namespace pgb {
@@ -688,84 +687,18 @@ __global__ void __launch_bounds__(64) k_heev_mixed(int64_t count, const double *
 
 }  // namespace
 
-// Cos/sin coefficient table of X(k) = sum_R e^{ik.R} X(R) (see the top of this
-// file; X = H or the mass-scaled D), built on the host when the model is set:
-// representatives R = 0 and every R that is lexicographically positive;
-// T[2r][c] = C_R, T[2r+1][c] = S_R in the packed column order.  X is complex
+// Cos/sin coefficient table of X(k) = sum_R e^{ik.R} X(R) (X = H or the mass-scaled
+// D; herm_table.h builds it on the host), uploaded when the model is set together
+// with its split into (hi, lo) floats for the double-float sum.  X is complex
 // [nR][n][n], interleaved (re, im).
 pgb_status build_herm_table(pgb_ctx *c, HermTab *tab, const int32_t *R, const double *H, int nR, int nw) {
-    using Key = std::tuple<int, int, int>;
-    std::map<Key, int> idx;
-    for (int r = 0; r < nR; ++r) idx[Key(R[3 * r], R[3 * r + 1], R[3 * r + 2])] = r;
-    const int ncol = nw * nw;
     std::vector<int32_t> reps;
     std::vector<double> T;
     int M = 0;
-    // entry (i, j) of H(X) and of its adjoint-based parts A(X), B(X)
-    auto hx = [&](int X, int i, int j, double &re, double &im) {
-        re = H[2 * ((size_t)X * ncol + i * nw + j)];
-        im = H[2 * ((size_t)X * ncol + i * nw + j) + 1];
-    };
-    auto parts = [&](int X, int i, int j, double A[2], double B[2]) {
-        double hr, hi, tr, ti;
-        hx(X, i, j, hr, hi);
-        hx(X, j, i, tr, ti);               // conj(H_ji) = (tr, -ti)
-        A[0] = 0.5 * (hr + tr);
-        A[1] = 0.5 * (hi - ti);
-        const double dr = hr - tr, di = hi + ti;   // H_ij - conj(H_ji)
-        B[0] = -0.5 * di;                  // i * d / 2
-        B[1] = 0.5 * dr;
-    };
-    for (int r = 0; r < nR; ++r) {
-        const int x = R[3 * r], y = R[3 * r + 1], z = R[3 * r + 2];
-        const bool zero = x == 0 && y == 0 && z == 0;
-        const bool pos = x > 0 || (x == 0 && (y > 0 || (y == 0 && z > 0)));
-        if (!zero && !pos) continue;
-        int rn = r;
-        if (!zero) {
-            auto it = idx.find(Key(-x, -y, -z));
-            if (it == idx.end()) {
-                c->err = "set_model: an R list is not closed under inversion";
-                return PGB_EINVAL;
-            }
-            rn = it->second;
-        }
-        reps.push_back(x);
-        reps.push_back(y);
-        reps.push_back(z);
-        M = std::max(M, std::max(std::abs(x), std::max(std::abs(y), std::abs(z))));
-        std::vector<double> Cr(ncol), Sr(ncol);
-        for (int i = 0; i < nw; ++i)
-            for (int j = i; j < nw; ++j) {
-                double Ap[2], Bp[2], An[2], Bn[2];
-                parts(r, i, j, Ap, Bp);
-                double C[2], Sv[2];
-                if (zero) {
-                    C[0] = Ap[0];
-                    C[1] = Ap[1];
-                    Sv[0] = Sv[1] = 0.0;
-                } else {
-                    parts(rn, i, j, An, Bn);
-                    C[0] = Ap[0] + An[0];
-                    C[1] = Ap[1] + An[1];
-                    Sv[0] = Bp[0] - Bn[0];
-                    Sv[1] = Bp[1] - Bn[1];
-                }
-                if (i == j) {
-                    Cr[i] = C[0];
-                    Sr[i] = Sv[0];
-                } else {
-                    const int pidx = nw + 2 * (i * nw - (i * (i + 1)) / 2 + (j - i - 1));
-                    Cr[pidx] = C[0];
-                    Cr[pidx + 1] = C[1];
-                    Sr[pidx] = Sv[0];
-                    Sr[pidx + 1] = Sv[1];
-                }
-            }
-        T.insert(T.end(), Cr.begin(), Cr.end());
-        T.insert(T.end(), Sr.begin(), Sr.end());
+    if (!herm_table_host(R, H, nR, nw, reps, T, M)) {
+        c->err = "set_model: an R list is not closed under inversion";
+        return PGB_EINVAL;
     }
-    free_herm_table(tab);
     std::vector<float> T2(2 * T.size());
     for (size_t x = 0; x < T.size(); ++x) {
         const float h = (float)T[x];
