@@ -380,7 +380,8 @@ enum {
     PGB_PROF_RSUM = 1,      /* Fourier sum over R_e for every k, with the U(k) fold        */
     PGB_PROF_EPILOGUE = 2,  /* rotation, mode projection, |g|^2, delta weights, Gamma      */
     PGB_PROF_COLLISION = 3, /* collision integral / RK4 stage                              */
-    PGB_PROF_BANDS = 4,     /* FP64 Fourier sum H(k) = sum_R e^{ik.R} H(R) at off-grid points */
+    PGB_PROF_BANDS = 4,     /* Fourier sum H(k) = sum_R e^{ik.R} H(R) at off-grid points (FP64, or the
+                               double-float cos/sin form of the FP32 paths) */
     PGB_PROF_ADJOINT = 5,   /* transposed-list column pass of the reverse-mode derivatives */
     PGB_PROF_NKERNELS = 6
 };
