@@ -755,7 +755,7 @@ def batched(args, world):
 
 
 def general_shape(args, world):
-    """A shape the fused kernel does not cover: config-5 instance 44 (16 bands, 5 atoms =
+    """A shape the fused kernel does not cover: batched instance 44 (16 bands, 5 atoms =
     15 modes, 123 R vectors, 32^3 k = q grid), Gamma_nk of 16 k-points over the whole q
     grid at 300 K and 5 meV.  BF16x3: tensor-core q-sums in L2-sized q slabs, each read
     at once by the warp epilogue; FP32: the SIMT complex GEMM into HBM, then the SIMT
@@ -777,7 +777,7 @@ def general_shape(args, world):
     pairs = 16 * nk
     flop_per_pair = 8.0 * len(m.R_gp) * m.nmode * m.nw ** 2
     stream = torch.cuda.current_stream()
-    out = {"workload": "config-5 instance 44: 16 bands, 15 modes, 123 R_e x 123 R_p, 32^3 k = q grid, "
+    out = {"workload": "batched-workload instance 44: 16 bands, 15 modes, 123 R_e x 123 R_p, 32^3 k = q grid, "
                        "16 k-points x all q, T = 300 K, sigma = 5 meV",
            "pairs": pairs, "algorithmic_flop_per_pair": flop_per_pair}
     peaks, _ = load_peaks()

@@ -45,7 +45,8 @@ struct EwaldArgs {
 
 // One warp per point.  The candidates G are screened 32 at a time in FP32 (the
 // exponent with a relative margin of 1e-4, far above the FP32 error of ~1e-6), the
-// survivors (~60 of the 1331 candidates of config 3) are compacted into a per-warp
+// survivors (~60 of 1331 candidates for the zincblende polar model, 8 bands, a = 10.68
+// bohr) are compacted into a per-warp
 // list by ballot, and the list is evaluated 32 terms at a time in FP64 (every
 // lane busy), so the FP64 work is that of the surviving terms only.  Each lane
 // sums its terms; the lanes' sums are then added by a butterfly.

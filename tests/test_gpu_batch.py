@@ -118,8 +118,8 @@ def test_batch_tensor_core_route(members, prec, tol):
 
 
 @pytest.mark.slow
-def test_batch_config5_settings_against_oracle():
-    """Config 5 at its own settings: sigma = 5 meV and T = 300 K on the instances'
+def test_batch_own_settings_against_oracle():
+    """The batched instances at their own settings: sigma = 5 meV and T = 300 K on the instances'
     own grids (8^3 to 32^3), with nw = 16, nat = 5 and the 123-vector R shell among
     them, in FP32, TF32x3 and BF16x3 through one batch, against the per-instance FP64
     oracle on sampled k-points (the full q grid of each)."""
@@ -156,7 +156,7 @@ def test_batch_config5_settings_against_oracle():
         b.pgb_batch_rates(ks, T, mus, sig, outs)
         for i, (o, r) in enumerate(zip(outs, refs)):
             assert np.abs(r).max() > 0
-            assert_rates_close(o, r, tol, label=f"config 5 {prec} instance {list(pick)[i]}")
+            assert_rates_close(o, r, tol, label=f"batched {prec} instance {list(pick)[i]}")
     b.close()
     for c in ctxs:
         c.close()

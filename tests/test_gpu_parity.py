@@ -627,7 +627,7 @@ def test_rk4_c2_grid_list_1000_steps(ctx, c2, c2_grid_list):
 
 @pytest.mark.slow
 def test_rk4_c2_12cubed_list_1000_steps(ctx, c2):
-    """Config 4 at the reduced 12^3 size: the device builds the list of the C2 model
+    """Hot-carrier dynamics at the reduced 12^3 size: the device builds the list of the C2 model
     (two lowest bands, states within 0.6 eV of the band minimum, 7 sigma screen at
     sigma = 10 meV, T = 300 K) and runs 1000 RK4 steps of 1 fs (Sec. 2.1.1) of the
     hot-carrier pulse; the oracle evolves the same entries (read back, |g|^2 as stored)

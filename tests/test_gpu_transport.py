@@ -273,7 +273,7 @@ def test_transport_grid_list_window(ctx, c3s):
 
 @pytest.mark.slow
 def test_transport_full_size_polar(ctx, c3):
-    # config-3 sizes: 60^3 k = q grid, states within 0.2 eV of the band minimum,
+    # the polar model at full size: 60^3 k = q grid, states within 0.2 eV of the band minimum,
     # tau from the BF16-split rates over all 216,000 q.  The oracle cannot run at
     # this size; check properties that hold at any size.
     from paper_2002_02045_gb300 import PGB_TC_BF16X3
