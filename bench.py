@@ -736,6 +736,19 @@ def batched(args, world):
             "first_call_s": t_first_tc, "tensor_core_instances": int(sum(tc_inst)),
             "tensor_core_flop_share": flops_tc / flops, "tuning": b.pgb_batch_tuning(),
             "tolerance_vs_fp64": 1e-3, "max_rel_dev_from_fp32_batch": dev}
+    # and with the TF32x3 split: the FP32 tier (1e-5) on the tensor cores
+    from paper_2002_02045_gb300 import PGB_TC_TF32X3
+    b.pgb_batch_set_precision(PGB_TC_TF32X3)
+    outs_tf = [np.zeros_like(o) for o in outs]
+    b.pgb_batch_rates(ks, T_K, mus, 0.005, outs_tf)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        b.pgb_batch_rates(ks, T_K, mus, 0.005, outs_tf)
+    dt_tf = max_over_ranks((time.perf_counter() - t0) / reps, world)
+    dev_tf = max(float(np.max(np.abs(x - y) / (np.abs(y) + 1e-6 * np.abs(y).max()))) for x, y in zip(outs_tf, outs))
+    tf32 = {"value": world * pairs / dt_tf, "unit": "pairs/s", "ms_per_call": 1e3 * dt_tf,
+            "tuning": b.pgb_batch_tuning(), "tolerance_vs_fp64": 1e-5, "max_rel_dev_from_fp32_batch": dev_tf}
     b.close()
     for c in ctxs:
         c.close()
@@ -745,7 +758,7 @@ def batched(args, world):
         "instances": len(models), "k_per_instance": BATCH_K, "first_call_s": t_first,
         "model_generation_s": t_gen, "setup_s": t_setup, "tuning": tun, "finite": finite,
         "timing": "host clock around pgb_batch_rates (graph replay + output copies, synchronised)",
-        "cpu_baseline": cb, "bf16x3": bf16,
+        "cpu_baseline": cb, "bf16x3": bf16, "tf32x3": tf32,
         "roofline": {"bound": "alu", "kernel": "batched graph (FP32): per-instance R_p sums on k_cgemm + the "
                                                "persistent warp epilogue k_batch_warp", "achieved": flops / dt / 1e12,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": flops / dt / 1e12 / fp32_peak,
