@@ -122,12 +122,13 @@ __device__ __forceinline__ void batch_chunk(const BInst &I, int64_t b, int qci, 
     const int ib = I.ib, el = nw / ib;
     const bool act = lane < nm * ib;
     const int ka = act ? lane / ib : 0, i0 = act ? (lane - (lane / ib) * ib) * el : 0;
-    // screen combos c = 32 j + lane -> (nu, m), packed as nu * 16 + m, four per word
+    // screen combos c = 32 j + lane -> (m, nu), m-major so that the live terms of one final
+    // band m arrive together and share its rotation; packed as nu * 16 + m, four per word
     uint32_t scm[kTPL / 4] = {0u, 0u};
 #pragma unroll
     for (int j = 0; j < kTPL; ++j) {
         const int cc = 32 * j + lane;
-        const uint32_t v = cc < nc ? (uint32_t)(cc / nw) : 0u, m = cc < nc ? (uint32_t)(cc - (cc / nw) * nw) : 0u;
+        const uint32_t m = cc < nc ? (uint32_t)(cc / nm) : 0u, v = cc < nc ? (uint32_t)(cc - (cc / nm) * nm) : 0u;
         scm[j / 4] |= ((v << 4) | m) << (8 * (j % 4));
     }
     const int nj = (nc + 31) / 32;
@@ -190,6 +191,8 @@ __device__ __forceinline__ void batch_chunk(const BInst &I, int64_t b, int qci, 
         for (int n = 0; n < nw; ++n) {
             const float en = __shfl_sync(0xffffffffu, en32_l, n);
             bool loaded = false;
+            int m_rot = -1;   // final band whose rotation rr_m holds (this row)
+            float2 rr_m = make_float2(0.f, 0.f);
             float2 cr[kMaxNw];
             for (int j = 0; j < nj; ++j) {
                 const uint32_t vm = (scm[j / 4] >> (8 * (j % 4))) & 0xffu;
@@ -227,10 +230,13 @@ __device__ __forceinline__ void batch_chunk(const BInst &I, int64_t b, int qci, 
 #pragma unroll
                     for (int u = 0; u < TB; ++u) {
                         g[u] = make_float2(0.f, 0.f);
-                        if (act && u < cnt) {
+                        if (u < cnt) {   // warp-uniform
                             const int v = (int)(tv[u] >> 4), m = (int)(tv[u] & 15u);
-                            const float2 rr = rot_dispatch(el, Ukq + m * nw, cr);
-                            cfma(g[u], cq[v * nm], rr);
+                            if (m != m_rot) {   // the rotation of final band m, once per run of its terms
+                                rr_m = act ? rot_dispatch(el, Ukq + m * nw, cr) : make_float2(0.f, 0.f);
+                                m_rot = m;
+                            }
+                            if (act) cfma(g[u], cq[v * nm], rr_m);
                         }
                     }
 #pragma unroll

@@ -68,12 +68,13 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_rates_warp(WarpRatesArgs a) 
     const int ib = a.ib, el = nw / ib;
     const bool act = lane < nm * ib;
     const int ka = act ? lane / ib : 0, i0 = act ? (lane - (lane / ib) * ib) * el : 0;
-    // screen combos c = 32 j + lane -> (nu, m), packed as nu * 16 + m, four per word
+    // screen combos c = 32 j + lane -> (m, nu), m-major so that the live terms of one final
+    // band m arrive together and share its rotation; packed as nu * 16 + m, four per word
     uint32_t scm[kTPL / 4] = {0u, 0u};
 #pragma unroll
     for (int j = 0; j < kTPL; ++j) {
         const int cc = 32 * j + lane;
-        const uint32_t v = cc < nc ? (uint32_t)(cc / nw) : 0u, m = cc < nc ? (uint32_t)(cc - (cc / nw) * nw) : 0u;
+        const uint32_t m = cc < nc ? (uint32_t)(cc / nm) : 0u, v = cc < nc ? (uint32_t)(cc - (cc / nm) * nm) : 0u;
         scm[j / 4] |= ((v << 4) | m) << (8 * (j % 4));
     }
     const int nj = (nc + 31) / 32;
@@ -145,6 +146,8 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_rates_warp(WarpRatesArgs a) 
             const float2 *cq = a.coef + q * nm * nm + ka;
             {
                 bool loaded = false;
+                int m_rot = -1;   // final band whose rotation rr_m holds (this row)
+                float2 rr_m = make_float2(0.f, 0.f);
                 float2 cr[kMaxNw];
                 for (int j = 0; j < nj; ++j) {
                     const uint32_t vm = (scm[j / 4] >> (8 * (j % 4))) & 0xffu;
@@ -179,10 +182,13 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_rates_warp(WarpRatesArgs a) 
 #pragma unroll
                         for (int u = 0; u < TB; ++u) {
                             g[u] = make_float2(0.f, 0.f);
-                            if (act && u < cnt) {
+                            if (u < cnt) {   // warp-uniform
                                 const int v = (int)(tv[u] >> 4), m = (int)(tv[u] & 15u);
-                                const float2 rr = rot_dispatch(el, Uk + m, nw, cr);
-                                cfma(g[u], cq[v * nm], rr);
+                                if (m != m_rot) {   // the rotation of final band m, once per run of its terms
+                                    rr_m = act ? rot_dispatch(el, Uk + m, nw, cr) : make_float2(0.f, 0.f);
+                                    m_rot = m;
+                                }
+                                if (act) cfma(g[u], cq[v * nm], rr_m);
                             }
                         }
 #pragma unroll
