@@ -961,10 +961,14 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
     const int KpE = tc_kpad(c->nRge);
     const int qpb = std::max(1, 256 / nw);
     const int qiters = 8;
-    const int wqc = 8;    // q-points per warp task of the slab epilogue (tensor-core route, other shapes)
+    const int wqc = 8;    // q-points per task of the warp epilogue (tensor-core slabs, and the FP32 form)
+    // The FP32 form takes the warp epilogue when a row holds at least 96 (nu, m) combos: 16 bands x
+    // 15 modes 42.6 -> 23.9 ms; with 8 bands x 6 modes (48 combos, a quarter of the lanes idle) the
+    // thread-per-(q, n) epilogue was 10 % faster over the whole pass.
+    const bool f32_warp = f32 && !tcp && nm * nw >= 96;
     const int64_t nqblk = fused ? (c->Nq + 127) / 128
-                          : tcp ? (c->Nq + wqc - 1) / wqc
-                                : (c->Nq + (int64_t)qpb * qiters - 1) / ((int64_t)qpb * qiters);
+                          : (tcp || f32_warp) ? (c->Nq + wqc - 1) / wqc
+                                              : (c->Nq + (int64_t)qpb * qiters - 1) / ((int64_t)qpb * qiters);
     // scratch carve-up, every piece 256-byte aligned (TMA and vector loads)
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     int64_t nbmax = 0;
@@ -1103,10 +1107,7 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
         ra.nqblk = nqblk;
         ra.qpb = qpb;
         ra.qiters = qiters;
-        if (tcp) {
-            // q slabs: tensor-core q-sum into the L2-sized buffer, then the warp epilogue on that slab
-            TRY(launch_split_g(c, tf32, nb, c->nKp, (int)ncol, Kp, G, Bsplit, (int)ldc));
-            const int64_t sq = std::max<int64_t>(128, kSlabBytes / (nb * ldc * (int64_t)sizeof(float2)) / 128 * 128);
+        auto warp_args = [&](int64_t ld) {
             WarpRatesArgs wa;
             wa.nw = nw;
             wa.nm = nm;
@@ -1118,7 +1119,7 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
             wa.qc = wqc;
             wa.nb = nb;
             wa.C = (const float2 *)Cb;
-            wa.ldc = ldc;
+            wa.ldc = ld;
             wa.kidx = kb;
             wa.eps = c->d_eps;
             wa.eps32 = eps32.p;
@@ -1131,6 +1132,13 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
             wa.sigma = sigma;
             wa.partial = partial;
             wa.nqblk = nqblk;
+            return wa;
+        };
+        if (tcp) {
+            // q slabs: tensor-core q-sum into the L2-sized buffer, then the warp epilogue on that slab
+            TRY(launch_split_g(c, tf32, nb, c->nKp, (int)ncol, Kp, G, Bsplit, (int)ldc));
+            const int64_t sq = std::max<int64_t>(128, kSlabBytes / (nb * ldc * (int64_t)sizeof(float2)) / 128 * 128);
+            WarpRatesArgs wa = warp_args(ldc);
             for (int64_t qs = 0; qs < c->Nq; qs += sq) {
                 const int64_t nqs = std::min(sq, c->Nq - qs);
                 prof_mark(c, PGB_PROF_QSUM);
@@ -1151,7 +1159,16 @@ pgb_status pgb_scattering_rates(pgb_ctx *c, const int32_t *k_idx, int64_t nk, do
                              c->Nq * ncol));
             prof_mark(c, PGB_PROF_QSUM);
             prof_mark(c, PGB_PROF_EPILOGUE);
-            TRY(launch_rates_epilogue(c, f32, ra));
+            if (f32_warp) {   // the warp epilogue over the whole q range (rows read from HBM)
+                WarpRatesArgs wa = warp_args(ncol);
+                wa.q_off = 0;
+                wa.nqs = c->Nq;
+                wa.nch = (int)((c->Nq + wqc - 1) / wqc);
+                wa.blk0 = 0;
+                TRY(launch_rates_warp(c, wa));
+            } else {
+                TRY(launch_rates_epilogue(c, f32, ra));
+            }
             prof_mark(c, PGB_PROF_EPILOGUE);
         }
         TRY(launch_rates_reduce(c, nb, nqblk, nm, nw, scale, partial, Gm.dev + b0 * nw,

@@ -368,7 +368,9 @@ def test_rates_general_shape_tensor_core(ctx, inst, grid):
     """Shapes the fused kernel does not cover (16 bands x 15 modes, 12 bands x 12
     modes, an odd 3-band cut with 54 columns padded to 96): the tensor-core q-sum in
     L2-sized q slabs followed by the warp epilogue, against the oracle in both split
-    precisions, mode-resolved sums equal to the total."""
+    precisions, and the FP32 form (SIMT q-sum; the warp epilogue for rows of at least 96
+    (nu, m) combos, the thread-per-(q, n) one for the 3-band cut); mode-resolved sums equal
+    to the total."""
     from paper_2002_02045_gb300 import PRECISIONS
     if inst == "c2-3band":
         c2m = S.model_c2()
@@ -386,7 +388,7 @@ def test_rates_general_shape_tensor_core(ctx, inst, grid):
     ks = np.array([0, nk // 3, nk - 1], np.int32)
     ref = O.scattering_rates_grid(m, g, g, ks, T, mu, sig, q_chunk=4096)
     assert np.abs(ref).max() > 0
-    for prec, tol in (("bf16x3", 1e-3), ("tf32x3", 1e-5)):
+    for prec, tol in (("bf16x3", 1e-3), ("tf32x3", 1e-5), ("fp32", 1e-5)):
         gam = empty((3, m.nw))
         gmode = empty((3, m.nmode, m.nw))
         ctx.pgb_scattering_rates(dev(ks), T, mu, sig, PRECISIONS[prec], gam, gmode)
