@@ -740,7 +740,9 @@ pgb_status launch_herm_sum(pgb_ctx *c, const HermTab &t, const double *d_pts, in
     const int M = t.M;
     const size_t smem = M <= kHermMaxM ? (size_t)3 * (2 * M + 1) * HS_P * sizeof(float4) : 0;
     const dim3 grid(div_up(np, HS_P), div_up(ncol, HS_C));
-    if (smem > 48 * 1024)
+    // static buffers (Ah, Al, Bh, Bl) plus the dynamic tables above 48 KB need the opt-in
+    constexpr size_t kStatic = 4 * (size_t)HS_K * HS_P * sizeof(float);
+    if (smem + kStatic > 48 * 1024)
         PGB_CUDA_TRY(c, cudaFuncSetAttribute(k_herm_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_herm_sum<<<grid, 256, smem, c->stream>>>(np, d_pts, t.nrep, t.d_R, M, ncol, t.d_T2, d_out);
     PGB_LAUNCH_CHECK(c);
